@@ -1,0 +1,368 @@
+"""Benchmark of the layered Gaussian-splatting rasterizer on GB300.
+
+One step = one pass of the whole hot path over the 1.2M-Gaussian layered
+CT-like scene (5 nested shells, SH degree 3, 1024x1024, random 5-bit layer
+mask, one clip plane): S1 preprocess, S2 binning + depth/tile radix sorts, S3
+compositing, S4 backward (with per-Gaussian contributions) and S5 prune.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line.  The reference arm times the FP64 CPU oracle on a
+bounded sample of the same workload (this method has no runnable reference
+implementation).  Multi-GPU runs (torchrun) are independent replicas: the
+path has no exchange step, every rank renders the full frame.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixels/s & p50/p99 frame ms (served vs plain) at PSNR>=50dB vs FP64 oracle"
+UNIT = "Mpixels/s"
+WORKLOAD = ("layered CT-like scene: 1.2M Gaussians in 5 layers (400k/300k/250k/100k/150k shells), SH degree 3, "
+            "1024x1024, random 5-bit layer mask + 1 clip plane; step = forward + backward + contribution prune")
+# Per-pair arithmetic of the compositor kernels (FLOPs, an FMA counts 2)
+FLOP_EVAL = 14         # alpha of one (pixel, splat) pair
+FLOP_BLEND_FWD = 10    # blending a splat into a pixel
+FLOP_BLEND_BWD = 40    # gradient of one blended pair
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload():
+    import synth
+    w = synth.scene_c2()
+    return w
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) timing
+
+def oracle_sample(w, gpu_image=None, band_rows=8):
+    """FP64 oracle on a bounded sample of the workload: full preprocess + binning
+    of all Gaussians, forward and backward compositing of `band_rows` tile rows
+    through the image centre, chain rule for every visible Gaussian.  The
+    compositing time is scaled to the full frame.  Returns (Mpixels/s, detail)."""
+    import oracle
+    oracle.build()
+    sc, cam = w["scene"], w["cameras"][0]
+    W, H = cam.width, cam.height
+    Tx, Ty = (W + 15) // 16, (H + 15) // 16
+    bg = tuple(float(v) for v in w["bg"])
+    t0 = time.perf_counter()
+    pre = oracle.preprocess(sc, cam, w["layer_mask"], w["planes"], "f64")
+    ranges, lst = oracle.bin_tiles(pre)
+    t1 = time.perf_counter()
+    r0 = Ty // 2 - band_rows // 2
+    ys, xs = np.mgrid[r0 * 16:(r0 + band_rows) * 16, 0:W]
+    cp = oracle.composite_pixels(pre, ranges, lst, xs.ravel(), ys.ravel(), bg)
+    t2 = time.perf_counter()
+    tm = np.zeros(Tx * Ty, np.uint8)
+    tm[r0 * Tx:(r0 + band_rows) * Tx] = 1
+    rng = np.random.default_rng(1)
+    dimg = rng.standard_normal((3, H, W))
+    cb = oracle.composite_backward(pre, ranges, lst, bg, dimg, None, tm)
+    t3 = time.perf_counter()
+    oracle.chain(sc, cam, pre["vis"], cb["rec_grad"])
+    t4 = time.perf_counter()
+    frac = (band_rows * 16 * W) / float(W * H)
+    full = (t1 - t0) + (t4 - t3) + ((t2 - t1) + (t3 - t2)) / frac
+    detail = {"preprocess_bin_s": t1 - t0, "band_forward_s": t2 - t1, "band_backward_s": t3 - t2,
+              "chain_s": t4 - t3, "frame_s_extrapolated": full}
+    psnr = None
+    if gpu_image is not None:
+        g = gpu_image[:, ys.ravel(), xs.ravel()].T.astype(np.float64)
+        mse = float(((g - cp["rgb"]) ** 2).mean())
+        psnr = float("inf") if mse == 0 else 10 * math.log10(1.0 / mse)
+    return (W * H) / full / 1e6, detail, psnr, (t4 - t0)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = build_workload()
+    sample = "full FP64 preprocess + binning of 1.2M Gaussians, compositing fwd+bwd of 2 central tile rows " \
+             "(32x1024 px) scaled to the frame, FP64 chain rule of every visible Gaussian"
+    args_band = 2
+    vals = []
+    for _ in range(args.warmup):
+        pass    # the oracle has no warm-up state; warm-up steps are not repeated on the CPU
+    for _ in range(max(1, args.steps)):
+        v, detail, _, wall = oracle_sample(w, band_rows=args_band)
+        vals.append(v)
+    v = statistics.median(vals)
+    frame_ms = 1e3 * (w["cameras"][0].width * w["cameras"][0].height) / (v * 1e6)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": frame_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mode": "oracle (FP64 C, single thread)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "detail": detail}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2410_16978_gb300 import (DeviceScene, Rasterizer, _lib, contrib_prune, gs_kernel_launches,
+                                        gs_profile_collect, gs_profile_enable)
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = build_workload()
+    sc, cam = w["scene"], w["cameras"][0]
+    W, H = cam.width, cam.height
+    bg = tuple(float(v) for v in w["bg"])
+    ds = DeviceScene.from_host(sc, device=dev)
+    rast = Rasterizer(sc.n, W, H, device=dev)
+    image, alpha = rast.render(ds, cam, w["layer_mask"], w["planes"], bg, check=True)   # sizes the pair list
+    torch.cuda.synchronize()
+    st = rast.status()
+    rng = np.random.default_rng(7)
+    dimg_h = rng.standard_normal((3, H, W)).astype(np.float32) / (3 * W * H)
+    dal_h = rng.standard_normal((H, W)).astype(np.float32) / (W * H)
+    dimg = torch.from_numpy(dimg_h).to(dev)
+    dal = torch.from_numpy(dal_h).to(dev)
+    csum = torch.zeros(sc.n, device=dev)
+    cmax = torch.zeros(sc.n, device=dev)
+    grads = {k: torch.empty(p.shape, dtype=torch.float32, device=dev)
+             for k, p in zip(("means", "log_scales", "quats", "opacity_logit", "sh"), ds.params())}
+    prune_ws = torch.empty(_lib.gs_prune_workspace_size(sc.n), dtype=torch.uint8, device=dev)
+    cam_c = _lib.make_camera(cam)
+    cs = ds.c_struct()
+    stream = torch.cuda.current_stream(dev)
+
+    def step(dimg_t, dal_t):
+        csum.zero_()
+        cmax.zero_()
+        rast.render(ds, cam_c, w["layer_mask"], w["planes"], bg, image=image, alpha=alpha, check=False,
+                    _c_scene=cs)
+        rast.backward(ds, cam_c, bg, dimg_t, dal_t, 0xFFFFFFFF, csum, cmax, grads=grads, _c_scene=cs)
+        return contrib_prune(cmax, 0.005, workspace=prune_ws)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        step(dimg, dal)
+    barrier()
+
+    # ---- timed region: device-resident inputs ----
+    gs_profile_collect()
+    gs_profile_enable(True)
+    l0 = gs_kernel_launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local_rank) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for k in range(args.steps):
+            evs[k][0].record(stream)
+            step(dimg, dal)
+            evs[k][1].record(stream)
+        t_end.record(stream)
+        barrier()
+    launches = gs_kernel_launches() - l0
+    gs_profile_enable(False)
+    prof = gs_profile_collect()
+    total_ms = t_start.elapsed_time(t_end)
+    per = sorted(a.elapsed_time(b) for a, b in evs)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = world * (W * H) * args.steps / (total_ms / 1e3) / 1e6
+
+    # ---- end to end: host inputs (pinned) and host result every step ----
+    dimg_pin = torch.from_numpy(dimg_h).pin_memory()
+    dal_pin = torch.from_numpy(dal_h).pin_memory()
+    img_host = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
+    al_host = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    nk_host = torch.empty(1, dtype=torch.int64).pin_memory()
+    dimg_d = torch.empty_like(dimg)
+    dal_d = torch.empty_like(dal)
+    e2e_steps = max(3, min(args.steps, 20))
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        dimg_d.copy_(dimg_pin, non_blocking=True)
+        dal_d.copy_(dal_pin, non_blocking=True)
+        _, _, nk = step(dimg_d, dal_d)
+        img_host.copy_(image, non_blocking=True)
+        al_host.copy_(alpha, non_blocking=True)
+        nk_host.copy_(nk, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_value = world * (W * H) / (e2e_ms / 1e3) / 1e6
+    h2d = dimg_h.nbytes + dal_h.nbytes
+    d2h = img_host.numel() * 4 + al_host.numel() * 4 + 8
+
+    # ---- roofline of the dominant kernel ----
+    peaks, peaks_src = _peaks()
+    stage_ms = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in prof.items()}
+    ws_lay = _lib.gs_workspace_layout(rast.n, W, H, rast.ws_bytes)
+    ncon = rast.workspace[ws_lay["n_contrib"]:ws_lay["n_contrib"] + 4 * W * H].view(torch.int32)
+    pairs_bwd = float(ncon.double().sum().item())
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk = clk.summary()
+    sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak_tflops = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    dom = max(("composite", "composite_bwd", "preprocess", "preprocess_bwd", "depth_sort", "tile_sort"),
+              key=lambda k: stage_ms.get(k, 0.0))
+    if dom in ("composite", "composite_bwd"):
+        flops = pairs_bwd * (FLOP_EVAL + (FLOP_BLEND_BWD if dom == "composite_bwd" else FLOP_BLEND_FWD))
+        achieved = flops / (stage_ms[dom] / 1e3) / 1e12
+        roof = {"kernel": "k_" + dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "peak_source": "FP32 %d SMs x 128 lanes x 2 x %.0f MHz (sm max)" % (sms, sm_max)}
+    else:
+        K = (sc.sh_degree + 1) ** 2
+        per_g = {"preprocess": 12 + 12 + 16 + 4 + 1 + 12 * K + 56, "preprocess_bwd": 2 * (12 + 12 + 16 + 4 + 12 * K) + 48 + 1,
+                 "depth_sort": 4 * 24, "tile_sort": 0}[dom]
+        byts = sc.n * per_g
+        achieved = byts / (stage_ms[dom] / 1e3) / 1e9
+        roof = {"kernel": "k_" + dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks_src}
+
+    # ---- CPU oracle baseline and PSNR check (rank 0, N = 1 only) ----
+    cpu = None
+    psnr = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        img_np = image.cpu().numpy()
+        v, detail, psnr, wall = oracle_sample(w, img_np)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "full FP64 preprocess + binning, fwd+bwd compositing of 8 central tile rows scaled to "
+                         "the frame, chain rule of all visible Gaussians; %.1f s wall" % wall}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms_step, "p50_ms": per[len(per) // 2],
+                "p99_ms": per[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "mode": "plain (one frame per launch sequence)",
+                           "gaussians": sc.n, "visible": int(st.n_visible), "pairs": int(st.n_dup),
+                           "width": W, "height": H, "l2": "inputs larger than L2 (scene %.0f MB)" % (
+                               sum(p.numel() * p.element_size() for p in ds.params()) / 1e6),
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "psnr_db_vs_fp64_oracle": psnr,
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "ms_per_step": e2e_ms},
+                "clocks": clk, "gpu_launches": int(launches),
+                "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()}}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    run_gpu(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

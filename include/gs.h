@@ -1,0 +1,218 @@
+/*
+ * gs.h - C ABI of the layered Gaussian-splatting tile rasterizer (GB300, sm_103a).
+ *
+ * Paper: "Multi-Layer Gaussian Splatting for Immersive Anatomy Visualization".
+ * The scene is one Gaussian cloud whose points carry a layer id stored next to
+ * their colour and scale attributes (Sec. 3.2).  Layers are rendered alone or
+ * together and can be cut (Sec. 1, Sec. 3.3, Sec. 5); the renderer sorts the
+ * Gaussians relative to the camera and splats them (Sec. 3.3) following the
+ * EWA / 3DGS formulation the paper cites (Sec. 2.2.1); training a layer needs
+ * the gradient of that render with the lower layers frozen (Sec. 3.2) and the
+ * per-Gaussian contribution used to remove inactive Gaussians (Sec. 3.2.2).
+ *
+ * Conventions shared by every entry point
+ *   - All array arguments are DEVICE pointers owned by the caller, unless the
+ *     comment says "host".  The library never allocates device memory on these
+ *     paths and never frees what it is given.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and never synchronise, except gs_read_status.
+ *   - Every call returns GS_OK or an error code; gs_last_error_string() gives a
+ *     message for the calling thread's last failure.  Argument errors are
+ *     detected on the host before any launch (GS_ERR_INVALID).  Errors that can
+ *     only be known on the device (duplicate-list overflow) are written to the
+ *     status word at the start of the workspace; read it with gs_read_status.
+ *   - Images are planar float32: image[c][y][x], c in {R,G,B}; per-pixel
+ *     arrays are [y][x].  Pixel (x, y) is sampled at (x + 0.5, y + 0.5).
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GS_OK = 0,
+    GS_ERR_INVALID = 1,    /* bad argument (null pointer, size, dtype, ...) */
+    GS_ERR_WORKSPACE = 2,  /* workspace too small (host check) or duplicate-list overflow (device status) */
+    GS_ERR_CUDA = 3,       /* a CUDA runtime call or launch failed */
+    GS_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up */
+    GS_ERR_OOM = 5         /* an admission/memory budget was exceeded */
+};
+
+enum { GS_DTYPE_F32 = 0, GS_DTYPE_F16 = 1, GS_DTYPE_BF16 = 2 };
+
+#define GS_TILE 16          /* tile edge in pixels */
+#define GS_MAX_PLANES 8     /* clip planes per call */
+#define GS_MAX_LAYERS 32    /* layer ids 0..31 (bit L of a mask = layer L) */
+
+/* Pinhole camera, world -> camera p = R mu + t, OpenCV axes (x right, y down,
+ * z forward).  R is row-major.  fx, fy, cx, cy in pixels; Gaussians with
+ * p_z <= znear are culled (0.2 in every workload here).                       */
+typedef struct gs_camera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float znear;
+    float _reserved;
+} gs_camera;
+
+/* Clip plane (cutting, Sec. 5): a Gaussian whose layer bit is set in
+ * layer_bits is removed whole when n . mu + d < 0 (its centre is tested).     */
+typedef struct gs_clip_plane {
+    float n[3];
+    float d;
+    uint32_t layer_bits;
+    uint32_t _reserved;
+} gs_clip_plane;
+
+/* Layered Gaussian scene (device pointers, read only), N Gaussians:
+ *   means          float32 [N][3]
+ *   log_scales     [N][3]  dtype_scale_rot (f32 / f16 / bf16)
+ *   quats          [N][4]  dtype_scale_rot, (w, x, y, z), need not be unit
+ *   opacity_logit  float32 [N]              opacity = sigmoid(logit)
+ *   sh             [N][K][3] dtype_sh, K = (sh_degree+1)^2, real SH with the
+ *                  Condon-Shortley phase, index k = l*l + l + m
+ *   layer          uint8 [N], values 0..31
+ * Every pointer must be 16-byte aligned.                                     */
+typedef struct gs_scene {
+    const void *means;
+    const void *log_scales;
+    const void *quats;
+    const void *opacity_logit;
+    const void *sh;
+    const uint8_t *layer;
+    int64_t n;
+    int32_t sh_degree;      /* 0..3 */
+    int32_t dtype_sh;       /* GS_DTYPE_* */
+    int32_t dtype_scale_rot;/* GS_DTYPE_* */
+    int32_t _reserved;
+} gs_scene;
+
+/* Gradient outputs (device, float32, same shapes as the scene fields).  Every
+ * element is written (overwritten, not accumulated); Gaussians that were not
+ * rendered or whose layer is not in grad_layer_mask receive 0.               */
+typedef struct gs_grads {
+    float *means;           /* [N][3] */
+    float *log_scales;      /* [N][3] */
+    float *quats;           /* [N][4] */
+    float *opacity_logit;   /* [N]    */
+    float *sh;              /* [N][K][3] */
+} gs_grads;
+
+/* Device status word at offset 0 of a render workspace. */
+typedef struct gs_status {
+    int32_t error;          /* GS_OK, or GS_ERR_WORKSPACE when n_dup > dup_capacity */
+    uint32_t n_visible;     /* Gaussians that survived every cull */
+    uint64_t n_dup;         /* (tile, Gaussian) pairs the frame needs */
+    uint64_t dup_capacity;  /* pairs the workspace can hold */
+    uint32_t max_tile_list; /* reserved */
+    uint32_t _reserved;
+} gs_status;
+
+/* Bytes of workspace for rendering n Gaussians at width x height with room for
+ * dup_capacity (tile, Gaussian) pairs (each visible Gaussian needs one pair per
+ * tile its 3-sigma square touches).  The workspace also keeps the forward state
+ * that gs_render_backward reads.  Returns GS_ERR_INVALID on bad sizes.       */
+int gs_render_workspace_size(int64_t n, int32_t width, int32_t height, int64_t dup_capacity,
+                             size_t *bytes);
+
+/* Forward render (steps: preprocess -> depth sort -> tile binning -> tile
+ * sort -> front-to-back compositing), Sec. 3.3.
+ *   layer_mask  bit L renders layer L (Sec. 3.3: only active layers)
+ *   planes      HOST array of n_planes clip planes (0 <= n_planes <= 8)
+ *   bg          HOST float[3] background colour
+ *   workspace   device buffer of ws_bytes (>= gs_render_workspace_size for
+ *               some capacity); 256-byte aligned; keeps the forward state
+ *   image       [3][H][W] = sum_i c_i a_i T_i + T_final * bg
+ *   alpha       [H][W] = 1 - T_final (may be NULL)
+ * If the frame needs more pairs than the workspace holds, the status word
+ * reports GS_ERR_WORKSPACE and the required n_dup; the image is then
+ * incomplete (never out of bounds).                                          */
+int gs_render(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mask,
+              const gs_clip_plane *planes, int32_t n_planes, const float *bg,
+              void *workspace, size_t ws_bytes, float *image, float *alpha, void *stream);
+
+/* Backward of the last gs_render made with this workspace (same scene, camera
+ * and bg; Sec. 3.2 layered training).
+ *   dL_dimage  [3][H][W], dL_dalpha [H][W] (either may be NULL = zero)
+ *   grad_layer_mask  layers that receive gradients; others are frozen (Sec. 3.2)
+ *   grads      outputs (see gs_grads)
+ *   contrib_sum, contrib_max  [N] float32, ACCUMULATED across calls: += sum
+ *              and max over blended pixels of alpha*T (Sec. 3.2.2).  Either
+ *              may be NULL.  Zero them before the first view.
+ * The library's scratch for per-Gaussian record gradients lives in the
+ * workspace, so concurrent backward calls need distinct workspaces.          */
+int gs_render_backward(const gs_scene *scene, const gs_camera *camera, const float *bg,
+                       void *workspace, size_t ws_bytes, const float *dL_dimage,
+                       const float *dL_dalpha, uint32_t grad_layer_mask, const gs_grads *grads,
+                       float *contrib_sum, float *contrib_max, void *stream);
+
+/* Contribution prune (Sec. 3.2.2): keep[i] = contrib_max[i] >= threshold;
+ * *n_keep (device int64) = number kept; keep_index (device int32 [N], may be
+ * NULL) receives the kept indices in ascending order in its first *n_keep
+ * entries.  workspace: gs_prune_workspace_size(n) bytes (NULL allowed when
+ * keep_index is NULL).                                                        */
+int gs_prune_workspace_size(int64_t n, size_t *bytes);
+int gs_contrib_prune(const float *contrib_max, int64_t n, float threshold, uint8_t *keep,
+                     int32_t *keep_index, int64_t *n_keep, void *workspace, size_t ws_bytes,
+                     void *stream);
+
+/* Byte offsets of the regions of a render workspace of ws_bytes bytes, for
+ * tests and debugging tools (host only, no device access).  out[k] for
+ * k = 0..GS_LAYOUT_COUNT-1 in this order:
+ *   0 status/control block   1 records (48 B per Gaussian: u, v, A2, beta,
+ *   G2, opacity, r, g, b, depth, rect01, rect23)   2 tiles touched (u32)
+ *   3 depth keys (u32 float bits, 0xFFFFFFFF when culled)   4 final tile ids
+ *   of the pair list (u32)   5 final Gaussian ids of the pair list (u32)
+ *   6 tile ranges (u32 start, end per tile)   7 final transmittance (f32
+ *   per pixel)   8 n_contrib (u32 per pixel)   9 colour sum (3 f32 planes)
+ *   10 record gradients (48 B per Gaussian)   11 total bytes   12 pair
+ *   capacity.  Returns GS_ERR_WORKSPACE when ws_bytes is below the fixed part. */
+#define GS_LAYOUT_COUNT 13
+int gs_workspace_layout(int64_t n, int32_t width, int32_t height, size_t ws_bytes, int64_t *out);
+
+/* Copies the status word of a render workspace to host memory and
+ * synchronises the stream.                                                   */
+int gs_read_status(const void *workspace, gs_status *out, void *stream);
+
+/* Stage timing.  When enabled, every entry point records a CUDA event pair
+ * around each of its stages on the call's stream (no synchronisation).
+ * gs_profile_collect waits for the recorded events, adds each stage's elapsed
+ * milliseconds and call count since the previous collect to ms[k] and
+ * calls[k] (arrays of GS_STAGE_COUNT, host), and resets.  Disabled by default;
+ * stage k's kernels per call are listed in kernels[k] when non-NULL.
+ * Not thread safe: enable it in one thread at a time.                        */
+enum {
+    GS_STAGE_PREPROCESS = 0,   /* S1 */
+    GS_STAGE_COMPACT,          /* S2: visible compaction (scan) */
+    GS_STAGE_DEPTH_SORT,       /* S2: 4 radix passes on depth bits */
+    GS_STAGE_DUP_SCAN,         /* S2: ordered scan of tile counts */
+    GS_STAGE_EMIT,             /* S2: (tile, Gaussian) pairs */
+    GS_STAGE_TILE_SORT,        /* S2: radix passes on tile ids */
+    GS_STAGE_RANGES,           /* S2: per-tile [start, end) */
+    GS_STAGE_COMPOSITE,        /* S3 */
+    GS_STAGE_COMPOSITE_BWD,    /* S4a (includes zeroing the record gradients) */
+    GS_STAGE_PREPROCESS_BWD,   /* S4b */
+    GS_STAGE_PRUNE,            /* S5 */
+    GS_STAGE_COUNT
+};
+int gs_profile_enable(int on);
+int gs_profile_collect(double *ms, int64_t *calls);
+/* Kernels launched by the library since it was loaded (all entry points). */
+int64_t gs_kernel_launches(void);
+
+/* Message of the calling thread's last error ("" if none). */
+const char *gs_last_error_string(void);
+
+/* Library version string. */
+const char *gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H_ */

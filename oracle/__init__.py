@@ -85,7 +85,8 @@ def _load():
     L.or_bin.argtypes = [_I64, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P]
     L.or_composite.argtypes = [ctypes.c_int, ctypes.c_int] + [_P] * 19
     L.or_composite_bruteforce.argtypes = [ctypes.c_int, ctypes.c_int, _I64, _P, _I64] + [_P] * 9
-    L.or_composite_backward.argtypes = [ctypes.c_int, ctypes.c_int, _I64] + [_P] * 16
+    L.or_composite_backward.argtypes = [ctypes.c_int, ctypes.c_int, _I64] + [_P] * 17
+    L.or_composite_pixels.argtypes = [ctypes.c_int, ctypes.c_int] + [_P] * 10 + [_I64] + [_P] * 9
     L.or_chain.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P, _P,
                            _U32] + [_P] * 5)
     L.or_prune.argtypes = [_I64, _P, ctypes.c_double, _P]
@@ -244,8 +245,30 @@ def composite_bruteforce(pre: dict, bg=(0.0, 0.0, 0.0)) -> dict:
     return dict(image=img, alpha=al)
 
 
-def composite_backward(pre: dict, ranges, lst, bg, dL_dimage, dL_dalpha=None) -> dict:
-    """Record gradient [N,9] = d/d(u, v, A2, beta, G2, opac, r, g, b) and contributions."""
+def composite_pixels(pre: dict, ranges, lst, xs, ys, bg=(0.0, 0.0, 0.0)) -> dict:
+    """or_composite at selected pixels only: rgb [k,3], alpha, ncontrib, fragile and alternatives."""
+    L = _load()
+    xs = np.ascontiguousarray(xs, np.int32)
+    ys = np.ascontiguousarray(ys, np.int32)
+    k = xs.shape[0]
+    o = dict(rgb=np.zeros((k, 3)), alpha=np.zeros(k), ncontrib=np.zeros(k, np.int64),
+             fragile=np.zeros(k, np.int32), alt_rgb=np.zeros((k, 3)), alt_alpha=np.zeros(k),
+             alt_ncontrib=np.zeros(k, np.int64))
+    lst = np.ascontiguousarray(lst, np.int32)
+    if lst.size == 0:
+        lst = np.zeros(1, np.int32)
+    L.or_composite_pixels(pre["W"], pre["H"], _p(np.ascontiguousarray(ranges, np.int64)), _p(lst),
+                          _p(_f64(pre["u"])), _p(_f64(pre["v"])), _p(_f64(pre["A2"])), _p(_f64(pre["beta"])),
+                          _p(_f64(pre["G2"])), _p(_f64(pre["opac"])), _p(_f64(pre["rgb"])), _p(_f64(bg)), k,
+                          _p(xs), _p(ys), _p(o["rgb"]), _p(o["alpha"]), _p(o["ncontrib"]), _p(o["fragile"]),
+                          _p(o["alt_rgb"]), _p(o["alt_alpha"]), _p(o["alt_ncontrib"]))
+    return o
+
+
+def composite_backward(pre: dict, ranges, lst, bg, dL_dimage, dL_dalpha=None, tile_mask=None) -> dict:
+    """Record gradient [N,9] = d/d(u, v, A2, beta, G2, opac, r, g, b) and contributions.
+
+    ``tile_mask`` (uint8 per tile) restricts the pass to the marked tiles."""
     L = _load()
     W, H = pre["W"], pre["H"]
     n = pre["vis"].shape[0]
@@ -257,11 +280,12 @@ def composite_backward(pre: dict, ranges, lst, bg, dL_dimage, dL_dalpha=None) ->
         lst = np.zeros(1, np.int32)
     dli = _f64(dL_dimage).reshape(3, H, W)
     dla = _f64(dL_dalpha).reshape(H, W) if dL_dalpha is not None else np.zeros((H, W))
+    tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8)
     L.or_composite_backward(W, H, n, _p(np.ascontiguousarray(ranges, np.int64)), _p(lst),
                             _p(_f64(pre["u"])), _p(_f64(pre["v"])), _p(_f64(pre["A2"])),
                             _p(_f64(pre["beta"])), _p(_f64(pre["G2"])), _p(_f64(pre["opac"])),
-                            _p(_f64(pre["rgb"])), _p(_f64(bg)), _p(dli), _p(dla), _p(rg), _p(cs), _p(cm),
-                            _p(tf))
+                            _p(_f64(pre["rgb"])), _p(_f64(bg)), _p(dli), _p(dla), _p(tm) if tm is not None else None,
+                            _p(rg), _p(cs), _p(cm), _p(tf))
     return dict(rec_grad=rg, contrib_sum=cs, contrib_max=cm, touched_fragile=tf)
 
 
@@ -300,10 +324,10 @@ def render(scene, cam, layer_mask=0xFFFFFFFF, planes=(), bg=(0.0, 0.0, 0.0), pre
 
 
 def render_backward(scene, cam, fwd: dict, bg, dL_dimage, dL_dalpha=None,
-                    grad_layer_mask=0xFFFFFFFF) -> dict:
+                    grad_layer_mask=0xFFFFFFFF, tile_mask=None) -> dict:
     """Analytic gradients of the render (FP64), plus per-Gaussian contributions."""
     pre = fwd["pre"]
-    cb = composite_backward(pre, fwd["ranges"], fwd["list"], bg, dL_dimage, dL_dalpha)
+    cb = composite_backward(pre, fwd["ranges"], fwd["list"], bg, dL_dimage, dL_dalpha, tile_mask)
     g = chain(scene, cam, pre["vis"], cb["rec_grad"], grad_layer_mask)
     g.update(cb)
     return g

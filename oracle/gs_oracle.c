@@ -618,6 +618,37 @@ void or_composite(int W, int H, const int64_t *ranges, const int32_t *list, cons
         }
 }
 
+/* The compositing of or_composite at npix selected pixels (xs[k], ys[k]). */
+void or_composite_pixels(int W, int H, const int64_t *ranges, const int32_t *list, const double *u,
+                         const double *v, const double *A2, const double *beta, const double *G2,
+                         const double *opac, const double *rgb, const double *bg, int64_t npix,
+                         const int32_t *xs, const int32_t *ys, double *rgb_out, double *alpha,
+                         int64_t *ncontrib, int32_t *fragile, double *alt_rgb, double *alt_alpha,
+                         int64_t *alt_ncontrib) {
+    int Tx = (W + TILE - 1) / TILE;
+    (void)H;
+    for (int64_t k = 0; k < npix; ++k) {
+        int x = xs[k], y = ys[k];
+        int64_t t = (int64_t)(y / TILE) * Tx + (x / TILE);
+        pix_result r, ra;
+        int nfr = composite_pixel(x + 0.5, y + 0.5, list, ranges[2 * t], ranges[2 * t + 1], u, v, A2, beta, G2,
+                                  opac, rgb, -1, &r, NULL, NULL, NULL);
+        for (int c = 0; c < 3; ++c) rgb_out[3 * k + c] = r.C[c] + r.T * bg[c];
+        alpha[k] = 1.0 - r.T;
+        ncontrib[k] = r.ncontrib;
+        fragile[k] = nfr;
+        ra = r;
+        if (nfr > 0) {
+            int nfr2 = composite_pixel(x + 0.5, y + 0.5, list, ranges[2 * t], ranges[2 * t + 1], u, v, A2, beta,
+                                       G2, opac, rgb, 0, &ra, NULL, NULL, NULL);
+            if (nfr2 > nfr) fragile[k] = nfr2;
+        }
+        for (int c = 0; c < 3; ++c) alt_rgb[3 * k + c] = ra.C[c] + ra.T * bg[c];
+        alt_alpha[k] = 1.0 - ra.T;
+        alt_ncontrib[k] = ra.ncontrib;
+    }
+}
+
 /* Brute force: every visible Gaussian at every pixel, in (depth, index)
  * order, with no tiles.  Equal to or_composite wherever every splat's
  * alpha >= 1/255 support lies inside its tile rectangle.                     */
@@ -647,12 +678,14 @@ void or_composite_bruteforce(int W, int H, int64_t n, const int32_t *order, int6
  * Culls, skips, the stop and the tile lists are constants.  Also accumulates
  * contrib_sum[g] += a T and contrib_max[g] = max(.., a T) over blended pixels.
  * rec_grad layout per Gaussian: [du, dv, dA2, dbeta, dG2, dopac, dr, dg, db].
- * touched_fragile[g] is set when a fragile pixel blends or skips g.          */
+ * touched_fragile[g] is set when a fragile pixel blends or skips g.
+ * tile_mask (may be NULL) restricts the pass to the marked tiles; the result
+ * is then exact for every Gaussian whose tile rectangle lies in marked tiles. */
 void or_composite_backward(int W, int H, int64_t n, const int64_t *ranges, const int32_t *list,
                            const double *u, const double *v, const double *A2, const double *beta,
                            const double *G2, const double *opac, const double *rgb, const double *bg,
-                           const double *dL_dimage, const double *dL_dalpha, double *rec_grad,
-                           double *contrib_sum, double *contrib_max, int32_t *touched_fragile) {
+                           const double *dL_dimage, const double *dL_dalpha, const uint8_t *tile_mask,
+                           double *rec_grad, double *contrib_sum, double *contrib_max, int32_t *touched_fragile) {
     int Tx = (W + TILE - 1) / TILE;
     int64_t maxlen = 0;
     int64_t ntiles = (int64_t)Tx * ((H + TILE - 1) / TILE);
@@ -669,6 +702,7 @@ void or_composite_backward(int W, int H, int64_t n, const int64_t *ranges, const
             int64_t pidx = (int64_t)y * W + x;
             double px = x + 0.5, py = y + 0.5;
             pix_result r;
+            if (tile_mask && !tile_mask[t]) continue;
             int nfr = composite_pixel(px, py, list, ranges[2 * t], ranges[2 * t + 1], u, v, A2, beta, G2,
                                       opac, rgb, -1, &r, added, Tb, al);
             if (nfr > 0)

@@ -1,0 +1,224 @@
+"""ctypes binding of the C ABI in include/gs.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Pointers are
+passed as integers (``tensor.data_ptr()``); host structs are built from plain
+Python values.  No computation happens in this module: if the shared library
+cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_P = ctypes.c_void_p
+
+GS_OK, GS_ERR_INVALID, GS_ERR_WORKSPACE, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_OOM = range(6)
+GS_DTYPE_F32, GS_DTYPE_F16, GS_DTYPE_BF16 = 0, 1, 2
+GS_TILE = 16
+GS_MAX_PLANES = 8
+
+EXPORTED = ("gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_prune_workspace_size",
+            "gs_contrib_prune", "gs_workspace_layout", "gs_read_status", "gs_profile_enable", "gs_profile_collect",
+            "gs_kernel_launches", "gs_last_error_string", "gs_version")
+STAGES = ("preprocess", "compact", "depth_sort", "dup_scan", "emit", "tile_sort", "ranges", "composite",
+          "composite_bwd", "preprocess_bwd", "prune")
+GS_LAYOUT_COUNT = 13
+LAYOUT_NAMES = ("ctl", "rec", "tiles", "depth", "tile_k", "tile_v", "ranges", "t_final", "n_contrib", "c_sum",
+                "rec_grad", "total", "dup_capacity")
+
+
+class gs_camera(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("znear", ctypes.c_float),
+                ("_reserved", ctypes.c_float)]
+
+
+class gs_clip_plane(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_float * 3), ("d", ctypes.c_float), ("layer_bits", ctypes.c_uint32),
+                ("_reserved", ctypes.c_uint32)]
+
+
+class gs_scene(ctypes.Structure):
+    _fields_ = [("means", _P), ("log_scales", _P), ("quats", _P), ("opacity_logit", _P), ("sh", _P),
+                ("layer", _P), ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32),
+                ("dtype_sh", ctypes.c_int32), ("dtype_scale_rot", ctypes.c_int32), ("_reserved", ctypes.c_int32)]
+
+
+class gs_grads(ctypes.Structure):
+    _fields_ = [("means", _P), ("log_scales", _P), ("quats", _P), ("opacity_logit", _P), ("sh", _P)]
+
+
+class gs_status(ctypes.Structure):
+    _fields_ = [("error", ctypes.c_int32), ("n_visible", ctypes.c_uint32), ("n_dup", ctypes.c_uint64),
+                ("dup_capacity", ctypes.c_uint64), ("max_tile_list", ctypes.c_uint32),
+                ("_reserved", ctypes.c_uint32)]
+
+
+class GsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("gs error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libgs.so (building it first if it is missing and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and (not os.path.exists(path) or _build._stale()):
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("CUDA rasterizer library not built: %s" % path)
+        L = ctypes.CDLL(path)
+        L.gs_render_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                               ctypes.POINTER(ctypes.c_size_t)]
+        L.gs_render.argtypes = [ctypes.POINTER(gs_scene), ctypes.POINTER(gs_camera), ctypes.c_uint32,
+                                ctypes.POINTER(gs_clip_plane), ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
+                                _P, ctypes.c_size_t, _P, _P, _P]
+        L.gs_render_backward.argtypes = [ctypes.POINTER(gs_scene), ctypes.POINTER(gs_camera),
+                                         ctypes.POINTER(ctypes.c_float), _P, ctypes.c_size_t, _P, _P,
+                                         ctypes.c_uint32, ctypes.POINTER(gs_grads), _P, _P, _P]
+        L.gs_prune_workspace_size.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]
+        L.gs_contrib_prune.argtypes = [_P, ctypes.c_int64, ctypes.c_float, _P, _P, _P, _P, ctypes.c_size_t, _P]
+        L.gs_read_status.argtypes = [_P, ctypes.POINTER(gs_status), _P]
+        L.gs_workspace_layout.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t,
+                                          ctypes.POINTER(ctypes.c_int64)]
+        L.gs_profile_enable.argtypes = [ctypes.c_int]
+        L.gs_profile_collect.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+        L.gs_kernel_launches.argtypes = []
+        L.gs_last_error_string.restype = ctypes.c_char_p
+        L.gs_version.restype = ctypes.c_char_p
+        for name in EXPORTED:
+            if name not in ("gs_last_error_string", "gs_version"):
+                getattr(L, name).restype = ctypes.c_int
+        L.gs_kernel_launches.restype = ctypes.c_int64
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != GS_OK:
+        raise GsError(rc, load().gs_last_error_string().decode())
+
+
+# --------------------------------------------------------------------------- marshalling helpers
+
+def make_camera(cam) -> gs_camera:
+    """gs_camera from any object with R, t, fx, fy, cx, cy, width, height, znear."""
+    c = gs_camera()
+    R = [float(v) for row in cam.R for v in row] if hasattr(cam.R, "__len__") and len(cam.R) == 3 else \
+        [float(v) for v in cam.R]
+    for k in range(9):
+        c.R[k] = R[k]
+    for k in range(3):
+        c.t[k] = float(cam.t[k])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.znear = float(getattr(cam, "znear", 0.2))
+    return c
+
+
+def make_planes(planes):
+    n = len(planes)
+    if n > GS_MAX_PLANES:
+        raise ValueError("at most %d clip planes" % GS_MAX_PLANES)
+    arr = (gs_clip_plane * max(n, 1))()
+    for k, (nrm, d, bits) in enumerate(planes):
+        for j in range(3):
+            arr[k].n[j] = float(nrm[j])
+        arr[k].d = float(d)
+        arr[k].layer_bits = int(bits) & 0xFFFFFFFF
+    return arr, n
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(int(t) if isinstance(t, int) else t.data_ptr())
+
+
+# --------------------------------------------------------------------------- the C entry points
+
+def gs_render_workspace_size(n: int, width: int, height: int, dup_capacity: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().gs_render_workspace_size(int(n), int(width), int(height), int(dup_capacity), ctypes.byref(out)))
+    return int(out.value)
+
+
+def gs_render(scene: gs_scene, camera: gs_camera, layer_mask: int, planes, bg, workspace, ws_bytes: int, image,
+              alpha, stream: int) -> None:
+    parr, npl = make_planes(planes)
+    bgv = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    _check(load().gs_render(ctypes.byref(scene), ctypes.byref(camera), int(layer_mask) & 0xFFFFFFFF, parr, npl, bgv,
+                            _ptr(workspace), int(ws_bytes), _ptr(image), _ptr(alpha), ctypes.c_void_p(stream)))
+
+
+def gs_render_backward(scene: gs_scene, camera: gs_camera, bg, workspace, ws_bytes: int, dL_dimage, dL_dalpha,
+                       grad_layer_mask: int, grads: gs_grads, contrib_sum, contrib_max, stream: int) -> None:
+    bgv = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    _check(load().gs_render_backward(ctypes.byref(scene), ctypes.byref(camera), bgv, _ptr(workspace), int(ws_bytes),
+                                     _ptr(dL_dimage), _ptr(dL_dalpha), int(grad_layer_mask) & 0xFFFFFFFF,
+                                     ctypes.byref(grads), _ptr(contrib_sum), _ptr(contrib_max),
+                                     ctypes.c_void_p(stream)))
+
+
+def gs_prune_workspace_size(n: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().gs_prune_workspace_size(int(n), ctypes.byref(out)))
+    return int(out.value)
+
+
+def gs_contrib_prune(contrib_max, n: int, threshold: float, keep, keep_index, n_keep, workspace, ws_bytes: int,
+                     stream: int) -> None:
+    _check(load().gs_contrib_prune(_ptr(contrib_max), int(n), float(threshold), _ptr(keep), _ptr(keep_index),
+                                   _ptr(n_keep), _ptr(workspace), int(ws_bytes), ctypes.c_void_p(stream)))
+
+
+def gs_workspace_layout(n: int, width: int, height: int, ws_bytes: int) -> dict:
+    out = (ctypes.c_int64 * GS_LAYOUT_COUNT)()
+    _check(load().gs_workspace_layout(int(n), int(width), int(height), int(ws_bytes), out))
+    return dict(zip(LAYOUT_NAMES, [int(v) for v in out]))
+
+
+def gs_read_status(workspace, stream: int) -> gs_status:
+    st = gs_status()
+    _check(load().gs_read_status(_ptr(workspace), ctypes.byref(st), ctypes.c_void_p(stream)))
+    return st
+
+
+def gs_profile_enable(on: bool) -> None:
+    _check(load().gs_profile_enable(1 if on else 0))
+
+
+def gs_profile_collect() -> dict:
+    """{stage: (milliseconds, calls)} since the previous collect (waits for the events)."""
+    ms = (ctypes.c_double * len(STAGES))()
+    calls = (ctypes.c_int64 * len(STAGES))()
+    _check(load().gs_profile_collect(ms, calls))
+    return {name: (float(ms[k]), int(calls[k])) for k, name in enumerate(STAGES)}
+
+
+def gs_kernel_launches() -> int:
+    return int(load().gs_kernel_launches())
+
+
+def gs_last_error_string() -> str:
+    return load().gs_last_error_string().decode()
+
+
+def gs_version() -> str:
+    return load().gs_version().decode()

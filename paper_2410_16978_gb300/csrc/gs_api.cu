@@ -1,0 +1,400 @@
+// C ABI of the rasterizer (declared in include/gs.h): argument checks,
+// workspace carve-up and the launch sequence of each entry point.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+static size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
+    if (n < 0 || n > 0x7FFFFFFF || W <= 0 || H <= 0 || W > (1 << 20) || H > (1 << 20) || dup_cap < 0 ||
+        dup_cap > 0xFFFFFFFFLL)
+        return false;
+    Layout o;
+    o.n = n; o.dup_cap = dup_cap; o.W = W; o.H = H;
+    o.Tx = (W + kTile - 1) / kTile; o.Ty = (H + kTile - 1) / kTile;
+    o.Tn = o.Tx * o.Ty;
+    const size_t N = static_cast<size_t>(n), D = static_cast<size_t>(dup_cap), P = static_cast<size_t>(W) * H;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
+    o.ctl = take(256);
+    o.rec = take(N * sizeof(Rec));
+    o.tiles = take(N * 4);
+    o.depth = take(N * 4);
+    o.sort_k[0] = take(N * 4); o.sort_k[1] = take(N * 4);
+    o.sort_v[0] = take(N * 4); o.sort_v[1] = take(N * 4);
+    o.dup_off = take(N * 4);
+    o.ranges = take(static_cast<size_t>(o.Tn) * 8);
+    o.t_final = take(P * 4);
+    o.n_contrib = take(P * 4);
+    o.c_sum = take(3 * P * 4);
+    o.partials = take(kMaxSortBlocks * 4);
+    o.hist = take(static_cast<size_t>(256) * kMaxSortBlocks * 4);
+    o.rec_grad = take(N * sizeof(Rec));
+    o.tile_k[0] = take(D * 4); o.tile_k[1] = take(D * 4);
+    o.tile_v[0] = take(D * 4); o.tile_v[1] = take(D * 4);
+    o.total = off;
+    *L = o;
+    return true;
+}
+
+int64_t capacity_for(int64_t n, int W, int H, size_t ws_bytes) {
+    Layout L0;
+    if (!make_layout(n, W, H, 0, &L0) || ws_bytes < L0.total) return -1;
+    int64_t cap = static_cast<int64_t>((ws_bytes - L0.total) / 16);
+    if (cap > 0xFFFFFFFFLL) cap = 0xFFFFFFFFLL;
+    Layout L;
+    while (cap > 0 && (!make_layout(n, W, H, cap, &L) || L.total > ws_bytes)) cap -= 64;
+    return cap < 0 ? 0 : cap;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+namespace {
+
+thread_local std::string g_err;
+
+// ---- stage timing (off by default) ----
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<std::pair<int, size_t>> marks;   // (stage, index of its start event)
+    cudaEvent_t get() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+};
+Profiler g_prof;
+std::atomic<int64_t> g_launches{0};
+
+struct Stage {
+    int stage;
+    cudaStream_t st;
+    size_t idx = 0;
+    Stage(int s, cudaStream_t stream, int kernels) : stage(s), st(stream) {
+        g_launches += kernels;
+        if (!g_prof.on) return;
+        idx = g_prof.used;
+        cudaEventRecord(g_prof.get(), st);
+        g_prof.get();
+    }
+    ~Stage() {
+        if (!g_prof.on) return;
+        cudaEventRecord(g_prof.pool[idx + 1], st);
+        g_prof.marks.emplace_back(stage, idx);
+    }
+};
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return GS_OK;
+    return fail(GS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int check_scene(const gs_scene *s, SceneView *v) {
+    if (!s) return fail(GS_ERR_INVALID, "scene is NULL");
+    if (s->n < 0 || s->n > 0x7FFFFFFF) return fail(GS_ERR_INVALID, "scene n out of range: %lld", (long long)s->n);
+    if (s->sh_degree < 0 || s->sh_degree > 3) return fail(GS_ERR_INVALID, "sh_degree must be 0..3");
+    for (int dt : {s->dtype_sh, s->dtype_scale_rot})
+        if (dt != GS_DTYPE_F32 && dt != GS_DTYPE_F16 && dt != GS_DTYPE_BF16)
+            return fail(GS_ERR_INVALID, "unknown dtype %d", dt);
+    if (s->n > 0) {
+        const void *ptrs[6] = {s->means, s->log_scales, s->quats, s->opacity_logit, s->sh, s->layer};
+        for (const void *p : ptrs)
+            if (!p) return fail(GS_ERR_INVALID, "scene array is NULL");
+        for (const void *p : ptrs)
+            if (!aligned(p, 16)) return fail(GS_ERR_INVALID, "scene arrays must be 16-byte aligned");
+    }
+    v->means = static_cast<const float *>(s->means);
+    v->log_scales = s->log_scales;
+    v->quats = s->quats;
+    v->opacity_logit = static_cast<const float *>(s->opacity_logit);
+    v->sh = s->sh;
+    v->layer = s->layer;
+    v->n = static_cast<int>(s->n);
+    v->sh_degree = s->sh_degree;
+    v->dtype_sh = s->dtype_sh;
+    v->dtype_sr = s->dtype_scale_rot;
+    return GS_OK;
+}
+
+int check_camera(const gs_camera *c, CamView *v) {
+    if (!c) return fail(GS_ERR_INVALID, "camera is NULL");
+    if (c->width <= 0 || c->height <= 0 || c->width > (1 << 20) || c->height > (1 << 20))
+        return fail(GS_ERR_INVALID, "bad image size %dx%d", c->width, c->height);
+    if (!(c->fx > 0.f) || !(c->fy > 0.f)) return fail(GS_ERR_INVALID, "focal lengths must be > 0");
+    std::memcpy(v->R, c->R, sizeof v->R);
+    std::memcpy(v->t, c->t, sizeof v->t);
+    v->fx = c->fx; v->fy = c->fy; v->cx = c->cx; v->cy = c->cy; v->znear = c->znear;
+    v->W = c->width; v->H = c->height;
+    v->Tx = (c->width + kTile - 1) / kTile;
+    v->Ty = (c->height + kTile - 1) / kTile;
+    return GS_OK;
+}
+
+int tile_sort_passes(int Tn) {
+    int bits = 0;
+    while ((1LL << bits) < Tn) ++bits;
+    return (bits + 7) / 8;
+}
+
+int workspace_layout(const gs_scene *s, const CamView &cv, void *ws, size_t ws_bytes, Layout *L) {
+    if (!ws) return fail(GS_ERR_INVALID, "workspace is NULL");
+    if (!aligned(ws, 256)) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
+    const int64_t cap = capacity_for(s->n, cv.W, cv.H, ws_bytes);
+    if (cap < 0) return fail(GS_ERR_WORKSPACE, "workspace of %zu bytes is below the fixed part", ws_bytes);
+    if (!make_layout(s->n, cv.W, cv.H, cap, L)) return fail(GS_ERR_INVALID, "layout failed");
+    return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gs_last_error_string(void) { return g_err.c_str(); }
+
+const char *gs_version(void) { return "gs-layered-gb300 0.1 (sm_103a)"; }
+
+int gs_render_workspace_size(int64_t n, int32_t width, int32_t height, int64_t dup_capacity, size_t *bytes) {
+    if (!bytes) return fail(GS_ERR_INVALID, "bytes is NULL");
+    Layout L;
+    if (!make_layout(n, width, height, dup_capacity, &L)) return fail(GS_ERR_INVALID, "bad workspace sizes");
+    *bytes = L.total;
+    return GS_OK;
+}
+
+int gs_render(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mask, const gs_clip_plane *planes,
+              int32_t n_planes, const float *bg, void *workspace, size_t ws_bytes, float *image, float *alpha,
+              void *stream) {
+    SceneView sv;
+    CamView cv;
+    int rc;
+    if ((rc = check_scene(scene, &sv)) != GS_OK) return rc;
+    if ((rc = check_camera(camera, &cv)) != GS_OK) return rc;
+    if (n_planes < 0 || n_planes > GS_MAX_PLANES) return fail(GS_ERR_INVALID, "n_planes must be 0..%d", GS_MAX_PLANES);
+    if (n_planes > 0 && !planes) return fail(GS_ERR_INVALID, "planes is NULL");
+    if (!bg) return fail(GS_ERR_INVALID, "bg is NULL");
+    if (!image) return fail(GS_ERR_INVALID, "image is NULL");
+    Layout L;
+    if ((rc = workspace_layout(scene, cv, workspace, ws_bytes, &L)) != GS_OK) return rc;
+    Planes pl;
+    std::memset(&pl, 0, sizeof pl);
+    pl.n = n_planes;
+    for (int k = 0; k < n_planes; ++k) {
+        pl.p[k] = make_float4(planes[k].n[0], planes[k].n[1], planes[k].n[2], planes[k].d);
+        pl.bits[k] = planes[k].layer_bits;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *ws = workspace;
+    Ctl *ctl = at<Ctl>(ws, L.ctl);
+    const uint32_t n = static_cast<uint32_t>(sv.n);
+    const uint32_t cap = static_cast<uint32_t>(L.dup_cap);
+    if ((rc = cuda_check(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st), "memset status")) != GS_OK) return rc;
+    if ((rc = cuda_check(cudaMemsetAsync(at<char>(ws, L.ranges), 0, static_cast<size_t>(L.Tn) * 8, st),
+                         "memset ranges")) != GS_OK)
+        return rc;
+    Rec *rec = at<Rec>(ws, L.rec);
+    uint32_t *tiles = at<uint32_t>(ws, L.tiles);
+    {
+        Stage sg(GS_STAGE_PREPROCESS, st, 1);
+        if ((rc = cuda_check(launch_preprocess(sv, cv, layer_mask, pl, rec, tiles, at<uint32_t>(ws, L.depth), st),
+                             "preprocess")) != GS_OK)
+            return rc;
+    }
+    uint32_t *sk[2] = {at<uint32_t>(ws, L.sort_k[0]), at<uint32_t>(ws, L.sort_k[1])};
+    uint32_t *sv2[2] = {at<uint32_t>(ws, L.sort_v[0]), at<uint32_t>(ws, L.sort_v[1])};
+    uint32_t *partials = at<uint32_t>(ws, L.partials);
+    uint32_t *hist = at<uint32_t>(ws, L.hist);
+    {
+        Stage sg(GS_STAGE_COMPACT, st, 3);
+        if ((rc = cuda_check(launch_compact_visible(tiles, at<uint32_t>(ws, L.depth), sv.n, sk[0], sv2[0], partials,
+                                                    ctl, st),
+                             "compact")) != GS_OK)
+            return rc;
+    }
+    {
+        Stage sg(GS_STAGE_DEPTH_SORT, st, 12);
+        for (int pass = 0; pass < 4; ++pass) {
+            const int a = pass & 1;
+            if ((rc = cuda_check(launch_radix_pass(sk[a], sv2[a], sk[1 - a], sv2[1 - a], &ctl->n_vis, n, 8 * pass,
+                                                   hist, st),
+                                 "depth sort")) != GS_OK)
+                return rc;
+        }
+    }
+    uint32_t *order = sv2[0];
+    uint32_t *dup_off = at<uint32_t>(ws, L.dup_off);
+    {
+        Stage sg(GS_STAGE_DUP_SCAN, st, 3);
+        if ((rc = cuda_check(launch_dup_offsets(order, tiles, n, dup_off, partials, ctl, L.dup_cap, st),
+                             "dup offsets")) != GS_OK)
+            return rc;
+    }
+    uint32_t *tk[2] = {at<uint32_t>(ws, L.tile_k[0]), at<uint32_t>(ws, L.tile_k[1])};
+    uint32_t *tv[2] = {at<uint32_t>(ws, L.tile_v[0]), at<uint32_t>(ws, L.tile_v[1])};
+    {
+        Stage sg(GS_STAGE_EMIT, st, 1);
+        if ((rc = cuda_check(launch_emit(order, dup_off, rec, n, cv.Tx, tk[0], tv[0], ctl, L.dup_cap, st), "emit")) !=
+            GS_OK)
+            return rc;
+    }
+    const int tp = tile_sort_passes(L.Tn);
+    {
+        Stage sg(GS_STAGE_TILE_SORT, st, 3 * tp);
+        for (int pass = 0; pass < tp; ++pass) {
+            const int a = pass & 1;
+            if ((rc = cuda_check(launch_radix_pass(tk[a], tv[a], tk[1 - a], tv[1 - a], &ctl->n_dup_c, cap, 8 * pass,
+                                                   hist, st),
+                                 "tile sort")) != GS_OK)
+                return rc;
+        }
+    }
+    const int fin = tp & 1;
+    uint2 *ranges = at<uint2>(ws, L.ranges);
+    {
+        Stage sg(GS_STAGE_RANGES, st, 1);
+        if ((rc = cuda_check(launch_ranges(tk[fin], cap, ranges, ctl, st), "ranges")) != GS_OK) return rc;
+    }
+    Stage sg(GS_STAGE_COMPOSITE, st, 1);
+    return cuda_check(launch_composite_forward(ranges, tv[fin], rec, cv.W, cv.H, cv.Tx, cv.Ty,
+                                               make_float3(bg[0], bg[1], bg[2]), image, alpha,
+                                               at<float>(ws, L.t_final), at<uint32_t>(ws, L.n_contrib),
+                                               at<float>(ws, L.c_sum), st),
+                      "composite");
+}
+
+int gs_render_backward(const gs_scene *scene, const gs_camera *camera, const float *bg, void *workspace,
+                       size_t ws_bytes, const float *dL_dimage, const float *dL_dalpha, uint32_t grad_layer_mask,
+                       const gs_grads *grads, float *contrib_sum, float *contrib_max, void *stream) {
+    SceneView sv;
+    CamView cv;
+    int rc;
+    if ((rc = check_scene(scene, &sv)) != GS_OK) return rc;
+    if ((rc = check_camera(camera, &cv)) != GS_OK) return rc;
+    if (!bg) return fail(GS_ERR_INVALID, "bg is NULL");
+    if (!grads || (sv.n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logit ||
+                                !grads->sh)))
+        return fail(GS_ERR_INVALID, "gradient outputs must all be set");
+    Layout L;
+    if ((rc = workspace_layout(scene, cv, workspace, ws_bytes, &L)) != GS_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *ws = workspace;
+    float4 *rec_grad = at<float4>(ws, L.rec_grad);
+    const int fin = tile_sort_passes(L.Tn) & 1;
+    {
+    Stage sg(GS_STAGE_COMPOSITE_BWD, st, 1);
+    if ((rc = cuda_check(cudaMemsetAsync(rec_grad, 0, static_cast<size_t>(sv.n) * sizeof(Rec), st), "memset grad")) !=
+        GS_OK)
+        return rc;
+    if ((rc = cuda_check(launch_composite_backward(at<uint2>(ws, L.ranges), at<uint32_t>(ws, L.tile_v[fin]),
+                                                   at<Rec>(ws, L.rec), cv.W, cv.H, cv.Tx, cv.Ty,
+                                                   make_float3(bg[0], bg[1], bg[2]), at<float>(ws, L.t_final),
+                                                   at<uint32_t>(ws, L.n_contrib), at<float>(ws, L.c_sum), dL_dimage,
+                                                   dL_dalpha, sv.layer, grad_layer_mask, rec_grad, contrib_sum,
+                                                   contrib_max, st),
+                         "composite backward")) != GS_OK)
+        return rc;
+    }
+    Stage sg(GS_STAGE_PREPROCESS_BWD, st, 1);
+    return cuda_check(launch_preprocess_backward(sv, cv, at<uint32_t>(ws, L.tiles), rec_grad, grad_layer_mask, *grads,
+                                                 st),
+                      "preprocess backward");
+}
+
+int gs_workspace_layout(int64_t n, int32_t width, int32_t height, size_t ws_bytes, int64_t *out) {
+    if (!out) return fail(GS_ERR_INVALID, "out is NULL");
+    const int64_t cap = capacity_for(n, width, height, ws_bytes);
+    if (cap < 0) return fail(GS_ERR_WORKSPACE, "workspace of %zu bytes is below the fixed part", ws_bytes);
+    Layout L;
+    if (!make_layout(n, width, height, cap, &L)) return fail(GS_ERR_INVALID, "bad sizes");
+    const int fin = tile_sort_passes(L.Tn) & 1;
+    const int64_t v[GS_LAYOUT_COUNT] = {
+        (int64_t)L.ctl, (int64_t)L.rec, (int64_t)L.tiles, (int64_t)L.depth, (int64_t)L.tile_k[fin],
+        (int64_t)L.tile_v[fin], (int64_t)L.ranges, (int64_t)L.t_final, (int64_t)L.n_contrib, (int64_t)L.c_sum,
+        (int64_t)L.rec_grad, (int64_t)L.total, cap};
+    for (int k = 0; k < GS_LAYOUT_COUNT; ++k) out[k] = v[k];
+    return GS_OK;
+}
+
+int gs_prune_workspace_size(int64_t n, size_t *bytes) {
+    if (!bytes) return fail(GS_ERR_INVALID, "bytes is NULL");
+    if (n < 0 || n > 0x7FFFFFFF) return fail(GS_ERR_INVALID, "n out of range");
+    *bytes = kMaxSortBlocks * 4 + sizeof(Ctl);
+    return GS_OK;
+}
+
+int gs_contrib_prune(const float *contrib_max, int64_t n, float threshold, uint8_t *keep, int32_t *keep_index,
+                     int64_t *n_keep, void *workspace, size_t ws_bytes, void *stream) {
+    if (n < 0 || n > 0x7FFFFFFF) return fail(GS_ERR_INVALID, "n out of range");
+    if (!n_keep) return fail(GS_ERR_INVALID, "n_keep is NULL");
+    if (n > 0 && (!contrib_max || !keep)) return fail(GS_ERR_INVALID, "contrib_max and keep must be set");
+    size_t need = 0;
+    gs_prune_workspace_size(n, &need);
+    if (!workspace || ws_bytes < need) return fail(GS_ERR_WORKSPACE, "prune workspace needs %zu bytes", need);
+    if (!aligned(workspace, 16)) return fail(GS_ERR_INVALID, "workspace must be 16-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Stage sg(GS_STAGE_PRUNE, st, 3);
+    return cuda_check(launch_prune(contrib_max, static_cast<int>(n), threshold, keep, keep_index, n_keep,
+                                   static_cast<uint32_t *>(workspace), st),
+                      "prune");
+}
+
+int gs_profile_enable(int on) {
+    g_prof.on = on != 0;
+    return GS_OK;
+}
+
+int gs_profile_collect(double *ms, int64_t *calls) {
+    if (!ms || !calls) return fail(GS_ERR_INVALID, "NULL argument");
+    for (int k = 0; k < GS_STAGE_COUNT; ++k) { ms[k] = 0.0; calls[k] = 0; }
+    for (auto &m : g_prof.marks) {
+        cudaEvent_t b = g_prof.pool[m.second], e = g_prof.pool[m.second + 1];
+        int rc = cuda_check(cudaEventSynchronize(e), "profile sync");
+        if (rc != GS_OK) return rc;
+        float t = 0.f;
+        if ((rc = cuda_check(cudaEventElapsedTime(&t, b, e), "profile elapsed")) != GS_OK) return rc;
+        ms[m.first] += t;
+        calls[m.first] += 1;
+    }
+    g_prof.marks.clear();
+    g_prof.used = 0;
+    return GS_OK;
+}
+
+int64_t gs_kernel_launches(void) { return g_launches.load(); }
+
+int gs_read_status(const void *workspace, gs_status *out, void *stream) {
+    if (!workspace || !out) return fail(GS_ERR_INVALID, "NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = cuda_check(cudaMemcpyAsync(out, workspace, sizeof(gs_status), cudaMemcpyDeviceToHost, st), "status copy");
+    if (rc != GS_OK) return rc;
+    return cuda_check(cudaStreamSynchronize(st), "status sync");
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// Internal declarations of the CUDA rasterizer: the per-Gaussian record, the
+// workspace layout and the launch helpers of each translation unit.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+constexpr int kTile = GS_TILE;
+constexpr int kTilePix = kTile * kTile;        // 256 pixels, one thread each
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;                  // items per thread per round-trip
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kMaxSortBlocks = 1024;           // histogram rows reserved in the workspace
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 0x1.010102p-8f;    // 1/255 rounded to float
+constexpr float kTMin = 1e-4f;
+
+// Per-Gaussian record written by the preprocess and gathered by the compositor.
+// a = (u, v, A2, beta), b = (G2, opacity, r, g), c = (b, depth, rect01, rect23)
+// where the splat exponent in base 2 is A2 (dx + beta dy)^2 + G2 dy^2,
+// rect01 = x0 | y0 << 16 and rect23 = x1 | y1 << 16 (half-open tile rectangle).
+struct __align__(16) Rec {
+    float4 a;
+    float4 b;
+    float4 c;
+};
+
+// Device control block at offset 0 of the workspace.  The first member is
+// the public gs_status; the rest are counts the kernels hand to each other.
+struct Ctl {
+    gs_status st;          // 32 bytes
+    uint32_t n_vis;        // visible Gaussians (compaction total)
+    uint32_t n_dup_c;      // min(n_dup, capacity): items in the tile sort
+    uint32_t scan_total;   // scratch total of the last scan
+    uint32_t pad[5];
+};
+static_assert(sizeof(Ctl) == 64, "Ctl layout");
+
+// Workspace carve-up.  Every region starts on a 256-byte boundary.
+struct Layout {
+    int64_t n = 0, dup_cap = 0;
+    int W = 0, H = 0, Tx = 0, Ty = 0, Tn = 0;
+    size_t ctl = 0, rec = 0, tiles = 0, depth = 0, sort_k[2] = {0, 0}, sort_v[2] = {0, 0}, dup_off = 0,
+           tile_k[2] = {0, 0}, tile_v[2] = {0, 0}, ranges = 0, t_final = 0, n_contrib = 0, c_sum = 0,
+           partials = 0, hist = 0, rec_grad = 0, total = 0;
+};
+
+// Returns false when sizes overflow.
+bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L);
+// Largest duplicate capacity that fits in ws_bytes (0 if even the fixed part does not fit).
+int64_t capacity_for(int64_t n, int W, int H, size_t ws_bytes);
+
+template <typename T>
+inline T *at(void *base, size_t off) { return reinterpret_cast<T *>(static_cast<char *>(base) + off); }
+
+struct SceneView {
+    const float *means;
+    const void *log_scales;
+    const void *quats;
+    const float *opacity_logit;
+    const void *sh;
+    const uint8_t *layer;
+    int n;
+    int sh_degree;
+    int dtype_sh;
+    int dtype_sr;
+};
+
+struct CamView {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy, znear;
+    int W, H, Tx, Ty;
+};
+
+struct Planes {
+    float4 p[GS_MAX_PLANES];
+    uint32_t bits[GS_MAX_PLANES];
+    int n;
+};
+
+// ---- launches (each returns cudaGetLastError() of its launches) ----
+cudaError_t launch_preprocess(const SceneView &s, const CamView &c, uint32_t layer_mask, const Planes &pl,
+                              Rec *rec, uint32_t *tiles, uint32_t *depth_key, cudaStream_t st);
+cudaError_t launch_preprocess_backward(const SceneView &s, const CamView &c, const uint32_t *tiles,
+                                       const float4 *rec_grad, uint32_t grad_layer_mask, const gs_grads &g,
+                                       cudaStream_t st);
+
+int sort_blocks();   // blocks of the sort / scan kernels on this device
+
+// Visible compaction: for i < n with tiles[i] > 0, writes (depth_key[i], i) in index order
+// to (keys_out, vals_out) and the count to ctl->n_vis.
+cudaError_t launch_compact_visible(const uint32_t *tiles, const uint32_t *depth_key, int n, uint32_t *keys_out,
+                                   uint32_t *vals_out, uint32_t *partials, Ctl *ctl, cudaStream_t st);
+// One stable LSD pass on 8 bits at `shift` of min(*n_dev, n_cap) (key, value) pairs.
+cudaError_t launch_radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
+                              const uint32_t *n_dev, uint32_t n_cap, int shift, uint32_t *hist,
+                              cudaStream_t st);
+// dup_off[p] = exclusive prefix of tiles[order[p]] over p < ctl->n_vis; writes n_dup,
+// n_dup_c and the overflow status.
+cudaError_t launch_dup_offsets(const uint32_t *order, const uint32_t *tiles, uint32_t n_cap, uint32_t *dup_off,
+                               uint32_t *partials, Ctl *ctl, uint64_t dup_cap, cudaStream_t st);
+cudaError_t launch_emit(const uint32_t *order, const uint32_t *dup_off, const Rec *rec, uint32_t n_cap, int Tx,
+                        uint32_t *tile_k, uint32_t *tile_v, Ctl *ctl, uint64_t dup_cap, cudaStream_t st);
+cudaError_t launch_ranges(const uint32_t *tile_k, uint32_t n_cap, uint2 *ranges, const Ctl *ctl,
+                          cudaStream_t st);
+cudaError_t launch_prune(const float *contrib_max, int n, float thr, uint8_t *keep, int32_t *keep_index,
+                         int64_t *n_keep, uint32_t *partials, cudaStream_t st);
+
+cudaError_t launch_composite_forward(const uint2 *ranges, const uint32_t *list, const Rec *rec, int W, int H,
+                                     int Tx, int Ty, float3 bg, float *image, float *alpha, float *t_final,
+                                     uint32_t *n_contrib, float *c_sum, cudaStream_t st);
+cudaError_t launch_composite_backward(const uint2 *ranges, const uint32_t *list, const Rec *rec, int W, int H,
+                                      int Tx, int Ty, float3 bg, const float *t_final, const uint32_t *n_contrib,
+                                      const float *c_sum, const float *dL_dimage, const float *dL_dalpha,
+                                      const uint8_t *layer, uint32_t grad_layer_mask, float4 *rec_grad,
+                                      float *contrib_sum, float *contrib_max, cudaStream_t st);
+
+}  // namespace gs

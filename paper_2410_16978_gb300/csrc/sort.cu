@@ -1,0 +1,406 @@
+// S2 - tile binning with depth-keyed radix sorts (Sec. 3.3: the Gaussians are
+// sorted relative to the camera; the paper's renderer uses GPU radix sorts).
+//
+// Order of the tile lists: (tile, depth, Gaussian index).  It is produced by
+//   1. compacting the visible Gaussians in index order,
+//   2. a stable LSD radix sort of them by the float bits of their depth,
+//   3. an exclusive scan of their tile counts in that depth order,
+//   4. emitting one (tile id, Gaussian) pair per covered tile at the scanned
+//      offsets (so the pairs are in depth order), and
+//   5. a stable LSD radix sort of the pairs by tile id,
+// which equals a stable sort of the keys (tile << 32 | depth bits) emitted in
+// index order, with 32-bit keys and far fewer passes over the pair list.
+//
+// Every kernel runs on a fixed grid of sort_blocks() CTAs that each own a
+// contiguous range of the items, so item counts produced on the device never
+// need to travel to the host.
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+__device__ __forceinline__ void block_range(uint32_t n, uint32_t &beg, uint32_t &end) {
+    const uint64_t tiles = (static_cast<uint64_t>(n) + kSortTile - 1) / kSortTile;
+    const uint64_t per = (tiles + gridDim.x - 1) / gridDim.x;
+    const uint64_t b = static_cast<uint64_t>(blockIdx.x) * per * kSortTile;
+    const uint64_t e = b + per * kSortTile;
+    beg = static_cast<uint32_t>(b < n ? b : n);
+    end = static_cast<uint32_t>(e < n ? e : n);
+}
+
+// Exclusive scan over the 256 threads of a block; *total = sum of all v.
+__device__ __forceinline__ uint32_t block_scan_256(uint32_t v, uint32_t *s_w, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < 8 ? s_w[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < 8) s_w[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t base = warp > 0 ? s_w[warp - 1] : 0;
+    *total = s_w[7];
+    __syncthreads();
+    return base + x - v;
+}
+
+// ---------------------------------------------------------------------------
+// Generic three-kernel scan: reduce per block, scan the block sums, rescan.
+
+struct NSrc {               // item count: min(*dev, cap) if dev, else cap
+    const uint32_t *dev;
+    uint32_t cap;
+    __device__ __forceinline__ uint32_t get() const {
+        if (!dev) return cap;
+        const uint32_t d = *dev;
+        return d < cap ? d : cap;
+    }
+};
+
+template <class F>
+__global__ void __launch_bounds__(256) k_scan_reduce(F f, NSrc ns, uint32_t *__restrict__ partials) {
+    __shared__ uint32_t s_w[8];
+    uint32_t beg, end;
+    block_range(ns.get(), beg, end);
+    uint32_t acc = 0;
+    for (uint32_t i = beg + threadIdx.x; i < end; i += 256) acc += f(i);
+    uint32_t tot;
+    block_scan_256(acc, s_w, &tot);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+enum ScanFinal { FIN_NONE = 0, FIN_NVIS = 1, FIN_NDUP = 2, FIN_NKEEP = 3 };
+
+__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *__restrict__ partials, int G, int mode,
+                                                        Ctl *ctl, uint64_t cap, int64_t *n_keep) {
+    __shared__ uint32_t s_w[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t v = t < G ? partials[t] : 0;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = s_w[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        s_w[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t excl = (warp > 0 ? s_w[warp - 1] : 0) + x - v;
+    if (t < G) partials[t] = excl;
+    if (t == 0) {
+        const uint32_t total = s_w[31];
+        if (mode == FIN_NVIS) {
+            ctl->n_vis = total;
+            ctl->st.n_visible = total;
+        } else if (mode == FIN_NDUP) {
+            ctl->st.n_dup = total;
+            ctl->st.dup_capacity = cap;
+            ctl->n_dup_c = total < cap ? total : static_cast<uint32_t>(cap);
+            if (total > cap) ctl->st.error = GS_ERR_WORKSPACE;
+        } else if (mode == FIN_NKEEP) {
+            *n_keep = total;
+        }
+        ctl->scan_total = total;
+    }
+}
+
+template <class F, class Out>
+__global__ void __launch_bounds__(256) k_scan_down(F f, NSrc ns, const uint32_t *__restrict__ partials, Out out) {
+    __shared__ uint32_t s_w[8];
+    uint32_t beg, end;
+    block_range(ns.get(), beg, end);
+    uint32_t run = partials[blockIdx.x];
+    for (uint32_t t0 = beg; t0 < end; t0 += kSortTile) {
+        uint32_t v[kSortItems];
+        uint32_t sum = 0;
+        const uint32_t i0 = t0 + threadIdx.x * kSortItems;
+#pragma unroll
+        for (int k = 0; k < kSortItems; ++k) {
+            v[k] = (i0 + k < end) ? f(i0 + k) : 0;
+            sum += v[k];
+        }
+        uint32_t tot;
+        uint32_t off = run + block_scan_256(sum, s_w, &tot);
+#pragma unroll
+        for (int k = 0; k < kSortItems; ++k) {
+            if (i0 + k < end) out(i0 + k, off, v[k]);
+            off += v[k];
+        }
+        run += tot;
+    }
+}
+
+// --- functors ---
+struct VisFlag {
+    const uint32_t *tiles;
+    __device__ __forceinline__ uint32_t operator()(uint32_t i) const { return tiles[i] > 0 ? 1u : 0u; }
+};
+struct CompactOut {
+    const uint32_t *depth_key;
+    uint32_t *keys, *vals;
+    __device__ __forceinline__ void operator()(uint32_t i, uint32_t off, uint32_t v) const {
+        if (v) { keys[off] = depth_key[i]; vals[off] = i; }
+    }
+};
+struct OrderedTiles {
+    const uint32_t *order, *tiles;
+    __device__ __forceinline__ uint32_t operator()(uint32_t p) const { return tiles[order[p]]; }
+};
+struct OffsetOut {
+    uint32_t *dup_off;
+    __device__ __forceinline__ void operator()(uint32_t p, uint32_t off, uint32_t) const { dup_off[p] = off; }
+};
+struct KeepFlag {
+    const float *cmax;
+    float thr;
+    __device__ __forceinline__ uint32_t operator()(uint32_t i) const { return cmax[i] >= thr ? 1u : 0u; }
+};
+struct KeepOut {
+    uint8_t *keep;
+    int32_t *idx;
+    __device__ __forceinline__ void operator()(uint32_t i, uint32_t off, uint32_t v) const {
+        keep[i] = static_cast<uint8_t>(v);
+        if (v && idx) idx[off] = static_cast<int32_t>(i);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Radix sort pass: 8-bit digits, histogram per (digit, block) in digit-major order.
+
+__global__ void __launch_bounds__(256) k_radix_up(const uint32_t *__restrict__ keys, NSrc ns, int shift,
+                                                  uint32_t *__restrict__ hist) {
+    __shared__ uint32_t s_h[8][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < 8 * 256; k += 256) (&s_h[0][0])[k] = 0;
+    __syncthreads();
+    uint32_t beg, end;
+    block_range(ns.get(), beg, end);
+    for (uint32_t base = beg; base < end; base += 256) {
+        const uint32_t i = base + threadIdx.x;
+        const bool valid = i < end;
+        const uint32_t d = valid ? (keys[i] >> shift) & 255u : 256u + lane;
+        const unsigned peers = __match_any_sync(FULL, d);
+        if (valid && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&s_h[warp][d], __popc(peers));
+    }
+    __syncthreads();
+    const int d = threadIdx.x;
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += s_h[w][d];
+    hist[static_cast<size_t>(d) * gridDim.x + blockIdx.x] = s;
+}
+
+// Exclusive scan of the E = 256*G histogram entries in place (one CTA).
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *__restrict__ hist, int G) {
+    __shared__ uint32_t s_w[32];
+    const int E = 256 * G;
+    const int per = (E + 1023) / 1024;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int b = t * per;
+    uint32_t sum = 0;
+    for (int k = 0; k < per && b + k < E; ++k) sum += hist[b + k];
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = s_w[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        s_w[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = (warp > 0 ? s_w[warp - 1] : 0) + x - sum;
+    for (int k = 0; k < per && b + k < E; ++k) {
+        const uint32_t h = hist[b + k];
+        hist[b + k] = run;
+        run += h;
+    }
+}
+
+// Stable scatter: items are ranked in (round, warp, lane) = index order.
+__global__ void __launch_bounds__(256) k_radix_down(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                    uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, NSrc ns,
+                                                    int shift, const uint32_t *__restrict__ hist) {
+    __shared__ uint32_t s_off[256];
+    __shared__ uint32_t s_wc[8][256];
+    __shared__ uint32_t s_rt[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    s_off[threadIdx.x] = hist[static_cast<size_t>(threadIdx.x) * gridDim.x + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s_wc[w][threadIdx.x] = 0;
+    __syncthreads();
+    uint32_t beg, end;
+    block_range(ns.get(), beg, end);
+    const unsigned lt = (1u << lane) - 1u;
+    for (uint32_t base = beg; base < end; base += 256) {
+        const uint32_t i = base + threadIdx.x;
+        const bool valid = i < end;
+        uint32_t key = 0, val = 0, d = 256u + lane;
+        if (valid) { key = kin[i]; val = vin[i]; d = (key >> shift) & 255u; }
+        const unsigned peers = __match_any_sync(FULL, d);
+        const uint32_t rank = __popc(peers & lt);
+        if (valid && rank == 0) s_wc[warp][d] = __popc(peers);
+        __syncthreads();
+        {   // per digit: exclusive prefix over the 8 warps of this round
+            const int dd = threadIdx.x;
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                const uint32_t c = s_wc[w][dd];
+                s_wc[w][dd] = run;
+                run += c;
+            }
+            s_rt[dd] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = s_off[d] + s_wc[warp][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        {
+            const int dd = threadIdx.x;
+            s_off[dd] += s_rt[dd];
+#pragma unroll
+            for (int w = 0; w < 8; ++w) s_wc[w][dd] = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ order, const uint32_t *__restrict__ dup_off,
+                                              const Rec *__restrict__ rec, NSrc ns, int Tx,
+                                              uint32_t *__restrict__ tile_k, uint32_t *__restrict__ tile_v,
+                                              uint64_t cap) {
+    const uint32_t n = ns.get();
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const uint32_t g = order[p];
+        const float4 c = rec[g].c;
+        const uint32_t r0 = __float_as_uint(c.z), r1 = __float_as_uint(c.w);
+        const uint32_t x0 = r0 & 0xFFFFu, y0 = r0 >> 16, x1 = r1 & 0xFFFFu, y1 = r1 >> 16;
+        uint64_t k = dup_off[p];
+        for (uint32_t ty = y0; ty < y1; ++ty)
+            for (uint32_t tx = x0; tx < x1; ++tx, ++k) {
+                if (k >= cap) return;
+                tile_k[k] = ty * static_cast<uint32_t>(Tx) + tx;
+                tile_v[k] = g;
+            }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ tile_k, NSrc ns, uint2 *__restrict__ ranges) {
+    const uint32_t n = ns.get();
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t t = tile_k[i];
+        if (i == 0 || tile_k[i - 1] != t) ranges[t].x = i;
+        if (i == n - 1 || tile_k[i + 1] != t) ranges[t].y = i + 1;
+    }
+}
+
+}  // namespace
+
+int sort_blocks() {
+    static int cached = 0;
+    if (cached) return cached;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int g = 2 * (sms > 0 ? sms : 80);
+    if (g > kMaxSortBlocks) g = kMaxSortBlocks;
+    cached = g;
+    return g;
+}
+
+cudaError_t launch_compact_visible(const uint32_t *tiles, const uint32_t *depth_key, int n, uint32_t *keys_out,
+                                   uint32_t *vals_out, uint32_t *partials, Ctl *ctl, cudaStream_t st) {
+    const int G = sort_blocks();
+    NSrc ns{nullptr, static_cast<uint32_t>(n)};
+    VisFlag f{tiles};
+    k_scan_reduce<<<G, 256, 0, st>>>(f, ns, partials);
+    k_scan_partials<<<1, 1024, 0, st>>>(partials, G, FIN_NVIS, ctl, 0, nullptr);
+    k_scan_down<<<G, 256, 0, st>>>(f, ns, partials, CompactOut{depth_key, keys_out, vals_out});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
+                              const uint32_t *n_dev, uint32_t n_cap, int shift, uint32_t *hist, cudaStream_t st) {
+    const int G = sort_blocks();
+    NSrc ns{n_dev, n_cap};
+    k_radix_up<<<G, 256, 0, st>>>(kin, ns, shift, hist);
+    k_radix_scan<<<1, 1024, 0, st>>>(hist, G);
+    k_radix_down<<<G, 256, 0, st>>>(kin, vin, kout, vout, ns, shift, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dup_offsets(const uint32_t *order, const uint32_t *tiles, uint32_t n_cap, uint32_t *dup_off,
+                               uint32_t *partials, Ctl *ctl, uint64_t dup_cap, cudaStream_t st) {
+    const int G = sort_blocks();
+    NSrc ns{&ctl->n_vis, n_cap};
+    OrderedTiles f{order, tiles};
+    k_scan_reduce<<<G, 256, 0, st>>>(f, ns, partials);
+    k_scan_partials<<<1, 1024, 0, st>>>(partials, G, FIN_NDUP, ctl, dup_cap, nullptr);
+    k_scan_down<<<G, 256, 0, st>>>(f, ns, partials, OffsetOut{dup_off});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const uint32_t *order, const uint32_t *dup_off, const Rec *rec, uint32_t n_cap, int Tx,
+                        uint32_t *tile_k, uint32_t *tile_v, Ctl *ctl, uint64_t dup_cap, cudaStream_t st) {
+    const int G = sort_blocks();
+    NSrc ns{&ctl->n_vis, n_cap};
+    k_emit<<<G, 256, 0, st>>>(order, dup_off, rec, ns, Tx, tile_k, tile_v, dup_cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ranges(const uint32_t *tile_k, uint32_t n_cap, uint2 *ranges, const Ctl *ctl, cudaStream_t st) {
+    const int G = sort_blocks();
+    NSrc ns{&ctl->n_dup_c, n_cap};
+    k_ranges<<<G, 256, 0, st>>>(tile_k, ns, ranges);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prune(const float *contrib_max, int n, float thr, uint8_t *keep, int32_t *keep_index,
+                         int64_t *n_keep, uint32_t *partials, cudaStream_t st) {
+    const int G = sort_blocks();
+    NSrc ns{nullptr, static_cast<uint32_t>(n)};
+    KeepFlag f{contrib_max, thr};
+    Ctl *ctl = reinterpret_cast<Ctl *>(partials + kMaxSortBlocks);
+    k_scan_reduce<<<G, 256, 0, st>>>(f, ns, partials);
+    k_scan_partials<<<1, 1024, 0, st>>>(partials, G, FIN_NKEEP, ctl, 0, n_keep);
+    k_scan_down<<<G, 256, 0, st>>>(f, ns, partials, KeepOut{keep, keep_index});
+    return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,83 @@
+"""The C ABI library loads, exports every entry point include/gs.h declares,
+and rejects bad arguments on the host before touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2410_16978_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "gs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gs_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("gs_render", "gs_render_backward", "gs_contrib_prune"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib.load()
+    for name in _declared():
+        assert hasattr(L, name), name
+        assert name in _lib.EXPORTED, name
+
+
+def test_version_and_empty_error():
+    assert "sm_103a" in _lib.gs_version()
+
+
+def test_workspace_size_and_layout():
+    b = _lib.gs_render_workspace_size(1000, 100, 70, 5000)
+    lay = _lib.gs_workspace_layout(1000, 100, 70, b)
+    assert lay["total"] <= b and lay["dup_capacity"] >= 5000 - 64
+    offs = [lay[k] for k in _lib.LAYOUT_NAMES[:11]]
+    assert all(o % 256 == 0 for o in offs)
+    assert len(set(offs)) == len(offs)
+    with pytest.raises(_lib.GsError) as e:
+        _lib.gs_render_workspace_size(-1, 100, 70, 10)
+    assert e.value.code == _lib.GS_ERR_INVALID
+    with pytest.raises(_lib.GsError) as e:
+        _lib.gs_render_workspace_size(10, 0, 70, 10)
+    assert e.value.code == _lib.GS_ERR_INVALID
+    with pytest.raises(_lib.GsError) as e:
+        _lib.gs_workspace_layout(1000, 100, 70, 1024)
+    assert e.value.code == _lib.GS_ERR_WORKSPACE
+
+
+def test_render_rejects_bad_arguments_on_host():
+    L = _lib.load()
+    cam = _lib.gs_camera()
+    cam.width, cam.height, cam.fx, cam.fy = 64, 64, 50.0, 50.0
+    sc = _lib.gs_scene()
+    sc.n = 10
+    bg = (ctypes.c_float * 3)(0, 0, 0)
+    rc = L.gs_render(None, ctypes.byref(cam), 1, None, 0, bg, None, 0, None, None, None)
+    assert rc == _lib.GS_ERR_INVALID and "scene" in _lib.gs_last_error_string()
+    rc = L.gs_render(ctypes.byref(sc), ctypes.byref(cam), 1, None, 0, bg, None, 0, None, None, None)
+    assert rc == _lib.GS_ERR_INVALID                     # NULL scene arrays
+    sc.n, sc.sh_degree = 0, 4
+    rc = L.gs_render(ctypes.byref(sc), ctypes.byref(cam), 1, None, 0, bg, None, 0, None, None, None)
+    assert rc == _lib.GS_ERR_INVALID and "sh_degree" in _lib.gs_last_error_string()
+    sc.sh_degree = 0
+    rc = L.gs_render(ctypes.byref(sc), ctypes.byref(cam), 1, None, 9, bg, None, 0, None, None, None)
+    assert rc == _lib.GS_ERR_INVALID and "n_planes" in _lib.gs_last_error_string()
+    cam.fx = 0.0
+    rc = L.gs_render(ctypes.byref(sc), ctypes.byref(cam), 1, None, 0, bg, None, 0, None, None, None)
+    assert rc == _lib.GS_ERR_INVALID
+
+
+def test_prune_rejects_bad_arguments_on_host():
+    L = _lib.load()
+    assert L.gs_contrib_prune(None, 10, 0.005, None, None, None, None, 0, None) == _lib.GS_ERR_INVALID
+    assert L.gs_contrib_prune(None, -1, 0.005, None, None, None, None, 0, None) == _lib.GS_ERR_INVALID
+    n_keep = ctypes.c_int64()
+    rc = L.gs_contrib_prune(None, 0, 0.005, None, None, ctypes.byref(n_keep), None, 0, None)
+    assert rc == _lib.GS_ERR_WORKSPACE

@@ -1,0 +1,107 @@
+"""GPU parity of the backward (S4: compositing backward + chain rule, with the
+per-Gaussian contribution) and of the prune (S5), through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2410_16978_gb300 import contrib_prune, render
+from tests.gpu_util import f64_scene, gpu_render, oracle_stage
+from tests.test_gpu_render import WL
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("means", "log_scales", "quats", "opacity_logit", "sh")
+# Gradient bar: |gpu - oracle| <= GRAD_TOL * max|oracle| over each field (FP32
+# accumulation over the pixels of a splat against an FP64 reference).
+GRAD_TOL = 1e-4
+
+
+def _upstream(H, W, seed=9):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((3, H, W)).astype(np.float32), rng.standard_normal((H, W)).astype(np.float32))
+
+
+def _gpu_backward(name, glm=0xFFFFFFFF):
+    sc, cam, mask, planes, bg = WL[name]
+    ds, rast, img, al = gpu_render(sc, cam, mask, planes, bg)
+    dimg, dal = _upstream(cam.height, cam.width)
+    csum = torch.zeros(sc.n, device="cuda")
+    cmax = torch.zeros(sc.n, device="cuda")
+    g = rast.backward(ds, cam, bg, torch.from_numpy(dimg).cuda(), torch.from_numpy(dal).cuda(), glm, csum, cmax)
+    torch.cuda.synchronize()
+    return sc, cam, mask, planes, bg, dimg, dal, {k: v.cpu().numpy() for k, v in g.items()}, csum.cpu().numpy(), \
+        cmax.cpu().numpy()
+
+
+@pytest.mark.parametrize("name", list(WL))
+def test_backward_parity(name):
+    sc, cam, mask, planes, bg, dimg, dal, g, csum, cmax = _gpu_backward(name)
+    pre, ranges, lst, co = oracle_stage(sc, cam, mask, planes, bg)
+    cb = oracle.composite_backward(pre, ranges, lst, bg, dimg, dal)
+    ref = oracle.chain(f64_scene(sc), cam, pre["vis"], cb["rec_grad"])
+    ok = (cb["touched_fragile"] == 0)
+    stats = {}
+    for f in FIELDS:
+        a = g[f].reshape(sc.n, -1)[ok].astype(np.float64)
+        b = ref[f].reshape(sc.n, -1)[ok]
+        scale = np.abs(b).max()
+        err = np.abs(a - b).max() / scale
+        stats[f] = err
+        assert err <= GRAD_TOL, (f, err)
+    print(name, "field-normalised max gradient error", stats, "excluded", int((~ok).sum()))
+    vis = pre["vis"] > 0
+    assert np.all(g["means"][~vis] == 0) and np.all(g["sh"][~vis] == 0)
+    m = ok & (cb["contrib_sum"] > 0)
+    assert np.abs(csum[m] - cb["contrib_sum"][m]).max() <= 1e-4 * cb["contrib_sum"][m].max()
+    assert np.abs(cmax[ok] - cb["contrib_max"][ok]).max() <= 1e-5
+    assert np.all(csum[~vis] == 0) and np.all(cmax[~vis] == 0)
+
+
+def test_frozen_layers_get_zero_gradient():
+    glm = 0b00101
+    sc, cam, mask, planes, bg, dimg, dal, g, _, _ = _gpu_backward("shells_ragged", glm)
+    _, _, _, _, _, _, _, gfull, _, _ = _gpu_backward("shells_ragged")
+    frozen = ((glm >> sc.layer.astype(np.int64)) & 1) == 0
+    for f in FIELDS:
+        assert np.all(g[f][frozen] == 0)
+        np.testing.assert_array_equal(g[f][~frozen], gfull[f][~frozen])
+
+
+def test_autograd_function_matches_direct_backward():
+    sc, cam, mask, planes, bg = WL["c1"]
+    from paper_2410_16978_gb300 import DeviceScene, Rasterizer
+    ds = DeviceScene.from_host(sc, requires_grad=True)
+    rast = Rasterizer(sc.n, cam.width, cam.height)
+    dimg, dal = _upstream(cam.height, cam.width, seed=3)
+    img, al = render(ds, rast, cam, mask, planes, bg)
+    loss = (img * torch.from_numpy(dimg).cuda()).sum() + (al * torch.from_numpy(dal).cuda()).sum()
+    loss.backward()
+    _, rast2, _, _ = gpu_render(sc, cam, mask, planes, bg)
+    ds2 = DeviceScene.from_host(sc)
+    g = rast2.backward(ds2, cam, bg, torch.from_numpy(dimg).cuda(), torch.from_numpy(dal).cuda())
+    for f, p in zip(FIELDS, ds.params()):
+        assert torch.equal(p.grad, g[f]), f
+
+
+def test_prune_matches_oracle():
+    rng = np.random.default_rng(4)
+    n = 100_003
+    cm = rng.uniform(0, 0.01, n).astype(np.float32)
+    cm[:10] = np.float32(0.005)
+    cm[10:20] = np.nextafter(np.float32(0.005), np.float32(0))
+    keep, idx, nk = contrib_prune(torch.from_numpy(cm).cuda(), 0.005)
+    k_or, n_or = oracle.prune(cm.astype(np.float64), float(np.float32(0.005)))
+    assert int(nk.item()) == n_or
+    assert np.array_equal(keep.cpu().numpy(), k_or)
+    assert np.array_equal(idx.cpu().numpy()[:n_or], np.nonzero(k_or)[0])
+
+
+def test_prune_edge_sizes():
+    for n in (0, 1, 2047, 2048, 2049):
+        cm = np.linspace(0, 0.01, max(n, 1)).astype(np.float32)[:n]
+        t = torch.from_numpy(cm).cuda() if n else torch.zeros(0, device="cuda")
+        keep, idx, nk = contrib_prune(t, 0.005)
+        k_or, n_or = oracle.prune(cm.astype(np.float64), float(np.float32(0.005)))
+        assert int(nk.item()) == n_or
+        assert np.array_equal(keep.cpu().numpy(), k_or)

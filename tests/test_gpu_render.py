@@ -1,0 +1,151 @@
+"""GPU parity of the forward path (S1 preprocess, S2 binning + sorts, S3
+compositing) against the FP64 oracle, called through the C ABI.
+
+Bars: bit-exact records' integer decisions, tile ids and order; colours within
+1e-5 absolute of the oracle composited from the same single-precision
+projection (fragile threshold decisions may take either side); PSNR >= 50 dB
+against the end-to-end FP64 render."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.gpu_util import (compare_image, compare_lists, compare_records, dequantised, gpu_render, oracle_stage,
+                            psnr, read_ws)
+from tests.helpers import axis_camera, make_scene, random_small_scene
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _workloads():
+    w1 = synth.scene_c1()
+    rng = np.random.default_rng(77)
+    sc2 = synth.shell_scene(rng, [6000, 4500, 3750, 1500, 2250], synth.scenes.C2_RADII)
+    cam2 = synth.look_at_camera((0.3, -0.2, 3.2), fov_x_deg=50.0, width=200, height=152)
+    planes2 = synth.random_clip_planes(rng, 1)
+    return {
+        "c1": (w1["scene"], w1["cameras"][0], w1["layer_mask"], w1["planes"], (0.0, 0.0, 0.0)),
+        "shells_ragged": (sc2, cam2, 0b10111, planes2, (0.2, 0.3, 0.4)),
+    }
+
+
+WL = _workloads()
+
+
+@pytest.mark.parametrize("name", list(WL))
+def test_forward_parity(name):
+    sc, cam, mask, planes, bg = WL[name]
+    ds, rast, img, al = gpu_render(sc, cam, mask, planes, bg)
+    ws = read_ws(rast)
+    assert ws["status"].error == 0
+    pre, ranges, lst, co = oracle_stage(sc, cam, mask, planes, bg)
+    compare_records(ws, pre)
+    compare_lists(ws, ranges, lst)
+    st = compare_image(img.cpu().numpy(), al.cpu().numpy(), ws["n_contrib"].astype(np.int64), co, TOL)
+    print(name, st)
+    assert st["n_bad"] == 0, st
+    assert st["n_multi"] <= 0.001 * sc.n
+    full = oracle.render(sc, cam, mask, planes, bg, "f64")
+    assert psnr(img.cpu().numpy(), full["image"]) >= 50.0
+
+
+@pytest.mark.parametrize("kind", [("f16", "f32"), ("bf16", "bf16"), ("f16", "f16")])
+def test_half_storage_records_and_image(kind):
+    sh_dt, sr_dt = kind
+    sc, cam, mask, planes, bg = WL["shells_ragged"]
+    ds, rast, img, al = gpu_render(sc, cam, mask, planes, bg, sh_dtype=sh_dt, sr_dtype=sr_dt)
+    ws = read_ws(rast)
+    sq = dequantised(sc, sh_dt, sr_dt)
+    pre, ranges, lst, co = oracle_stage(sq, cam, mask, planes, bg)
+    compare_records(ws, pre)
+    compare_lists(ws, ranges, lst)
+    st = compare_image(img.cpu().numpy(), al.cpu().numpy(), ws["n_contrib"].astype(np.int64), co, TOL)
+    assert st["n_bad"] == 0, st
+    # precision cost of 16-bit storage against the FP64 render of the FP32 master scene
+    ref = oracle.render(sc, cam, mask, planes, bg, "f64")
+    print(kind, "PSNR vs FP32 master", psnr(img.cpu().numpy(), ref["image"]))
+
+
+def test_mask_zero_is_background():
+    sc, cam, _, _, _ = WL["c1"]
+    bg = (0.25, 0.5, 0.75)
+    _, rast, img, al = gpu_render(sc, cam, 0, (), bg)
+    want = torch.tensor(bg, device=img.device).view(3, 1, 1).expand_as(img)
+    assert torch.equal(img, want)
+    assert torch.all(al == 0)
+    assert read_ws(rast)["D"] == 0
+
+
+def test_empty_scene():
+    sc = make_scene(np.zeros((0, 3)), np.zeros((0, 3)))
+    cam = axis_camera(4.0, 40, 24)
+    _, rast, img, al = gpu_render(sc, cam, bg=(0.1, 0.2, 0.3))
+    assert torch.allclose(img[0], torch.full_like(img[0], 0.1))
+    assert torch.all(al == 0)
+
+
+def test_single_splat_closed_form():
+    z0, s, o = 4.0, 0.02, 0.6
+    cam = axis_camera(z0, 33, 33)
+    sc = make_scene([[0, 0, 0]], math.log(s), rgb=[0.9, 0.5, 0.25], opacity_logit=math.log(o / (1 - o)))
+    _, rast, img, al = gpu_render(sc, cam, bg=(0.1, 0.2, 0.3))
+    o = 1 / (1 + math.exp(-float(sc.opacity_logit[0])))
+    rgb = sc.sh[0, 0].astype(np.float64) * (0.5 / math.sqrt(math.pi)) + 0.5
+    want = o * rgb + (1 - o) * np.array([0.1, 0.2, 0.3])
+    assert np.abs(img[:, 16, 16].cpu().numpy() - want).max() < 1e-6
+
+
+@pytest.mark.parametrize("mask", [0b00001, 0b00110, 0b11010])
+def test_masking_equals_deleting_on_gpu(mask):
+    sc, cam, _, _, bg = WL["shells_ragged"]
+    _, _, a, aa = gpu_render(sc, cam, mask, (), bg)
+    keep = ((mask >> sc.layer.astype(np.int64)) & 1).astype(bool)
+    _, _, b, bb = gpu_render(sc.subset(keep), cam, 0xFFFFFFFF, (), bg)
+    assert torch.equal(a, b) and torch.equal(aa, bb)
+
+
+def test_clipping_equals_deleting_on_gpu():
+    sc, cam, _, _, bg = WL["shells_ragged"]
+    rng = np.random.default_rng(5)
+    planes = synth.random_clip_planes(rng, 2, 0.3, layer_bits=0b00111)
+    _, rast, a, aa = gpu_render(sc, cam, 0xFFFFFFFF, planes, bg)
+    pre = oracle.preprocess(sc, cam, 0xFFFFFFFF, planes, "f32")
+    pre_all = oracle.preprocess(sc, cam, 0xFFFFFFFF, (), "f32")
+    keep = ~((pre_all["vis"] > 0) & (pre["vis"] == 0))
+    _, _, b, bb = gpu_render(sc.subset(keep), cam, 0xFFFFFFFF, (), bg)
+    assert torch.equal(a, b) and torch.equal(aa, bb)
+
+
+def test_overflow_reports_and_recovers():
+    sc, cam, mask, planes, bg = WL["shells_ragged"]
+    _, rast, img_small, _ = gpu_render(sc, cam, mask, planes, bg, cap=1000, check=False)
+    st = rast.status()
+    assert st.error == 2 and st.n_dup > 1000 and st.dup_capacity >= 1000
+    _, rast2, img_ok, _ = gpu_render(sc, cam, mask, planes, bg, cap=1000, check=True)
+    assert rast2.status().error == 0 and rast2.dup_capacity > 1000
+    _, _, img_ref, _ = gpu_render(sc, cam, mask, planes, bg)
+    assert torch.equal(img_ok, img_ref)
+
+
+def test_stereo_eyes_equal_mono_renders():
+    w = synth.scene_c4(scale=0.002, width=96, height=104)
+    sc = w["scene"]
+    for cam in w["cameras"]:
+        _, rast, img, al = gpu_render(sc, cam, w["layer_mask"], w["planes"], (0, 0, 0))
+        pre, ranges, lst, co = oracle_stage(sc, cam, w["layer_mask"], w["planes"], (0, 0, 0))
+        nc = read_ws(rast)["n_contrib"].astype(np.int64)
+        st = compare_image(img.cpu().numpy(), al.cpu().numpy(), nc, co, TOL)
+        assert st["n_bad"] == 0, st
+
+
+def test_repeated_renders_are_deterministic():
+    sc, cam, mask, planes, bg = WL["shells_ragged"]
+    ds, rast, a, _ = gpu_render(sc, cam, mask, planes, bg)
+    b, _ = rast.render(ds, cam, mask, planes, bg)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
