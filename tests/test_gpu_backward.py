@@ -12,9 +12,10 @@ from tests.test_gpu_render import WL
 pytestmark = pytest.mark.gpu
 
 FIELDS = ("means", "log_scales", "quats", "opacity_logit", "sh")
-# Gradient bar: |gpu - oracle| <= GRAD_TOL * max|oracle| over each field (FP32
-# accumulation over the pixels of a splat against an FP64 reference).
-GRAD_TOL = 1e-4
+# Gradient bar: |gpu - oracle| <= GRAD_TOL * max|oracle| over each field, i.e. the
+# 1e-5 absolute bar applied to each gradient field normalised by its largest
+# magnitude (FP32 accumulation over the pixels of a splat against FP64).
+GRAD_TOL = 1e-5
 
 
 def _upstream(H, W, seed=9):
@@ -65,7 +66,9 @@ def test_frozen_layers_get_zero_gradient():
     frozen = ((glm >> sc.layer.astype(np.int64)) & 1) == 0
     for f in FIELDS:
         assert np.all(g[f][frozen] == 0)
-        np.testing.assert_array_equal(g[f][~frozen], gfull[f][~frozen])
+        # float atomics across tiles sum in a run-dependent order: equal up to rounding
+        scale = np.abs(gfull[f]).max()
+        assert np.abs(g[f][~frozen] - gfull[f][~frozen]).max() <= 1e-6 * scale, f
 
 
 def test_autograd_function_matches_direct_backward():
@@ -81,7 +84,8 @@ def test_autograd_function_matches_direct_backward():
     ds2 = DeviceScene.from_host(sc)
     g = rast2.backward(ds2, cam, bg, torch.from_numpy(dimg).cuda(), torch.from_numpy(dal).cuda())
     for f, p in zip(FIELDS, ds.params()):
-        assert torch.equal(p.grad, g[f]), f
+        # float atomics across tiles sum in a run-dependent order: equal up to rounding
+        assert (p.grad - g[f]).abs().max().item() <= 1e-6 * g[f].abs().max().item(), f
 
 
 def test_prune_matches_oracle():
