@@ -176,6 +176,24 @@ int gs_contrib_prune(const float *contrib_max, int64_t n, float threshold, uint8
 #define GS_LAYOUT_COUNT 13
 int gs_workspace_layout(int64_t n, int32_t width, int32_t height, size_t ws_bytes, int64_t *out);
 
+/* gs_contrib_prune without a workspace, for callers that cannot allocate
+ * device memory: code running inside a host application's frame callback or
+ * plugin (a game engine or VR compositor render thread) where a device
+ * allocation would stall every stream or is forbidden outright, and code that
+ * must not touch the allocator at all between set-up and shutdown.  The paper
+ * has no counterpart; this is an interface convenience of this library.
+ * Same arguments and results as gs_contrib_prune minus the workspace.  The
+ * scan scratch (8 KiB: 1024 32-bit partial counts + a 64-byte control block)
+ * is a static device array in the library, held by every GPU that loads the
+ * library until the process exits; no cudaMalloc/cudaFree or allocating
+ * library routine is called.  n must be in 0 .. 2^31-1 (GS_ERR_INVALID
+ * otherwise).  The first call on each device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture.  Every call shares the one array, so calls that overlap on the
+ * GPU (different streams, or host threads without ordering) race.            */
+int gs_contrib_prune_noalloc(const float *contrib_max, int64_t n, float threshold, uint8_t *keep,
+                             int32_t *keep_index, int64_t *n_keep, void *stream);
+
 /* Copies the status word of a render workspace to host memory and
  * synchronises the stream.                                                   */
 int gs_read_status(const void *workspace, gs_status *out, void *stream);

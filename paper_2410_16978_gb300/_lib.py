@@ -21,7 +21,7 @@ GS_TILE = 16
 GS_MAX_PLANES = 8
 
 EXPORTED = ("gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_prune_workspace_size",
-            "gs_contrib_prune", "gs_workspace_layout", "gs_read_status", "gs_profile_enable", "gs_profile_collect",
+            "gs_contrib_prune", "gs_contrib_prune_noalloc", "gs_workspace_layout", "gs_read_status", "gs_profile_enable", "gs_profile_collect",
             "gs_kernel_launches", "gs_last_error_string", "gs_version")
 STAGES = ("preprocess", "compact", "depth_sort", "dup_scan", "emit", "tile_sort", "ranges", "composite",
           "composite_bwd", "preprocess_bwd", "prune")
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
         L.gs_prune_workspace_size.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]
         L.gs_contrib_prune.argtypes = [_P, ctypes.c_int64, ctypes.c_float, _P, _P, _P, _P, ctypes.c_size_t, _P]
         L.gs_read_status.argtypes = [_P, ctypes.POINTER(gs_status), _P]
+        L.gs_contrib_prune_noalloc.argtypes = [_P, ctypes.c_int64, ctypes.c_float, _P, _P, _P, _P]
         L.gs_workspace_layout.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t,
                                           ctypes.POINTER(ctypes.c_int64)]
         L.gs_profile_enable.argtypes = [ctypes.c_int]
@@ -186,6 +187,11 @@ def gs_contrib_prune(contrib_max, n: int, threshold: float, keep, keep_index, n_
                      stream: int) -> None:
     _check(load().gs_contrib_prune(_ptr(contrib_max), int(n), float(threshold), _ptr(keep), _ptr(keep_index),
                                    _ptr(n_keep), _ptr(workspace), int(ws_bytes), ctypes.c_void_p(stream)))
+
+
+def gs_contrib_prune_noalloc(contrib_max, n: int, threshold: float, keep, keep_index, n_keep, stream: int) -> None:
+    _check(load().gs_contrib_prune_noalloc(_ptr(contrib_max), int(n), float(threshold), _ptr(keep), _ptr(keep_index),
+                                           _ptr(n_keep), ctypes.c_void_p(stream)))
 
 
 def gs_workspace_layout(n: int, width: int, height: int, ws_bytes: int) -> dict:

@@ -175,6 +175,11 @@ int workspace_layout(const gs_scene *s, const CamView &cv, void *ws, size_t ws_b
 
 }  // namespace
 
+namespace gs {
+// Records a message for gs_last_error_string() from other translation units.
+int report(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace gs
+
 extern "C" {
 
 const char *gs_last_error_string(void) { return g_err.c_str(); }

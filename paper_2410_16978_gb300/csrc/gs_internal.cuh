@@ -92,6 +92,7 @@ cudaError_t launch_preprocess_backward(const SceneView &s, const CamView &c, con
                                        cudaStream_t st);
 
 int sort_blocks();   // blocks of the sort / scan kernels on this device
+int report(int code, const char *msg);   // sets gs_last_error_string(), returns code
 
 // Visible compaction: for i < n with tiles[i] > 0, writes (depth_key[i], i) in index order
 // to (keys_out, vals_out) and the count to ctl->n_vis.
