@@ -3,11 +3,13 @@
 // and its exact backward with the per-Gaussian blend weight alpha*T that
 // drives contribution pruning (Sec. 3.2.2).
 //
-// One CTA per tile, one thread per pixel; each warp owns an 8x4 pixel block.
-// Splat records are gathered 256 at a time into shared memory; the CTA stops
-// when every pixel has reached T < 1e-4 (vote with __syncthreads_count).
-// Compositing is FP32 FMA + MUFU work, not a dense contraction, so no tensor
-// cores are involved.
+// Work layout: one CTA per tile.  Every warp walks the tile's list on its own
+// (no CTA-wide barriers, so a warp whose pixels are done leaves at once): the
+// forward warp owns an 8x4 pixel block (one pixel per lane), the backward warp
+// an 8x8 block (two pixels per lane, which halves the cost of reducing each
+// splat's gradient over the warp).  Tiles are launched heaviest first
+// (k_tile_order) so that the long lists do not end up in the last wave.  Compositing is FP32 FMA + MUFU work, not a
+// dense contraction, so no tensor cores are involved.
 //
 // splat_alpha() is the single definition of the per-(pixel, splat) alpha used
 // by both passes; every operation is an explicitly rounded intrinsic, so the
@@ -20,6 +22,7 @@ namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr float kLn2 = 0x1.62e430p-1f;
+constexpr int kThreads = 128;
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -40,41 +43,102 @@ __device__ __forceinline__ float splat_alpha(float px, float py, const float4 a,
     return fminf(kAlphaMax, ao);
 }
 
-__device__ __forceinline__ void pixel_of(int tile, int Tx, int &x, int &y) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Pixel of lane `lane` of warp `warp`, j-th of its two pixels.
+__device__ __forceinline__ void pixel_of(int tile, int Tx, int warp, int lane, int j, int &x, int &y) {
     x = (tile % Tx) * kTile + (warp & 1) * 8 + (lane & 7);
-    y = (tile / Tx) * kTile + (warp >> 1) * 4 + (lane >> 3);
+    y = (tile / Tx) * kTile + (warp >> 1) * 8 + (lane >> 3) + 4 * j;
 }
 
-__global__ void __launch_bounds__(256) k_composite_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ list,
-                                                       const Rec *__restrict__ rec, int W, int H, int Tx, float3 bg,
-                                                       float *__restrict__ image, float *__restrict__ alpha_out,
-                                                       float *__restrict__ t_final, uint32_t *__restrict__ n_contrib,
-                                                       float *__restrict__ c_sum) {
-    __shared__ float4 s_a[256], s_b[256];
-    __shared__ float s_c[256];
-    const int tile = blockIdx.x;
-    int x, y;
-    pixel_of(tile, Tx, x, y);
+// Heaviest-first launch order of the tiles: a one-CTA counting sort of the
+// tiles by a logarithmic bucket of their work (list length, or the longest
+// blended prefix for the backward).  Ties keep no particular order; tiles are
+// independent, so the order changes no result.
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ ranges,
+                                                     const uint32_t *__restrict__ work, int Tn,
+                                                     uint32_t *__restrict__ order) {
+    constexpr int kBuckets = 513;
+    __shared__ uint32_t s_cnt[kBuckets];
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) s_cnt[b] = 0;
+    __syncthreads();
+    auto bucket = [&](int t) -> int {
+        const uint32_t w = work ? work[t] : ranges[t].y - ranges[t].x;
+        if (w == 0) return kBuckets - 1;                      // empty tiles last
+        const int lz = 31 - __clz(w);
+        const uint32_t sub = lz >= 4 ? (w >> (lz - 4)) & 15u : (w << (4 - lz)) & 15u;
+        return (kBuckets - 2) - (lz * 16 + static_cast<int>(sub));   // heavier -> smaller bucket
+    };
+    for (int t = threadIdx.x; t < Tn; t += blockDim.x) atomicAdd(&s_cnt[bucket(t)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < kBuckets; ++b) {
+            const uint32_t c = s_cnt[b];
+            s_cnt[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < Tn; t += blockDim.x) order[atomicAdd(&s_cnt[bucket(t)], 1u)] = t;
+}
+
+// Each warp walks the tile's list on its own (no CTA barriers): it stages 32
+// records at a time in a warp-private shared buffer while the next 32 are
+// already in flight in registers, and stops once all 64 of its pixels are done.
+struct Chunk {
+    float4 a, b;
+    float c;
+    uint32_t g;
+};
+
+__device__ __forceinline__ void fetch_chunk(const uint32_t *__restrict__ list, const Rec *__restrict__ rec,
+                                            uint32_t pos, uint32_t end, Chunk &ch) {
+    if (pos < end) {
+        ch.g = list[pos];
+        const Rec *r = rec + ch.g;
+        ch.a = r->a;
+        ch.b = r->b;
+        ch.c = r->c.x;
+    }
+}
+
+constexpr int kFwdThreads = 256;
+
+// Forward: 256 threads per tile, one pixel per lane; warp w owns the 8x4 block
+// ((w & 1) * 8, (w >> 1) * 4) and walks the list until its 32 pixels are done.
+__global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const uint32_t *__restrict__ order,
+                                                               const uint2 *__restrict__ ranges,
+                                                               const uint32_t *__restrict__ list,
+                                                               const Rec *__restrict__ rec, int W, int H, int Tx,
+                                                               float3 bg, float *__restrict__ image,
+                                                               float *__restrict__ alpha_out, float *__restrict__ t_final,
+                                                               uint32_t *__restrict__ n_contrib, float *__restrict__ c_sum,
+                                                               uint32_t *__restrict__ tile_work) {
+    __shared__ float4 s_a[kFwdThreads / 32][32], s_b[kFwdThreads / 32][32];
+    __shared__ float s_c[kFwdThreads / 32][32];
+    __shared__ uint32_t s_wmax[kFwdThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tile = order[blockIdx.x];
+    const uint2 rg = ranges[tile];
+    const int x = (tile % Tx) * kTile + (warp & 1) * 8 + (lane & 7);
+    const int y = (tile / Tx) * kTile + (warp >> 1) * 4 + (lane >> 3);
     const bool inside = x < W && y < H;
     const float px = x + 0.5f, py = y + 0.5f;
-    const uint2 rg = ranges[tile];
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t last = 0;
     bool done = !inside;
-    for (uint32_t base = rg.x; base < rg.y; base += 256) {
-        if (__syncthreads_count(done) == 256) break;
-        const uint32_t j = base + threadIdx.x;
-        if (j < rg.y) {
-            const Rec *r = rec + list[j];
-            s_a[threadIdx.x] = r->a;
-            s_b[threadIdx.x] = r->b;
-            s_c[threadIdx.x] = r->c.x;
-        }
-        __syncthreads();
-        const int cnt = min(256u, rg.y - base);
+    Chunk nxt;
+    fetch_chunk(list, rec, rg.x + lane, rg.y, nxt);
+    for (uint32_t base = rg.x; base < rg.y; base += 32) {
+        if (__all_sync(FULL, done)) break;
+        __syncwarp();
+        s_a[warp][lane] = nxt.a;
+        s_b[warp][lane] = nxt.b;
+        s_c[warp][lane] = nxt.c;
+        __syncwarp();
+        fetch_chunk(list, rec, base + 32 + lane, rg.y, nxt);
+        const int cnt = min(32u, rg.y - base);
         for (int k = 0; k < cnt && !done; ++k) {
-            const float4 a = s_a[k], b = s_b[k];
+            const float4 a = s_a[warp][k], b = s_b[warp][k];
             float p, dy, ex, ao;
             const float al = splat_alpha(px, py, a, b, p, dy, ex, ao);
             if (al < kAlphaMin) continue;
@@ -83,14 +147,14 @@ __global__ void __launch_bounds__(256) k_composite_fwd(const uint2 *__restrict__
             const float w = __fmul_rn(al, T);
             C0 = __fmaf_rn(b.z, w, C0);
             C1 = __fmaf_rn(b.w, w, C1);
-            C2 = __fmaf_rn(s_c[k], w, C2);
+            C2 = __fmaf_rn(s_c[warp][k], w, C2);
             T = Tn;
             last = base + k - rg.x + 1;
         }
     }
     if (inside) {
-        const size_t pix = static_cast<size_t>(y) * W + x;
         const size_t plane = static_cast<size_t>(W) * H;
+        const size_t pix = static_cast<size_t>(y) * W + x;
         image[pix] = __fmaf_rn(T, bg.x, C0);
         image[plane + pix] = __fmaf_rn(T, bg.y, C1);
         image[2 * plane + pix] = __fmaf_rn(T, bg.z, C2);
@@ -101,155 +165,183 @@ __global__ void __launch_bounds__(256) k_composite_fwd(const uint2 *__restrict__
         c_sum[plane + pix] = C1;
         c_sum[2 * plane + pix] = C2;
     }
+    const uint32_t wm = __reduce_max_sync(FULL, last);
+    if (lane == 0) s_wmax[warp] = wm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t m = 0;
+#pragma unroll
+        for (int w = 0; w < kFwdThreads / 32; ++w) m = max(m, s_wmax[w]);
+        tile_work[tile] = m;
+    }
+}
+
+// Reduce-scatter of 16 values across a warp: at step o (16, 8, 4, 2) each
+// lane keeps the half of its values selected by bit o of its lane id and adds
+// its partner's copy of that half; a last exchange at 1 completes the sums.
+// Afterwards lanes 2i and 2i+1 hold the warp sum of value i.
+__device__ __forceinline__ float reduce_scatter16(float v[16], int lane) {
+#pragma unroll
+    for (int h = 8; h >= 1; h >>= 1) {
+        const int o = 2 * h;                    // xor distance 16, 8, 4, 2
+        const bool hi = lane & o;
+#pragma unroll
+        for (int q = 0; q < h; ++q) {
+            const float send = hi ? v[q] : v[q + h];
+            const float recv = __shfl_xor_sync(FULL, send, o);
+            v[q] = (hi ? v[q + h] : v[q]) + recv;
+        }
+    }
+    return v[0] + __shfl_xor_sync(FULL, v[0], 1);
 }
 
 // Backward, front to back.  With S_i = sum_{j>i} c_j a_j T_j + T_N bg:
 //   dL/da_i = dC.(c_i T_i - S_i/(1-a_i)) + dA T_N/(1-a_i)
 //           = T_i (dC.c_i) - (dC.(Csum - P_i) + T_N (dC.bg) - dA T_N)/(1-a_i)
-// where P_i is the running colour sum including splat i.  dC.P_i is carried
-// as the scalar Q.
-__global__ void __launch_bounds__(256) k_composite_bwd(
-    const uint2 *__restrict__ ranges, const uint32_t *__restrict__ list, const Rec *__restrict__ rec, int W, int H,
-    int Tx, float3 bg, const float *__restrict__ t_final, const uint32_t *__restrict__ n_contrib,
-    const float *__restrict__ c_sum, const float *__restrict__ dL_dimage, const float *__restrict__ dL_dalpha,
-    const uint8_t *__restrict__ layer, uint32_t grad_layer_mask, float4 *__restrict__ rec_grad,
-    float *__restrict__ contrib_sum, float *__restrict__ contrib_max) {
-    __shared__ float4 s_a[256], s_b[256];
-    __shared__ float s_c[256];
-    __shared__ uint32_t s_idx[256];
-    __shared__ float s_acc[256][12];
-    __shared__ uint32_t s_wmax[8];
+// where P_i is the running colour sum including splat i; dC.P_i is carried as
+// the scalar Q.  Each warp walks the list only up to the longest blended
+// prefix of its own 64 pixels, reduces each splat's 10 sums over its pixels
+// and adds them to the record gradient with vector atomics:
+//   rec_grad[3g]   += (du, dv, dA2, dbeta)
+//   rec_grad[3g+1] += (dG2, dopacity, dr, dg)
+//   rec_grad[3g+2] += (db, sum of alpha*T, 0, 0);  contrib_max[g] = max(.., alpha*T)
+__global__ void __launch_bounds__(kThreads) k_composite_bwd(
+    const uint32_t *__restrict__ order, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ list,
+    const Rec *__restrict__ rec, int W, int H, int Tx, float3 bg, const float *__restrict__ t_final,
+    const uint32_t *__restrict__ n_contrib, const float *__restrict__ c_sum, const float *__restrict__ dL_dimage,
+    const float *__restrict__ dL_dalpha, const uint8_t *__restrict__ layer, uint32_t grad_layer_mask,
+    float4 *__restrict__ rec_grad, float *__restrict__ contrib_max) {
+    __shared__ float4 s_a[kThreads / 32][32], s_b[kThreads / 32][32];
+    __shared__ float s_c[kThreads / 32][32];
+    __shared__ uint32_t s_g[kThreads / 32][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tile = blockIdx.x;
-    int x, y;
-    pixel_of(tile, Tx, x, y);
-    const bool inside = x < W && y < H;
-    const float px = x + 0.5f, py = y + 0.5f;
+    const int tile = order[blockIdx.x];
     const uint2 rg = ranges[tile];
     const size_t plane = static_cast<size_t>(W) * H;
-    const size_t pix = inside ? static_cast<size_t>(y) * W + x : 0;
-    uint32_t nc = 0;
-    float TN = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f, dA = 0.f, QC = 0.f;
-    if (inside) {
-        nc = n_contrib[pix];
-        TN = t_final[pix];
-        if (dL_dimage) { dC0 = dL_dimage[pix]; dC1 = dL_dimage[plane + pix]; dC2 = dL_dimage[2 * plane + pix]; }
-        if (dL_dalpha) dA = dL_dalpha[pix];
-        QC = dC0 * c_sum[pix] + dC1 * c_sum[plane + pix] + dC2 * c_sum[2 * plane + pix];
-    }
-    const float K0 = TN * (dC0 * bg.x + dC1 * bg.y + dC2 * bg.z) - dA * TN;
-    // longest blended prefix in the tile
-    const uint32_t wm = __reduce_max_sync(FULL, nc);
-    if (lane == 0) s_wmax[warp] = wm;
-    for (int k = 0; k < 12; ++k) s_acc[threadIdx.x][k] = 0.f;
-    __syncthreads();
-    uint32_t maxnc = 0;
+    float px[2], py[2], TN[2], dC0[2], dC1[2], dC2[2], QC[2], K0[2], T[2], Q[2];
+    uint32_t nc[2];
 #pragma unroll
-    for (int w = 0; w < 8; ++w) maxnc = max(maxnc, s_wmax[w]);
-    const uint32_t stop = rg.x + min(maxnc, rg.y - rg.x);
-
-    float T = 1.f, Q = 0.f;
-    for (uint32_t base = rg.x; base < stop; base += 256) {
-        const uint32_t j = base + threadIdx.x;
-        if (j < stop) {
-            const uint32_t g = list[j];
-            const Rec *r = rec + g;
-            s_a[threadIdx.x] = r->a;
-            s_b[threadIdx.x] = r->b;
-            s_c[threadIdx.x] = r->c.x;
-            s_idx[threadIdx.x] = g;
+    for (int j = 0; j < 2; ++j) {
+        int x, y;
+        pixel_of(tile, Tx, warp, lane, j, x, y);
+        px[j] = x + 0.5f;
+        py[j] = y + 0.5f;
+        nc[j] = 0;
+        TN[j] = 1.f;
+        dC0[j] = dC1[j] = dC2[j] = QC[j] = 0.f;
+        float dA = 0.f;
+        if (x < W && y < H) {
+            const size_t pix = static_cast<size_t>(y) * W + x;
+            nc[j] = n_contrib[pix];
+            TN[j] = t_final[pix];
+            if (dL_dimage) {
+                dC0[j] = dL_dimage[pix];
+                dC1[j] = dL_dimage[plane + pix];
+                dC2[j] = dL_dimage[2 * plane + pix];
+            }
+            if (dL_dalpha) dA = dL_dalpha[pix];
+            QC[j] = dC0[j] * c_sum[pix] + dC1[j] * c_sum[plane + pix] + dC2[j] * c_sum[2 * plane + pix];
         }
-        __syncthreads();
-        const int cnt = min(256u, stop - base);
+        K0[j] = TN[j] * (dC0[j] * bg.x + dC1[j] * bg.y + dC2[j] * bg.z) - dA * TN[j];
+        T[j] = 1.f;
+        Q[j] = 0.f;
+    }
+    const uint32_t wbound = __reduce_max_sync(FULL, max(nc[0], nc[1]));
+    const uint32_t stop = rg.x + min(wbound, rg.y - rg.x);
+    Chunk nxt;
+    fetch_chunk(list, rec, rg.x + lane, stop, nxt);
+    for (uint32_t base = rg.x; base < stop; base += 32) {
+        __syncwarp();
+        s_a[warp][lane] = nxt.a;
+        s_b[warp][lane] = nxt.b;
+        s_c[warp][lane] = nxt.c;
+        s_g[warp][lane] = nxt.g;
+        __syncwarp();
+        fetch_chunk(list, rec, base + 32 + lane, stop, nxt);
+        const int cnt = min(32u, stop - base);
         for (int k = 0; k < cnt; ++k) {
             const uint32_t pos = base + k - rg.x;
-            bool act = pos < nc;
-            const float4 a = s_a[k], b = s_b[k];
-            const float cb = s_c[k];
-            float p = 0.f, dy = 0.f, ex = 0.f, ao = 0.f, al = 0.f;
-            if (act) {
-                al = splat_alpha(px, py, a, b, p, dy, ex, ao);
-                act = al >= kAlphaMin;
-            }
-            if (!__any_sync(FULL, act)) continue;
-            float v[10];
-            float wgt = 0.f;
+            const float4 a = s_a[warp][k], b = s_b[warp][k];
+            const float cb = s_c[warp][k];
+            float p[2], dy[2], ex[2], ao[2], al[2];
+            al[0] = splat_alpha(px[0], py[0], a, b, p[0], dy[0], ex[0], ao[0]);
+            al[1] = splat_alpha(px[1], py[1], a, b, p[1], dy[1], ex[1], ao[1]);
+            bool act[2];
+            act[0] = pos < nc[0] && al[0] >= kAlphaMin;
+            act[1] = pos < nc[1] && al[1] >= kAlphaMin;
+            if (!__any_sync(FULL, act[0] || act[1])) continue;
+            // v: du, dv, dA2, dbeta, dG2, dopacity, dr, dg, db, sum of alpha*T (10..15 unused)
+            float v[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float wmx = 0.f;
 #pragma unroll
-            for (int q = 0; q < 10; ++q) v[q] = 0.f;
-            if (act) {
-                const float dcc = dC0 * b.z + dC1 * b.w + dC2 * cb;
-                wgt = __fmul_rn(al, T);
-                Q = fmaf(wgt, dcc, Q);
-                const float inv = 1.f / (1.f - al);
-                const float dLda = T * dcc - ((QC - Q) + K0) * inv;
-                v[6] = wgt * dC0;
-                v[7] = wgt * dC1;
-                v[8] = wgt * dC2;
-                if (ao < kAlphaMax) {
-                    const float dLde = dLda * al * kLn2;
-                    const float A2p = a.z * p;
-                    v[5] = dLda * ex;
-                    v[2] = dLde * p * p;
-                    v[3] = dLde * 2.f * A2p * dy;
-                    v[4] = dLde * dy * dy;
-                    v[0] = -dLde * 2.f * A2p;
-                    v[1] = -dLde * (2.f * A2p * a.w + 2.f * b.x * dy);
+            for (int j = 0; j < 2; ++j) {
+                if (!act[j]) continue;
+                const float dcc = dC0[j] * b.z + dC1[j] * b.w + dC2[j] * cb;
+                const float wgt = __fmul_rn(al[j], T[j]);
+                Q[j] = fmaf(wgt, dcc, Q[j]);
+                const float inv = __frcp_rn(1.f - al[j]);
+                const float dLda = T[j] * dcc - ((QC[j] - Q[j]) + K0[j]) * inv;
+                v[6] += wgt * dC0[j];
+                v[7] += wgt * dC1[j];
+                v[8] += wgt * dC2[j];
+                if (ao[j] < kAlphaMax) {
+                    const float dLde = dLda * al[j] * kLn2;
+                    const float A2p = a.z * p[j];
+                    v[5] += dLda * ex[j];
+                    v[2] += dLde * p[j] * p[j];
+                    v[3] += dLde * 2.f * A2p * dy[j];
+                    v[4] += dLde * dy[j] * dy[j];
+                    v[0] -= dLde * 2.f * A2p;
+                    v[1] -= dLde * (2.f * A2p * a.w + 2.f * b.x * dy[j]);
                 }
-                v[9] = wgt;
-                T = __fmul_rn(T, __fsub_rn(1.f, al));
+                v[9] += wgt;
+                wmx = fmaxf(wmx, wgt);
+                T[j] = __fmul_rn(T[j], __fsub_rn(1.f, al[j]));
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int q = 0; q < 10; ++q) v[q] += __shfl_xor_sync(FULL, v[q], o);
-            const uint32_t wmx = __reduce_max_sync(FULL, __float_as_uint(wgt));
-            if (lane == 0) {
-#pragma unroll
-                for (int q = 0; q < 10; ++q) atomicAdd(&s_acc[k][q], v[q]);
-                atomicMax(reinterpret_cast<unsigned int *>(&s_acc[k][10]), wmx);
-            }
+            const float sv = reduce_scatter16(v, lane);
+            // value i sits in lane 2i: lanes 0, 8, 16 gather (i, i+1, i+2, i+3)
+            const float s1 = __shfl_down_sync(FULL, sv, 2);
+            const float s2 = __shfl_down_sync(FULL, sv, 4);
+            const float s3 = __shfl_down_sync(FULL, sv, 6);
+            const uint32_t smx = __reduce_max_sync(FULL, __float_as_uint(wmx));
+            const uint32_t g = s_g[warp][k];
+            const bool train = (grad_layer_mask >> layer[g]) & 1u;
+            if (lane == 0 && train) atomicAdd(&rec_grad[3 * g], make_float4(sv, s1, s2, s3));
+            if (lane == 8 && train) atomicAdd(&rec_grad[3 * g + 1], make_float4(sv, s1, s2, s3));
+            if (lane == 16) atomicAdd(reinterpret_cast<float2 *>(&rec_grad[3 * g + 2]), make_float2(train ? sv : 0.f, s1));
+            if (lane == 1 && contrib_max) atomicMax(reinterpret_cast<unsigned int *>(&contrib_max[g]), smx);
         }
-        __syncthreads();
-        if (j < stop) {
-            float *acc = s_acc[threadIdx.x];
-            const uint32_t g = s_idx[threadIdx.x];
-            if (acc[9] > 0.f) {
-                if ((grad_layer_mask >> layer[g]) & 1u) {
-                    atomicAdd(&rec_grad[3 * g], make_float4(acc[0], acc[1], acc[2], acc[3]));
-                    atomicAdd(&rec_grad[3 * g + 1], make_float4(acc[4], acc[5], acc[6], acc[7]));
-                    atomicAdd(&rec_grad[3 * g + 2], make_float4(acc[8], 0.f, 0.f, 0.f));
-                }
-                if (contrib_sum) atomicAdd(&contrib_sum[g], acc[9]);
-                if (contrib_max) atomicMax(reinterpret_cast<unsigned int *>(&contrib_max[g]),
-                                           __float_as_uint(acc[10]));
-            }
-#pragma unroll
-            for (int q = 0; q < 12; ++q) acc[q] = 0.f;
-        }
-        __syncthreads();
     }
 }
 
 }  // namespace
 
-cudaError_t launch_composite_forward(const uint2 *ranges, const uint32_t *list, const Rec *rec, int W, int H, int Tx,
-                                     int Ty, float3 bg, float *image, float *alpha, float *t_final, uint32_t *n_contrib,
-                                     float *c_sum, cudaStream_t st) {
-    const int tiles = Tx * Ty;
-    if (tiles == 0) return cudaSuccess;
-    k_composite_fwd<<<tiles, 256, 0, st>>>(ranges, list, rec, W, H, Tx, bg, image, alpha, t_final, n_contrib, c_sum);
+cudaError_t launch_tile_order(const uint2 *ranges, const uint32_t *work, int Tn, uint32_t *order, cudaStream_t st) {
+    if (Tn == 0) return cudaSuccess;
+    k_tile_order<<<1, 1024, 0, st>>>(ranges, work, Tn, order);
     return cudaGetLastError();
 }
 
-cudaError_t launch_composite_backward(const uint2 *ranges, const uint32_t *list, const Rec *rec, int W, int H, int Tx,
-                                      int Ty, float3 bg, const float *t_final, const uint32_t *n_contrib,
-                                      const float *c_sum, const float *dL_dimage, const float *dL_dalpha,
-                                      const uint8_t *layer, uint32_t grad_layer_mask, float4 *rec_grad,
-                                      float *contrib_sum, float *contrib_max, cudaStream_t st) {
+cudaError_t launch_composite_forward(const uint32_t *order, const uint2 *ranges, const uint32_t *list, const Rec *rec,
+                                     int W, int H, int Tx, int Ty, float3 bg, float *image, float *alpha,
+                                     float *t_final, uint32_t *n_contrib, float *c_sum, uint32_t *tile_work,
+                                     cudaStream_t st) {
     const int tiles = Tx * Ty;
     if (tiles == 0) return cudaSuccess;
-    k_composite_bwd<<<tiles, 256, 0, st>>>(ranges, list, rec, W, H, Tx, bg, t_final, n_contrib, c_sum, dL_dimage,
-                                           dL_dalpha, layer, grad_layer_mask, rec_grad, contrib_sum, contrib_max);
+    k_composite_fwd<<<tiles, kFwdThreads, 0, st>>>(order, ranges, list, rec, W, H, Tx, bg, image, alpha, t_final,
+                                                   n_contrib, c_sum, tile_work);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite_backward(const uint32_t *order, const uint2 *ranges, const uint32_t *list, const Rec *rec,
+                                      int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
+                                      const uint32_t *n_contrib, const float *c_sum, const float *dL_dimage,
+                                      const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
+                                      float4 *rec_grad, float *contrib_max, cudaStream_t st) {
+    const int tiles = Tx * Ty;
+    if (tiles == 0) return cudaSuccess;
+    k_composite_bwd<<<tiles, kThreads, 0, st>>>(order, ranges, list, rec, W, H, Tx, bg, t_final, n_contrib, c_sum,
+                                                dL_dimage, dL_dalpha, layer, grad_layer_mask, rec_grad, contrib_max);
     return cudaGetLastError();
 }
 

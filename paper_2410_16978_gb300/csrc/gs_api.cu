@@ -37,8 +37,11 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     o.n_contrib = take(P * 4);
     o.c_sum = take(3 * P * 4);
     o.partials = take(kMaxSortBlocks * 4);
-    o.hist = take(static_cast<size_t>(256) * kMaxSortBlocks * 4);
+    o.hist = take((static_cast<size_t>(256) * kMaxSortBlocks + 256) * 4);   // + digit totals
     o.rec_grad = take(N * sizeof(Rec));
+    o.tile_order = take(static_cast<size_t>(o.Tn) * 4);
+    o.tile_work = take(static_cast<size_t>(o.Tn) * 4);
+    o.tile_order_bwd = take(static_cast<size_t>(o.Tn) * 4);
     o.tile_k[0] = take(D * 4); o.tile_k[1] = take(D * 4);
     o.tile_v[0] = take(D * 4); o.tile_v[1] = take(D * 4);
     o.total = off;
@@ -248,7 +251,7 @@ int gs_render(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mas
         for (int pass = 0; pass < 4; ++pass) {
             const int a = pass & 1;
             if ((rc = cuda_check(launch_radix_pass(sk[a], sv2[a], sk[1 - a], sv2[1 - a], &ctl->n_vis, n, 8 * pass,
-                                                   hist, st),
+                                                   hist, ctl->depth_mm, pass == 0, st),
                                  "depth sort")) != GS_OK)
                 return rc;
         }
@@ -275,7 +278,7 @@ int gs_render(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mas
         for (int pass = 0; pass < tp; ++pass) {
             const int a = pass & 1;
             if ((rc = cuda_check(launch_radix_pass(tk[a], tv[a], tk[1 - a], tv[1 - a], &ctl->n_dup_c, cap, 8 * pass,
-                                                   hist, st),
+                                                   hist, ctl->tile_mm, pass == 0, st),
                                  "tile sort")) != GS_OK)
                 return rc;
         }
@@ -286,11 +289,13 @@ int gs_render(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mas
         Stage sg(GS_STAGE_RANGES, st, 1);
         if ((rc = cuda_check(launch_ranges(tk[fin], cap, ranges, ctl, st), "ranges")) != GS_OK) return rc;
     }
-    Stage sg(GS_STAGE_COMPOSITE, st, 1);
-    return cuda_check(launch_composite_forward(ranges, tv[fin], rec, cv.W, cv.H, cv.Tx, cv.Ty,
+    Stage sg(GS_STAGE_COMPOSITE, st, 2);
+    uint32_t *order_f = at<uint32_t>(ws, L.tile_order);
+    if ((rc = cuda_check(launch_tile_order(ranges, nullptr, L.Tn, order_f, st), "tile order")) != GS_OK) return rc;
+    return cuda_check(launch_composite_forward(order_f, ranges, tv[fin], rec, cv.W, cv.H, cv.Tx, cv.Ty,
                                                make_float3(bg[0], bg[1], bg[2]), image, alpha,
                                                at<float>(ws, L.t_final), at<uint32_t>(ws, L.n_contrib),
-                                               at<float>(ws, L.c_sum), st),
+                                               at<float>(ws, L.c_sum), at<uint32_t>(ws, L.tile_work), st),
                       "composite");
 }
 
@@ -313,22 +318,25 @@ int gs_render_backward(const gs_scene *scene, const gs_camera *camera, const flo
     float4 *rec_grad = at<float4>(ws, L.rec_grad);
     const int fin = tile_sort_passes(L.Tn) & 1;
     {
-    Stage sg(GS_STAGE_COMPOSITE_BWD, st, 1);
+    Stage sg(GS_STAGE_COMPOSITE_BWD, st, 2);
     if ((rc = cuda_check(cudaMemsetAsync(rec_grad, 0, static_cast<size_t>(sv.n) * sizeof(Rec), st), "memset grad")) !=
         GS_OK)
         return rc;
-    if ((rc = cuda_check(launch_composite_backward(at<uint2>(ws, L.ranges), at<uint32_t>(ws, L.tile_v[fin]),
+    uint32_t *order_b = at<uint32_t>(ws, L.tile_order_bwd);
+    if ((rc = cuda_check(launch_tile_order(at<uint2>(ws, L.ranges), at<uint32_t>(ws, L.tile_work), L.Tn, order_b, st),
+                         "tile order")) != GS_OK)
+        return rc;
+    if ((rc = cuda_check(launch_composite_backward(order_b, at<uint2>(ws, L.ranges), at<uint32_t>(ws, L.tile_v[fin]),
                                                    at<Rec>(ws, L.rec), cv.W, cv.H, cv.Tx, cv.Ty,
                                                    make_float3(bg[0], bg[1], bg[2]), at<float>(ws, L.t_final),
                                                    at<uint32_t>(ws, L.n_contrib), at<float>(ws, L.c_sum), dL_dimage,
-                                                   dL_dalpha, sv.layer, grad_layer_mask, rec_grad, contrib_sum,
-                                                   contrib_max, st),
+                                                   dL_dalpha, sv.layer, grad_layer_mask, rec_grad, contrib_max, st),
                          "composite backward")) != GS_OK)
         return rc;
     }
     Stage sg(GS_STAGE_PREPROCESS_BWD, st, 1);
     return cuda_check(launch_preprocess_backward(sv, cv, at<uint32_t>(ws, L.tiles), rec_grad, grad_layer_mask, *grads,
-                                                 st),
+                                                 contrib_sum, st),
                       "preprocess backward");
 }
 

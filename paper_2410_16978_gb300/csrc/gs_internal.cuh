@@ -37,7 +37,9 @@ struct Ctl {
     uint32_t n_vis;        // visible Gaussians (compaction total)
     uint32_t n_dup_c;      // min(n_dup, capacity): items in the tile sort
     uint32_t scan_total;   // scratch total of the last scan
-    uint32_t pad[5];
+    uint32_t depth_mm[2];  // ~min and max of the depth keys (radix pass skipping)
+    uint32_t tile_mm[2];   // ~min and max of the tile keys
+    uint32_t pad;
 };
 static_assert(sizeof(Ctl) == 64, "Ctl layout");
 
@@ -47,7 +49,7 @@ struct Layout {
     int W = 0, H = 0, Tx = 0, Ty = 0, Tn = 0;
     size_t ctl = 0, rec = 0, tiles = 0, depth = 0, sort_k[2] = {0, 0}, sort_v[2] = {0, 0}, dup_off = 0,
            tile_k[2] = {0, 0}, tile_v[2] = {0, 0}, ranges = 0, t_final = 0, n_contrib = 0, c_sum = 0,
-           partials = 0, hist = 0, rec_grad = 0, total = 0;
+           partials = 0, hist = 0, rec_grad = 0, tile_order = 0, tile_work = 0, tile_order_bwd = 0, total = 0;
 };
 
 // Returns false when sizes overflow.
@@ -87,9 +89,11 @@ struct Planes {
 // ---- launches (each returns cudaGetLastError() of its launches) ----
 cudaError_t launch_preprocess(const SceneView &s, const CamView &c, uint32_t layer_mask, const Planes &pl,
                               Rec *rec, uint32_t *tiles, uint32_t *depth_key, cudaStream_t st);
+// Also adds the per-Gaussian blend-weight sums (record-gradient slot 9) to
+// contrib_sum when it is not null.
 cudaError_t launch_preprocess_backward(const SceneView &s, const CamView &c, const uint32_t *tiles,
                                        const float4 *rec_grad, uint32_t grad_layer_mask, const gs_grads &g,
-                                       cudaStream_t st);
+                                       float *contrib_sum, cudaStream_t st);
 
 int sort_blocks();   // blocks of the sort / scan kernels on this device
 int report(int code, const char *msg);   // sets gs_last_error_string(), returns code
@@ -99,9 +103,11 @@ int report(int code, const char *msg);   // sets gs_last_error_string(), returns
 cudaError_t launch_compact_visible(const uint32_t *tiles, const uint32_t *depth_key, int n, uint32_t *keys_out,
                                    uint32_t *vals_out, uint32_t *partials, Ctl *ctl, cudaStream_t st);
 // One stable LSD pass on 8 bits at `shift` of min(*n_dev, n_cap) (key, value) pairs.
+// minmax (2 words, zeroed before the sort) receives ~min and max key in the
+// first pass; later passes whose digit is constant only copy.
 cudaError_t launch_radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
-                              const uint32_t *n_dev, uint32_t n_cap, int shift, uint32_t *hist,
-                              cudaStream_t st);
+                              const uint32_t *n_dev, uint32_t n_cap, int shift, uint32_t *hist, uint32_t *minmax,
+                              bool first, cudaStream_t st);
 // dup_off[p] = exclusive prefix of tiles[order[p]] over p < ctl->n_vis; writes n_dup,
 // n_dup_c and the overflow status.
 cudaError_t launch_dup_offsets(const uint32_t *order, const uint32_t *tiles, uint32_t n_cap, uint32_t *dup_off,
@@ -113,13 +119,16 @@ cudaError_t launch_ranges(const uint32_t *tile_k, uint32_t n_cap, uint2 *ranges,
 cudaError_t launch_prune(const float *contrib_max, int n, float thr, uint8_t *keep, int32_t *keep_index,
                          int64_t *n_keep, uint32_t *partials, cudaStream_t st);
 
-cudaError_t launch_composite_forward(const uint2 *ranges, const uint32_t *list, const Rec *rec, int W, int H,
-                                     int Tx, int Ty, float3 bg, float *image, float *alpha, float *t_final,
-                                     uint32_t *n_contrib, float *c_sum, cudaStream_t st);
-cudaError_t launch_composite_backward(const uint2 *ranges, const uint32_t *list, const Rec *rec, int W, int H,
-                                      int Tx, int Ty, float3 bg, const float *t_final, const uint32_t *n_contrib,
-                                      const float *c_sum, const float *dL_dimage, const float *dL_dalpha,
-                                      const uint8_t *layer, uint32_t grad_layer_mask, float4 *rec_grad,
-                                      float *contrib_sum, float *contrib_max, cudaStream_t st);
+// Heaviest-first tile order by list length (work == nullptr) or by work[t].
+cudaError_t launch_tile_order(const uint2 *ranges, const uint32_t *work, int Tn, uint32_t *order, cudaStream_t st);
+cudaError_t launch_composite_forward(const uint32_t *order, const uint2 *ranges, const uint32_t *list, const Rec *rec,
+                                     int W, int H, int Tx, int Ty, float3 bg, float *image, float *alpha,
+                                     float *t_final, uint32_t *n_contrib, float *c_sum, uint32_t *tile_work,
+                                     cudaStream_t st);
+cudaError_t launch_composite_backward(const uint32_t *order, const uint2 *ranges, const uint32_t *list, const Rec *rec,
+                                      int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
+                                      const uint32_t *n_contrib, const float *c_sum, const float *dL_dimage,
+                                      const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
+                                      float4 *rec_grad, float *contrib_max, cudaStream_t st);
 
 }  // namespace gs

@@ -42,14 +42,15 @@ __device__ __forceinline__ float ld_half(const void *p, int64_t idx, int dtype) 
 
 // Real SH basis (Condon-Shortley phase, index l*l+l+m) from the textbook
 // Cartesian forms; constants are the float nearest the exact normalisations.
-__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float *b) {
+template <int deg>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float *b) {
     b[0] = 0x1.20dd76p-2f;                                  // 1/(2 sqrt(pi))
-    if (deg < 1) return;
+    if constexpr (deg < 1) return;
     const float C1 = 0x1.f45438p-2f;                        // sqrt(3/(4 pi))
     b[1] = -C1 * y;
     b[2] = C1 * z;
     b[3] = -C1 * x;
-    if (deg < 2) return;
+    if constexpr (deg < 2) return;
     const float C2A = 0x1.17b142p+0f, C2C = 0x1.42f602p-2f, C2E = 0x1.17b142p-1f;
     float xx = x * x, yy = y * y, zz = z * z, xy = x * y, yz = y * z, xz = x * z;
     b[4] = C2A * xy;
@@ -57,7 +58,7 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
     b[6] = C2C * ((2.0f * zz - xx) - yy);
     b[7] = -C2A * xz;
     b[8] = C2E * (xx - yy);
-    if (deg < 3) return;
+    if constexpr (deg < 3) return;
     const float C3A = 0x1.2e1a32p-1f, C3B = 0x1.71ff8ep+1f, C3C = 0x1.d403d0p-2f, C3D = 0x1.7e21f0p-2f,
                 C3F = 0x1.71ff8ep+0f;
     b[9] = (-C3A * y) * (3.0f * xx - yy);
@@ -69,6 +70,7 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
     b[15] = (-C3A * x) * (xx - 3.0f * yy);
 }
 
+template <int DEG>
 __global__ void __launch_bounds__(128) k_preprocess(SceneView s, CamView c, uint32_t layer_mask, Planes pl,
                                                     Rec *__restrict__ rec, uint32_t *__restrict__ tiles,
                                                     uint32_t *__restrict__ depth_key) {
@@ -160,14 +162,15 @@ __global__ void __launch_bounds__(128) k_preprocess(SceneView s, CamView c, uint
                 const float campos2 = -((R[2] * c.t[0] + R[5] * c.t[1]) + R[8] * c.t[2]);
                 const float dx = mx - campos0, dy = my - campos1, dz = mz - campos2;
                 const float dn = sqrtf((dx * dx + dy * dy) + dz * dz);
-                float b[16];
-                sh_basis(s.sh_degree, dx / dn, dy / dn, dz / dn, b);
-                const int K = (s.sh_degree + 1) * (s.sh_degree + 1);
+                constexpr int K = (DEG + 1) * (DEG + 1);
+                float b[K];
+                sh_basis<DEG>(dx / dn, dy / dn, dz / dn, b);
                 const int64_t base = static_cast<int64_t>(i) * K * 3;
                 float rgb[3];
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
                     float acc = b[0] * ld_half(s.sh, base + ch, s.dtype_sh);
+#pragma unroll
                     for (int k = 1; k < K; ++k) acc = acc + b[k] * ld_half(s.sh, base + 3 * k + ch, s.dtype_sh);
                     rgb[ch] = fmaxf(acc + 0.5f, 0.0f);
                 }
@@ -192,8 +195,13 @@ __global__ void __launch_bounds__(128) k_preprocess(SceneView s, CamView c, uint
 cudaError_t launch_preprocess(const SceneView &s, const CamView &c, uint32_t layer_mask, const Planes &pl, Rec *rec,
                               uint32_t *tiles, uint32_t *depth_key, cudaStream_t st) {
     if (s.n == 0) return cudaSuccess;
-    const int threads = 128;
-    k_preprocess<<<(s.n + threads - 1) / threads, threads, 0, st>>>(s, c, layer_mask, pl, rec, tiles, depth_key);
+    const int threads = 128, blocks = (s.n + threads - 1) / threads;
+    switch (s.sh_degree) {
+        case 0: k_preprocess<0><<<blocks, threads, 0, st>>>(s, c, layer_mask, pl, rec, tiles, depth_key); break;
+        case 1: k_preprocess<1><<<blocks, threads, 0, st>>>(s, c, layer_mask, pl, rec, tiles, depth_key); break;
+        case 2: k_preprocess<2><<<blocks, threads, 0, st>>>(s, c, layer_mask, pl, rec, tiles, depth_key); break;
+        default: k_preprocess<3><<<blocks, threads, 0, st>>>(s, c, layer_mask, pl, rec, tiles, depth_key); break;
+    }
     return cudaGetLastError();
 }
 

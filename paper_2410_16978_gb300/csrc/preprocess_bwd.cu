@@ -19,15 +19,16 @@ __device__ __forceinline__ float ldv(const void *p, int64_t idx, int dtype) {
 
 // Cartesian real SH (Condon-Shortley phase) and the gradient of each
 // polynomial with respect to (x, y, z).
-__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, float *b, float3 *db) {
+template <int deg>
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float *b, float3 *db) {
     b[0] = 0x1.20dd76p-2f;
     db[0] = make_float3(0.f, 0.f, 0.f);
-    if (deg < 1) return;
+    if constexpr (deg < 1) return;
     const float C1 = 0x1.f45438p-2f;
     b[1] = -C1 * y; db[1] = make_float3(0.f, -C1, 0.f);
     b[2] = C1 * z;  db[2] = make_float3(0.f, 0.f, C1);
     b[3] = -C1 * x; db[3] = make_float3(-C1, 0.f, 0.f);
-    if (deg < 2) return;
+    if constexpr (deg < 2) return;
     const float C2A = 0x1.17b142p+0f, C2C = 0x1.42f602p-2f, C2E = 0x1.17b142p-1f;
     const float xx = x * x, yy = y * y, zz = z * z, xy = x * y, yz = y * z, xz = x * z;
     b[4] = C2A * xy;                     db[4] = make_float3(C2A * y, C2A * x, 0.f);
@@ -35,7 +36,7 @@ __device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z
     b[6] = C2C * ((2.f * zz - xx) - yy); db[6] = make_float3(-2.f * C2C * x, -2.f * C2C * y, 4.f * C2C * z);
     b[7] = -C2A * xz;                    db[7] = make_float3(-C2A * z, 0.f, -C2A * x);
     b[8] = C2E * (xx - yy);              db[8] = make_float3(2.f * C2E * x, -2.f * C2E * y, 0.f);
-    if (deg < 3) return;
+    if constexpr (deg < 3) return;
     const float C3A = 0x1.2e1a32p-1f, C3B = 0x1.71ff8ep+1f, C3C = 0x1.d403d0p-2f, C3D = 0x1.7e21f0p-2f,
                 C3F = 0x1.71ff8ep+0f;
     b[9] = (-C3A * y) * (3.f * xx - yy);
@@ -54,168 +55,212 @@ __device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z
     db[15] = make_float3(-C3A * (3.f * xx - 3.f * yy), 6.f * C3A * xy, 0.f);
 }
 
-__global__ void __launch_bounds__(128) k_preprocess_bwd(SceneView s, CamView c, const uint32_t *__restrict__ tiles,
-                                                        const float4 *__restrict__ rec_grad,
-                                                        uint32_t grad_layer_mask, gs_grads g) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= s.n) return;
-    const int K = (s.sh_degree + 1) * (s.sh_degree + 1);
-    float *gsh = g.sh + static_cast<int64_t>(i) * K * 3;
-    const bool live = tiles[i] > 0 && ((grad_layer_mask >> s.layer[i]) & 1u);
+constexpr int kBwdThreads = 128;
+
+template <int DEG>
+__global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd(SceneView s, CamView c,
+                                                                const uint32_t *__restrict__ tiles,
+                                                                const float4 *__restrict__ rec_grad,
+                                                                uint32_t grad_layer_mask, gs_grads g,
+                                                                float *__restrict__ contrib_sum) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int KS = 3 * K + 1;                     // odd stride: conflict-free rows
+    __shared__ float s_gsh[kBwdThreads * KS];
+    const int i = blockIdx.x * kBwdThreads + threadIdx.x;
+    float *my = s_gsh + threadIdx.x * KS;
+    const bool visible = i < s.n && tiles[i] > 0;
+    if (visible && contrib_sum) contrib_sum[i] += rec_grad[3 * i + 2].y;
+    const bool live = visible && ((grad_layer_mask >> s.layer[i]) & 1u);
     if (!live) {
-        for (int k = 0; k < 3; ++k) { g.means[3 * i + k] = 0.f; g.log_scales[3 * i + k] = 0.f; }
-        for (int k = 0; k < 4; ++k) g.quats[4 * i + k] = 0.f;
-        g.opacity_logit[i] = 0.f;
-        for (int k = 0; k < 3 * K; ++k) gsh[k] = 0.f;
-        return;
-    }
-    const float4 ga = rec_grad[3 * i], gb = rec_grad[3 * i + 1], gc = rec_grad[3 * i + 2];
-    const float dU = ga.x, dV = ga.y, dA2 = ga.z, dBeta = ga.w, dG2 = gb.x, dOp = gb.y;
-    const float dRgb[3] = {gb.z, gb.w, gc.x};
-    const float mx = s.means[3 * i], my = s.means[3 * i + 1], mz = s.means[3 * i + 2];
-    const float *R = c.R;
-
-    // opacity
-    const float o = 1.f / (1.f + expf(-s.opacity_logit[i]));
-    g.opacity_logit[i] = dOp * o * (1.f - o);
-
-    // colour and the view-direction part of d(mean)
-    const float cp0 = -(R[0] * c.t[0] + R[3] * c.t[1] + R[6] * c.t[2]);
-    const float cp1 = -(R[1] * c.t[0] + R[4] * c.t[1] + R[7] * c.t[2]);
-    const float cp2 = -(R[2] * c.t[0] + R[5] * c.t[1] + R[8] * c.t[2]);
-    const float vx = mx - cp0, vy = my - cp1, vz = mz - cp2;
-    const float vn = sqrtf(vx * vx + vy * vy + vz * vz);
-    const float ivn = 1.f / vn;
-    const float dx = vx * ivn, dy = vy * ivn, dz = vz * ivn;
-    float b[16];
-    float3 db[16];
-    sh_basis_grad(s.sh_degree, dx, dy, dz, b, db);
-    const int64_t base = static_cast<int64_t>(i) * K * 3;
-    float ddx = 0.f, ddy = 0.f, ddz = 0.f;
-    for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.f;
-        for (int k = 0; k < K; ++k) acc += b[k] * ldv(s.sh, base + 3 * k + ch, s.dtype_sh);
-        const bool pass = acc + 0.5f > 0.f;
-        const float gch = pass ? dRgb[ch] : 0.f;
-        for (int k = 0; k < K; ++k) {
-            gsh[3 * k + ch] = gch * b[k];
-            const float shv = ldv(s.sh, base + 3 * k + ch, s.dtype_sh) * gch;
-            ddx += shv * db[k].x; ddy += shv * db[k].y; ddz += shv * db[k].z;
+#pragma unroll
+        for (int k = 0; k < 3 * K; ++k) my[k] = 0.f;
+        if (i < s.n) {
+            for (int k = 0; k < 3; ++k) { g.means[3 * i + k] = 0.f; g.log_scales[3 * i + k] = 0.f; }
+            for (int k = 0; k < 4; ++k) g.quats[4 * i + k] = 0.f;
+            g.opacity_logit[i] = 0.f;
         }
-    }
-    const float dd = ddx * dx + ddy * dy + ddz * dz;
-    float gmx = (ddx - dx * dd) * ivn, gmy = (ddy - dy * dd) * ivn, gmz = (ddz - dz * dd) * ivn;
+    } else {
+        const float4 ga = rec_grad[3 * i], gb = rec_grad[3 * i + 1], gc = rec_grad[3 * i + 2];
+        const float dU = ga.x, dV = ga.y, dA2 = ga.z, dBeta = ga.w, dG2 = gb.x, dOp = gb.y;
+        const float dRgb[3] = {gb.z, gb.w, gc.x};
+        const float mx = s.means[3 * i], my_ = s.means[3 * i + 1], mz = s.means[3 * i + 2];
+        const float *R = c.R;
 
-    // recompute the projection
-    const float px = R[0] * mx + R[1] * my + R[2] * mz + c.t[0];
-    const float py = R[3] * mx + R[4] * my + R[5] * mz + c.t[1];
-    const float pz = R[6] * mx + R[7] * my + R[8] * mz + c.t[2];
-    float sc[3];
-    for (int k = 0; k < 3; ++k) sc[k] = expf(ldv(s.log_scales, 3 * (int64_t)i + k, s.dtype_sr));
-    float q[4];
-    for (int k = 0; k < 4; ++k) q[k] = ldv(s.quats, 4 * (int64_t)i + k, s.dtype_sr);
-    const float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    const float iqn = 1.f / qn;
-    const float w = q[0] * iqn, x = q[1] * iqn, y = q[2] * iqn, z = q[3] * iqn;
-    const float Rq[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
-                         2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
-                         2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
-    float M[9];
-    for (int a = 0; a < 3; ++a)
-        for (int j = 0; j < 3; ++j) M[3 * a + j] = Rq[3 * a + j] * sc[j];
-    float Sg[9];
-    for (int a = 0; a < 3; ++a)
-        for (int bb = 0; bb < 3; ++bb)
-            Sg[3 * a + bb] = M[3 * a] * M[3 * bb] + M[3 * a + 1] * M[3 * bb + 1] + M[3 * a + 2] * M[3 * bb + 2];
-    const float limx = 1.3f * (0.5f * c.W / c.fx), limy = 1.3f * (0.5f * c.H / c.fy);
-    const float iz = 1.f / pz;
-    const float rx = px * iz, ry = py * iz;
-    const bool clx = rx < -limx || rx > limx, cly = ry < -limy || ry > limy;
-    const float cxz = fminf(limx, fmaxf(-limx, rx)), cyz = fminf(limy, fmaxf(-limy, ry));
-    const float J00 = c.fx * iz, J02 = -c.fx * cxz * iz, J11 = c.fy * iz, J12 = -c.fy * cyz * iz;
-    float T[6];
-    for (int bb = 0; bb < 3; ++bb) {
-        T[bb] = J00 * R[bb] + J02 * R[6 + bb];
-        T[3 + bb] = J11 * R[3 + bb] + J12 * R[6 + bb];
-    }
-    float U[6];   // T Sigma
-    for (int a = 0; a < 2; ++a)
-        for (int bb = 0; bb < 3; ++bb)
-            U[3 * a + bb] = T[3 * a] * Sg[bb] + T[3 * a + 1] * Sg[3 + bb] + T[3 * a + 2] * Sg[6 + bb];
-    const float s00 = U[0] * T[0] + U[1] * T[1] + U[2] * T[2] + 0.3f;
-    const float s01 = U[0] * T[3] + U[1] * T[4] + U[2] * T[5];
-    const float s11 = U[3] * T[3] + U[4] * T[4] + U[5] * T[5] + 0.3f;
-    const float det = s00 * s11 - s01 * s01;
-    const float NHL = -0x1.715476p-1f;
-    const float idet2 = 1.f / (det * det);
-    const float ds00 = dA2 * (-NHL * s11 * s11 * idet2);
-    const float ds11 = dA2 * (-NHL * s01 * s01 * idet2) + dBeta * (s01 / (s11 * s11)) + dG2 * (-NHL / (s11 * s11));
-    const float ds01 = dA2 * (2.f * NHL * s11 * s01 * idet2) - dBeta / s11;
-    const float G00 = ds00, G01 = 0.5f * ds01, G11 = ds11;
+        // opacity
+        const float o = 1.f / (1.f + expf(-s.opacity_logit[i]));
+        g.opacity_logit[i] = dOp * o * (1.f - o);
 
-    // dSigma = T^T G T (symmetric), dT = 2 G T Sigma = 2 G U
-    float dSg[9];
-    for (int a = 0; a < 3; ++a)
-        for (int bb = 0; bb < 3; ++bb)
-            dSg[3 * a + bb] = T[a] * (G00 * T[bb] + G01 * T[3 + bb]) + T[3 + a] * (G01 * T[bb] + G11 * T[3 + bb]);
-    float dT[6];
-    for (int bb = 0; bb < 3; ++bb) {
-        dT[bb] = 2.f * (G00 * U[bb] + G01 * U[3 + bb]);
-        dT[3 + bb] = 2.f * (G01 * U[bb] + G11 * U[3 + bb]);
-    }
-    // dJ = dT W^T (only the entries that are not identically zero)
-    const float dJ00 = dT[0] * R[0] + dT[1] * R[1] + dT[2] * R[2];
-    const float dJ02 = dT[0] * R[6] + dT[1] * R[7] + dT[2] * R[8];
-    const float dJ11 = dT[3] * R[3] + dT[4] * R[4] + dT[5] * R[5];
-    const float dJ12 = dT[3] * R[6] + dT[4] * R[7] + dT[5] * R[8];
-    const float iz2 = iz * iz;
-    float dpx = 0.f, dpy = 0.f, dpz = 0.f;
-    dpz += -dJ00 * c.fx * iz2 + dJ02 * c.fx * cxz * iz2 - dJ11 * c.fy * iz2 + dJ12 * c.fy * cyz * iz2;
-    const float dcx = -dJ02 * c.fx * iz, dcy = -dJ12 * c.fy * iz;
-    if (!clx) { dpx += dcx * iz; dpz -= dcx * px * iz2; }
-    if (!cly) { dpy += dcy * iz; dpz -= dcy * py * iz2; }
-    dpx += dU * c.fx * iz;
-    dpy += dV * c.fy * iz;
-    dpz -= (dU * c.fx * px + dV * c.fy * py) * iz2;
-    gmx += R[0] * dpx + R[3] * dpy + R[6] * dpz;
-    gmy += R[1] * dpx + R[4] * dpy + R[7] * dpz;
-    gmz += R[2] * dpx + R[5] * dpy + R[8] * dpz;
-    g.means[3 * i] = gmx; g.means[3 * i + 1] = gmy; g.means[3 * i + 2] = gmz;
-
-    // Sigma = M M^T: dM = 2 dSigma M;  M = Rq diag(s)
-    float dR[9];
-    for (int j = 0; j < 3; ++j) {
-        float ds = 0.f;
-        for (int a = 0; a < 3; ++a) {
-            const float dM = 2.f * (dSg[3 * a] * M[j] + dSg[3 * a + 1] * M[3 + j] + dSg[3 * a + 2] * M[6 + j]);
-            ds += dM * Rq[3 * a + j];
-            dR[3 * a + j] = dM * sc[j];
+        // colour and the view-direction part of d(mean)
+        const float cp0 = -(R[0] * c.t[0] + R[3] * c.t[1] + R[6] * c.t[2]);
+        const float cp1 = -(R[1] * c.t[0] + R[4] * c.t[1] + R[7] * c.t[2]);
+        const float cp2 = -(R[2] * c.t[0] + R[5] * c.t[1] + R[8] * c.t[2]);
+        const float vx = mx - cp0, vy = my_ - cp1, vz = mz - cp2;
+        const float ivn = rsqrtf(vx * vx + vy * vy + vz * vz);
+        const float dx = vx * ivn, dy = vy * ivn, dz = vz * ivn;
+        float b[K];
+        float3 db[K];
+        sh_basis_grad<DEG>(dx, dy, dz, b, db);
+        const int64_t base = static_cast<int64_t>(i) * K * 3;
+        float ddx = 0.f, ddy = 0.f, ddz = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float shv[K];
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                shv[k] = ldv(s.sh, base + 3 * k + ch, s.dtype_sh);
+                acc += b[k] * shv[k];
+            }
+            const float gch = acc + 0.5f > 0.f ? dRgb[ch] : 0.f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                my[3 * k + ch] = gch * b[k];
+                const float t = shv[k] * gch;
+                ddx += t * db[k].x; ddy += t * db[k].y; ddz += t * db[k].z;
+            }
         }
-        g.log_scales[3 * i + j] = ds * sc[j];
+        const float dd = ddx * dx + ddy * dy + ddz * dz;
+        float gmx = (ddx - dx * dd) * ivn, gmy = (ddy - dy * dd) * ivn, gmz = (ddz - dz * dd) * ivn;
+
+        // recompute the projection
+        const float px = R[0] * mx + R[1] * my_ + R[2] * mz + c.t[0];
+        const float py = R[3] * mx + R[4] * my_ + R[5] * mz + c.t[1];
+        const float pz = R[6] * mx + R[7] * my_ + R[8] * mz + c.t[2];
+        float sc[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sc[k] = expf(ldv(s.log_scales, 3 * (int64_t)i + k, s.dtype_sr));
+        float q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = ldv(s.quats, 4 * (int64_t)i + k, s.dtype_sr);
+        const float iqn = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        const float w = q[0] * iqn, x = q[1] * iqn, y = q[2] * iqn, z = q[3] * iqn;
+        const float Rq[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
+                             2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
+                             2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
+        float M[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) M[3 * a + j] = Rq[3 * a + j] * sc[j];
+        float Sg[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb)
+                Sg[3 * a + bb] = M[3 * a] * M[3 * bb] + M[3 * a + 1] * M[3 * bb + 1] + M[3 * a + 2] * M[3 * bb + 2];
+        const float limx = 1.3f * (0.5f * c.W / c.fx), limy = 1.3f * (0.5f * c.H / c.fy);
+        const float iz = 1.f / pz;
+        const float rx = px * iz, ry = py * iz;
+        const bool clx = rx < -limx || rx > limx, cly = ry < -limy || ry > limy;
+        const float cxz = fminf(limx, fmaxf(-limx, rx)), cyz = fminf(limy, fmaxf(-limy, ry));
+        const float J00 = c.fx * iz, J02 = -c.fx * cxz * iz, J11 = c.fy * iz, J12 = -c.fy * cyz * iz;
+        float T[6];
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+            T[bb] = J00 * R[bb] + J02 * R[6 + bb];
+            T[3 + bb] = J11 * R[3 + bb] + J12 * R[6 + bb];
+        }
+        float U[6];   // T Sigma
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb)
+                U[3 * a + bb] = T[3 * a] * Sg[bb] + T[3 * a + 1] * Sg[3 + bb] + T[3 * a + 2] * Sg[6 + bb];
+        const float s00 = U[0] * T[0] + U[1] * T[1] + U[2] * T[2] + 0.3f;
+        const float s01 = U[0] * T[3] + U[1] * T[4] + U[2] * T[5];
+        const float s11 = U[3] * T[3] + U[4] * T[4] + U[5] * T[5] + 0.3f;
+        const float det = s00 * s11 - s01 * s01;
+        const float NHL = -0x1.715476p-1f;
+        const float idet2 = 1.f / (det * det);
+        const float is11 = 1.f / s11;
+        const float ds00 = dA2 * (-NHL * s11 * s11 * idet2);
+        const float ds11 = dA2 * (-NHL * s01 * s01 * idet2) + dBeta * (s01 * is11 * is11) + dG2 * (-NHL * is11 * is11);
+        const float ds01 = dA2 * (2.f * NHL * s11 * s01 * idet2) - dBeta * is11;
+        const float G00 = ds00, G01 = 0.5f * ds01, G11 = ds11;
+
+        // dSigma = T^T G T (symmetric), dT = 2 G T Sigma = 2 G U
+        float dSg[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb)
+                dSg[3 * a + bb] = T[a] * (G00 * T[bb] + G01 * T[3 + bb]) + T[3 + a] * (G01 * T[bb] + G11 * T[3 + bb]);
+        float dT[6];
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+            dT[bb] = 2.f * (G00 * U[bb] + G01 * U[3 + bb]);
+            dT[3 + bb] = 2.f * (G01 * U[bb] + G11 * U[3 + bb]);
+        }
+        // dJ = dT W^T (only the entries that are not identically zero)
+        const float dJ00 = dT[0] * R[0] + dT[1] * R[1] + dT[2] * R[2];
+        const float dJ02 = dT[0] * R[6] + dT[1] * R[7] + dT[2] * R[8];
+        const float dJ11 = dT[3] * R[3] + dT[4] * R[4] + dT[5] * R[5];
+        const float dJ12 = dT[3] * R[6] + dT[4] * R[7] + dT[5] * R[8];
+        const float iz2 = iz * iz;
+        float dpx = 0.f, dpy = 0.f, dpz = 0.f;
+        dpz += -dJ00 * c.fx * iz2 + dJ02 * c.fx * cxz * iz2 - dJ11 * c.fy * iz2 + dJ12 * c.fy * cyz * iz2;
+        const float dcx = -dJ02 * c.fx * iz, dcy = -dJ12 * c.fy * iz;
+        if (!clx) { dpx += dcx * iz; dpz -= dcx * px * iz2; }
+        if (!cly) { dpy += dcy * iz; dpz -= dcy * py * iz2; }
+        dpx += dU * c.fx * iz;
+        dpy += dV * c.fy * iz;
+        dpz -= (dU * c.fx * px + dV * c.fy * py) * iz2;
+        gmx += R[0] * dpx + R[3] * dpy + R[6] * dpz;
+        gmy += R[1] * dpx + R[4] * dpy + R[7] * dpz;
+        gmz += R[2] * dpx + R[5] * dpy + R[8] * dpz;
+        g.means[3 * i] = gmx; g.means[3 * i + 1] = gmy; g.means[3 * i + 2] = gmz;
+
+        // Sigma = M M^T: dM = 2 dSigma M;  M = Rq diag(s)
+        float dR[9];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float ds = 0.f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float dM = 2.f * (dSg[3 * a] * M[j] + dSg[3 * a + 1] * M[3 + j] + dSg[3 * a + 2] * M[6 + j]);
+                ds += dM * Rq[3 * a + j];
+                dR[3 * a + j] = dM * sc[j];
+            }
+            g.log_scales[3 * i + j] = ds * sc[j];
+        }
+        // rotation matrix of the unit quaternion -> (w, x, y, z)
+        const float dw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+        const float dxq = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] +
+                                 w * dR[7] - 2.f * x * dR[8]);
+        const float dyq = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] +
+                                 z * dR[7] - 2.f * y * dR[8]);
+        const float dzq = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
+                                 x * dR[6] + y * dR[7]);
+        const float qd = dw * w + dxq * x + dyq * y + dzq * z;
+        g.quats[4 * i] = (dw - w * qd) * iqn;
+        g.quats[4 * i + 1] = (dxq - x * qd) * iqn;
+        g.quats[4 * i + 2] = (dyq - y * qd) * iqn;
+        g.quats[4 * i + 3] = (dzq - z * qd) * iqn;
     }
-    // rotation matrix of the unit quaternion -> (w, x, y, z)
-    const float dw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
-    const float dxq = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] +
-                             w * dR[7] - 2.f * x * dR[8]);
-    const float dyq = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] +
-                             z * dR[7] - 2.f * y * dR[8]);
-    const float dzq = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
-                             x * dR[6] + y * dR[7]);
-    const float qd = dw * w + dxq * x + dyq * y + dzq * z;
-    g.quats[4 * i] = (dw - w * qd) * iqn;
-    g.quats[4 * i + 1] = (dxq - x * qd) * iqn;
-    g.quats[4 * i + 2] = (dyq - y * qd) * iqn;
-    g.quats[4 * i + 3] = (dzq - z * qd) * iqn;
+    // the block's SH gradients are one contiguous slab: write it with coalesced stores
+    __syncthreads();
+    const int first = blockIdx.x * kBwdThreads;
+    const int nrows = min(kBwdThreads, s.n - first);
+    float *dst = g.sh + static_cast<int64_t>(first) * 3 * K;
+    for (int e = threadIdx.x; e < nrows * 3 * K; e += kBwdThreads) {
+        const int row = e / (3 * K), col = e - row * (3 * K);
+        dst[e] = s_gsh[row * KS + col];
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_preprocess_backward(const SceneView &s, const CamView &c, const uint32_t *tiles,
                                        const float4 *rec_grad, uint32_t grad_layer_mask, const gs_grads &g,
-                                       cudaStream_t st) {
+                                       float *contrib_sum, cudaStream_t st) {
     if (s.n == 0) return cudaSuccess;
-    const int threads = 128;
-    k_preprocess_bwd<<<(s.n + threads - 1) / threads, threads, 0, st>>>(s, c, tiles, rec_grad, grad_layer_mask, g);
+    const int blocks = (s.n + kBwdThreads - 1) / kBwdThreads;
+    switch (s.sh_degree) {
+        case 0: k_preprocess_bwd<0><<<blocks, kBwdThreads, 0, st>>>(s, c, tiles, rec_grad, grad_layer_mask, g, contrib_sum); break;
+        case 1: k_preprocess_bwd<1><<<blocks, kBwdThreads, 0, st>>>(s, c, tiles, rec_grad, grad_layer_mask, g, contrib_sum); break;
+        case 2: k_preprocess_bwd<2><<<blocks, kBwdThreads, 0, st>>>(s, c, tiles, rec_grad, grad_layer_mask, g, contrib_sum); break;
+        default: k_preprocess_bwd<3><<<blocks, kBwdThreads, 0, st>>>(s, c, tiles, rec_grad, grad_layer_mask, g, contrib_sum); break;
+    }
     return cudaGetLastError();
 }
 

@@ -187,80 +187,112 @@ struct KeepOut {
 };
 
 // ---------------------------------------------------------------------------
-// Radix sort pass: 8-bit digits, histogram per (digit, block) in digit-major order.
+// Radix sort pass: 8-bit digits, histogram per (digit, block) in digit-major
+// order.  The first pass of a sort also records min and max key (as max of
+// ~key and max of key); a later pass whose digit is the same in every key
+// (all keys agree on the bits at and above its shift) is an identity
+// permutation and only copies.
+
+__device__ __forceinline__ bool pass_is_constant(const uint32_t *mm, int shift) {
+    const uint32_t kmin = ~mm[0], kmax = mm[1];
+    return ((kmin ^ kmax) >> shift) == 0;
+}
 
 __global__ void __launch_bounds__(256) k_radix_up(const uint32_t *__restrict__ keys, NSrc ns, int shift,
-                                                  uint32_t *__restrict__ hist) {
+                                                  uint32_t *__restrict__ hist, uint32_t *__restrict__ mm, int first) {
     __shared__ uint32_t s_h[8][256];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (!first && pass_is_constant(mm, shift)) return;
     for (int k = threadIdx.x; k < 8 * 256; k += 256) (&s_h[0][0])[k] = 0;
     __syncthreads();
     uint32_t beg, end;
     block_range(ns.get(), beg, end);
+    uint32_t kinv = 0, kmax = 0;
     for (uint32_t base = beg; base < end; base += 256) {
         const uint32_t i = base + threadIdx.x;
         const bool valid = i < end;
-        const uint32_t d = valid ? (keys[i] >> shift) & 255u : 256u + lane;
+        uint32_t key = 0, d = 256u + lane;
+        if (valid) {
+            key = keys[i];
+            d = (key >> shift) & 255u;
+            kinv = max(kinv, ~key);
+            kmax = max(kmax, key);
+        }
         const unsigned peers = __match_any_sync(FULL, d);
         if (valid && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&s_h[warp][d], __popc(peers));
     }
+    if (first) {
+        kinv = __reduce_max_sync(FULL, kinv);
+        kmax = __reduce_max_sync(FULL, kmax);
+        if (lane == 0) {    // 0 is neutral for both maxima: warps without items change nothing
+            atomicMax(&mm[0], kinv);
+            atomicMax(&mm[1], kmax);
+        }
+    }
     __syncthreads();
     const int d = threadIdx.x;
-    uint32_t s = 0;
+    uint32_t sum = 0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) s += s_h[w][d];
-    hist[static_cast<size_t>(d) * gridDim.x + blockIdx.x] = s;
+    for (int w = 0; w < 8; ++w) sum += s_h[w][d];
+    hist[static_cast<size_t>(d) * gridDim.x + blockIdx.x] = sum;
 }
 
-// Exclusive scan of the E = 256*G histogram entries in place (one CTA).
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *__restrict__ hist, int G) {
-    __shared__ uint32_t s_w[32];
-    const int E = 256 * G;
-    const int per = (E + 1023) / 1024;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int b = t * per;
+// Per digit (one CTA each): exclusive scan of its G block counts in place and
+// the digit's total.
+__global__ void __launch_bounds__(256) k_radix_rowscan(uint32_t *__restrict__ hist, int G,
+                                                       uint32_t *__restrict__ rowtot, const uint32_t *__restrict__ mm,
+                                                       int shift, int first) {
+    __shared__ uint32_t s_w[8];
+    if (!first && pass_is_constant(mm, shift)) return;
+    uint32_t *row = hist + static_cast<size_t>(blockIdx.x) * G;
+    constexpr int per = kMaxSortBlocks / 256;
+    uint32_t v[per];
     uint32_t sum = 0;
-    for (int k = 0; k < per && b + k < E; ++k) sum += hist[b + k];
-    uint32_t x = sum;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
+    for (int k = 0; k < per; ++k) {
+        const int b = threadIdx.x * per + k;
+        v[k] = b < G ? row[b] : 0;
+        sum += v[k];
     }
-    if (lane == 31) s_w[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = s_w[lane];
+    uint32_t tot;
+    uint32_t run = block_scan_256(sum, s_w, &tot);
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, w, o);
-            if (lane >= o) w += y;
-        }
-        s_w[lane] = w;
+    for (int k = 0; k < per; ++k) {
+        const int b = threadIdx.x * per + k;
+        if (b < G) row[b] = run;
+        run += v[k];
     }
-    __syncthreads();
-    uint32_t run = (warp > 0 ? s_w[warp - 1] : 0) + x - sum;
-    for (int k = 0; k < per && b + k < E; ++k) {
-        const uint32_t h = hist[b + k];
-        hist[b + k] = run;
-        run += h;
-    }
+    if (threadIdx.x == 0) rowtot[blockIdx.x] = tot;
 }
 
 // Stable scatter: items are ranked in (round, warp, lane) = index order.
 __global__ void __launch_bounds__(256) k_radix_down(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                     uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, NSrc ns,
-                                                    int shift, const uint32_t *__restrict__ hist) {
+                                                    int shift, const uint32_t *__restrict__ hist,
+                                                    const uint32_t *__restrict__ rowtot,
+                                                    const uint32_t *__restrict__ mm, int first) {
     __shared__ uint32_t s_off[256];
     __shared__ uint32_t s_wc[8][256];
     __shared__ uint32_t s_rt[256];
+    __shared__ uint32_t s_w[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    s_off[threadIdx.x] = hist[static_cast<size_t>(threadIdx.x) * gridDim.x + blockIdx.x];
+    uint32_t beg, end;
+    block_range(ns.get(), beg, end);
+    if (!first && pass_is_constant(mm, shift)) {
+        for (uint32_t i = beg + threadIdx.x; i < end; i += 256) {
+            kout[i] = kin[i];
+            vout[i] = vin[i];
+        }
+        return;
+    }
+    {
+        uint32_t tot;
+        const uint32_t digit_base = block_scan_256(rowtot[threadIdx.x], s_w, &tot);
+        s_off[threadIdx.x] = digit_base + hist[static_cast<size_t>(threadIdx.x) * gridDim.x + blockIdx.x];
+    }
 #pragma unroll
     for (int w = 0; w < 8; ++w) s_wc[w][threadIdx.x] = 0;
     __syncthreads();
-    uint32_t beg, end;
-    block_range(ns.get(), beg, end);
     const unsigned lt = (1u << lane) - 1u;
     for (uint32_t base = beg; base < end; base += 256) {
         const uint32_t i = base + threadIdx.x;
@@ -301,23 +333,55 @@ __global__ void __launch_bounds__(256) k_radix_down(const uint32_t *__restrict__
 
 // ---------------------------------------------------------------------------
 
+// Each warp takes 32 consecutive visible Gaussians (in depth order).  Their
+// pairs occupy one contiguous range of the pair list (the offsets are an
+// exclusive scan), which the warp writes with coalesced stores: for output
+// slot k the owning Gaussian is found by a binary search over the 32 start
+// offsets, and the tile within its rectangle by one division.
 __global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ order, const uint32_t *__restrict__ dup_off,
                                               const Rec *__restrict__ rec, NSrc ns, int Tx,
                                               uint32_t *__restrict__ tile_k, uint32_t *__restrict__ tile_v,
                                               uint64_t cap) {
+    __shared__ uint32_t s_start[8][33];
+    __shared__ uint32_t s_g[8][32], s_x0[8][32], s_y0[8][32], s_w[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t n = ns.get();
-    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const uint32_t g = order[p];
-        const float4 c = rec[g].c;
-        const uint32_t r0 = __float_as_uint(c.z), r1 = __float_as_uint(c.w);
-        const uint32_t x0 = r0 & 0xFFFFu, y0 = r0 >> 16, x1 = r1 & 0xFFFFu, y1 = r1 >> 16;
-        uint64_t k = dup_off[p];
-        for (uint32_t ty = y0; ty < y1; ++ty)
-            for (uint32_t tx = x0; tx < x1; ++tx, ++k) {
-                if (k >= cap) return;
-                tile_k[k] = ty * static_cast<uint32_t>(Tx) + tx;
-                tile_v[k] = g;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t p0 = (blockIdx.x * (blockDim.x >> 5) + warp) * 32u; p0 < n; p0 += nwarps * 32u) {
+        const uint32_t p = p0 + lane;
+        uint32_t start = 0, cnt = 0, g = 0, x0 = 0, y0 = 0, w = 1;
+        if (p < n) {
+            g = order[p];
+            start = dup_off[p];
+            const float4 c = rec[g].c;
+            const uint32_t r0 = __float_as_uint(c.z), r1 = __float_as_uint(c.w);
+            x0 = r0 & 0xFFFFu; y0 = r0 >> 16;
+            w = (r1 & 0xFFFFu) - x0;
+            cnt = w * ((r1 >> 16) - y0);
+        }
+        // range end of the warp: the last valid lane's start + count
+        const uint32_t nvalid = min(32u, n - p0);
+        const uint32_t end = __shfl_sync(FULL, start + cnt, nvalid - 1);
+        const uint32_t first = __shfl_sync(FULL, start, 0);
+        s_start[warp][lane] = p < n ? start : end;
+        if (lane == 0) s_start[warp][32] = end;
+        s_g[warp][lane] = g; s_x0[warp][lane] = x0; s_y0[warp][lane] = y0; s_w[warp][lane] = w;
+        __syncwarp();
+        for (uint64_t k = static_cast<uint64_t>(first) + lane; k < end; k += 32) {
+            if (k >= cap) break;
+            // largest j with s_start[j] <= k (lanes with no pairs share the next start)
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_start[warp][mid] <= k) lo = mid; else hi = mid - 1;
             }
+            const uint32_t r = static_cast<uint32_t>(k) - s_start[warp][lo];
+            const uint32_t wj = s_w[warp][lo];
+            const uint32_t ty = r / wj, tx = r - ty * wj;
+            tile_k[k] = (s_y0[warp][lo] + ty) * static_cast<uint32_t>(Tx) + s_x0[warp][lo] + tx;
+            tile_v[k] = s_g[warp][lo];
+        }
+        __syncwarp();
     }
 }
 
@@ -356,12 +420,14 @@ cudaError_t launch_compact_visible(const uint32_t *tiles, const uint32_t *depth_
 }
 
 cudaError_t launch_radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
-                              const uint32_t *n_dev, uint32_t n_cap, int shift, uint32_t *hist, cudaStream_t st) {
+                              const uint32_t *n_dev, uint32_t n_cap, int shift, uint32_t *hist, uint32_t *minmax,
+                              bool first, cudaStream_t st) {
     const int G = sort_blocks();
     NSrc ns{n_dev, n_cap};
-    k_radix_up<<<G, 256, 0, st>>>(kin, ns, shift, hist);
-    k_radix_scan<<<1, 1024, 0, st>>>(hist, G);
-    k_radix_down<<<G, 256, 0, st>>>(kin, vin, kout, vout, ns, shift, hist);
+    uint32_t *rowtot = hist + static_cast<size_t>(256) * kMaxSortBlocks;
+    k_radix_up<<<G, 256, 0, st>>>(kin, ns, shift, hist, minmax, first ? 1 : 0);
+    k_radix_rowscan<<<256, 256, 0, st>>>(hist, G, rowtot, minmax, shift, first ? 1 : 0);
+    k_radix_down<<<G, 256, 0, st>>>(kin, vin, kout, vout, ns, shift, hist, rowtot, minmax, first ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -385,9 +451,10 @@ cudaError_t launch_emit(const uint32_t *order, const uint32_t *dup_off, const Re
 }
 
 cudaError_t launch_ranges(const uint32_t *tile_k, uint32_t n_cap, uint2 *ranges, const Ctl *ctl, cudaStream_t st) {
-    const int G = sort_blocks();
     NSrc ns{&ctl->n_dup_c, n_cap};
-    k_ranges<<<G, 256, 0, st>>>(tile_k, ns, ranges);
+    // one thread per pair of the capacity (blocks past the device count exit at once)
+    const uint32_t blocks = n_cap == 0 ? 1 : min(static_cast<uint32_t>((n_cap + 255) / 256), 1u << 20);
+    k_ranges<<<blocks, 256, 0, st>>>(tile_k, ns, ranges);
     return cudaGetLastError();
 }
 
