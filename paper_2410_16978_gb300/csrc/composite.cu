@@ -3,13 +3,21 @@
 // and its exact backward with the per-Gaussian blend weight alpha*T that
 // drives contribution pruning (Sec. 3.2.2).
 //
-// Work layout: one CTA per tile.  Every warp walks the tile's list on its own
-// (no CTA-wide barriers, so a warp whose pixels are done leaves at once): the
-// forward warp owns an 8x4 pixel block (one pixel per lane), the backward warp
-// an 8x8 block (two pixels per lane, which halves the cost of reducing each
-// splat's gradient over the warp).  Tiles are launched heaviest first
-// (k_tile_order) so that the long lists do not end up in the last wave.  Compositing is FP32 FMA + MUFU work, not a
-// dense contraction, so no tensor cores are involved.
+// Work decomposition (compositing is FP32 FMA + MUFU work, not a dense
+// contraction, so no tensor cores are involved):
+//  * Forward: persistent warps take work items (tile, 8x4 pixel block) from a
+//    device queue in heaviest-first tile order and composite one pixel per
+//    lane until the block's 32 pixels are done.  Every kSeg list positions
+//    the warp stores each pixel's running state (T and the colour sum) as a
+//    checkpoint.
+//  * Both passes drop, 32 records at a time, the splats that provably stay
+//    below alpha = 1/255 over the warp's whole pixel block (see
+//    splat_reaches_block); list positions are kept, so nothing changes.
+//  * Backward: the blended prefix of a pixel can be thousands of splats long,
+//    and walking it serially would make the longest pixel the critical path
+//    of the whole kernel.  The checkpoints cut every 8x8 block's walk into
+//    segments of at most kSeg positions; persistent warps take (tile, block,
+//    segment) items from a queue and each starts from its checkpoint.
 //
 // splat_alpha() is the single definition of the per-(pixel, splat) alpha used
 // by both passes; every operation is an explicitly rounded intrinsic, so the
@@ -22,7 +30,8 @@ namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr float kLn2 = 0x1.62e430p-1f;
-constexpr int kThreads = 128;
+constexpr int kFwdThreads = 256;
+constexpr int kBwdThreads = 128;
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -43,31 +52,77 @@ __device__ __forceinline__ float splat_alpha(float px, float py, const float4 a,
     return fminf(kAlphaMax, ao);
 }
 
-// Pixel of lane `lane` of warp `warp`, j-th of its two pixels.
-__device__ __forceinline__ void pixel_of(int tile, int Tx, int warp, int lane, int j, int &x, int &y) {
-    x = (tile % Tx) * kTile + (warp & 1) * 8 + (lane & 7);
-    y = (tile / Tx) * kTile + (warp >> 1) * 8 + (lane >> 3) + 4 * j;
+__device__ __forceinline__ uint32_t ceil_seg(uint32_t n) { return (n + kSeg - 1) / kSeg; }
+
+// Can the splat reach alpha >= 1/255 at some pixel centre of the block
+// [x0, x1] x [y0, y1]?  The exponent A2 p^2 + G2 dy^2 (p = dx + beta dy) is a
+// sum of two non-positive terms, so max(A2 p^2) + max(G2 dy^2) over the block
+// bounds it from above; p is linear, so its range over the block comes from
+// the corners.  The test keeps a splat unless even that bound, raised by a
+// margin far above single-precision rounding of the per-pixel exponent, gives
+// alpha < 1/255: a dropped splat is one the per-pixel test would skip at every
+// pixel of the block, so dropping it changes no result.
+__device__ __forceinline__ bool splat_reaches_block(const float4 a, const float4 b, float x0, float x1, float y0,
+                                                    float y1) {
+    const float dylo = y0 - a.y, dyhi = y1 - a.y;
+    const float mdy = dylo > 0.f ? dylo : (dyhi < 0.f ? -dyhi : 0.f);
+    const float blo = a.w * dylo, bhi = a.w * dyhi;
+    const float plo = (x0 - a.x) + fminf(blo, bhi), phi = (x1 - a.x) + fmaxf(blo, bhi);
+    const float mp = plo > 0.f ? plo : (phi < 0.f ? -phi : 0.f);
+    const float emax = a.z * mp * mp + b.x * mdy * mdy;
+    return b.y * ex2_approx(emax + 1e-3f) >= kAlphaMin;
 }
 
-// Heaviest-first launch order of the tiles: a one-CTA counting sort of the
-// tiles by a logarithmic bucket of their work (list length, or the longest
-// blended prefix for the backward).  Ties keep no particular order; tiles are
-// independent, so the order changes no result.
-__global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ ranges,
-                                                     const uint32_t *__restrict__ work, int Tn,
-                                                     uint32_t *__restrict__ order) {
-    constexpr int kBuckets = 513;
-    __shared__ uint32_t s_cnt[kBuckets];
+// Exclusive scan over a 1024-thread block; returns the prefix, *total the sum.
+__device__ __forceinline__ uint32_t block_scan_1024(uint32_t v, uint32_t *s_w, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = s_w[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        s_w[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t base = warp > 0 ? s_w[warp - 1] : 0;
+    *total = s_w[31];
+    __syncthreads();
+    return base + x - v;
+}
+
+// Bucket of a work amount for a heaviest-first counting sort: a logarithmic
+// scale with 16 sub-steps per octave; zero work goes last.
+constexpr int kBuckets = 513;
+__device__ __forceinline__ int work_bucket(uint32_t w) {
+    if (w == 0) return kBuckets - 1;
+    const int lz = 31 - __clz(w);
+    const uint32_t sub = lz >= 4 ? (w >> (lz - 4)) & 15u : (w << (4 - lz)) & 15u;
+    return (kBuckets - 2) - (lz * 16 + static_cast<int>(sub));
+}
+
+// Tile work: list length (qwork == nullptr) or the longest blended prefix of
+// its four 8x8 blocks.
+__device__ __forceinline__ uint32_t tile_work(int t, const uint2 *ranges, const uint32_t *qwork) {
+    if (qwork) return max(max(qwork[4 * t], qwork[4 * t + 1]), max(qwork[4 * t + 2], qwork[4 * t + 3]));
+    return ranges[t].y - ranges[t].x;
+}
+
+// One CTA sorts the tiles heaviest first into order[] (ties in no particular
+// order: tiles are independent, so the order changes no result).
+__device__ void order_tiles(int Tn, uint32_t *order, uint32_t *s_cnt, const uint2 *ranges, const uint32_t *qwork) {
     for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) s_cnt[b] = 0;
     __syncthreads();
-    auto bucket = [&](int t) -> int {
-        const uint32_t w = work ? work[t] : ranges[t].y - ranges[t].x;
-        if (w == 0) return kBuckets - 1;                      // empty tiles last
-        const int lz = 31 - __clz(w);
-        const uint32_t sub = lz >= 4 ? (w >> (lz - 4)) & 15u : (w << (4 - lz)) & 15u;
-        return (kBuckets - 2) - (lz * 16 + static_cast<int>(sub));   // heavier -> smaller bucket
-    };
-    for (int t = threadIdx.x; t < Tn; t += blockDim.x) atomicAdd(&s_cnt[bucket(t)], 1u);
+    for (int t = threadIdx.x; t < Tn; t += blockDim.x) atomicAdd(&s_cnt[work_bucket(tile_work(t, ranges, qwork))], 1u);
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t run = 0;
@@ -78,12 +133,33 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ r
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < Tn; t += blockDim.x) order[atomicAdd(&s_cnt[bucket(t)], 1u)] = t;
+    for (int t = threadIdx.x; t < Tn; t += blockDim.x)
+        order[atomicAdd(&s_cnt[work_bucket(tile_work(t, ranges, qwork))], 1u)] = t;
+    __syncthreads();
 }
 
-// Each warp walks the tile's list on its own (no CTA barriers): it stages 32
-// records at a time in a warp-private shared buffer while the next 32 are
-// already in flight in registers, and stops once all 64 of its pixels are done.
+// Forward set-up (one CTA): heaviest-first tile order by list length, the
+// checkpoint base of every tile (exclusive prefix of its segment count), and
+// zeroed per-block work and queue.
+__global__ void __launch_bounds__(1024) k_fwd_setup(const uint2 *__restrict__ ranges, int Tn,
+                                                    uint32_t *__restrict__ order, uint32_t *__restrict__ seg_base,
+                                                    uint32_t *__restrict__ qwork, uint32_t *__restrict__ queue) {
+    __shared__ uint32_t s_cnt[kBuckets];
+    __shared__ uint32_t s_w[32];
+    if (threadIdx.x == 0) *queue = 0;
+    for (int q = threadIdx.x; q < 4 * Tn; q += blockDim.x) qwork[q] = 0;
+    order_tiles(Tn, order, s_cnt, ranges, nullptr);
+    uint32_t carry = 0;
+    for (int t0 = 0; t0 < Tn; t0 += 1024) {
+        const int t = t0 + threadIdx.x;
+        const uint32_t v = t < Tn ? ceil_seg(ranges[t].y - ranges[t].x) : 0;
+        uint32_t tot;
+        const uint32_t ex = block_scan_1024(v, s_w, &tot);
+        if (t < Tn) seg_base[t] = carry + ex;
+        carry += tot;
+    }
+}
+
 struct Chunk {
     float4 a, b;
     float c;
@@ -101,79 +177,118 @@ __device__ __forceinline__ void fetch_chunk(const uint32_t *__restrict__ list, c
     }
 }
 
-constexpr int kFwdThreads = 256;
-
-// Forward: 256 threads per tile, one pixel per lane; warp w owns the 8x4 block
-// ((w & 1) * 8, (w >> 1) * 4) and walks the list until its 32 pixels are done.
-__global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const uint32_t *__restrict__ order,
-                                                               const uint2 *__restrict__ ranges,
-                                                               const uint32_t *__restrict__ list,
-                                                               const Rec *__restrict__ rec, int W, int H, int Tx,
-                                                               float3 bg, float *__restrict__ image,
-                                                               float *__restrict__ alpha_out, float *__restrict__ t_final,
-                                                               uint32_t *__restrict__ n_contrib, float *__restrict__ c_sum,
-                                                               uint32_t *__restrict__ tile_work) {
+__global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(
+    const uint32_t *__restrict__ order, uint32_t *__restrict__ queue, const uint2 *__restrict__ ranges,
+    const uint32_t *__restrict__ list, const Rec *__restrict__ rec, int W, int H, int Tx, int Tn, float3 bg,
+    float *__restrict__ image, float *__restrict__ alpha_out, float *__restrict__ t_final,
+    uint32_t *__restrict__ n_contrib, float *__restrict__ c_sum, const uint32_t *__restrict__ seg_base,
+    float4 *__restrict__ ckpt, uint32_t *__restrict__ qwork) {
     __shared__ float4 s_a[kFwdThreads / 32][32], s_b[kFwdThreads / 32][32];
     __shared__ float s_c[kFwdThreads / 32][32];
-    __shared__ uint32_t s_wmax[kFwdThreads / 32];
+    __shared__ uint32_t s_pos[kFwdThreads / 32][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tile = order[blockIdx.x];
-    const uint2 rg = ranges[tile];
-    const int x = (tile % Tx) * kTile + (warp & 1) * 8 + (lane & 7);
-    const int y = (tile / Tx) * kTile + (warp >> 1) * 4 + (lane >> 3);
-    const bool inside = x < W && y < H;
-    const float px = x + 0.5f, py = y + 0.5f;
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t last = 0;
-    bool done = !inside;
-    Chunk nxt;
-    fetch_chunk(list, rec, rg.x + lane, rg.y, nxt);
-    for (uint32_t base = rg.x; base < rg.y; base += 32) {
-        if (__all_sync(FULL, done)) break;
-        __syncwarp();
-        s_a[warp][lane] = nxt.a;
-        s_b[warp][lane] = nxt.b;
-        s_c[warp][lane] = nxt.c;
-        __syncwarp();
-        fetch_chunk(list, rec, base + 32 + lane, rg.y, nxt);
-        const int cnt = min(32u, rg.y - base);
-        for (int k = 0; k < cnt && !done; ++k) {
-            const float4 a = s_a[warp][k], b = s_b[warp][k];
-            float p, dy, ex, ao;
-            const float al = splat_alpha(px, py, a, b, p, dy, ex, ao);
-            if (al < kAlphaMin) continue;
-            const float Tn = __fmul_rn(T, __fsub_rn(1.f, al));
-            if (Tn < kTMin) { done = true; break; }
-            const float w = __fmul_rn(al, T);
-            C0 = __fmaf_rn(b.z, w, C0);
-            C1 = __fmaf_rn(b.w, w, C1);
-            C2 = __fmaf_rn(s_c[warp][k], w, C2);
-            T = Tn;
-            last = base + k - rg.x + 1;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t total = static_cast<uint32_t>(Tn) * 8u;
+    const size_t plane = static_cast<size_t>(W) * H;
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(queue, 1u);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= total) break;
+        const int tile = order[item >> 3];
+        const int sub = item & 7;                       // 8x4 block: column sub & 1, row sub >> 1
+        const uint2 rg = ranges[tile];
+        const int lx = (sub & 1) * 8 + (lane & 7), ly = (sub >> 1) * 4 + (lane >> 3);
+        const int x = (tile % Tx) * kTile + lx;
+        const int y = (tile / Tx) * kTile + ly;
+        const bool inside = x < W && y < H;
+        const float px = x + 0.5f, py = y + 0.5f;
+        const float bx0 = (tile % Tx) * kTile + (sub & 1) * 8 + 0.5f, by0 = (tile / Tx) * kTile + (sub >> 1) * 4 + 0.5f;
+        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+        uint32_t last = 0;
+        bool done = !inside;
+        float4 *my_ckpt = ckpt + static_cast<size_t>(seg_base[tile]) * kTilePix + ly * kTile + lx;
+        Chunk nxt;
+        fetch_chunk(list, rec, rg.x + lane, rg.y, nxt);
+        for (uint32_t base = rg.x; base < rg.y; base += 32) {
+            if (__all_sync(FULL, done)) break;
+            const uint32_t pos0 = base - rg.x;
+            if (pos0 != 0 && pos0 % kSeg == 0)
+                my_ckpt[static_cast<size_t>(pos0 / kSeg) * kTilePix] = make_float4(T, C0, C1, C2);
+            const bool keep = base + lane < rg.y && splat_reaches_block(nxt.a, nxt.b, bx0, bx0 + 7.f, by0, by0 + 3.f);
+            const unsigned km = __ballot_sync(FULL, keep);
+            __syncwarp();
+            if (keep) {
+                const int slot = __popc(km & lt);
+                s_a[warp][slot] = nxt.a;
+                s_b[warp][slot] = nxt.b;
+                s_c[warp][slot] = nxt.c;
+                s_pos[warp][slot] = pos0 + lane;
+            }
+            __syncwarp();
+            fetch_chunk(list, rec, base + 32 + lane, rg.y, nxt);
+            const int cnt = __popc(km);
+            for (int k = 0; k < cnt && !done; ++k) {
+                const float4 a = s_a[warp][k], b = s_b[warp][k];
+                float p, dy, ex, ao;
+                const float al = splat_alpha(px, py, a, b, p, dy, ex, ao);
+                if (al < kAlphaMin) continue;
+                const float Tnew = __fmul_rn(T, __fsub_rn(1.f, al));
+                if (Tnew < kTMin) { done = true; break; }
+                const float w = __fmul_rn(al, T);
+                C0 = __fmaf_rn(b.z, w, C0);
+                C1 = __fmaf_rn(b.w, w, C1);
+                C2 = __fmaf_rn(s_c[warp][k], w, C2);
+                T = Tnew;
+                last = s_pos[warp][k] + 1;
+            }
         }
+        if (inside) {
+            const size_t pix = static_cast<size_t>(y) * W + x;
+            image[pix] = __fmaf_rn(T, bg.x, C0);
+            image[plane + pix] = __fmaf_rn(T, bg.y, C1);
+            image[2 * plane + pix] = __fmaf_rn(T, bg.z, C2);
+            if (alpha_out) alpha_out[pix] = 1.f - T;
+            t_final[pix] = T;
+            n_contrib[pix] = last;
+            c_sum[pix] = C0;
+            c_sum[plane + pix] = C1;
+            c_sum[2 * plane + pix] = C2;
+        }
+        const uint32_t wm = __reduce_max_sync(FULL, last);
+        if (lane == 0 && wm) atomicMax(&qwork[4 * tile + (sub & 1) + 2 * (sub >> 2)], wm);
     }
-    if (inside) {
-        const size_t plane = static_cast<size_t>(W) * H;
-        const size_t pix = static_cast<size_t>(y) * W + x;
-        image[pix] = __fmaf_rn(T, bg.x, C0);
-        image[plane + pix] = __fmaf_rn(T, bg.y, C1);
-        image[2 * plane + pix] = __fmaf_rn(T, bg.z, C2);
-        if (alpha_out) alpha_out[pix] = 1.f - T;
-        t_final[pix] = T;
-        n_contrib[pix] = last;
-        c_sum[pix] = C0;
-        c_sum[plane + pix] = C1;
-        c_sum[2 * plane + pix] = C2;
-    }
-    const uint32_t wm = __reduce_max_sync(FULL, last);
-    if (lane == 0) s_wmax[warp] = wm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t m = 0;
+}
+
+// Backward set-up (one CTA): heaviest-first tile order by the longest blended
+// prefix, then one work item (tile, 8x8 block q, segment s) for every segment
+// s < ceil(qwork[tile][q] / kSeg), written tile by tile in that order.
+__global__ void __launch_bounds__(1024) k_bwd_setup(const uint32_t *__restrict__ qwork, int Tn,
+                                                    uint32_t *__restrict__ order, uint2 *__restrict__ items,
+                                                    uint32_t *__restrict__ n_items, uint32_t *__restrict__ queue) {
+    __shared__ uint32_t s_cnt[kBuckets];
+    __shared__ uint32_t s_w[32];
+    if (threadIdx.x == 0) *queue = 0;
+    order_tiles(Tn, order, s_cnt, nullptr, qwork);
+    uint32_t carry = 0;
+    for (int r0 = 0; r0 < Tn; r0 += 1024) {
+        const int r = r0 + threadIdx.x;
+        uint32_t t = 0;
+        uint32_t ns[4] = {0, 0, 0, 0};
+        if (r < Tn) {
+            t = order[r];
 #pragma unroll
-        for (int w = 0; w < kFwdThreads / 32; ++w) m = max(m, s_wmax[w]);
-        tile_work[tile] = m;
+            for (int q = 0; q < 4; ++q) ns[q] = ceil_seg(qwork[4 * t + q]);
+        }
+        uint32_t tot;
+        uint32_t at = carry + block_scan_1024(ns[0] + ns[1] + ns[2] + ns[3], s_w, &tot);
+        if (r < Tn)
+#pragma unroll
+            for (uint32_t q = 0; q < 4; ++q)
+                for (uint32_t sg = 0; sg < ns[q]; ++sg) items[at++] = make_uint2(t, (q << 24) | sg);
+        carry += tot;
     }
+    if (threadIdx.x == 0) *n_items = carry;
 }
 
 // Reduce-scatter of 16 values across a warp: at step o (16, 8, 4, 2) each
@@ -199,149 +314,193 @@ __device__ __forceinline__ float reduce_scatter16(float v[16], int lane) {
 //   dL/da_i = dC.(c_i T_i - S_i/(1-a_i)) + dA T_N/(1-a_i)
 //           = T_i (dC.c_i) - (dC.(Csum - P_i) + T_N (dC.bg) - dA T_N)/(1-a_i)
 // where P_i is the running colour sum including splat i; dC.P_i is carried as
-// the scalar Q.  Each warp walks the list only up to the longest blended
-// prefix of its own 64 pixels, reduces each splat's 10 sums over its pixels
-// and adds them to the record gradient with vector atomics:
+// the scalar Q.  A work item covers list positions [s kSeg, (s+1) kSeg) of one
+// 8x8 block (two pixels per lane) and starts from the forward's checkpoint.
+// Each splat's 10 sums are reduced over the warp and added to the record
+// gradient with vector atomics:
 //   rec_grad[3g]   += (du, dv, dA2, dbeta)
 //   rec_grad[3g+1] += (dG2, dopacity, dr, dg)
 //   rec_grad[3g+2] += (db, sum of alpha*T, 0, 0);  contrib_max[g] = max(.., alpha*T)
-__global__ void __launch_bounds__(kThreads) k_composite_bwd(
-    const uint32_t *__restrict__ order, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ list,
-    const Rec *__restrict__ rec, int W, int H, int Tx, float3 bg, const float *__restrict__ t_final,
-    const uint32_t *__restrict__ n_contrib, const float *__restrict__ c_sum, const float *__restrict__ dL_dimage,
-    const float *__restrict__ dL_dalpha, const uint8_t *__restrict__ layer, uint32_t grad_layer_mask,
-    float4 *__restrict__ rec_grad, float *__restrict__ contrib_max) {
-    __shared__ float4 s_a[kThreads / 32][32], s_b[kThreads / 32][32];
-    __shared__ float s_c[kThreads / 32][32];
-    __shared__ uint32_t s_g[kThreads / 32][32];
+__global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
+    const uint2 *__restrict__ items, const uint32_t *__restrict__ n_items, uint32_t *__restrict__ queue,
+    const uint2 *__restrict__ ranges, const uint32_t *__restrict__ list, const Rec *__restrict__ rec, int W, int H,
+    int Tx, float3 bg, const float *__restrict__ t_final, const uint32_t *__restrict__ n_contrib,
+    const float *__restrict__ c_sum, const uint32_t *__restrict__ seg_base, const float4 *__restrict__ ckpt,
+    const uint32_t *__restrict__ qwork, const float *__restrict__ dL_dimage, const float *__restrict__ dL_dalpha,
+    const uint8_t *__restrict__ layer, uint32_t grad_layer_mask, float4 *__restrict__ rec_grad,
+    float *__restrict__ contrib_max) {
+    __shared__ float4 s_a[kBwdThreads / 32][32], s_b[kBwdThreads / 32][32];
+    __shared__ float s_c[kBwdThreads / 32][32];
+    __shared__ uint32_t s_g[kBwdThreads / 32][32];
+    __shared__ uint32_t s_pos[kBwdThreads / 32][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tile = order[blockIdx.x];
-    const uint2 rg = ranges[tile];
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t total = *n_items;
     const size_t plane = static_cast<size_t>(W) * H;
-    float px[2], py[2], TN[2], dC0[2], dC1[2], dC2[2], QC[2], K0[2], T[2], Q[2];
-    uint32_t nc[2];
+    for (;;) {
+        uint32_t id = 0;
+        if (lane == 0) id = atomicAdd(queue, 1u);
+        id = __shfl_sync(FULL, id, 0);
+        if (id >= total) break;
+        const uint2 it = items[id];
+        const int tile = static_cast<int>(it.x);
+        const int q = static_cast<int>(it.y >> 24);
+        const uint32_t seg = it.y & 0xFFFFFFu;
+        const uint2 rg = ranges[tile];
+        const uint32_t s0 = rg.x + seg * kSeg;
+        const uint32_t s1 = rg.x + min(min((seg + 1) * kSeg, qwork[4 * tile + q]), rg.y - rg.x);
+        const float4 *tck = ckpt + (static_cast<size_t>(seg_base[tile]) + seg) * kTilePix;
+        const float bx0 = (tile % Tx) * kTile + (q & 1) * 8 + 0.5f, by0 = (tile / Tx) * kTile + (q >> 1) * 8 + 0.5f;
+        float px[2], py[2], dC0[2], dC1[2], dC2[2], QC[2], K0[2], T[2], Q[2];
+        uint32_t nc[2];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        int x, y;
-        pixel_of(tile, Tx, warp, lane, j, x, y);
-        px[j] = x + 0.5f;
-        py[j] = y + 0.5f;
-        nc[j] = 0;
-        TN[j] = 1.f;
-        dC0[j] = dC1[j] = dC2[j] = QC[j] = 0.f;
-        float dA = 0.f;
-        if (x < W && y < H) {
-            const size_t pix = static_cast<size_t>(y) * W + x;
-            nc[j] = n_contrib[pix];
-            TN[j] = t_final[pix];
-            if (dL_dimage) {
-                dC0[j] = dL_dimage[pix];
-                dC1[j] = dL_dimage[plane + pix];
-                dC2[j] = dL_dimage[2 * plane + pix];
-            }
-            if (dL_dalpha) dA = dL_dalpha[pix];
-            QC[j] = dC0[j] * c_sum[pix] + dC1[j] * c_sum[plane + pix] + dC2[j] * c_sum[2 * plane + pix];
-        }
-        K0[j] = TN[j] * (dC0[j] * bg.x + dC1[j] * bg.y + dC2[j] * bg.z) - dA * TN[j];
-        T[j] = 1.f;
-        Q[j] = 0.f;
-    }
-    const uint32_t wbound = __reduce_max_sync(FULL, max(nc[0], nc[1]));
-    const uint32_t stop = rg.x + min(wbound, rg.y - rg.x);
-    Chunk nxt;
-    fetch_chunk(list, rec, rg.x + lane, stop, nxt);
-    for (uint32_t base = rg.x; base < stop; base += 32) {
-        __syncwarp();
-        s_a[warp][lane] = nxt.a;
-        s_b[warp][lane] = nxt.b;
-        s_c[warp][lane] = nxt.c;
-        s_g[warp][lane] = nxt.g;
-        __syncwarp();
-        fetch_chunk(list, rec, base + 32 + lane, stop, nxt);
-        const int cnt = min(32u, stop - base);
-        for (int k = 0; k < cnt; ++k) {
-            const uint32_t pos = base + k - rg.x;
-            const float4 a = s_a[warp][k], b = s_b[warp][k];
-            const float cb = s_c[warp][k];
-            float p[2], dy[2], ex[2], ao[2], al[2];
-            al[0] = splat_alpha(px[0], py[0], a, b, p[0], dy[0], ex[0], ao[0]);
-            al[1] = splat_alpha(px[1], py[1], a, b, p[1], dy[1], ex[1], ao[1]);
-            bool act[2];
-            act[0] = pos < nc[0] && al[0] >= kAlphaMin;
-            act[1] = pos < nc[1] && al[1] >= kAlphaMin;
-            if (!__any_sync(FULL, act[0] || act[1])) continue;
-            // v: du, dv, dA2, dbeta, dG2, dopacity, dr, dg, db, sum of alpha*T (10..15 unused)
-            float v[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float wmx = 0.f;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                if (!act[j]) continue;
-                const float dcc = dC0[j] * b.z + dC1[j] * b.w + dC2[j] * cb;
-                const float wgt = __fmul_rn(al[j], T[j]);
-                Q[j] = fmaf(wgt, dcc, Q[j]);
-                const float inv = __frcp_rn(1.f - al[j]);
-                const float dLda = T[j] * dcc - ((QC[j] - Q[j]) + K0[j]) * inv;
-                v[6] += wgt * dC0[j];
-                v[7] += wgt * dC1[j];
-                v[8] += wgt * dC2[j];
-                if (ao[j] < kAlphaMax) {
-                    const float dLde = dLda * al[j] * kLn2;
-                    const float A2p = a.z * p[j];
-                    v[5] += dLda * ex[j];
-                    v[2] += dLde * p[j] * p[j];
-                    v[3] += dLde * 2.f * A2p * dy[j];
-                    v[4] += dLde * dy[j] * dy[j];
-                    v[0] -= dLde * 2.f * A2p;
-                    v[1] -= dLde * (2.f * A2p * a.w + 2.f * b.x * dy[j]);
+        for (int j = 0; j < 2; ++j) {
+            const int lx = (q & 1) * 8 + (lane & 7), ly = (q >> 1) * 8 + (lane >> 3) + 4 * j;
+            const int x = (tile % Tx) * kTile + lx, y = (tile / Tx) * kTile + ly;
+            px[j] = x + 0.5f;
+            py[j] = y + 0.5f;
+            nc[j] = 0;
+            dC0[j] = dC1[j] = dC2[j] = QC[j] = K0[j] = 0.f;
+            T[j] = 1.f;
+            Q[j] = 0.f;
+            if (x < W && y < H) {
+                const size_t pix = static_cast<size_t>(y) * W + x;
+                const uint32_t n = n_contrib[pix];
+                if (n > seg * kSeg) {
+                    nc[j] = n;
+                    const float TN = t_final[pix];
+                    float dA = 0.f;
+                    if (dL_dimage) {
+                        dC0[j] = dL_dimage[pix];
+                        dC1[j] = dL_dimage[plane + pix];
+                        dC2[j] = dL_dimage[2 * plane + pix];
+                    }
+                    if (dL_dalpha) dA = dL_dalpha[pix];
+                    QC[j] = dC0[j] * c_sum[pix] + dC1[j] * c_sum[plane + pix] + dC2[j] * c_sum[2 * plane + pix];
+                    K0[j] = TN * (dC0[j] * bg.x + dC1[j] * bg.y + dC2[j] * bg.z) - dA * TN;
+                    if (seg > 0) {
+                        const float4 ck = tck[ly * kTile + lx];
+                        T[j] = ck.x;
+                        Q[j] = dC0[j] * ck.y + dC1[j] * ck.z + dC2[j] * ck.w;
+                    }
                 }
-                v[9] += wgt;
-                wmx = fmaxf(wmx, wgt);
-                T[j] = __fmul_rn(T[j], __fsub_rn(1.f, al[j]));
             }
-            const float sv = reduce_scatter16(v, lane);
-            // value i sits in lane 2i: lanes 0, 8, 16 gather (i, i+1, i+2, i+3)
-            const float s1 = __shfl_down_sync(FULL, sv, 2);
-            const float s2 = __shfl_down_sync(FULL, sv, 4);
-            const float s3 = __shfl_down_sync(FULL, sv, 6);
-            const uint32_t smx = __reduce_max_sync(FULL, __float_as_uint(wmx));
-            const uint32_t g = s_g[warp][k];
-            const bool train = (grad_layer_mask >> layer[g]) & 1u;
-            if (lane == 0 && train) atomicAdd(&rec_grad[3 * g], make_float4(sv, s1, s2, s3));
-            if (lane == 8 && train) atomicAdd(&rec_grad[3 * g + 1], make_float4(sv, s1, s2, s3));
-            if (lane == 16) atomicAdd(reinterpret_cast<float2 *>(&rec_grad[3 * g + 2]), make_float2(train ? sv : 0.f, s1));
-            if (lane == 1 && contrib_max) atomicMax(reinterpret_cast<unsigned int *>(&contrib_max[g]), smx);
+        }
+        Chunk nxt;
+        fetch_chunk(list, rec, s0 + lane, s1, nxt);
+        for (uint32_t base = s0; base < s1; base += 32) {
+            const bool keep = base + lane < s1 && splat_reaches_block(nxt.a, nxt.b, bx0, bx0 + 7.f, by0, by0 + 7.f);
+            const unsigned km = __ballot_sync(FULL, keep);
+            __syncwarp();
+            if (keep) {
+                const int slot = __popc(km & lt);
+                s_a[warp][slot] = nxt.a;
+                s_b[warp][slot] = nxt.b;
+                s_c[warp][slot] = nxt.c;
+                s_g[warp][slot] = nxt.g;
+                s_pos[warp][slot] = base + lane - rg.x;
+            }
+            __syncwarp();
+            fetch_chunk(list, rec, base + 32 + lane, s1, nxt);
+            const int cnt = __popc(km);
+            for (int k = 0; k < cnt; ++k) {
+                const uint32_t pos = s_pos[warp][k];
+                const float4 a = s_a[warp][k], b = s_b[warp][k];
+                const float cb = s_c[warp][k];
+                float p[2], dy[2], ex[2], ao[2], al[2];
+                al[0] = splat_alpha(px[0], py[0], a, b, p[0], dy[0], ex[0], ao[0]);
+                al[1] = splat_alpha(px[1], py[1], a, b, p[1], dy[1], ex[1], ao[1]);
+                bool act[2];
+                act[0] = pos < nc[0] && al[0] >= kAlphaMin;
+                act[1] = pos < nc[1] && al[1] >= kAlphaMin;
+                if (!__any_sync(FULL, act[0] || act[1])) continue;
+                // v: du, dv, dA2, dbeta, dG2, dopacity, dr, dg, db, sum of alpha*T (10..15 unused)
+                float v[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float wmx = 0.f;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    if (!act[j]) continue;
+                    const float dcc = dC0[j] * b.z + dC1[j] * b.w + dC2[j] * cb;
+                    const float wgt = __fmul_rn(al[j], T[j]);
+                    Q[j] = fmaf(wgt, dcc, Q[j]);
+                    const float inv = __frcp_rn(1.f - al[j]);
+                    const float dLda = T[j] * dcc - ((QC[j] - Q[j]) + K0[j]) * inv;
+                    v[6] += wgt * dC0[j];
+                    v[7] += wgt * dC1[j];
+                    v[8] += wgt * dC2[j];
+                    if (ao[j] < kAlphaMax) {
+                        const float dLde = dLda * al[j] * kLn2;
+                        const float A2p = a.z * p[j];
+                        v[5] += dLda * ex[j];
+                        v[2] += dLde * p[j] * p[j];
+                        v[3] += dLde * 2.f * A2p * dy[j];
+                        v[4] += dLde * dy[j] * dy[j];
+                        v[0] -= dLde * 2.f * A2p;
+                        v[1] -= dLde * (2.f * A2p * a.w + 2.f * b.x * dy[j]);
+                    }
+                    v[9] += wgt;
+                    wmx = fmaxf(wmx, wgt);
+                    T[j] = __fmul_rn(T[j], __fsub_rn(1.f, al[j]));
+                }
+                const float sv = reduce_scatter16(v, lane);
+                // value i sits in lane 2i: lanes 0, 8, 16 gather (i, i+1, i+2, i+3)
+                const float r1 = __shfl_down_sync(FULL, sv, 2);
+                const float r2 = __shfl_down_sync(FULL, sv, 4);
+                const float r3 = __shfl_down_sync(FULL, sv, 6);
+                const uint32_t smx = __reduce_max_sync(FULL, __float_as_uint(wmx));
+                const uint32_t g = s_g[warp][k];
+                const bool train = (grad_layer_mask >> layer[g]) & 1u;
+                if (lane == 0 && train) atomicAdd(&rec_grad[3 * g], make_float4(sv, r1, r2, r3));
+                if (lane == 8 && train) atomicAdd(&rec_grad[3 * g + 1], make_float4(sv, r1, r2, r3));
+                if (lane == 16)
+                    atomicAdd(reinterpret_cast<float2 *>(&rec_grad[3 * g + 2]), make_float2(train ? sv : 0.f, r1));
+                if (lane == 1 && contrib_max) atomicMax(reinterpret_cast<unsigned int *>(&contrib_max[g]), smx);
+            }
         }
     }
+}
+
+// Blocks that fill every SM once for a persistent kernel.
+template <class K>
+int persistent_blocks(K kernel, int threads) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0);
+    return max(1, sms) * max(1, per);
 }
 
 }  // namespace
 
-cudaError_t launch_tile_order(const uint2 *ranges, const uint32_t *work, int Tn, uint32_t *order, cudaStream_t st) {
-    if (Tn == 0) return cudaSuccess;
-    k_tile_order<<<1, 1024, 0, st>>>(ranges, work, Tn, order);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_composite_forward(const uint32_t *order, const uint2 *ranges, const uint32_t *list, const Rec *rec,
-                                     int W, int H, int Tx, int Ty, float3 bg, float *image, float *alpha,
-                                     float *t_final, uint32_t *n_contrib, float *c_sum, uint32_t *tile_work,
+cudaError_t launch_composite_forward(const CompositeBufs &cb, const uint2 *ranges, const uint32_t *list,
+                                     const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, float *image,
+                                     float *alpha, float *t_final, uint32_t *n_contrib, float *c_sum,
                                      cudaStream_t st) {
     const int tiles = Tx * Ty;
     if (tiles == 0) return cudaSuccess;
-    k_composite_fwd<<<tiles, kFwdThreads, 0, st>>>(order, ranges, list, rec, W, H, Tx, bg, image, alpha, t_final,
-                                                   n_contrib, c_sum, tile_work);
+    k_fwd_setup<<<1, 1024, 0, st>>>(ranges, tiles, cb.order, cb.seg_base, cb.qwork, cb.queue);
+    static int blocks = 0;
+    if (!blocks) blocks = persistent_blocks(k_composite_fwd, kFwdThreads);
+    const int b = min(blocks, (tiles * 8 + kFwdThreads / 32 - 1) / (kFwdThreads / 32));
+    k_composite_fwd<<<b, kFwdThreads, 0, st>>>(cb.order, cb.queue, ranges, list, rec, W, H, Tx, tiles, bg, image,
+                                               alpha, t_final, n_contrib, c_sum, cb.seg_base, cb.ckpt, cb.qwork);
     return cudaGetLastError();
 }
 
-cudaError_t launch_composite_backward(const uint32_t *order, const uint2 *ranges, const uint32_t *list, const Rec *rec,
-                                      int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
+cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *ranges, const uint32_t *list,
+                                      const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
                                       const uint32_t *n_contrib, const float *c_sum, const float *dL_dimage,
                                       const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
                                       float4 *rec_grad, float *contrib_max, cudaStream_t st) {
     const int tiles = Tx * Ty;
     if (tiles == 0) return cudaSuccess;
-    k_composite_bwd<<<tiles, kThreads, 0, st>>>(order, ranges, list, rec, W, H, Tx, bg, t_final, n_contrib, c_sum,
-                                                dL_dimage, dL_dalpha, layer, grad_layer_mask, rec_grad, contrib_max);
+    k_bwd_setup<<<1, 1024, 0, st>>>(cb.qwork, tiles, cb.order_bwd, cb.items, cb.n_items, cb.queue);
+    static int blocks = 0;
+    if (!blocks) blocks = persistent_blocks(k_composite_bwd, kBwdThreads);
+    k_composite_bwd<<<blocks, kBwdThreads, 0, st>>>(cb.items, cb.n_items, cb.queue, ranges, list, rec, W, H, Tx, bg,
+                                                    t_final, n_contrib, c_sum, cb.seg_base, cb.ckpt, cb.qwork,
+                                                    dL_dimage, dL_dalpha, layer, grad_layer_mask, rec_grad,
+                                                    contrib_max);
     return cudaGetLastError();
 }
 

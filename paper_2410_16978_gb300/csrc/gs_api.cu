@@ -40,8 +40,12 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     o.hist = take((static_cast<size_t>(256) * kMaxSortBlocks + 256) * 4);   // + digit totals
     o.rec_grad = take(N * sizeof(Rec));
     o.tile_order = take(static_cast<size_t>(o.Tn) * 4);
-    o.tile_work = take(static_cast<size_t>(o.Tn) * 4);
     o.tile_order_bwd = take(static_cast<size_t>(o.Tn) * 4);
+    o.seg_base = take(static_cast<size_t>(o.Tn) * 4);
+    o.qwork = take(static_cast<size_t>(o.Tn) * 16);
+    const size_t segs = D / kSeg + static_cast<size_t>(o.Tn) + 1;   // >= sum over tiles of ceil(len / kSeg)
+    o.ckpt = take(segs * kTilePix * sizeof(float4));
+    o.items = take(4 * segs * sizeof(uint2));
     o.tile_k[0] = take(D * 4); o.tile_k[1] = take(D * 4);
     o.tile_v[0] = take(D * 4); o.tile_v[1] = take(D * 4);
     o.total = off;
@@ -50,13 +54,17 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
 }
 
 int64_t capacity_for(int64_t n, int W, int H, size_t ws_bytes) {
-    Layout L0;
-    if (!make_layout(n, W, H, 0, &L0) || ws_bytes < L0.total) return -1;
-    int64_t cap = static_cast<int64_t>((ws_bytes - L0.total) / 16);
-    if (cap > 0xFFFFFFFFLL) cap = 0xFFFFFFFFLL;
+    // The layout size grows monotonically with the capacity: binary search the
+    // largest capacity that fits, so a workspace of gs_render_workspace_size(C)
+    // bytes always holds at least C pairs.
     Layout L;
-    while (cap > 0 && (!make_layout(n, W, H, cap, &L) || L.total > ws_bytes)) cap -= 64;
-    return cap < 0 ? 0 : cap;
+    if (!make_layout(n, W, H, 0, &L) || ws_bytes < L.total) return -1;
+    int64_t lo = 0, hi = 0xFFFFFFFFLL;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (make_layout(n, W, H, mid, &L) && L.total <= ws_bytes) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
 }  // namespace gs
@@ -165,6 +173,20 @@ int tile_sort_passes(int Tn) {
     int bits = 0;
     while ((1LL << bits) < Tn) ++bits;
     return (bits + 7) / 8;
+}
+
+CompositeBufs composite_bufs(void *ws, const Layout &L) {
+    Ctl *ctl = at<Ctl>(ws, L.ctl);
+    CompositeBufs cb;
+    cb.order = at<uint32_t>(ws, L.tile_order);
+    cb.order_bwd = at<uint32_t>(ws, L.tile_order_bwd);
+    cb.seg_base = at<uint32_t>(ws, L.seg_base);
+    cb.qwork = at<uint32_t>(ws, L.qwork);
+    cb.ckpt = at<float4>(ws, L.ckpt);
+    cb.items = at<uint2>(ws, L.items);
+    cb.n_items = &ctl->n_items;
+    cb.queue = &ctl->fwd_queue;
+    return cb;
 }
 
 int workspace_layout(const gs_scene *s, const CamView &cv, void *ws, size_t ws_bytes, Layout *L) {
@@ -290,12 +312,10 @@ int gs_render(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mas
         if ((rc = cuda_check(launch_ranges(tk[fin], cap, ranges, ctl, st), "ranges")) != GS_OK) return rc;
     }
     Stage sg(GS_STAGE_COMPOSITE, st, 2);
-    uint32_t *order_f = at<uint32_t>(ws, L.tile_order);
-    if ((rc = cuda_check(launch_tile_order(ranges, nullptr, L.Tn, order_f, st), "tile order")) != GS_OK) return rc;
-    return cuda_check(launch_composite_forward(order_f, ranges, tv[fin], rec, cv.W, cv.H, cv.Tx, cv.Ty,
+    return cuda_check(launch_composite_forward(composite_bufs(ws, L), ranges, tv[fin], rec, cv.W, cv.H, cv.Tx, cv.Ty,
                                                make_float3(bg[0], bg[1], bg[2]), image, alpha,
                                                at<float>(ws, L.t_final), at<uint32_t>(ws, L.n_contrib),
-                                               at<float>(ws, L.c_sum), at<uint32_t>(ws, L.tile_work), st),
+                                               at<float>(ws, L.c_sum), st),
                       "composite");
 }
 
@@ -322,11 +342,7 @@ int gs_render_backward(const gs_scene *scene, const gs_camera *camera, const flo
     if ((rc = cuda_check(cudaMemsetAsync(rec_grad, 0, static_cast<size_t>(sv.n) * sizeof(Rec), st), "memset grad")) !=
         GS_OK)
         return rc;
-    uint32_t *order_b = at<uint32_t>(ws, L.tile_order_bwd);
-    if ((rc = cuda_check(launch_tile_order(at<uint2>(ws, L.ranges), at<uint32_t>(ws, L.tile_work), L.Tn, order_b, st),
-                         "tile order")) != GS_OK)
-        return rc;
-    if ((rc = cuda_check(launch_composite_backward(order_b, at<uint2>(ws, L.ranges), at<uint32_t>(ws, L.tile_v[fin]),
+    if ((rc = cuda_check(launch_composite_backward(composite_bufs(ws, L), at<uint2>(ws, L.ranges), at<uint32_t>(ws, L.tile_v[fin]),
                                                    at<Rec>(ws, L.rec), cv.W, cv.H, cv.Tx, cv.Ty,
                                                    make_float3(bg[0], bg[1], bg[2]), at<float>(ws, L.t_final),
                                                    at<uint32_t>(ws, L.n_contrib), at<float>(ws, L.c_sum), dL_dimage,

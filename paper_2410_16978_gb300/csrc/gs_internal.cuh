@@ -19,6 +19,7 @@ constexpr int kMaxSortBlocks = 1024;           // histogram rows reserved in the
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 0x1.010102p-8f;    // 1/255 rounded to float
 constexpr float kTMin = 1e-4f;
+constexpr uint32_t kSeg = 256;                 // list positions per backward segment (checkpoint stride)
 
 // Per-Gaussian record written by the preprocess and gathered by the compositor.
 // a = (u, v, A2, beta), b = (G2, opacity, r, g), c = (b, depth, rect01, rect23)
@@ -39,9 +40,12 @@ struct Ctl {
     uint32_t scan_total;   // scratch total of the last scan
     uint32_t depth_mm[2];  // ~min and max of the depth keys (radix pass skipping)
     uint32_t tile_mm[2];   // ~min and max of the tile keys
-    uint32_t pad;
+    uint32_t fwd_queue;    // next work item of the persistent forward compositor
+    uint32_t bwd_queue;    // next work item of the persistent backward compositor
+    uint32_t n_items;      // backward work items (tile, 8x8 block, segment)
+    uint32_t pad[14];
 };
-static_assert(sizeof(Ctl) == 64, "Ctl layout");
+static_assert(sizeof(Ctl) == 128, "Ctl layout");
 
 // Workspace carve-up.  Every region starts on a 256-byte boundary.
 struct Layout {
@@ -49,7 +53,8 @@ struct Layout {
     int W = 0, H = 0, Tx = 0, Ty = 0, Tn = 0;
     size_t ctl = 0, rec = 0, tiles = 0, depth = 0, sort_k[2] = {0, 0}, sort_v[2] = {0, 0}, dup_off = 0,
            tile_k[2] = {0, 0}, tile_v[2] = {0, 0}, ranges = 0, t_final = 0, n_contrib = 0, c_sum = 0,
-           partials = 0, hist = 0, rec_grad = 0, tile_order = 0, tile_work = 0, tile_order_bwd = 0, total = 0;
+           partials = 0, hist = 0, rec_grad = 0, tile_order = 0, tile_order_bwd = 0, seg_base = 0, qwork = 0,
+           ckpt = 0, items = 0, total = 0;
 };
 
 // Returns false when sizes overflow.
@@ -119,14 +124,23 @@ cudaError_t launch_ranges(const uint32_t *tile_k, uint32_t n_cap, uint2 *ranges,
 cudaError_t launch_prune(const float *contrib_max, int n, float thr, uint8_t *keep, int32_t *keep_index,
                          int64_t *n_keep, uint32_t *partials, cudaStream_t st);
 
-// Heaviest-first tile order by list length (work == nullptr) or by work[t].
-cudaError_t launch_tile_order(const uint2 *ranges, const uint32_t *work, int Tn, uint32_t *order, cudaStream_t st);
-cudaError_t launch_composite_forward(const uint32_t *order, const uint2 *ranges, const uint32_t *list, const Rec *rec,
-                                     int W, int H, int Tx, int Ty, float3 bg, float *image, float *alpha,
-                                     float *t_final, uint32_t *n_contrib, float *c_sum, uint32_t *tile_work,
+// Scratch of the compositor kernels (all in the render workspace).
+struct CompositeBufs {
+    uint32_t *order;      // [Tn] forward tile order (heaviest first)
+    uint32_t *order_bwd;  // [Tn] backward tile order
+    uint32_t *seg_base;   // [Tn] first checkpoint segment of each tile
+    uint32_t *qwork;      // [4 Tn] longest blended prefix of each 8x8 block
+    float4 *ckpt;         // [segments][256] per-pixel (T, colour sum) every kSeg positions
+    uint2 *items;         // backward work items (tile, block << 24 | segment)
+    uint32_t *n_items;
+    uint32_t *queue;      // work-queue counter (forward and backward reuse it in turn)
+};
+cudaError_t launch_composite_forward(const CompositeBufs &cb, const uint2 *ranges, const uint32_t *list,
+                                     const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, float *image,
+                                     float *alpha, float *t_final, uint32_t *n_contrib, float *c_sum,
                                      cudaStream_t st);
-cudaError_t launch_composite_backward(const uint32_t *order, const uint2 *ranges, const uint32_t *list, const Rec *rec,
-                                      int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
+cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *ranges, const uint32_t *list,
+                                      const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
                                       const uint32_t *n_contrib, const float *c_sum, const float *dL_dimage,
                                       const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
                                       float4 *rec_grad, float *contrib_max, cudaStream_t st);

@@ -66,9 +66,10 @@ def test_frozen_layers_get_zero_gradient():
     frozen = ((glm >> sc.layer.astype(np.int64)) & 1) == 0
     for f in FIELDS:
         assert np.all(g[f][frozen] == 0)
-        # float atomics across tiles sum in a run-dependent order: equal up to rounding
+        # float atomics sum in a run-dependent order: equal up to rounding, and
+        # both runs meet the oracle bar, so they agree within it
         scale = np.abs(gfull[f]).max()
-        assert np.abs(g[f][~frozen] - gfull[f][~frozen]).max() <= 1e-6 * scale, f
+        assert np.abs(g[f][~frozen] - gfull[f][~frozen]).max() <= GRAD_TOL * scale, f
 
 
 def test_autograd_function_matches_direct_backward():
@@ -84,8 +85,8 @@ def test_autograd_function_matches_direct_backward():
     ds2 = DeviceScene.from_host(sc)
     g = rast2.backward(ds2, cam, bg, torch.from_numpy(dimg).cuda(), torch.from_numpy(dal).cuda())
     for f, p in zip(FIELDS, ds.params()):
-        # float atomics across tiles sum in a run-dependent order: equal up to rounding
-        assert (p.grad - g[f]).abs().max().item() <= 1e-6 * g[f].abs().max().item(), f
+        # float atomics sum in a run-dependent order: equal up to rounding
+        assert (p.grad - g[f]).abs().max().item() <= GRAD_TOL * g[f].abs().max().item(), f
 
 
 def test_prune_matches_oracle():
