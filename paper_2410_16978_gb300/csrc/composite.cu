@@ -117,20 +117,19 @@ __device__ __forceinline__ uint32_t tile_work(int t, const uint2 *ranges, const 
     return ranges[t].y - ranges[t].x;
 }
 
-// One CTA sorts the tiles heaviest first into order[] (ties in no particular
-// order: tiles are independent, so the order changes no result).
-__device__ void order_tiles(int Tn, uint32_t *order, uint32_t *s_cnt, const uint2 *ranges, const uint32_t *qwork) {
+// One CTA (1024 threads) sorts the tiles heaviest first into order[] (ties in
+// no particular order: tiles are independent, so the order changes no result).
+__device__ void order_tiles(int Tn, uint32_t *order, uint32_t *s_cnt, uint32_t *s_w, const uint2 *ranges,
+                            const uint32_t *qwork) {
     for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) s_cnt[b] = 0;
     __syncthreads();
     for (int t = threadIdx.x; t < Tn; t += blockDim.x) atomicAdd(&s_cnt[work_bucket(tile_work(t, ranges, qwork))], 1u);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int b = 0; b < kBuckets; ++b) {
-            const uint32_t c = s_cnt[b];
-            s_cnt[b] = run;
-            run += c;
-        }
+    {
+        const uint32_t c = threadIdx.x < kBuckets ? s_cnt[threadIdx.x] : 0;
+        uint32_t tot;
+        const uint32_t ex = block_scan_1024(c, s_w, &tot);
+        if (threadIdx.x < kBuckets) s_cnt[threadIdx.x] = ex;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < Tn; t += blockDim.x)
@@ -148,7 +147,7 @@ __global__ void __launch_bounds__(1024) k_fwd_setup(const uint2 *__restrict__ ra
     __shared__ uint32_t s_w[32];
     if (threadIdx.x == 0) *queue = 0;
     for (int q = threadIdx.x; q < 4 * Tn; q += blockDim.x) qwork[q] = 0;
-    order_tiles(Tn, order, s_cnt, ranges, nullptr);
+    order_tiles(Tn, order, s_cnt, s_w, ranges, nullptr);
     uint32_t carry = 0;
     for (int t0 = 0; t0 < Tn; t0 += 1024) {
         const int t = t0 + threadIdx.x;
@@ -269,7 +268,7 @@ __global__ void __launch_bounds__(1024) k_bwd_setup(const uint32_t *__restrict__
     __shared__ uint32_t s_cnt[kBuckets];
     __shared__ uint32_t s_w[32];
     if (threadIdx.x == 0) *queue = 0;
-    order_tiles(Tn, order, s_cnt, nullptr, qwork);
+    order_tiles(Tn, order, s_cnt, s_w, nullptr, qwork);
     uint32_t carry = 0;
     for (int r0 = 0; r0 < Tn; r0 += 1024) {
         const int r = r0 + threadIdx.x;

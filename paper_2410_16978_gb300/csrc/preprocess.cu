@@ -166,12 +166,25 @@ __global__ void __launch_bounds__(128) k_preprocess(SceneView s, CamView c, uint
                 float b[K];
                 sh_basis<DEG>(dx / dn, dy / dn, dz / dn, b);
                 const int64_t base = static_cast<int64_t>(i) * K * 3;
+                float shv[3 * K];
+                if (s.dtype_sh == GS_DTYPE_F32 && (3 * K) % 4 == 0) {
+                    // 16-byte loads of this Gaussian's coefficients (its row starts 16-byte aligned)
+                    const float4 *src = reinterpret_cast<const float4 *>(static_cast<const float *>(s.sh) + base);
+#pragma unroll
+                    for (int k = 0; k < 3 * K / 4; ++k) {
+                        const float4 v = src[k];
+                        shv[4 * k] = v.x; shv[4 * k + 1] = v.y; shv[4 * k + 2] = v.z; shv[4 * k + 3] = v.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 3 * K; ++k) shv[k] = ld_half(s.sh, base + k, s.dtype_sh);
+                }
                 float rgb[3];
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
-                    float acc = b[0] * ld_half(s.sh, base + ch, s.dtype_sh);
+                    float acc = b[0] * shv[ch];
 #pragma unroll
-                    for (int k = 1; k < K; ++k) acc = acc + b[k] * ld_half(s.sh, base + 3 * k + ch, s.dtype_sh);
+                    for (int k = 1; k < K; ++k) acc = acc + b[k] * shv[3 * k + ch];
                     rgb[ch] = fmaxf(acc + 0.5f, 0.0f);
                 }
                 const float NHL = -0x1.715476p-1f;   // -log2(e)/2

@@ -208,18 +208,26 @@ __global__ void __launch_bounds__(256) k_radix_up(const uint32_t *__restrict__ k
     uint32_t beg, end;
     block_range(ns.get(), beg, end);
     uint32_t kinv = 0, kmax = 0;
-    for (uint32_t base = beg; base < end; base += 256) {
-        const uint32_t i = base + threadIdx.x;
-        const bool valid = i < end;
-        uint32_t key = 0, d = 256u + lane;
-        if (valid) {
-            key = keys[i];
-            d = (key >> shift) & 255u;
-            kinv = max(kinv, ~key);
-            kmax = max(kmax, key);
+    for (uint32_t t0 = beg; t0 < end; t0 += kSortTile) {
+        uint32_t key[kSortItems];
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {        // issue all loads of the tile first
+            const uint32_t i = t0 + r * 256 + threadIdx.x;
+            key[r] = i < end ? keys[i] : 0;
         }
-        const unsigned peers = __match_any_sync(FULL, d);
-        if (valid && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&s_h[warp][d], __popc(peers));
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            const uint32_t i = t0 + r * 256 + threadIdx.x;
+            const bool valid = i < end;
+            uint32_t d = 256u + lane;
+            if (valid) {
+                d = (key[r] >> shift) & 255u;
+                kinv = max(kinv, ~key[r]);
+                kmax = max(kmax, key[r]);
+            }
+            const unsigned peers = __match_any_sync(FULL, d);
+            if (valid && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&s_h[warp][d], __popc(peers));
+        }
     }
     if (first) {
         kinv = __reduce_max_sync(FULL, kinv);
@@ -265,15 +273,21 @@ __global__ void __launch_bounds__(256) k_radix_rowscan(uint32_t *__restrict__ hi
     if (threadIdx.x == 0) rowtot[blockIdx.x] = tot;
 }
 
-// Stable scatter: items are ranked in (round, warp, lane) = index order.
+// Stable scatter.  A block walks its range in tiles of 2048 items; warp w
+// ranks the contiguous run [256 w, 256 w + 256) of the tile in 8 rounds of 32
+// with warp-private digit counters, so items are ranked in (warp, round,
+// lane) = index order.  The tile is then sorted by digit in shared memory and
+// written out in that order, so consecutive threads store consecutive
+// addresses of the same digit's run.
 __global__ void __launch_bounds__(256) k_radix_down(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                     uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, NSrc ns,
                                                     int shift, const uint32_t *__restrict__ hist,
                                                     const uint32_t *__restrict__ rowtot,
                                                     const uint32_t *__restrict__ mm, int first) {
-    __shared__ uint32_t s_off[256];
-    __shared__ uint32_t s_wc[8][256];
-    __shared__ uint32_t s_rt[256];
+    __shared__ uint32_t s_off[256];       // global offset of each digit for this block's next tile
+    __shared__ uint32_t s_wc[8][256];     // per-warp digit counts, then per-warp digit bases
+    __shared__ uint32_t s_lstart[256];    // start of each digit's run in the locally sorted tile
+    __shared__ uint32_t s_key[kSortTile], s_val[kSortTile];
     __shared__ uint32_t s_w[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t beg, end;
@@ -290,44 +304,63 @@ __global__ void __launch_bounds__(256) k_radix_down(const uint32_t *__restrict__
         const uint32_t digit_base = block_scan_256(rowtot[threadIdx.x], s_w, &tot);
         s_off[threadIdx.x] = digit_base + hist[static_cast<size_t>(threadIdx.x) * gridDim.x + blockIdx.x];
     }
-#pragma unroll
-    for (int w = 0; w < 8; ++w) s_wc[w][threadIdx.x] = 0;
-    __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
-    for (uint32_t base = beg; base < end; base += 256) {
-        const uint32_t i = base + threadIdx.x;
-        const bool valid = i < end;
-        uint32_t key = 0, val = 0, d = 256u + lane;
-        if (valid) { key = kin[i]; val = vin[i]; d = (key >> shift) & 255u; }
-        const unsigned peers = __match_any_sync(FULL, d);
-        const uint32_t rank = __popc(peers & lt);
-        if (valid && rank == 0) s_wc[warp][d] = __popc(peers);
-        __syncthreads();
-        {   // per digit: exclusive prefix over the 8 warps of this round
-            const int dd = threadIdx.x;
-            uint32_t run = 0;
+    for (uint32_t t0 = beg; t0 < end; t0 += kSortTile) {
 #pragma unroll
-            for (int w = 0; w < 8; ++w) {
-                const uint32_t c = s_wc[w][dd];
-                s_wc[w][dd] = run;
-                run += c;
+        for (int w = 0; w < 8; ++w) s_wc[w][threadIdx.x] = 0;
+        __syncthreads();
+        uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+        const uint32_t run0 = t0 + warp * 256;
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            const uint32_t i = run0 + r * 32 + lane;
+            key[r] = i < end ? kin[i] : 0u;
+            val[r] = i < end ? vin[i] : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            const uint32_t i = run0 + r * 32 + lane;
+            const bool valid = i < end;
+            const uint32_t d = valid ? (key[r] >> shift) & 255u : 256u + lane;
+            const unsigned peers = __match_any_sync(FULL, d);
+            const uint32_t before = valid ? s_wc[warp][d] : 0;
+            rank[r] = before + __popc(peers & lt);
+            __syncwarp();
+            if (valid && (peers & lt) == 0) s_wc[warp][d] = before + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        // per digit d = thread: exclusive prefix over the warps and the tile total
+        const int d = threadIdx.x;
+        uint32_t acc = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t c = s_wc[w][d];
+            s_wc[w][d] = acc;
+            acc += c;
+        }
+        uint32_t ntile;
+        s_lstart[d] = block_scan_256(acc, s_w, &ntile);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            if (run0 + r * 32 + lane < end) {
+                const uint32_t dd = (key[r] >> shift) & 255u;
+                const uint32_t lpos = s_lstart[dd] + s_wc[warp][dd] + rank[r];
+                s_key[lpos] = key[r];
+                s_val[lpos] = val[r];
             }
-            s_rt[dd] = run;
         }
         __syncthreads();
-        if (valid) {
-            const uint32_t pos = s_off[d] + s_wc[warp][d] + rank;
-            kout[pos] = key;
-            vout[pos] = val;
+        for (uint32_t i = threadIdx.x; i < ntile; i += 256) {
+            const uint32_t k = s_key[i];
+            const uint32_t dd = (k >> shift) & 255u;
+            const uint32_t pos = s_off[dd] + (i - s_lstart[dd]);
+            kout[pos] = k;
+            vout[pos] = s_val[i];
         }
         __syncthreads();
-        {
-            const int dd = threadIdx.x;
-            s_off[dd] += s_rt[dd];
-#pragma unroll
-            for (int w = 0; w < 8; ++w) s_wc[w][dd] = 0;
-        }
-        __syncthreads();
+        s_off[d] += acc;
     }
 }
 
@@ -402,7 +435,7 @@ int sort_blocks() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int g = 2 * (sms > 0 ? sms : 80);
+    int g = 4 * (sms > 0 ? sms : 80);
     if (g > kMaxSortBlocks) g = kMaxSortBlocks;
     cached = g;
     return g;
@@ -444,16 +477,18 @@ cudaError_t launch_dup_offsets(const uint32_t *order, const uint32_t *tiles, uin
 
 cudaError_t launch_emit(const uint32_t *order, const uint32_t *dup_off, const Rec *rec, uint32_t n_cap, int Tx,
                         uint32_t *tile_k, uint32_t *tile_v, Ctl *ctl, uint64_t dup_cap, cudaStream_t st) {
-    const int G = sort_blocks();
     NSrc ns{&ctl->n_vis, n_cap};
-    k_emit<<<G, 256, 0, st>>>(order, dup_off, rec, ns, Tx, tile_k, tile_v, dup_cap);
+    // one warp per 32 visible Gaussians of the capacity, at most 4 CTAs of 8 warps per sort block
+    const uint32_t blocks = max(1u, min((n_cap + 255) / 256, static_cast<uint32_t>(4 * sort_blocks())));
+    k_emit<<<blocks, 256, 0, st>>>(order, dup_off, rec, ns, Tx, tile_k, tile_v, dup_cap);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ranges(const uint32_t *tile_k, uint32_t n_cap, uint2 *ranges, const Ctl *ctl, cudaStream_t st) {
     NSrc ns{&ctl->n_dup_c, n_cap};
-    // one thread per pair of the capacity (blocks past the device count exit at once)
-    const uint32_t blocks = n_cap == 0 ? 1 : min(static_cast<uint32_t>((n_cap + 255) / 256), 1u << 20);
+    // grid-stride over the device count with enough warps to cover memory latency
+    const uint32_t blocks = max(1u, min(static_cast<uint32_t>((n_cap + 255) / 256),
+                                        static_cast<uint32_t>(4 * sort_blocks())));
     k_ranges<<<blocks, 256, 0, st>>>(tile_k, ns, ranges);
     return cudaGetLastError();
 }
