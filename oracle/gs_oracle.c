@@ -518,11 +518,17 @@ void or_bin(int64_t n, const int32_t *vis, const int32_t *rect, const double *de
 /* Front-to-back compositing of one pixel over an ordered splat list.
  * flip >= 0 inverts the outcome of the flip-th "fragile" decision: a
  * threshold test (alpha vs 1/255, T' vs 1e-4) whose operands lie within a
- * relative margin of the threshold, where single-precision evaluation may
- * legitimately fall on the other side.  Returns the number of fragile
+ * relative margin of the threshold (FRAGILE_*_REL), where single-precision
+ * evaluation may legitimately fall on the other side.  Returns the number of fragile
  * decisions met.                                                             */
 
-#define FRAGILE_REL 1e-4
+/* Margins of a fragile decision.  The single-precision alpha of a pixel and
+ * splat is a few correctly rounded operations plus an approximate 2^x on
+ * bit-identical inputs, a relative error near 2e-6; the single-precision
+ * transmittance is a product of up to thousands of factors, each adding a
+ * rounding.                                                                   */
+#define FRAGILE_ALPHA_REL 1e-5
+#define FRAGILE_T_REL 1e-4
 
 typedef struct {
     double C[3], T;
@@ -559,11 +565,11 @@ static int composite_pixel(double px, double py, const int32_t *list, int64_t st
         double e = splat_exponent(px, py, u[g], v[g], A2[g], beta[g], G2[g], NULL, NULL);
         double a = fmin(ALPHA_MAX, opac[g] * exp2(e));
         int skip = a < ALPHA_MIN;
-        if (fabs(a - ALPHA_MIN) <= FRAGILE_REL * ALPHA_MIN) { if (nfr == flip) skip = !skip; ++nfr; }
+        if (fabs(a - ALPHA_MIN) <= FRAGILE_ALPHA_REL * ALPHA_MIN) { if (nfr == flip) skip = !skip; ++nfr; }
         if (skip) continue;
         double Tn = T * (1.0 - a);
         int stop = Tn < T_MIN;
-        if (fabs(Tn - T_MIN) <= FRAGILE_REL * T_MIN) { if (nfr == flip) stop = !stop; ++nfr; }
+        if (fabs(Tn - T_MIN) <= FRAGILE_T_REL * T_MIN) { if (nfr == flip) stop = !stop; ++nfr; }
         if (stop) break;
         if (added) { added[nadd] = g; Tbefore[nadd] = T; alphas[nadd] = a; }
         h = fnv1a(h, ((uint64_t)(uint32_t)g << 1) | (uint64_t)(a >= ALPHA_MAX));
@@ -725,7 +731,7 @@ void or_composite_backward(int W, int H, int64_t n, const int64_t *ranges, const
                 double p, dy;
                 double e = splat_exponent(px, py, u[g], v[g], A2[g], beta[g], G2[g], &p, &dy);
                 double ex = exp2(e);
-                if (fabs(opac[g] * ex - ALPHA_MAX) <= FRAGILE_REL * ALPHA_MAX) touched_fragile[g] = 1;
+                if (fabs(opac[g] * ex - ALPHA_MAX) <= FRAGILE_ALPHA_REL * ALPHA_MAX) touched_fragile[g] = 1;
                 if (opac[g] * ex < ALPHA_MAX) {
                     double dLde = dLda * a * LN2;
                     rec_grad[9 * g + 5] += dLda * ex;

@@ -216,7 +216,7 @@ def test_tiled_render_equals_brute_force(seed):
 def test_fragile_alternative_flips_first_decision():
     # a splat whose alpha sits within the relative margin of 1/255 at the centre
     cam = axis_camera(4.0, 33, 33)
-    o = (1 / 255) * (1 + 2e-5)
+    o = (1 / 255) * (1 + 2e-6)
     sc = make_scene([[0, 0, 0]], math.log(0.02), rgb=[1, 1, 1], opacity_logit=logit(o))
     r = _render(sc, cam, bg=np.zeros(3))
     assert r["fragile"][16, 16] == 1
