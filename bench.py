@@ -7,6 +7,12 @@ compositing, S4 backward (with per-Gaussian contributions) and S5 prune.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
+After the timed steps (rank 0, N = 1) a serving leg replays 512 Poisson
+requests at 300/s against three resident models (0.5M, 1.5M, 3M Gaussians)
+through the served path (continuous batching into batched launches) and the
+plain path (one request at a time), in real time and saturated; its p50/p99
+latencies and Mpixels/s go under "serving".
+
 Prints one JSON line.  The reference arm times the FP64 CPU oracle on a
 bounded sample of the same workload (this method has no runnable reference
 implementation).  Multi-GPU runs (torchrun) are independent replicas: the
@@ -15,6 +21,7 @@ path has no exchange step, every rank renders the full frame.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -182,6 +189,47 @@ def run_reference(args, rank, world):
 
 # ----------------------------------------------------------------------------- GPU arm
 
+SERVE_MODELS = (("0.5M", 0.5 / 1.2), ("1.5M", 1.25), ("3M", None))
+SERVE_SIZES = ((512, 512, 1), (1024, 1024, 1), (2064, 2208, 2))
+
+
+def run_serving(dev, n_requests=512, rate=300.0, budget=8 << 30):
+    """Three resident layered models (0.5M, 1.5M, 3M Gaussians, SH degree 3)
+    and a Poisson trace of mixed requests, replayed in real time through the
+    served path (continuous batching, 2 streams) and through the plain path
+    (one request per gs_render sequence, FIFO), then replayed saturated (all
+    requests at t = 0) for peak throughput."""
+    import synth
+    from paper_2410_16978_gb300 import DeviceScene
+    from paper_2410_16978_gb300.serve import RenderServer, make_trace, summarize
+
+    models = {}
+    for name, scale in SERVE_MODELS:
+        sc = synth.scene_c4()["scene"] if scale is None else synth.scene_c2(scale=scale)["scene"]
+        models[name] = DeviceScene.from_host(sc, device=dev)
+    srv = RenderServer(models, memory_budget=budget, device=dev)
+    rng = np.random.default_rng(synth.config_seed(4))
+    cal = make_trace(np.random.default_rng(1), list(models), n_requests=36, rate=None, sizes=SERVE_SIZES)
+    for req in cal:
+        srv.calibrate(req.model, req.cameras, req.layer_mask, req.planes)
+    trace = make_trace(rng, list(models), n_requests=n_requests, rate=rate, sizes=SERVE_SIZES)
+    sat = [dataclasses.replace(r, arrival=0.0) for r in trace]
+    out = {"models": {k: m.n for k, m in models.items()}, "requests": n_requests, "rate_rps": rate,
+           "memory_budget_gib": budget / 2 ** 30, "sizes": ["%dx%dx%d" % s for s in SERVE_SIZES],
+           "mpixels_total": sum(r.pixels for r in trace) / 1e6}
+    for mode in ("plain", "served"):
+        srv.run_trace(sat[:64], mode)            # warm-up: fills the buffer pools
+    for label, tr in (("trace", trace), ("saturated", sat)):
+        for mode in ("plain", "served"):
+            r0, b0, v0 = srv.retries, srv.batches, srv.views_launched
+            res, wall = srv.run_trace(tr, mode)
+            s = summarize(res, tr, wall)
+            s.update(retries=srv.retries - r0, launches=(srv.batches - b0) if mode == "served" else None,
+                     views=srv.views_launched - v0)
+            out["%s_%s" % (label, mode)] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()}
+    return out
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -321,6 +369,10 @@ def run_gpu(args, rank, world, local_rank):
                "sample": "full FP64 preprocess + binning, fwd+bwd compositing of 8 central tile rows scaled to "
                          "the frame, chain rule of all visible Gaussians; %.1f s wall" % wall}
 
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        serving = run_serving(dev)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms_step, "p50_ms": per[len(per) // 2],
@@ -336,7 +388,7 @@ def run_gpu(args, rank, world, local_rank):
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "ms_per_step": e2e_ms},
-                "clocks": clk, "gpu_launches": int(launches),
+                "clocks": clk, "gpu_launches": int(launches), "serving": serving,
                 "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()}}
         print(json.dumps(line), flush=True)
 
@@ -348,6 +400,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)

@@ -137,6 +137,30 @@ int gs_render(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mas
               const gs_clip_plane *planes, int32_t n_planes, const float *bg,
               void *workspace, size_t ws_bytes, float *image, float *alpha, void *stream);
 
+/* Several views rendered as one batch (serving; stereo eyes).  Equivalent to
+ * gs_render for each request in order on `stream` (each with its own
+ * workspace, image and alpha), except that the compositing of all views is
+ * one persistent launch whose work queue spans every view's tiles, so small
+ * views share the GPU instead of each leaving most of it idle.  1 <= n <=
+ * GS_MAX_BATCH; workspaces must be distinct (GS_ERR_INVALID otherwise).
+ * Each workspace afterwards holds its view's forward state, so
+ * gs_render_backward can be called per view.                                */
+#define GS_MAX_BATCH 16
+typedef struct gs_render_request {
+    const gs_scene *scene;
+    const gs_camera *camera;
+    uint32_t layer_mask;
+    int32_t n_planes;
+    const gs_clip_plane *planes;    /* host array */
+    float bg[3];                    /* host values */
+    float _reserved;
+    void *workspace;
+    size_t ws_bytes;
+    float *image;
+    float *alpha;                   /* may be NULL */
+} gs_render_request;
+int gs_render_batch(const gs_render_request *reqs, int32_t n, void *stream);
+
 /* Backward of the last gs_render made with this workspace (same scene, camera
  * and bg; Sec. 3.2 layered training).
  *   dL_dimage  [3][H][W], dL_dalpha [H][W] (either may be NULL = zero)
@@ -170,10 +194,10 @@ int gs_contrib_prune(const float *contrib_max, int64_t n, float threshold, uint8
  *   3 depth keys (u32 float bits, 0xFFFFFFFF when culled)   4 final tile ids
  *   of the pair list (u32)   5 final Gaussian ids of the pair list (u32)
  *   6 tile ranges (u32 start, end per tile)   7 final transmittance (f32
- *   per pixel)   8 n_contrib (u32 per pixel)   9 colour sum (3 f32 planes)
- *   10 record gradients (48 B per Gaussian)   11 total bytes   12 pair
- *   capacity.  Returns GS_ERR_WORKSPACE when ws_bytes is below the fixed part. */
-#define GS_LAYOUT_COUNT 13
+ *   per pixel)   8 n_contrib (u32 per pixel)   9 record gradients (48 B per
+ *   Gaussian)   10 total bytes   11 pair capacity.  Returns GS_ERR_WORKSPACE
+ *   when ws_bytes is below the fixed part.                                     */
+#define GS_LAYOUT_COUNT 12
 int gs_workspace_layout(int64_t n, int32_t width, int32_t height, size_t ws_bytes, int64_t *out);
 
 /* gs_contrib_prune without a workspace, for callers that cannot allocate
@@ -212,9 +236,9 @@ enum {
     GS_STAGE_DUP_SCAN,         /* S2: ordered scan of tile counts */
     GS_STAGE_EMIT,             /* S2: (tile, Gaussian) pairs */
     GS_STAGE_TILE_SORT,        /* S2: radix passes on tile ids */
-    GS_STAGE_RANGES,           /* S2: per-tile [start, end) */
-    GS_STAGE_COMPOSITE,        /* S3 */
-    GS_STAGE_COMPOSITE_BWD,    /* S4a (includes zeroing the record gradients) */
+    GS_STAGE_RANGES,           /* S2: per-tile [start, end), heaviest-first tile order, checkpoint bases */
+    GS_STAGE_COMPOSITE,        /* S3 (one launch per gs_render or gs_render_batch call) */
+    GS_STAGE_COMPOSITE_BWD,    /* S4a (zeroing the record gradients, work-item set-up, compositor) */
     GS_STAGE_PREPROCESS_BWD,   /* S4b */
     GS_STAGE_PRUNE,            /* S5 */
     GS_STAGE_COUNT

@@ -16,6 +16,7 @@ from ._lib import (  # noqa: F401
     gs_read_status,
     gs_render,
     gs_render_backward,
+    gs_render_batch,
     gs_render_workspace_size,
     gs_version,
     gs_workspace_layout,

@@ -19,15 +19,16 @@ GS_OK, GS_ERR_INVALID, GS_ERR_WORKSPACE, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_OOM
 GS_DTYPE_F32, GS_DTYPE_F16, GS_DTYPE_BF16 = 0, 1, 2
 GS_TILE = 16
 GS_MAX_PLANES = 8
+GS_MAX_BATCH = 16
 
-EXPORTED = ("gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_prune_workspace_size",
+EXPORTED = ("gs_render_workspace_size", "gs_render", "gs_render_batch", "gs_render_backward", "gs_prune_workspace_size",
             "gs_contrib_prune", "gs_contrib_prune_noalloc", "gs_workspace_layout", "gs_read_status", "gs_profile_enable", "gs_profile_collect",
             "gs_kernel_launches", "gs_last_error_string", "gs_version")
 STAGES = ("preprocess", "compact", "depth_sort", "dup_scan", "emit", "tile_sort", "ranges", "composite",
           "composite_bwd", "preprocess_bwd", "prune")
-GS_LAYOUT_COUNT = 13
-LAYOUT_NAMES = ("ctl", "rec", "tiles", "depth", "tile_k", "tile_v", "ranges", "t_final", "n_contrib", "c_sum",
-                "rec_grad", "total", "dup_capacity")
+GS_LAYOUT_COUNT = 12
+LAYOUT_NAMES = ("ctl", "rec", "tiles", "depth", "tile_k", "tile_v", "ranges", "t_final", "n_contrib", "rec_grad",
+                "total", "dup_capacity")
 
 
 class gs_camera(ctypes.Structure):
@@ -50,6 +51,13 @@ class gs_scene(ctypes.Structure):
 
 class gs_grads(ctypes.Structure):
     _fields_ = [("means", _P), ("log_scales", _P), ("quats", _P), ("opacity_logit", _P), ("sh", _P)]
+
+
+class gs_render_request(ctypes.Structure):
+    _fields_ = [("scene", ctypes.POINTER(gs_scene)), ("camera", ctypes.POINTER(gs_camera)),
+                ("layer_mask", ctypes.c_uint32), ("n_planes", ctypes.c_int32),
+                ("planes", ctypes.POINTER(gs_clip_plane)), ("bg", ctypes.c_float * 3), ("_reserved", ctypes.c_float),
+                ("workspace", _P), ("ws_bytes", ctypes.c_size_t), ("image", _P), ("alpha", _P)]
 
 
 class gs_status(ctypes.Structure):
@@ -91,6 +99,7 @@ def load(build_if_missing: bool = True):
         L.gs_render.argtypes = [ctypes.POINTER(gs_scene), ctypes.POINTER(gs_camera), ctypes.c_uint32,
                                 ctypes.POINTER(gs_clip_plane), ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
                                 _P, ctypes.c_size_t, _P, _P, _P]
+        L.gs_render_batch.argtypes = [ctypes.POINTER(gs_render_request), ctypes.c_int32, _P]
         L.gs_render_backward.argtypes = [ctypes.POINTER(gs_scene), ctypes.POINTER(gs_camera),
                                          ctypes.POINTER(ctypes.c_float), _P, ctypes.c_size_t, _P, _P,
                                          ctypes.c_uint32, ctypes.POINTER(gs_grads), _P, _P, _P]
@@ -166,6 +175,32 @@ def gs_render(scene: gs_scene, camera: gs_camera, layer_mask: int, planes, bg, w
     bgv = (ctypes.c_float * 3)(*[float(v) for v in bg])
     _check(load().gs_render(ctypes.byref(scene), ctypes.byref(camera), int(layer_mask) & 0xFFFFFFFF, parr, npl, bgv,
                             _ptr(workspace), int(ws_bytes), _ptr(image), _ptr(alpha), ctypes.c_void_p(stream)))
+
+
+def gs_render_batch(views, stream: int) -> None:
+    """views: sequence of dicts with scene (gs_scene), camera (gs_camera), layer_mask, planes, bg,
+    workspace, ws_bytes, image, alpha (alpha may be None)."""
+    n = len(views)
+    if not 1 <= n <= GS_MAX_BATCH:
+        raise ValueError("1..%d views per batch" % GS_MAX_BATCH)
+    reqs = (gs_render_request * n)()
+    keep = []
+    for k, v in enumerate(views):
+        parr, npl = make_planes(v.get("planes", ()))
+        keep.append((v["scene"], v["camera"], parr))
+        reqs[k].scene = ctypes.pointer(v["scene"])
+        reqs[k].camera = ctypes.pointer(v["camera"])
+        reqs[k].layer_mask = int(v.get("layer_mask", 0xFFFFFFFF)) & 0xFFFFFFFF
+        reqs[k].n_planes = npl
+        reqs[k].planes = ctypes.cast(parr, ctypes.POINTER(gs_clip_plane))
+        for j, b in enumerate(v.get("bg", (0.0, 0.0, 0.0))):
+            reqs[k].bg[j] = float(b)
+        reqs[k].workspace = _ptr(v["workspace"])
+        reqs[k].ws_bytes = int(v["ws_bytes"])
+        reqs[k].image = _ptr(v["image"])
+        reqs[k].alpha = _ptr(v.get("alpha"))
+    _check(load().gs_render_batch(reqs, n, ctypes.c_void_p(stream)))
+    del keep
 
 
 def gs_render_backward(scene: gs_scene, camera: gs_camera, bg, workspace, ws_bytes: int, dL_dimage, dL_dalpha,

@@ -8,8 +8,9 @@
 //  * Forward: persistent warps take work items (tile, 8x4 pixel block) from a
 //    device queue in heaviest-first tile order and composite one pixel per
 //    lane until the block's 32 pixels are done.  Every kSeg list positions
-//    the warp stores each pixel's running state (T and the colour sum) as a
-//    checkpoint.
+//    the warp stores each pixel's transmittance as a checkpoint, with the
+//    colour blended from there to the end of the pixel's walk (filled in
+//    when the walk ends).
 //  * Both passes drop, 32 records at a time, the splats that provably stay
 //    below alpha = 1/255 over the warp's whole pixel block (see
 //    splat_reaches_block); list positions are kept, so nothing changes.
@@ -17,7 +18,8 @@
 //    and walking it serially would make the longest pixel the critical path
 //    of the whole kernel.  The checkpoints cut every 8x8 block's walk into
 //    segments of at most kSeg positions; persistent warps take (tile, block,
-//    segment) items from a queue and each starts from its checkpoint.
+//    segment) items from a queue and each walks its segment back to front
+//    from the checkpoint at the segment's end.
 //
 // splat_alpha() is the single definition of the per-(pixel, splat) alpha used
 // by both passes; every operation is an explicitly rounded intrinsic, so the
@@ -176,44 +178,54 @@ __device__ __forceinline__ void fetch_chunk(const uint32_t *__restrict__ list, c
     }
 }
 
-__global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(
-    const uint32_t *__restrict__ order, uint32_t *__restrict__ queue, const uint2 *__restrict__ ranges,
-    const uint32_t *__restrict__ list, const Rec *__restrict__ rec, int W, int H, int Tx, int Tn, float3 bg,
-    float *__restrict__ image, float *__restrict__ alpha_out, float *__restrict__ t_final,
-    uint32_t *__restrict__ n_contrib, float *__restrict__ c_sum, const uint32_t *__restrict__ seg_base,
-    float4 *__restrict__ ckpt, uint32_t *__restrict__ qwork) {
+struct FwdBatch {
+    FwdJob job[kMaxBatch];
+    int n;
+    uint32_t total;
+};
+
+__global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_constant__ FwdBatch batch,
+                                                               uint32_t *__restrict__ queue) {
     __shared__ float4 s_a[kFwdThreads / 32][32], s_b[kFwdThreads / 32][32];
     __shared__ float s_c[kFwdThreads / 32][32];
     __shared__ uint32_t s_pos[kFwdThreads / 32][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    const uint32_t total = static_cast<uint32_t>(Tn) * 8u;
-    const size_t plane = static_cast<size_t>(W) * H;
     for (;;) {
         uint32_t item = 0;
         if (lane == 0) item = atomicAdd(queue, 1u);
         item = __shfl_sync(FULL, item, 0);
-        if (item >= total) break;
-        const int tile = order[item >> 3];
-        const int sub = item & 7;                       // 8x4 block: column sub & 1, row sub >> 1
-        const uint2 rg = ranges[tile];
+        if (item >= batch.total) break;
+        int v = 0;
+        while (v + 1 < batch.n && item >= batch.job[v + 1].item_begin) ++v;
+        const FwdJob &J = batch.job[v];
+        const uint32_t local = item - J.item_begin;
+        const int Tx = J.Tx, W = J.W, H = J.H;
+        const uint32_t *__restrict__ list = J.list;
+        const Rec *__restrict__ rec = J.rec;
+        const int tile = J.order[local >> 3];
+        const int sub = local & 7;                      // 8x4 block: column sub & 1, row sub >> 1
+        const uint2 rg = J.ranges[tile];
         const int lx = (sub & 1) * 8 + (lane & 7), ly = (sub >> 1) * 4 + (lane >> 3);
         const int x = (tile % Tx) * kTile + lx;
         const int y = (tile / Tx) * kTile + ly;
         const bool inside = x < W && y < H;
         const float px = x + 0.5f, py = y + 0.5f;
         const float bx0 = (tile % Tx) * kTile + (sub & 1) * 8 + 0.5f, by0 = (tile / Tx) * kTile + (sub >> 1) * 4 + 0.5f;
-        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-        uint32_t last = 0;
+        float T = 1.f, D0 = 0.f, D1 = 0.f, D2 = 0.f;     // D: colour blended in the current segment
+        uint32_t last = 0, sd = 0;
         bool done = !inside;
-        float4 *my_ckpt = ckpt + static_cast<size_t>(seg_base[tile]) * kTilePix + ly * kTile + lx;
+        float4 *my_ckpt = J.ckpt + static_cast<size_t>(J.seg_base[tile]) * kTilePix + ly * kTile + lx;
         Chunk nxt;
         fetch_chunk(list, rec, rg.x + lane, rg.y, nxt);
         for (uint32_t base = rg.x; base < rg.y; base += 32) {
             if (__all_sync(FULL, done)) break;
             const uint32_t pos0 = base - rg.x;
-            if (pos0 != 0 && pos0 % kSeg == 0)
-                my_ckpt[static_cast<size_t>(pos0 / kSeg) * kTilePix] = make_float4(T, C0, C1, C2);
+            if (pos0 != 0 && pos0 % kSeg == 0) {
+                sd = pos0 / kSeg;
+                my_ckpt[static_cast<size_t>(sd) * kTilePix] = make_float4(T, D0, D1, D2);
+                D0 = D1 = D2 = 0.f;
+            }
             const bool keep = base + lane < rg.y && splat_reaches_block(nxt.a, nxt.b, bx0, bx0 + 7.f, by0, by0 + 3.f);
             const unsigned km = __ballot_sync(FULL, keep);
             __syncwarp();
@@ -235,27 +247,38 @@ __global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(
                 const float Tnew = __fmul_rn(T, __fsub_rn(1.f, al));
                 if (Tnew < kTMin) { done = true; break; }
                 const float w = __fmul_rn(al, T);
-                C0 = __fmaf_rn(b.z, w, C0);
-                C1 = __fmaf_rn(b.w, w, C1);
-                C2 = __fmaf_rn(s_c[warp][k], w, C2);
+                D0 = __fmaf_rn(b.z, w, D0);
+                D1 = __fmaf_rn(b.w, w, D1);
+                D2 = __fmaf_rn(s_c[warp][k], w, D2);
                 T = Tnew;
                 last = s_pos[warp][k] + 1;
             }
         }
+        // Checkpoint s holds (T at segment start, D of segment s-1) as written
+        // above; rewrite it, deepest segment first, to (T at segment start,
+        // F_s), F_s = colour blended at list positions >= s kSeg.  F_0 is the
+        // pixel's colour sum.
+        float C0 = D0, C1 = D1, C2 = D2;
+        for (uint32_t s = sd; s > 0; --s) {
+            float4 *slot = my_ckpt + static_cast<size_t>(s) * kTilePix;
+            const float4 raw = *slot;
+            *slot = make_float4(raw.x, C0, C1, C2);
+            C0 = __fadd_rn(raw.y, C0);
+            C1 = __fadd_rn(raw.z, C1);
+            C2 = __fadd_rn(raw.w, C2);
+        }
         if (inside) {
+            const size_t plane = static_cast<size_t>(W) * H;
             const size_t pix = static_cast<size_t>(y) * W + x;
-            image[pix] = __fmaf_rn(T, bg.x, C0);
-            image[plane + pix] = __fmaf_rn(T, bg.y, C1);
-            image[2 * plane + pix] = __fmaf_rn(T, bg.z, C2);
-            if (alpha_out) alpha_out[pix] = 1.f - T;
-            t_final[pix] = T;
-            n_contrib[pix] = last;
-            c_sum[pix] = C0;
-            c_sum[plane + pix] = C1;
-            c_sum[2 * plane + pix] = C2;
+            J.image[pix] = __fmaf_rn(T, J.bg.x, C0);
+            J.image[plane + pix] = __fmaf_rn(T, J.bg.y, C1);
+            J.image[2 * plane + pix] = __fmaf_rn(T, J.bg.z, C2);
+            if (J.alpha) J.alpha[pix] = 1.f - T;
+            J.t_final[pix] = T;
+            J.n_contrib[pix] = last;
         }
         const uint32_t wm = __reduce_max_sync(FULL, last);
-        if (lane == 0 && wm) atomicMax(&qwork[4 * tile + (sub & 1) + 2 * (sub >> 2)], wm);
+        if (lane == 0 && wm) atomicMax(&J.qwork[4 * tile + (sub & 1) + 2 * (sub >> 2)], wm);
     }
 }
 
@@ -309,12 +332,18 @@ __device__ __forceinline__ float reduce_scatter16(float v[16], int lane) {
     return v[0] + __shfl_xor_sync(FULL, v[0], 1);
 }
 
-// Backward, front to back.  With S_i = sum_{j>i} c_j a_j T_j + T_N bg:
-//   dL/da_i = dC.(c_i T_i - S_i/(1-a_i)) + dA T_N/(1-a_i)
-//           = T_i (dC.c_i) - (dC.(Csum - P_i) + T_N (dC.bg) - dA T_N)/(1-a_i)
-// where P_i is the running colour sum including splat i; dC.P_i is carried as
-// the scalar Q.  A work item covers list positions [s kSeg, (s+1) kSeg) of one
-// 8x8 block (two pixels per lane) and starts from the forward's checkpoint.
+// Backward, back to front within a segment.  With
+//   S_i = sum_{j>i} c_j a_j T_j + T_N bg   (T_j: transmittance before splat j)
+//   dL/da_i = T_i (dC.c_i) - (dC.S_i - dA T_N) / (1 - a_i).
+// The scalar R_i = dC.S_i - dA T_N is carried from the back: a work item
+// covers list positions [s kSeg, (s+1) kSeg) of one 8x8 block (two pixels per
+// lane) and starts from the forward's checkpoint of segment s+1, which holds
+// the transmittance there and the colour blended from there on (or from T_N
+// and zero when the pixel stopped inside segment s).  Going back, T_i =
+// T_{i+1} / (1 - a_i) and R_{i-1} = R_i + (dC.c_i) a_i T_i: every term of R
+// is at most of the size of T there, so deep splats keep their relative
+// accuracy (a running total minus a prefix would not).
+//
 // Each splat's 10 sums are reduced over the warp and added to the record
 // gradient with vector atomics:
 //   rec_grad[3g]   += (du, dv, dA2, dbeta)
@@ -324,10 +353,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
     const uint2 *__restrict__ items, const uint32_t *__restrict__ n_items, uint32_t *__restrict__ queue,
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ list, const Rec *__restrict__ rec, int W, int H,
     int Tx, float3 bg, const float *__restrict__ t_final, const uint32_t *__restrict__ n_contrib,
-    const float *__restrict__ c_sum, const uint32_t *__restrict__ seg_base, const float4 *__restrict__ ckpt,
-    const uint32_t *__restrict__ qwork, const float *__restrict__ dL_dimage, const float *__restrict__ dL_dalpha,
-    const uint8_t *__restrict__ layer, uint32_t grad_layer_mask, float4 *__restrict__ rec_grad,
-    float *__restrict__ contrib_max) {
+    const uint32_t *__restrict__ seg_base, const float4 *__restrict__ ckpt, const uint32_t *__restrict__ qwork,
+    const float *__restrict__ dL_dimage, const float *__restrict__ dL_dalpha, const uint8_t *__restrict__ layer,
+    uint32_t grad_layer_mask, float4 *__restrict__ rec_grad, float *__restrict__ contrib_max) {
     __shared__ float4 s_a[kBwdThreads / 32][32], s_b[kBwdThreads / 32][32];
     __shared__ float s_c[kBwdThreads / 32][32];
     __shared__ uint32_t s_g[kBwdThreads / 32][32];
@@ -348,9 +376,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
         const uint2 rg = ranges[tile];
         const uint32_t s0 = rg.x + seg * kSeg;
         const uint32_t s1 = rg.x + min(min((seg + 1) * kSeg, qwork[4 * tile + q]), rg.y - rg.x);
-        const float4 *tck = ckpt + (static_cast<size_t>(seg_base[tile]) + seg) * kTilePix;
+        const float4 *nck = ckpt + (static_cast<size_t>(seg_base[tile]) + seg + 1) * kTilePix;
         const float bx0 = (tile % Tx) * kTile + (q & 1) * 8 + 0.5f, by0 = (tile / Tx) * kTile + (q >> 1) * 8 + 0.5f;
-        float px[2], py[2], dC0[2], dC1[2], dC2[2], QC[2], K0[2], T[2], Q[2];
+        float px[2], py[2], dC0[2], dC1[2], dC2[2], R[2], T[2];
         uint32_t nc[2];
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
@@ -359,9 +387,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
             px[j] = x + 0.5f;
             py[j] = y + 0.5f;
             nc[j] = 0;
-            dC0[j] = dC1[j] = dC2[j] = QC[j] = K0[j] = 0.f;
+            dC0[j] = dC1[j] = dC2[j] = R[j] = 0.f;
             T[j] = 1.f;
-            Q[j] = 0.f;
             if (x < W && y < H) {
                 const size_t pix = static_cast<size_t>(y) * W + x;
                 const uint32_t n = n_contrib[pix];
@@ -375,19 +402,21 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
                         dC2[j] = dL_dimage[2 * plane + pix];
                     }
                     if (dL_dalpha) dA = dL_dalpha[pix];
-                    QC[j] = dC0[j] * c_sum[pix] + dC1[j] * c_sum[plane + pix] + dC2[j] * c_sum[2 * plane + pix];
-                    K0[j] = TN * (dC0[j] * bg.x + dC1[j] * bg.y + dC2[j] * bg.z) - dA * TN;
-                    if (seg > 0) {
-                        const float4 ck = tck[ly * kTile + lx];
+                    R[j] = TN * (dC0[j] * bg.x + dC1[j] * bg.y + dC2[j] * bg.z) - dA * TN;
+                    T[j] = TN;
+                    if (n > (seg + 1) * kSeg) {
+                        const float4 ck = nck[ly * kTile + lx];
                         T[j] = ck.x;
-                        Q[j] = dC0[j] * ck.y + dC1[j] * ck.z + dC2[j] * ck.w;
+                        R[j] += dC0[j] * ck.y + dC1[j] * ck.z + dC2[j] * ck.w;
                     }
                 }
             }
         }
+        const uint32_t nchunk = (s1 - s0 + 31) / 32;
         Chunk nxt;
-        fetch_chunk(list, rec, s0 + lane, s1, nxt);
-        for (uint32_t base = s0; base < s1; base += 32) {
+        if (nchunk) fetch_chunk(list, rec, s0 + (nchunk - 1) * 32 + lane, s1, nxt);
+        for (uint32_t c = nchunk; c-- > 0;) {
+            const uint32_t base = s0 + c * 32;
             const bool keep = base + lane < s1 && splat_reaches_block(nxt.a, nxt.b, bx0, bx0 + 7.f, by0, by0 + 7.f);
             const unsigned km = __ballot_sync(FULL, keep);
             __syncwarp();
@@ -400,9 +429,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
                 s_pos[warp][slot] = base + lane - rg.x;
             }
             __syncwarp();
-            fetch_chunk(list, rec, base + 32 + lane, s1, nxt);
+            if (c > 0) fetch_chunk(list, rec, base - 32 + lane, s1, nxt);
             const int cnt = __popc(km);
-            for (int k = 0; k < cnt; ++k) {
+            for (int k = cnt - 1; k >= 0; --k) {
                 const uint32_t pos = s_pos[warp][k];
                 const float4 a = s_a[warp][k], b = s_b[warp][k];
                 const float cb = s_c[warp][k];
@@ -420,10 +449,12 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
                 for (int j = 0; j < 2; ++j) {
                     if (!act[j]) continue;
                     const float dcc = dC0[j] * b.z + dC1[j] * b.w + dC2[j] * cb;
-                    const float wgt = __fmul_rn(al[j], T[j]);
-                    Q[j] = fmaf(wgt, dcc, Q[j]);
-                    const float inv = __frcp_rn(1.f - al[j]);
-                    const float dLda = T[j] * dcc - ((QC[j] - Q[j]) + K0[j]) * inv;
+                    const float inv = __frcp_rn(__fsub_rn(1.f, al[j]));
+                    const float Ti = T[j] * inv;
+                    const float wgt = al[j] * Ti;
+                    const float dLda = Ti * dcc - R[j] * inv;
+                    R[j] = fmaf(wgt, dcc, R[j]);
+                    T[j] = Ti;
                     v[6] += wgt * dC0[j];
                     v[7] += wgt * dC1[j];
                     v[8] += wgt * dC2[j];
@@ -439,7 +470,6 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
                     }
                     v[9] += wgt;
                     wmx = fmaxf(wmx, wgt);
-                    T[j] = __fmul_rn(T[j], __fsub_rn(1.f, al[j]));
                 }
                 const float sv = reduce_scatter16(v, lane);
                 // value i sits in lane 2i: lanes 0, 8, 16 gather (i, i+1, i+2, i+3)
@@ -471,24 +501,35 @@ int persistent_blocks(K kernel, int threads) {
 
 }  // namespace
 
-cudaError_t launch_composite_forward(const CompositeBufs &cb, const uint2 *ranges, const uint32_t *list,
-                                     const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, float *image,
-                                     float *alpha, float *t_final, uint32_t *n_contrib, float *c_sum,
-                                     cudaStream_t st) {
-    const int tiles = Tx * Ty;
-    if (tiles == 0) return cudaSuccess;
-    k_fwd_setup<<<1, 1024, 0, st>>>(ranges, tiles, cb.order, cb.seg_base, cb.qwork, cb.queue);
+cudaError_t launch_fwd_setup(const CompositeBufs &cb, const uint2 *ranges, int Tn, cudaStream_t st) {
+    if (Tn == 0) return cudaSuccess;
+    k_fwd_setup<<<1, 1024, 0, st>>>(ranges, Tn, cb.order, cb.seg_base, cb.qwork, cb.queue);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite_forward(const FwdJob *jobs, int n, uint32_t *queue, cudaStream_t st) {
+    FwdBatch batch;
+    batch.n = 0;
+    uint32_t total = 0;
+    for (int i = 0; i < n && batch.n < kMaxBatch; ++i) {
+        if (jobs[i].Tn == 0) continue;
+        batch.job[batch.n] = jobs[i];
+        batch.job[batch.n].item_begin = total;
+        total += static_cast<uint32_t>(jobs[i].Tn) * 8u;
+        ++batch.n;
+    }
+    batch.total = total;
+    if (total == 0) return cudaSuccess;
     static int blocks = 0;
     if (!blocks) blocks = persistent_blocks(k_composite_fwd, kFwdThreads);
-    const int b = min(blocks, (tiles * 8 + kFwdThreads / 32 - 1) / (kFwdThreads / 32));
-    k_composite_fwd<<<b, kFwdThreads, 0, st>>>(cb.order, cb.queue, ranges, list, rec, W, H, Tx, tiles, bg, image,
-                                               alpha, t_final, n_contrib, c_sum, cb.seg_base, cb.ckpt, cb.qwork);
+    const int b = min(blocks, static_cast<int>((total + kFwdThreads / 32 - 1) / (kFwdThreads / 32)));
+    k_composite_fwd<<<b, kFwdThreads, 0, st>>>(batch, queue);
     return cudaGetLastError();
 }
 
 cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *ranges, const uint32_t *list,
                                       const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
-                                      const uint32_t *n_contrib, const float *c_sum, const float *dL_dimage,
+                                      const uint32_t *n_contrib, const float *dL_dimage,
                                       const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
                                       float4 *rec_grad, float *contrib_max, cudaStream_t st) {
     const int tiles = Tx * Ty;
@@ -497,7 +538,7 @@ cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *rang
     static int blocks = 0;
     if (!blocks) blocks = persistent_blocks(k_composite_bwd, kBwdThreads);
     k_composite_bwd<<<blocks, kBwdThreads, 0, st>>>(cb.items, cb.n_items, cb.queue, ranges, list, rec, W, H, Tx, bg,
-                                                    t_final, n_contrib, c_sum, cb.seg_base, cb.ckpt, cb.qwork,
+                                                    t_final, n_contrib, cb.seg_base, cb.ckpt, cb.qwork,
                                                     dL_dimage, dL_dalpha, layer, grad_layer_mask, rec_grad,
                                                     contrib_max);
     return cudaGetLastError();

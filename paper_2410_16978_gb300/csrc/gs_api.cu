@@ -35,7 +35,6 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     o.ranges = take(static_cast<size_t>(o.Tn) * 8);
     o.t_final = take(P * 4);
     o.n_contrib = take(P * 4);
-    o.c_sum = take(3 * P * 4);
     o.partials = take(kMaxSortBlocks * 4);
     o.hist = take((static_cast<size_t>(256) * kMaxSortBlocks + 256) * 4);   // + digit totals
     o.rec_grad = take(N * sizeof(Rec));
@@ -219,9 +218,15 @@ int gs_render_workspace_size(int64_t n, int32_t width, int32_t height, int64_t d
     return GS_OK;
 }
 
-int gs_render(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mask, const gs_clip_plane *planes,
-              int32_t n_planes, const float *bg, void *workspace, size_t ws_bytes, float *image, float *alpha,
-              void *stream) {
+}  // extern "C"
+
+namespace {
+
+// Validates one view, launches S1 (preprocess) and S2 (binning and sorts) and
+// the compositor set-up on st, and describes the view in *job.
+int render_front(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mask, const gs_clip_plane *planes,
+                 int32_t n_planes, const float *bg, void *workspace, size_t ws_bytes, float *image, float *alpha,
+                 cudaStream_t st, FwdJob *job, uint32_t **queue) {
     SceneView sv;
     CamView cv;
     int rc;
@@ -240,7 +245,6 @@ int gs_render(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mas
         pl.p[k] = make_float4(planes[k].n[0], planes[k].n[1], planes[k].n[2], planes[k].d);
         pl.bits[k] = planes[k].layer_bits;
     }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     void *ws = workspace;
     Ctl *ctl = at<Ctl>(ws, L.ctl);
     const uint32_t n = static_cast<uint32_t>(sv.n);
@@ -307,17 +311,71 @@ int gs_render(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mas
     }
     const int fin = tp & 1;
     uint2 *ranges = at<uint2>(ws, L.ranges);
+    const CompositeBufs cb = composite_bufs(ws, L);
     {
-        Stage sg(GS_STAGE_RANGES, st, 1);
+        Stage sg(GS_STAGE_RANGES, st, 2);
         if ((rc = cuda_check(launch_ranges(tk[fin], cap, ranges, ctl, st), "ranges")) != GS_OK) return rc;
+        if ((rc = cuda_check(launch_fwd_setup(cb, ranges, L.Tn, st), "compositor set-up")) != GS_OK) return rc;
     }
-    Stage sg(GS_STAGE_COMPOSITE, st, 2);
-    return cuda_check(launch_composite_forward(composite_bufs(ws, L), ranges, tv[fin], rec, cv.W, cv.H, cv.Tx, cv.Ty,
-                                               make_float3(bg[0], bg[1], bg[2]), image, alpha,
-                                               at<float>(ws, L.t_final), at<uint32_t>(ws, L.n_contrib),
-                                               at<float>(ws, L.c_sum), st),
-                      "composite");
+    job->order = cb.order;
+    job->ranges = ranges;
+    job->list = tv[fin];
+    job->rec = rec;
+    job->image = image;
+    job->alpha = alpha;
+    job->t_final = at<float>(ws, L.t_final);
+    job->n_contrib = at<uint32_t>(ws, L.n_contrib);
+    job->seg_base = cb.seg_base;
+    job->ckpt = cb.ckpt;
+    job->qwork = cb.qwork;
+    job->W = cv.W;
+    job->H = cv.H;
+    job->Tx = cv.Tx;
+    job->Tn = L.Tn;
+    job->bg = make_float3(bg[0], bg[1], bg[2]);
+    job->item_begin = 0;
+    *queue = cb.queue;
+    return GS_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+int gs_render(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mask, const gs_clip_plane *planes,
+              int32_t n_planes, const float *bg, void *workspace, size_t ws_bytes, float *image, float *alpha,
+              void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    FwdJob job;
+    uint32_t *queue = nullptr;
+    int rc = render_front(scene, camera, layer_mask, planes, n_planes, bg, workspace, ws_bytes, image, alpha, st, &job,
+                          &queue);
+    if (rc != GS_OK) return rc;
+    Stage sg(GS_STAGE_COMPOSITE, st, 1);
+    return cuda_check(launch_composite_forward(&job, 1, queue, st), "composite");
+}
+
+int gs_render_batch(const gs_render_request *reqs, int32_t n, void *stream) {
+    if (!reqs || n < 1 || n > GS_MAX_BATCH) return fail(GS_ERR_INVALID, "n must be 1..%d", GS_MAX_BATCH);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j)
+            if (reqs[i].workspace == reqs[j].workspace)
+                return fail(GS_ERR_INVALID, "requests %d and %d share a workspace", j, i);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    FwdJob jobs[GS_MAX_BATCH];
+    uint32_t *queue0 = nullptr;
+    for (int i = 0; i < n; ++i) {
+        const gs_render_request &r = reqs[i];
+        uint32_t *q = nullptr;
+        int rc = render_front(r.scene, r.camera, r.layer_mask, r.planes, r.n_planes, r.bg, r.workspace, r.ws_bytes,
+                              r.image, r.alpha, st, &jobs[i], &q);
+        if (rc != GS_OK) return rc;
+        if (i == 0) queue0 = q;
+    }
+    Stage sg(GS_STAGE_COMPOSITE, st, 1);
+    return cuda_check(launch_composite_forward(jobs, n, queue0, st), "batched composite");
+}
+
 
 int gs_render_backward(const gs_scene *scene, const gs_camera *camera, const float *bg, void *workspace,
                        size_t ws_bytes, const float *dL_dimage, const float *dL_dalpha, uint32_t grad_layer_mask,
@@ -345,7 +403,7 @@ int gs_render_backward(const gs_scene *scene, const gs_camera *camera, const flo
     if ((rc = cuda_check(launch_composite_backward(composite_bufs(ws, L), at<uint2>(ws, L.ranges), at<uint32_t>(ws, L.tile_v[fin]),
                                                    at<Rec>(ws, L.rec), cv.W, cv.H, cv.Tx, cv.Ty,
                                                    make_float3(bg[0], bg[1], bg[2]), at<float>(ws, L.t_final),
-                                                   at<uint32_t>(ws, L.n_contrib), at<float>(ws, L.c_sum), dL_dimage,
+                                                   at<uint32_t>(ws, L.n_contrib), dL_dimage,
                                                    dL_dalpha, sv.layer, grad_layer_mask, rec_grad, contrib_max, st),
                          "composite backward")) != GS_OK)
         return rc;
@@ -365,7 +423,7 @@ int gs_workspace_layout(int64_t n, int32_t width, int32_t height, size_t ws_byte
     const int fin = tile_sort_passes(L.Tn) & 1;
     const int64_t v[GS_LAYOUT_COUNT] = {
         (int64_t)L.ctl, (int64_t)L.rec, (int64_t)L.tiles, (int64_t)L.depth, (int64_t)L.tile_k[fin],
-        (int64_t)L.tile_v[fin], (int64_t)L.ranges, (int64_t)L.t_final, (int64_t)L.n_contrib, (int64_t)L.c_sum,
+        (int64_t)L.tile_v[fin], (int64_t)L.ranges, (int64_t)L.t_final, (int64_t)L.n_contrib,
         (int64_t)L.rec_grad, (int64_t)L.total, cap};
     for (int k = 0; k < GS_LAYOUT_COUNT; ++k) out[k] = v[k];
     return GS_OK;

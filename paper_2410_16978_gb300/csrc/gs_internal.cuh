@@ -52,7 +52,7 @@ struct Layout {
     int64_t n = 0, dup_cap = 0;
     int W = 0, H = 0, Tx = 0, Ty = 0, Tn = 0;
     size_t ctl = 0, rec = 0, tiles = 0, depth = 0, sort_k[2] = {0, 0}, sort_v[2] = {0, 0}, dup_off = 0,
-           tile_k[2] = {0, 0}, tile_v[2] = {0, 0}, ranges = 0, t_final = 0, n_contrib = 0, c_sum = 0,
+           tile_k[2] = {0, 0}, tile_v[2] = {0, 0}, ranges = 0, t_final = 0, n_contrib = 0,
            partials = 0, hist = 0, rec_grad = 0, tile_order = 0, tile_order_bwd = 0, seg_base = 0, qwork = 0,
            ckpt = 0, items = 0, total = 0;
 };
@@ -135,13 +135,32 @@ struct CompositeBufs {
     uint32_t *n_items;
     uint32_t *queue;      // work-queue counter (forward and backward reuse it in turn)
 };
-cudaError_t launch_composite_forward(const CompositeBufs &cb, const uint2 *ranges, const uint32_t *list,
-                                     const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, float *image,
-                                     float *alpha, float *t_final, uint32_t *n_contrib, float *c_sum,
-                                     cudaStream_t st);
+// One view for the forward compositor.  A batch of views is composited by
+// one persistent launch whose work queue spans all their tiles.
+constexpr int kMaxBatch = GS_MAX_BATCH;
+struct FwdJob {
+    const uint32_t *order;
+    const uint2 *ranges;
+    const uint32_t *list;
+    const Rec *rec;
+    float *image, *alpha, *t_final;
+    uint32_t *n_contrib;
+    const uint32_t *seg_base;
+    float4 *ckpt;
+    uint32_t *qwork;
+    int W, H, Tx, Tn;
+    float3 bg;
+    uint32_t item_begin;   // first global work item of this view (filled by the launcher)
+};
+// Per-view set-up before compositing: tile order, checkpoint bases, zeroed
+// block work and queue.
+cudaError_t launch_fwd_setup(const CompositeBufs &cb, const uint2 *ranges, int Tn, cudaStream_t st);
+// Composites n <= kMaxBatch views with one persistent launch; `queue` must
+// have been zeroed on the stream (launch_fwd_setup of any view does).
+cudaError_t launch_composite_forward(const FwdJob *jobs, int n, uint32_t *queue, cudaStream_t st);
 cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *ranges, const uint32_t *list,
                                       const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
-                                      const uint32_t *n_contrib, const float *c_sum, const float *dL_dimage,
+                                      const uint32_t *n_contrib, const float *dL_dimage,
                                       const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
                                       float4 *rec_grad, float *contrib_max, cudaStream_t st);
 

@@ -38,8 +38,7 @@ def read_ws(rast):
                tile_k=region("tile_k", D, np.uint32), tile_v=region("tile_v", D, np.uint32),
                ranges=region("ranges", 2 * Tn, np.uint32).reshape(Tn, 2),
                t_final=region("t_final", W * H, np.float32).reshape(H, W),
-               n_contrib=region("n_contrib", W * H, np.uint32).reshape(H, W),
-               c_sum=region("c_sum", 3 * W * H, np.float32).reshape(3, H, W), D=D)
+               n_contrib=region("n_contrib", W * H, np.uint32).reshape(H, W), D=D)
     r10 = rec[:, 10].view(np.uint32)
     r11 = rec[:, 11].view(np.uint32)
     out["rect"] = np.stack([r10 & 0xFFFF, r10 >> 16, r11 & 0xFFFF, r11 >> 16], 1).astype(np.int32)

@@ -1,0 +1,132 @@
+"""GPU parity at the workloads' full sizes, in the launch configuration of
+bench.py (Rasterizer with a sized workspace, default stream).
+
+For every Gaussian: the record and its integer decisions bit-exact against
+the oracle's single-precision path; the whole (tile, Gaussian) list and the
+tile ranges bit-exact.  Sampled outputs the oracle computes one by one:
+pixels (uniform plus the busiest tiles) within 1e-5, and the gradients of all
+Gaussians inside random tile patches from a backward restricted to those
+tiles, within 1e-5 of each field's largest magnitude."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.gpu_util import compare_lists, compare_records, dequantised, f64_scene, gpu_render, read_ws
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+GRAD_TOL = 1e-5
+FIELDS = ("means", "log_scales", "quats", "opacity_logit", "sh")
+
+
+def _case(name):
+    if name == "c2_1.2M_1024":
+        w = synth.scene_c2()
+        return w["scene"], w["cameras"][0], w["layer_mask"], w["planes"], tuple(w["bg"]), "f32", "f32"
+    if name == "c4_3M_2064x2208_left_f16sh_bf16sr":
+        w = synth.scene_c4()
+        return w["scene"], w["cameras"][0], w["layer_mask"], w["planes"], tuple(w["bg"]), "f16", "bf16"
+    if name == "c3_500k_800_view3":
+        w = synth.scene_c3()
+        return w["scene"], w["cameras"][3], w["layer_mask"], w["planes"], (0.2, 0.5, 0.8), "f32", "f32"
+    raise KeyError(name)
+
+
+CASES = ["c2_1.2M_1024", "c4_3M_2064x2208_left_f16sh_bf16sr", "c3_500k_800_view3"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_fullsize_parity(name):
+    sc, cam, mask, planes, bg, shdt, srdt = _case(name)
+    W, H = cam.width, cam.height
+    ds, rast, img, al = gpu_render(sc, cam, mask, planes, bg, shdt, srdt)
+    ws = read_ws(rast)
+    assert ws["status"].error == 0
+    sq = dequantised(sc, shdt, srdt)
+    pre = oracle.preprocess(sq, cam, mask, planes, "f32")
+    compare_records(ws, pre)
+    ranges, lst = oracle.bin_tiles(pre)
+    compare_lists(ws, ranges, lst)
+
+    # sampled pixels: uniform over the image plus whole rows of the busiest tiles
+    rng = np.random.default_rng(17)
+    xs = rng.integers(0, W, 3072)
+    ys = rng.integers(0, H, 3072)
+    Tx = (W + 15) // 16
+    busy = np.argsort(ranges[:, 1] - ranges[:, 0])[-4:]
+    bx, by = [], []
+    for t in busy:
+        ty, tx = divmod(int(t), Tx)
+        for k in range(256):
+            x, y = tx * 16 + k % 16, ty * 16 + k // 16
+            if x < W and y < H:
+                bx.append(x)
+                by.append(y)
+    xs = np.concatenate([xs, bx]).astype(np.int32)
+    ys = np.concatenate([ys, by]).astype(np.int32)
+    cp = oracle.composite_pixels(pre, ranges, lst, xs, ys, bg)
+    g_img = img.cpu().numpy()[:, ys, xs].T.astype(np.float64)
+    g_al = al.cpu().numpy()[ys, xs].astype(np.float64)
+    nc = ws["n_contrib"][ys, xs].astype(np.int64)
+    e1 = np.maximum(np.abs(g_img - cp["rgb"]).max(1), np.abs(g_al - cp["alpha"]))
+    e2 = np.maximum(np.abs(g_img - cp["alt_rgb"]).max(1), np.abs(g_al - cp["alt_alpha"]))
+    ok = ((e1 <= TOL) & (nc == cp["ncontrib"])) | ((cp["fragile"] > 0) & (e2 <= TOL) & (nc == cp["alt_ncontrib"]))
+    ok |= cp["fragile"] > 1
+    assert ok.all(), (name, int((~ok).sum()), float(e1.max()))
+    assert (cp["fragile"] > 1).sum() <= 2
+
+    # gradients of every Gaussian whose tile rectangle lies inside 24 random
+    # patches of 2x2 tiles (6x6 above 2 Mpixels): a backward restricted to
+    # those tiles is exact for them.  dL/dimage is zero at the pixels whose
+    # oracle composite has a fragile threshold decision, on both sides, so no
+    # Gaussian has to be left out.  Each field is normalised by its largest
+    # magnitude over the compared set, as in the small-scene tests.
+    dimg = rng.standard_normal((3, H, W)).astype(np.float32)
+    Ty = (H + 15) // 16
+    lens = ranges[:, 1] - ranges[:, 0]
+    centres = rng.choice(np.nonzero(lens > 0)[0], 24, replace=False)
+    ps = 6 if W * H > 2_000_000 else 2
+    tmask2 = np.zeros((Ty, Tx), np.uint8)
+    for t in centres:
+        ty, tx = divmod(int(t), Tx)
+        tmask2[ty:ty + ps, tx:tx + ps] = 1
+    tmask = tmask2.reshape(-1)
+    gy, gx = np.mgrid[0:H, 0:W]
+    inpatch = tmask2[gy // 16, gx // 16] > 0
+    pys, pxs = np.nonzero(inpatch)
+    cpp = oracle.composite_pixels(pre, ranges, lst, pxs.astype(np.int32), pys.astype(np.int32), bg)
+    fr = cpp["fragile"] > 0
+    dimg[:, pys[fr], pxs[fr]] = 0.0
+    csum = torch.zeros(sc.n, device="cuda")
+    cmax = torch.zeros(sc.n, device="cuda")
+    g = rast.backward(ds, cam, bg, torch.from_numpy(dimg).cuda(), None, 0xFFFFFFFF, csum, cmax)
+    torch.cuda.synchronize()
+    r = pre["rect"]
+    inside = np.zeros(sc.n, bool)
+    for i in np.nonzero(pre["vis"])[0]:
+        x0, y0, x1, y1 = r[i]
+        inside[i] = tmask2[y0:y1, x0:x1].all()
+    cb = oracle.composite_backward(pre, ranges, lst, bg, dimg, None, tmask)
+    ref = oracle.chain(f64_scene(sq), cam, pre["vis"], cb["rec_grad"])
+    keep = np.nonzero(inside & (cb["contrib_max"] > 0))[0]
+    assert keep.size >= 48, keep.size
+    errs = {}
+    for f in FIELDS:
+        assert np.isfinite(g[f].cpu().numpy()).all(), (name, f)
+        a = g[f].cpu().numpy().reshape(sc.n, -1)[keep].astype(np.float64)
+        b = ref[f].reshape(sc.n, -1)[keep]
+        errs[f] = np.abs(a - b).max() / np.abs(b).max()
+    print(name, "gradients of", keep.size, "Gaussians (%d fragile pixels zeroed), field-normalised max error"
+          % int(fr.sum()), errs)
+    for f in FIELDS:
+        assert errs[f] <= GRAD_TOL, (name, f, errs[f])
+    # blend weights: Gaussians that no fragile pixel touches
+    kc = keep[cb["touched_fragile"][keep] == 0]
+    assert kc.size >= 16, kc.size
+    cm = cmax.cpu().numpy()[kc]
+    assert np.abs(cm - cb["contrib_max"][kc]).max() <= 1e-5
+    cs = csum.cpu().numpy()[kc]
+    assert np.abs(cs - cb["contrib_sum"][kc]).max() <= 1e-4 * max(1.0, cb["contrib_sum"][kc].max())

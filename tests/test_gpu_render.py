@@ -149,3 +149,76 @@ def test_repeated_renders_are_deterministic():
     b, _ = rast.render(ds, cam, mask, planes, bg)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+def _batch_views():
+    """Mixed views: two scenes, four sizes, masks, planes, backgrounds, a stereo pair."""
+    sc1, cam1, m1, p1, bg1 = WL["c1"]
+    sc2, cam2, m2, p2, bg2 = WL["shells_ragged"]
+    w4 = synth.scene_c4(scale=0.002, width=96, height=104)
+    rng = np.random.default_rng(5)
+    views = [(sc1, cam1, m1, p1, bg1), (sc2, cam2, m2, p2, bg2), (sc2, cam2, 0b00011, (), (1.0, 1.0, 1.0)),
+             (sc1, synth.look_at_camera((0.0, 4.0, 0.5), width=72, height=40), 0b01, (), (0.1, 0.2, 0.3)),
+             (sc2, cam2, 0, (), (0.5, 0.5, 0.5))]
+    for cam in w4["cameras"]:
+        views.append((w4["scene"], cam, w4["layer_mask"], w4["planes"], (0.0, 0.0, 0.0)))
+    for k in range(3):
+        views.append((sc2, synth.look_at_camera(3.0 * rng.standard_normal(3) + 0.1, width=48 + 16 * k, height=33),
+                      int(rng.integers(1, 32)), tuple(synth.random_clip_planes(rng, 2)), (0.0, 0.0, 0.0)))
+    return views
+
+
+def test_render_batch_equals_single_renders():
+    """gs_render_batch composites all views in one launch; every view's image,
+    alpha and forward state equal those of its own gs_render call."""
+    from paper_2410_16978_gb300 import DeviceScene, Rasterizer, _lib
+    views = _batch_views()
+    dss = {}
+    singles, items, rasts = [], [], []
+    for sc, cam, m, p, bg in views:
+        ds = dss.setdefault(id(sc), DeviceScene.from_host(sc))
+        r0 = Rasterizer(sc.n, cam.width, cam.height)
+        a_img, a_al = r0.render(ds, cam, m, p, bg)
+        singles.append((a_img, a_al, read_ws(r0)))
+        r1 = Rasterizer(sc.n, cam.width, cam.height)
+        rasts.append(r1)
+        img = torch.full((3, cam.height, cam.width), float("nan"), device="cuda")
+        al = torch.full((cam.height, cam.width), float("nan"), device="cuda")
+        items.append(dict(scene=ds.c_struct(), camera=_lib.make_camera(cam), layer_mask=m, planes=list(p), bg=bg,
+                          workspace=r1.workspace, ws_bytes=r1.ws_bytes, image=img, alpha=al))
+    _lib.gs_render_batch(items, 0)
+    torch.cuda.synchronize()
+    for k, (it, r1, (a_img, a_al, wa)) in enumerate(zip(items, rasts, singles)):
+        wb = read_ws(r1)
+        assert wb["status"].error == 0, k
+        assert torch.equal(it["image"], a_img), k
+        assert torch.equal(it["alpha"], a_al), k
+        assert np.array_equal(wa["n_contrib"], wb["n_contrib"]), k
+        assert np.array_equal(wa["t_final"], wb["t_final"]), k
+
+
+def test_render_batch_limits_and_overflow_isolation():
+    """More than GS_MAX_BATCH views is refused; a view that overflows its pair
+    capacity reports it in its own status word and leaves the others intact."""
+    from paper_2410_16978_gb300 import DeviceScene, Rasterizer, _lib
+    sc, cam, m, p, bg = WL["shells_ragged"]
+    ds = DeviceScene.from_host(sc)
+    ref_img, _ = Rasterizer(sc.n, cam.width, cam.height).render(ds, cam, m, p, bg)
+
+    def item(r):
+        return dict(scene=ds.c_struct(), camera=_lib.make_camera(cam), layer_mask=m, planes=list(p), bg=bg,
+                    workspace=r.workspace, ws_bytes=r.ws_bytes,
+                    image=torch.empty((3, cam.height, cam.width), device="cuda"), alpha=None)
+
+    r_ok = Rasterizer(sc.n, cam.width, cam.height)
+    with pytest.raises(ValueError):
+        _lib.gs_render_batch([item(r_ok)] * (_lib.GS_MAX_BATCH + 1), 0)
+    with pytest.raises(_lib.GsError):
+        _lib.gs_render_batch([item(r_ok), item(r_ok)], 0)   # one workspace shared by two views
+    r_small = Rasterizer(sc.n, cam.width, cam.height, dup_capacity=1000)
+    its = [item(r_small), item(r_ok)]
+    _lib.gs_render_batch(its, 0)
+    torch.cuda.synchronize()
+    assert r_small.status().error == _lib.GS_ERR_WORKSPACE
+    assert r_ok.status().error == 0
+    assert torch.equal(its[1]["image"], ref_img)
