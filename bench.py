@@ -53,6 +53,22 @@ def _env_int(k, d):
         return d
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time (every rank gets it)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpix_s(pixels_per_step: int, steps: int, world: int, total_ms: float) -> float:
+    """Pixels of all replicas / the max-over-ranks time, in Mpixels/s."""
+    return world * pixels_per_step * steps / (total_ms / 1e3) / 1e6
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -230,6 +246,56 @@ def run_serving(dev, n_requests=512, rate=300.0, budget=8 << 30):
     return out
 
 
+def run_training(dev, steps=24):
+    """The training workload: 500k Gaussians in 3 shell layers (SH degree 3),
+    8 cameras on a sphere of radius 4 at 800x800, targets rendered from the
+    seeded perturbed copy of the scene.  One step = one view through the
+    autograd Functions: render, 0.8 L1 + 0.2 D-SSIM + 0.8 alpha-L1 loss under
+    a random background, backward with blend weights, Adam on every layer;
+    after the timed steps one contribution prune at 0.005."""
+    import torch
+    import synth
+    from paper_2410_16978_gb300 import DeviceScene, Rasterizer, gs_profile_collect, gs_profile_enable
+    from paper_2410_16978_gb300.train import TrainConfig, Trainer
+
+    w = synth.scene_c3()
+    cams = w["cameras"]
+    W, H = cams[0].width, cams[0].height
+    tds = DeviceScene.from_host(w["target_scene"], device=dev)
+    targets = []
+    for cam in cams:
+        r = Rasterizer(tds.n, W, H, device=dev)
+        img, al = r.render(tds, cam, w["layer_mask"], (), (0.0, 0.0, 0.0), check=True)
+        targets.append((img.clone(), al.clone()))
+    del tds
+    tr = Trainer(DeviceScene.from_host(w["scene"], device=dev), cams, TrainConfig(w_alpha=0.8))
+    rng = np.random.default_rng(synth.config_seed(3))
+    bgs = [tuple(float(v) for v in rng.uniform(0, 1, 3)) for _ in range(steps + 8)]
+    for k in range(8):                                        # warm-up: one pass over the views
+        tr.step(k % 8, *targets[k % 8], bgs[k])
+    torch.cuda.synchronize()
+    gs_profile_collect()
+    gs_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    losses = []
+    e0.record()
+    for k in range(steps):
+        losses.append(tr.step(k % 8, *targets[k % 8], bgs[8 + k]))
+    e1.record()
+    torch.cuda.synchronize()
+    gs_profile_enable(False)
+    prof = gs_profile_collect()
+    ms = e0.elapsed_time(e1) / steps
+    n0 = tr.scene.n
+    n1 = tr.prune()
+    return {"workload": "500k Gaussians, 3 layers, SH3, 8 views 800x800, Adam on all layers, random background",
+            "steps": steps, "ms_per_step": round(ms, 4), "mpix_s": round(W * H / (ms / 1e3) / 1e6, 2),
+            "loss_first": round(float(losses[0]), 6), "loss_last": round(float(losses[-1]), 6),
+            "prune_threshold": 0.005, "gaussians_before_prune": n0, "gaussians_after_prune": n1,
+            "stages_ms_per_step": {k: round(v[0] / steps, 4) for k, v in prof.items() if v[1]},
+            "targets": "rendered on the GPU from the perturbed scene (the parity tests use oracle renders)"}
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -297,14 +363,10 @@ def run_gpu(args, rank, world, local_rank):
     launches = gs_kernel_launches() - l0
     gs_profile_enable(False)
     prof = gs_profile_collect()
-    total_ms = t_start.elapsed_time(t_end)
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), world, dev)
     per = sorted(a.elapsed_time(b) for a, b in evs)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     ms_step = total_ms / args.steps
-    value = world * (W * H) * args.steps / (total_ms / 1e3) / 1e6
+    value = whole_job_mpix_s(W * H, args.steps, world, total_ms)
 
     # ---- end to end: host inputs (pinned) and host result every step ----
     dimg_pin = torch.from_numpy(dimg_h).pin_memory()
@@ -342,7 +404,7 @@ def run_gpu(args, rank, world, local_rank):
     clk = clk.summary()
     sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp32_peak_tflops = sms * 128 * 2 * sm_max * 1e6 / 1e12
-    dom = max(("composite", "composite_bwd", "preprocess", "preprocess_bwd", "depth_sort", "tile_sort"),
+    dom = max(("composite", "composite_bwd", "preprocess", "preprocess_bwd", "depth_sort", "bin_rows", "bin_tiles"),
               key=lambda k: stage_ms.get(k, 0.0))
     if dom in ("composite", "composite_bwd"):
         flops = pairs_bwd * (FLOP_EVAL + (FLOP_BLEND_BWD if dom == "composite_bwd" else FLOP_BLEND_FWD))
@@ -353,7 +415,7 @@ def run_gpu(args, rank, world, local_rank):
     else:
         K = (sc.sh_degree + 1) ** 2
         per_g = {"preprocess": 12 + 12 + 16 + 4 + 1 + 12 * K + 56, "preprocess_bwd": 2 * (12 + 12 + 16 + 4 + 12 * K) + 48 + 1,
-                 "depth_sort": 4 * 24, "tile_sort": 0}[dom]
+                 "depth_sort": 4 * 24, "bin_rows": 0, "bin_tiles": 0}[dom]
         byts = sc.n * per_g
         achieved = byts / (stage_ms[dom] / 1e3) / 1e9
         roof = {"kernel": "k_" + dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -372,6 +434,9 @@ def run_gpu(args, rank, world, local_rank):
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         serving = run_serving(dev)
+    training = None
+    if rank == 0 and world == 1 and not args.no_training:
+        training = run_training(dev)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -388,7 +453,7 @@ def run_gpu(args, rank, world, local_rank):
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "ms_per_step": e2e_ms},
-                "clocks": clk, "gpu_launches": int(launches), "serving": serving,
+                "clocks": clk, "gpu_launches": int(launches), "serving": serving, "training": training,
                 "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()}}
         print(json.dumps(line), flush=True)
 
@@ -401,6 +466,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-training", action="store_true")
     args = ap.parse_args()
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)

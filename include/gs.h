@@ -47,10 +47,12 @@ enum { GS_DTYPE_F32 = 0, GS_DTYPE_F16 = 1, GS_DTYPE_BF16 = 2 };
 
 #define GS_TILE 16          /* tile edge in pixels */
 #define GS_MAX_PLANES 8     /* clip planes per call */
+#define GS_MAX_IMAGE_DIM 4096   /* largest image width and height */
 #define GS_MAX_LAYERS 32    /* layer ids 0..31 (bit L of a mask = layer L) */
 
 /* Pinhole camera, world -> camera p = R mu + t, OpenCV axes (x right, y down,
- * z forward).  R is row-major.  fx, fy, cx, cy in pixels; Gaussians with
+ * z forward).  R is row-major.  fx, fy, cx, cy in pixels; width and height
+ * in 1..GS_MAX_IMAGE_DIM (GS_ERR_INVALID otherwise); Gaussians with
  * p_z <= znear are culled (0.2 in every workload here).                       */
 typedef struct gs_camera {
     float R[9];
@@ -186,18 +188,64 @@ int gs_contrib_prune(const float *contrib_max, int64_t n, float threshold, uint8
                      int32_t *keep_index, int64_t *n_keep, void *workspace, size_t ws_bytes,
                      void *stream);
 
+/* ---- Training step (Sec. 3.2: each layer is optimised with the layers below
+ * it frozen, a random background colour per frame and the alpha channel in
+ * the loss).  These are the pieces around gs_render / gs_render_backward.  */
+
+/* Image loss and its gradient, all device float32, row-major planes:
+ *   Y = target_rgb + (1 - target_alpha) bg        target under this frame's bg
+ *   loss = (1 - lambda_dssim) mean|image - Y|
+ *        + lambda_dssim (1 - mean SSIM(image, Y))
+ *        + w_alpha mean|alpha - target_alpha|
+ * image, target_rgb [3][H][W] (target_rgb premultiplied, without background),
+ * alpha, target_alpha [H][W]; alpha may be NULL (no alpha term; then
+ * dL_dalpha, if given, is zeroed).  SSIM (Wang et al. 2004) per channel with
+ * an 11x11 Gaussian window of sigma 1.5, zero outside the image, C1 = 1e-4,
+ * C2 = 9e-4.  Writes *loss (device float), dL_dimage [3][H][W] and, when not
+ * NULL, dL_dalpha [H][W].  workspace: gs_image_loss_workspace_size bytes
+ * (9 W H floats of per-pixel maps plus block sums), 256-byte aligned.
+ * Asynchronous; GS_ERR_INVALID for NULL inputs or bad sizes.                 */
+int gs_image_loss_workspace_size(int32_t width, int32_t height, size_t *bytes);
+int gs_image_loss(const float *image, const float *alpha, const float *target_rgb, const float *target_alpha,
+                  const float *bg, int32_t width, int32_t height, float lambda_dssim, float w_alpha,
+                  void *workspace, size_t ws_bytes, float *loss, float *dL_dimage, float *dL_dalpha,
+                  void *stream);
+
+/* Adam moments (device float32, shaped like the gs_grads fields), in the
+ * order means, log_scales, quats, opacity_logit, sh.                        */
+typedef struct gs_adam_state {
+    float *m[5];
+    float *v[5];
+} gs_adam_state;
+
+/* One Adam step (Kingma & Ba 2015, with bias correction) on the scene's
+ * parameters IN PLACE (the scene's pointers are written despite the const
+ * of gs_scene; every field must be float32).  lr[5] per field in the order
+ * of gs_adam_state; step t >= 1 is this update's index.  A Gaussian whose
+ * layer bit is not in train_layer_mask keeps parameters and moments
+ * (frozen layers).  GS_ERR_INVALID for non-float32 fields or NULL arrays.   */
+int gs_adam_step(const gs_scene *scene, const gs_grads *grads, const gs_adam_state *state, const float *lr,
+                 float beta1, float beta2, float eps, int32_t step, uint32_t train_layer_mask, void *stream);
+
+/* Row gather for applying a prune: dst row i = src row index[i] for
+ * i < n, rows of row_bytes > 0 bytes (2-byte aligned arrays when row_bytes is
+ * even; copied in 4-, 2- or 1-byte words); index (device int32) as written
+ * by gs_contrib_prune's keep_index, every entry a valid row of src.  dst must
+ * not overlap src.  Asynchronous.                                            */
+int gs_gather_rows(const void *src, void *dst, int64_t row_bytes, const int32_t *index, int64_t n, void *stream);
+
 /* Byte offsets of the regions of a render workspace of ws_bytes bytes, for
  * tests and debugging tools (host only, no device access).  out[k] for
  * k = 0..GS_LAYOUT_COUNT-1 in this order:
  *   0 status/control block   1 records (48 B per Gaussian: u, v, A2, beta,
  *   G2, opacity, r, g, b, depth, rect01, rect23)   2 tiles touched (u32)
- *   3 depth keys (u32 float bits, 0xFFFFFFFF when culled)   4 final tile ids
- *   of the pair list (u32)   5 final Gaussian ids of the pair list (u32)
- *   6 tile ranges (u32 start, end per tile)   7 final transmittance (f32
- *   per pixel)   8 n_contrib (u32 per pixel)   9 record gradients (48 B per
- *   Gaussian)   10 total bytes   11 pair capacity.  Returns GS_ERR_WORKSPACE
- *   when ws_bytes is below the fixed part.                                     */
-#define GS_LAYOUT_COUNT 12
+ *   3 depth keys (u32 float bits, 0xFFFFFFFF when culled)   4 the pair list:
+ *   Gaussian ids (u32) in tile order, depth order within a tile   5 tile
+ *   ranges (u32 start, end per tile)   6 final transmittance (f32 per pixel)
+ *   7 n_contrib (u32 per pixel)   8 record gradients (48 B per Gaussian)
+ *   9 total bytes   10 pair capacity.  Returns GS_ERR_WORKSPACE when
+ *   ws_bytes is below the fixed part.                                         */
+#define GS_LAYOUT_COUNT 11
 int gs_workspace_layout(int64_t n, int32_t width, int32_t height, size_t ws_bytes, int64_t *out);
 
 /* gs_contrib_prune without a workspace, for callers that cannot allocate
@@ -233,14 +281,15 @@ enum {
     GS_STAGE_PREPROCESS = 0,   /* S1 */
     GS_STAGE_COMPACT,          /* S2: visible compaction (scan) */
     GS_STAGE_DEPTH_SORT,       /* S2: 4 radix passes on depth bits */
-    GS_STAGE_DUP_SCAN,         /* S2: ordered scan of tile counts */
-    GS_STAGE_EMIT,             /* S2: (tile, Gaussian) pairs */
-    GS_STAGE_TILE_SORT,        /* S2: radix passes on tile ids */
-    GS_STAGE_RANGES,           /* S2: per-tile [start, end), heaviest-first tile order, checkpoint bases */
+    GS_STAGE_BIN_ROWS,         /* S2: depth-ordered split of the pairs into tile rows */
+    GS_STAGE_BIN_TILES,        /* S2: split of every row into its tiles, tile ranges */
+    GS_STAGE_COMPOSITE_SETUP,  /* S3: heaviest-first tile order, checkpoint bases */
     GS_STAGE_COMPOSITE,        /* S3 (one launch per gs_render or gs_render_batch call) */
     GS_STAGE_COMPOSITE_BWD,    /* S4a (zeroing the record gradients, work-item set-up, compositor) */
     GS_STAGE_PREPROCESS_BWD,   /* S4b */
     GS_STAGE_PRUNE,            /* S5 */
+    GS_STAGE_LOSS,             /* training: image loss and its gradient */
+    GS_STAGE_ADAM,             /* training: parameter update */
     GS_STAGE_COUNT
 };
 int gs_profile_enable(int on);

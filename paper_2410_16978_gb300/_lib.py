@@ -22,13 +22,14 @@ GS_MAX_PLANES = 8
 GS_MAX_BATCH = 16
 
 EXPORTED = ("gs_render_workspace_size", "gs_render", "gs_render_batch", "gs_render_backward", "gs_prune_workspace_size",
-            "gs_contrib_prune", "gs_contrib_prune_noalloc", "gs_workspace_layout", "gs_read_status", "gs_profile_enable", "gs_profile_collect",
-            "gs_kernel_launches", "gs_last_error_string", "gs_version")
-STAGES = ("preprocess", "compact", "depth_sort", "dup_scan", "emit", "tile_sort", "ranges", "composite",
-          "composite_bwd", "preprocess_bwd", "prune")
-GS_LAYOUT_COUNT = 12
-LAYOUT_NAMES = ("ctl", "rec", "tiles", "depth", "tile_k", "tile_v", "ranges", "t_final", "n_contrib", "rec_grad",
-                "total", "dup_capacity")
+            "gs_contrib_prune", "gs_contrib_prune_noalloc", "gs_image_loss_workspace_size", "gs_image_loss",
+            "gs_adam_step", "gs_gather_rows", "gs_workspace_layout", "gs_read_status", "gs_profile_enable",
+            "gs_profile_collect", "gs_kernel_launches", "gs_last_error_string", "gs_version")
+STAGES = ("preprocess", "compact", "depth_sort", "bin_rows", "bin_tiles", "composite_setup", "composite",
+          "composite_bwd", "preprocess_bwd", "prune", "loss", "adam")
+GS_LAYOUT_COUNT = 11
+LAYOUT_NAMES = ("ctl", "rec", "tiles", "depth", "list", "ranges", "t_final", "n_contrib", "rec_grad", "total",
+                "dup_capacity")
 
 
 class gs_camera(ctypes.Structure):
@@ -58,6 +59,10 @@ class gs_render_request(ctypes.Structure):
                 ("layer_mask", ctypes.c_uint32), ("n_planes", ctypes.c_int32),
                 ("planes", ctypes.POINTER(gs_clip_plane)), ("bg", ctypes.c_float * 3), ("_reserved", ctypes.c_float),
                 ("workspace", _P), ("ws_bytes", ctypes.c_size_t), ("image", _P), ("alpha", _P)]
+
+
+class gs_adam_state(ctypes.Structure):
+    _fields_ = [("m", _P * 5), ("v", _P * 5)]
 
 
 class gs_status(ctypes.Structure):
@@ -107,6 +112,13 @@ def load(build_if_missing: bool = True):
         L.gs_contrib_prune.argtypes = [_P, ctypes.c_int64, ctypes.c_float, _P, _P, _P, _P, ctypes.c_size_t, _P]
         L.gs_read_status.argtypes = [_P, ctypes.POINTER(gs_status), _P]
         L.gs_contrib_prune_noalloc.argtypes = [_P, ctypes.c_int64, ctypes.c_float, _P, _P, _P, _P]
+        L.gs_image_loss_workspace_size.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+        L.gs_image_loss.argtypes = [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_float, ctypes.c_float, _P, ctypes.c_size_t, _P, _P, _P, _P]
+        L.gs_adam_step.argtypes = [ctypes.POINTER(gs_scene), ctypes.POINTER(gs_grads), ctypes.POINTER(gs_adam_state),
+                                   ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_int32, ctypes.c_uint32, _P]
+        L.gs_gather_rows.argtypes = [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P]
         L.gs_workspace_layout.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t,
                                           ctypes.POINTER(ctypes.c_int64)]
         L.gs_profile_enable.argtypes = [ctypes.c_int]
@@ -227,6 +239,32 @@ def gs_contrib_prune(contrib_max, n: int, threshold: float, keep, keep_index, n_
 def gs_contrib_prune_noalloc(contrib_max, n: int, threshold: float, keep, keep_index, n_keep, stream: int) -> None:
     _check(load().gs_contrib_prune_noalloc(_ptr(contrib_max), int(n), float(threshold), _ptr(keep), _ptr(keep_index),
                                            _ptr(n_keep), ctypes.c_void_p(stream)))
+
+
+def gs_image_loss_workspace_size(width: int, height: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().gs_image_loss_workspace_size(int(width), int(height), ctypes.byref(out)))
+    return int(out.value)
+
+
+def gs_image_loss(image, alpha, target_rgb, target_alpha, bg, width: int, height: int, lambda_dssim: float,
+                  w_alpha: float, workspace, ws_bytes: int, loss, dL_dimage, dL_dalpha, stream: int) -> None:
+    bgv = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    _check(load().gs_image_loss(_ptr(image), _ptr(alpha), _ptr(target_rgb), _ptr(target_alpha), bgv, int(width),
+                                int(height), float(lambda_dssim), float(w_alpha), _ptr(workspace), int(ws_bytes),
+                                _ptr(loss), _ptr(dL_dimage), _ptr(dL_dalpha), ctypes.c_void_p(stream)))
+
+
+def gs_adam_step(scene: gs_scene, grads: gs_grads, state: gs_adam_state, lr, beta1: float, beta2: float, eps: float,
+                 step: int, train_layer_mask: int, stream: int) -> None:
+    lrv = (ctypes.c_float * 5)(*[float(v) for v in lr])
+    _check(load().gs_adam_step(ctypes.byref(scene), ctypes.byref(grads), ctypes.byref(state), lrv, float(beta1),
+                               float(beta2), float(eps), int(step), int(train_layer_mask) & 0xFFFFFFFF,
+                               ctypes.c_void_p(stream)))
+
+
+def gs_gather_rows(src, dst, row_bytes: int, index, n: int, stream: int) -> None:
+    _check(load().gs_gather_rows(_ptr(src), _ptr(dst), int(row_bytes), _ptr(index), int(n), ctypes.c_void_p(stream)))
 
 
 def gs_workspace_layout(n: int, width: int, height: int, ws_bytes: int) -> dict:

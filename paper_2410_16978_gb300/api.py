@@ -81,11 +81,25 @@ class DeviceScene:
         s.dtype_scale_rot = _DT[self.sr_dtype][0]
         return s
 
-    def subset(self, keep_index: torch.Tensor) -> "DeviceScene":
-        idx = keep_index.long()
-        return DeviceScene(*(p.index_select(0, idx).contiguous() for p in self.params()),
-                           self.layer.index_select(0, idx).contiguous(), self.sh_degree, self.sh_dtype,
+    def subset(self, keep_index: torch.Tensor, stream=None) -> "DeviceScene":
+        """The Gaussians keep_index (device int32, in order), gathered by gs_gather_rows."""
+        return DeviceScene(*(gather_rows(a, keep_index, stream) for a in self.params()),
+                           gather_rows(self.layer, keep_index, stream), self.sh_degree, self.sh_dtype,
                            self.sr_dtype)
+
+
+def gather_rows(src: torch.Tensor, keep_index: torch.Tensor, stream=None) -> torch.Tensor:
+    """dst[i] = src[keep_index[i]] along the first axis (gs_gather_rows)."""
+    _require_cuda(src, "src")
+    _require_cuda(keep_index, "keep_index")
+    if keep_index.dtype != torch.int32:
+        raise ValueError("keep_index must be int32")
+    n = int(keep_index.shape[0])
+    row_bytes = max(1, int(math.prod(src.shape[1:]))) * src.element_size()
+    dst = torch.empty((n,) + tuple(src.shape[1:]), dtype=src.dtype, device=src.device)
+    if n:
+        _lib.gs_gather_rows(src, dst, row_bytes, keep_index, n, _stream_handle(stream))
+    return dst
 
 
 def _stream_handle(stream: Optional[torch.cuda.Stream]) -> int:

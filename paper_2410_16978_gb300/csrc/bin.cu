@@ -1,0 +1,378 @@
+// S2 (second half) - tile binning by two stable bucket passes (Sec. 3.3: the
+// splats of each tile are composited in camera-sorted order).
+//
+// Input: the visible Gaussians in depth order (order[p], p < n_vis, from the
+// depth radix sort) and their tile rectangles.  Output: for every tile the
+// Gaussians whose rectangle covers it, in depth order (ties by index, as the
+// depth sort is stable), concatenated in tile order, and each tile's range.
+// That is the stable sort of the (tile, Gaussian) pairs by tile, built
+// without sorting the pairs:
+//
+//  1. Rows.  The (Gaussian, tile row) pairs, in depth order, are split into
+//     one list per tile row.  K = gridDim.x * 8 warps each take a contiguous
+//     chunk of the depth order; a first pass counts each chunk's entries per
+//     row in shared memory, an exclusive scan over the chunks of every row
+//     (row-major count matrix [Ty][K]) gives each chunk its place, and a
+//     second pass writes the entries (Gaussian, x0 | x1 << 16) there.  Within
+//     a chunk the entries go out in depth order: a warp expands 32 Gaussians
+//     into their row pairs 32 at a time and ranks equal rows by lane
+//     (__match_any_sync), and lanes hold consecutive pairs in depth order.
+//  2. Tiles.  Every row list is cut into pieces of a fixed number of entries
+//     (thousands of pieces per frame, so heavy rows spread over all SMs); a
+//     warp per piece counts its pairs per tile, a per-row scan over the
+//     pieces gives each (piece, tile) its first list position and each tile
+//     its range, and a second pass writes the Gaussian ids, again ranked in
+//     depth order within a warp.
+//
+// Per pair this writes the row entry once (8 B, per row of the rectangle, not
+// per tile) and the final Gaussian id once (4 B); the count matrix is a few MB.
+// Requires Tx, Ty <= kBinMaxDim (images up to 4096 x 4096).
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// Inclusive warp scan.
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Exclusive scan over a block of NT threads (NT / 32 <= 32 warps).
+template <int NT>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_w, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = NT / 32;
+    const uint32_t x = warp_incl_scan(v, lane);
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < NW ? s_w[lane] : 0;
+        w = warp_incl_scan(w, lane);
+        if (lane < NW) s_w[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t base = warp > 0 ? s_w[warp - 1] : 0;
+    *total = s_w[NW - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+// Lanes hold 32 consecutive list entries in order (the valid ones first),
+// entry j covering slots [start_j, start_j + w_j) of the expanded sequence.
+// Returns the entry that owns slot k0 + lane: entries starting before k0 plus
+// those starting in [k0, k0 + lane], minus one.  Valid entries have w > 0.
+__device__ __forceinline__ int window_owner(uint32_t start, uint32_t w, uint32_t k0, int lane) {
+    const unsigned before = __ballot_sync(FULL, w > 0 && start < k0);
+    const bool in = w > 0 && start >= k0 && start - k0 < 32u;
+    const unsigned mask = __reduce_or_sync(FULL, in ? 1u << (start - k0) : 0u);
+    return __popc(before) - 1 + __popc(mask & (0xFFFFFFFFu >> (31 - lane)));
+}
+
+// In-place inclusive prefix sum of a[0..n) (shared memory) by one warp.
+__device__ __forceinline__ void warp_prefix_inplace(uint32_t *a, int n, int lane) {
+    const int per = (n + 31) / 32;
+    const int b = min(n, lane * per), e = min(n, b + per);
+    uint32_t sum = 0;
+    for (int i = b; i < e; ++i) sum += a[i];
+    uint32_t run = warp_incl_scan(sum, lane) - sum;
+    for (int i = b; i < e; ++i) {
+        run += a[i];
+        a[i] = run;
+    }
+    __syncwarp();
+}
+
+struct RowInfo {           // per tile row, in the workspace
+    uint32_t start;        // first row-list entry of the row
+    uint32_t entries;      // row-list entries of the row
+    uint32_t pair_start;   // first pair (final list position) of the row
+    uint32_t pairs;        // pairs of the row
+    uint32_t piece_start;  // first piece of the row (pieces: kPiece-entry parts of row lists)
+    uint32_t pad[3];
+};
+
+// Pass 1 (SCATTER = false: count, true: write) over the chunks of the depth order.
+template <bool SCATTER>
+__global__ void __launch_bounds__(256) k_bin_rows(const uint32_t *__restrict__ order, const Rec *__restrict__ rec,
+                                                  uint32_t n_cap, int Ty, uint32_t *__restrict__ M,
+                                                  RowInfo *__restrict__ rows, uint2 *__restrict__ rowlist,
+                                                  const Ctl *__restrict__ ctl) {
+    __shared__ uint32_t s_cnt[8][kBinMaxDim + 1];
+    __shared__ uint32_t s_px[SCATTER ? 1 : 8][kBinMaxDim + 1];
+    if (SCATTER && ctl->st.error != GS_OK) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t K = gridDim.x * 8u, c = blockIdx.x * 8u + warp;
+    const uint32_t n = min(ctl->n_vis, n_cap);
+    const uint32_t b = static_cast<uint32_t>(static_cast<uint64_t>(n) * c / K);
+    const uint32_t e = static_cast<uint32_t>(static_cast<uint64_t>(n) * (c + 1) / K);
+    for (int r = lane; r <= Ty; r += 32) {
+        s_cnt[warp][r] = (SCATTER && r < Ty) ? rows[r].start + M[static_cast<size_t>(r) * K + c] : 0u;
+        if (!SCATTER) s_px[warp][r] = 0;
+    }
+    __syncwarp();
+    for (uint32_t p0 = b; p0 < e; p0 += 32) {
+        const uint32_t p = p0 + lane;
+        uint32_t g = 0, y0 = 0, x01 = 0, nrows = 0;
+        if (p < e) {
+            g = order[p];
+            const float4 cc = rec[g].c;
+            const uint32_t r0 = __float_as_uint(cc.z), r1 = __float_as_uint(cc.w);
+            y0 = r0 >> 16;
+            nrows = (r1 >> 16) - y0;
+            x01 = (r0 & 0xFFFFu) | (r1 << 16);     // x0 | x1 << 16
+        }
+        if (!SCATTER) {
+            // rows [y0, y0 + nrows) each get one entry and w pairs: difference array
+            if (nrows) {
+                const uint32_t w = (x01 >> 16) - (x01 & 0xFFFFu);
+                atomicAdd(&s_cnt[warp][y0], 1u);
+                atomicSub(&s_cnt[warp][y0 + nrows], 1u);
+                atomicAdd(&s_px[warp][y0], w);
+                atomicSub(&s_px[warp][y0 + nrows], w);
+            }
+            continue;
+        }
+        const uint32_t incl = warp_incl_scan(nrows, lane);
+        const uint32_t total = __shfl_sync(FULL, incl, 31);
+        const uint32_t start = incl - nrows;
+        for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+            const uint32_t k = k0 + lane;
+            const bool act = k < total;
+            const int j = window_owner(start, nrows, k0, lane);
+            const uint32_t sj = __shfl_sync(FULL, start, j), yj = __shfl_sync(FULL, y0, j);
+            const uint32_t gj = __shfl_sync(FULL, g, j), xj = __shfl_sync(FULL, x01, j);
+            const uint32_t r = act ? yj + (k - sj) : 0u;
+            const unsigned peers = __match_any_sync(FULL, act ? r : 0x10000u + lane);
+            const uint32_t before = act ? s_cnt[warp][r] : 0u;
+            __syncwarp();
+            if (act && (peers & lt) == 0) s_cnt[warp][r] = before + __popc(peers);
+            if (act) rowlist[before + __popc(peers & lt)] = make_uint2(gj, xj);
+            __syncwarp();
+        }
+    }
+    if (!SCATTER) {
+        __syncwarp();
+        warp_prefix_inplace(s_cnt[warp], Ty, lane);
+        warp_prefix_inplace(s_px[warp], Ty, lane);
+        for (int r = lane; r < Ty; r += 32) {
+            M[static_cast<size_t>(r) * K + c] = s_cnt[warp][r];
+            if (s_px[warp][r]) atomicAdd(&rows[r].pairs, s_px[warp][r]);
+        }
+    }
+}
+
+// Per row (one CTA each): exclusive scan of the row's K chunk counts in place.
+__global__ void __launch_bounds__(1024) k_bin_rowscan(uint32_t *__restrict__ M, int K, RowInfo *__restrict__ rows) {
+    __shared__ uint32_t s_w[32];
+    uint32_t *row = M + static_cast<size_t>(blockIdx.x) * K;
+    const int per = (K + 1023) / 1024;
+    uint32_t v[kBinChunksPerThread];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < kBinChunksPerThread; ++q) {
+        const int i = threadIdx.x * per + q;
+        v[q] = (q < per && i < K) ? row[i] : 0u;
+        sum += v[q];
+    }
+    uint32_t tot;
+    uint32_t run = block_excl_scan<1024>(sum, s_w, &tot);
+#pragma unroll
+    for (int q = 0; q < kBinChunksPerThread; ++q) {
+        const int i = threadIdx.x * per + q;
+        if (q < per && i < K) row[i] = run;
+        run += v[q];
+    }
+    if (threadIdx.x == 0) rows[blockIdx.x].entries = tot;
+}
+
+// One CTA: row starts, pair starts, piece starts, the pair total and the
+// capacity check.
+__global__ void __launch_bounds__(256) k_bin_rowstart(RowInfo *__restrict__ rows, int Ty, Ctl *__restrict__ ctl,
+                                                      uint64_t cap, uint32_t piece) {
+    __shared__ uint32_t s_w[8];
+    const int r = threadIdx.x;
+    uint32_t te, tp, tq;
+    const uint32_t ent = r < Ty ? rows[r].entries : 0u;
+    const uint32_t s0 = block_excl_scan<256>(ent, s_w, &te);
+    const uint32_t s1 = block_excl_scan<256>(r < Ty ? rows[r].pairs : 0u, s_w, &tp);
+    const uint32_t s2 = block_excl_scan<256>((ent + piece - 1) / piece, s_w, &tq);
+    if (r < Ty) {
+        rows[r].start = s0;
+        rows[r].pair_start = s1;
+        rows[r].piece_start = s2;
+    }
+    if (r == 0) {
+        ctl->st.n_dup = tp;
+        ctl->st.dup_capacity = cap;
+        ctl->n_pieces = tq;
+        if (tp > cap) ctl->st.error = GS_ERR_WORKSPACE;
+    }
+}
+
+// Pass 2 (SCATTER = false: count, true: write), one warp per piece of a row
+// list.  Count: per-(piece, tile) counts into P[piece][Tx].  Write: P holds
+// the first list position of every (piece, tile) (k_bin_tiles_scan).
+template <bool SCATTER>
+__global__ void __launch_bounds__(256) k_bin_tiles(const uint2 *__restrict__ rowlist, const RowInfo *__restrict__ rows,
+                                                   int Tx, int Ty, uint32_t piece, uint32_t *__restrict__ P,
+                                                   uint32_t *__restrict__ list, const Ctl *__restrict__ ctl) {
+    __shared__ uint32_t s_cnt[8][kBinMaxDim + 1];
+    __shared__ uint32_t s_ps[kBinMaxDim + 1];
+    if (ctl->st.error != GS_OK) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t npieces = ctl->n_pieces;
+    for (int r = threadIdx.x; r < Ty; r += blockDim.x) s_ps[r] = rows[r].piece_start;
+    if (threadIdx.x == 0) s_ps[Ty] = npieces;
+    __syncthreads();
+    const uint32_t nwarps = gridDim.x * 8u;
+    for (uint32_t p = blockIdx.x * 8u + warp; p < npieces; p += nwarps) {
+        int lo = 0, hi = Ty - 1;                 // largest row r with s_ps[r] <= p
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_ps[mid] <= p) lo = mid; else hi = mid - 1;
+        }
+        const RowInfo ri = rows[lo];
+        const uint32_t e0 = ri.start + (p - s_ps[lo]) * piece;
+        const uint32_t e1 = min(e0 + piece, ri.start + ri.entries);
+        uint32_t *Pp = P + static_cast<size_t>(p) * Tx;
+        for (int t = lane; t <= Tx; t += 32) s_cnt[warp][t] = (SCATTER && t < Tx) ? Pp[t] : 0u;
+        __syncwarp();
+        for (uint32_t q0 = e0; q0 < e1; q0 += 32) {
+            const uint32_t q = q0 + lane;
+            uint32_t g = 0, x0 = 0, w = 0;
+            if (q < e1) {
+                const uint2 en = rowlist[q];
+                g = en.x;
+                x0 = en.y & 0xFFFFu;
+                w = (en.y >> 16) - x0;
+            }
+            if (!SCATTER) {
+                // tiles [x0, x0 + w) each get one pair: difference array
+                if (w) {
+                    atomicAdd(&s_cnt[warp][x0], 1u);
+                    atomicSub(&s_cnt[warp][x0 + w], 1u);
+                }
+                continue;
+            }
+            const uint32_t incl = warp_incl_scan(w, lane);
+            const uint32_t total = __shfl_sync(FULL, incl, 31);
+            const uint32_t start = incl - w;
+            for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+                const uint32_t k = k0 + lane;
+                const bool act = k < total;
+                const int j = window_owner(start, w, k0, lane);
+                const uint32_t sj = __shfl_sync(FULL, start, j), xj = __shfl_sync(FULL, x0, j);
+                const uint32_t gj = __shfl_sync(FULL, g, j);
+                const uint32_t t = act ? xj + (k - sj) : 0u;
+                const unsigned peers = __match_any_sync(FULL, act ? t : 0x10000u + lane);
+                const uint32_t before = act ? s_cnt[warp][t] : 0u;
+                __syncwarp();
+                if (act && (peers & lt) == 0) s_cnt[warp][t] = before + __popc(peers);
+                if (SCATTER && act) list[before + __popc(peers & lt)] = gj;
+                __syncwarp();
+            }
+        }
+        if (!SCATTER) {
+            __syncwarp();
+            warp_prefix_inplace(s_cnt[warp], Tx, lane);
+            for (int t = lane; t < Tx; t += 32) Pp[t] = s_cnt[warp][t];
+        }
+        __syncwarp();
+    }
+}
+
+// Per row (one CTA of 4 x 256 threads): thread (slice s, tile t) sums the
+// counts of tile t over its quarter of the row's pieces; the slice sums give
+// each tile's total and range; then every (piece, tile) count is replaced by
+// its first list position.
+__global__ void __launch_bounds__(1024) k_bin_tiles_scan(const RowInfo *__restrict__ rows, int Tx, uint32_t piece,
+                                                         uint32_t *__restrict__ P, uint2 *__restrict__ ranges,
+                                                         const Ctl *__restrict__ ctl) {
+    __shared__ uint32_t s_sum[4][kBinMaxDim];
+    __shared__ uint32_t s_w[32];
+    if (ctl->st.error != GS_OK) return;
+    const int r = blockIdx.x;
+    const int t = threadIdx.x & (kBinMaxDim - 1), sl = threadIdx.x >> 8;
+    const RowInfo ri = rows[r];
+    const uint32_t npc = (ri.entries + piece - 1) / piece;
+    const uint32_t per = (npc + 3) / 4;
+    const uint32_t p0 = ri.piece_start + min(npc, sl * per), p1 = ri.piece_start + min(npc, (sl + 1) * per);
+    uint32_t sum = 0;
+    if (t < Tx)
+        for (uint32_t p = p0; p < p1; ++p) sum += P[static_cast<size_t>(p) * Tx + t];
+    s_sum[sl][t] = sum;
+    __syncthreads();
+    uint32_t tot = 0, before = 0;
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t v = s_sum[q][t];
+        if (q < sl) before += v;
+        tot += v;
+    }
+    uint32_t all;
+    const uint32_t toff = block_excl_scan<1024>(sl == 0 && t < Tx ? tot : 0u, s_w, &all);
+    if (sl == 0) s_sum[0][t] = toff;          // slice 0's tile offsets, read by every slice below
+    __syncthreads();
+    if (t < Tx) {
+        const uint32_t base = ri.pair_start + s_sum[0][t];
+        if (sl == 0) ranges[static_cast<size_t>(r) * Tx + t] = make_uint2(base, base + tot);
+        uint32_t run = base + before;
+        for (uint32_t p = p0; p < p1; ++p) {
+            uint32_t *c = P + static_cast<size_t>(p) * Tx + t;
+            const uint32_t v = *c;
+            *c = run;
+            run += v;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_bin_rows(const uint32_t *order, const Rec *rec, uint32_t n_cap, int Ty, uint32_t *M,
+                            void *rows_buf, uint2 *rowlist, Ctl *ctl, uint64_t cap, uint32_t piece, cudaStream_t st) {
+    if (Ty > kBinMaxDim) return cudaErrorInvalidValue;
+    RowInfo *rows = static_cast<RowInfo *>(rows_buf);
+    cudaError_t e = cudaMemsetAsync(rows, 0, static_cast<size_t>(Ty) * sizeof(RowInfo), st);
+    if (e != cudaSuccess) return e;
+    k_bin_rows<false><<<kBinBlocks, 256, 0, st>>>(order, rec, n_cap, Ty, M, rows, rowlist, ctl);
+    k_bin_rowscan<<<Ty, 1024, 0, st>>>(M, kBinBlocks * 8, rows);
+    k_bin_rowstart<<<1, 256, 0, st>>>(rows, Ty, ctl, cap, piece);
+    k_bin_rows<true><<<kBinBlocks, 256, 0, st>>>(order, rec, n_cap, Ty, M, rows, rowlist, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_tiles(const uint2 *rowlist, const void *rows_buf, int Tx, int Ty, uint32_t piece, uint32_t *P,
+                             uint32_t *list, uint2 *ranges, const Ctl *ctl, cudaStream_t st) {
+    if (Tx > kBinMaxDim || Ty > kBinMaxDim) return cudaErrorInvalidValue;
+    const RowInfo *rows = static_cast<const RowInfo *>(rows_buf);
+    const int G = 4 * sort_blocks();
+    k_bin_tiles<false><<<G, 256, 0, st>>>(rowlist, rows, Tx, Ty, piece, P, list, ctl);
+    k_bin_tiles_scan<<<Ty, 1024, 0, st>>>(rows, Tx, piece, P, ranges, ctl);
+    k_bin_tiles<true><<<G, 256, 0, st>>>(rowlist, rows, Tx, Ty, piece, P, list, ctl);
+    return cudaGetLastError();
+}
+
+uint32_t bin_piece_entries(int64_t dup_cap, int Tx) {
+    // pieces of 256 entries, doubled until the piece count matrix stays near 64 MB
+    uint32_t piece = 256;
+    while (piece < 4096 && static_cast<double>(dup_cap) / piece * Tx * 4.0 > 64.0 * (1 << 20)) piece *= 2;
+    return piece;
+}
+
+size_t bin_piece_bytes(int64_t dup_cap, int Tx, int Ty) {
+    const uint32_t piece = bin_piece_entries(dup_cap, Tx);
+    return (static_cast<size_t>(dup_cap) / piece + Ty + 1) * Tx * 4;
+}
+
+size_t bin_rows_bytes(int Ty) { return static_cast<size_t>(Ty) * sizeof(RowInfo); }
+static_assert(sizeof(RowInfo) == 32, "RowInfo layout");
+
+}  // namespace gs

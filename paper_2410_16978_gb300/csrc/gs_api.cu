@@ -15,7 +15,7 @@ namespace gs {
 static size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
-    if (n < 0 || n > 0x7FFFFFFF || W <= 0 || H <= 0 || W > (1 << 20) || H > (1 << 20) || dup_cap < 0 ||
+    if (n < 0 || n > 0x7FFFFFFF || W <= 0 || H <= 0 || W > GS_MAX_IMAGE_DIM || H > GS_MAX_IMAGE_DIM || dup_cap < 0 ||
         dup_cap > 0xFFFFFFFFLL)
         return false;
     Layout o;
@@ -31,7 +31,10 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     o.depth = take(N * 4);
     o.sort_k[0] = take(N * 4); o.sort_k[1] = take(N * 4);
     o.sort_v[0] = take(N * 4); o.sort_v[1] = take(N * 4);
-    o.dup_off = take(N * 4);
+    o.bin_m = take(static_cast<size_t>(kBinChunks) * o.Ty * 4);
+    o.bin_rows = take(bin_rows_bytes(o.Ty));
+    o.bin_piece = bin_piece_entries(dup_cap, o.Tx);
+    o.bin_p = take(bin_piece_bytes(dup_cap, o.Tx, o.Ty));
     o.ranges = take(static_cast<size_t>(o.Tn) * 8);
     o.t_final = take(P * 4);
     o.n_contrib = take(P * 4);
@@ -45,8 +48,8 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     const size_t segs = D / kSeg + static_cast<size_t>(o.Tn) + 1;   // >= sum over tiles of ceil(len / kSeg)
     o.ckpt = take(segs * kTilePix * sizeof(float4));
     o.items = take(4 * segs * sizeof(uint2));
-    o.tile_k[0] = take(D * 4); o.tile_k[1] = take(D * 4);
-    o.tile_v[0] = take(D * 4); o.tile_v[1] = take(D * 4);
+    o.rowlist = take(D * 8);     // row entries <= pairs
+    o.list = take(D * 4);
     o.total = off;
     *L = o;
     return true;
@@ -156,8 +159,8 @@ int check_scene(const gs_scene *s, SceneView *v) {
 
 int check_camera(const gs_camera *c, CamView *v) {
     if (!c) return fail(GS_ERR_INVALID, "camera is NULL");
-    if (c->width <= 0 || c->height <= 0 || c->width > (1 << 20) || c->height > (1 << 20))
-        return fail(GS_ERR_INVALID, "bad image size %dx%d", c->width, c->height);
+    if (c->width <= 0 || c->height <= 0 || c->width > GS_MAX_IMAGE_DIM || c->height > GS_MAX_IMAGE_DIM)
+        return fail(GS_ERR_INVALID, "image size %dx%d outside 1..%d", c->width, c->height, GS_MAX_IMAGE_DIM);
     if (!(c->fx > 0.f) || !(c->fy > 0.f)) return fail(GS_ERR_INVALID, "focal lengths must be > 0");
     std::memcpy(v->R, c->R, sizeof v->R);
     std::memcpy(v->t, c->t, sizeof v->t);
@@ -168,11 +171,6 @@ int check_camera(const gs_camera *c, CamView *v) {
     return GS_OK;
 }
 
-int tile_sort_passes(int Tn) {
-    int bits = 0;
-    while ((1LL << bits) < Tn) ++bits;
-    return (bits + 7) / 8;
-}
 
 CompositeBufs composite_bufs(void *ws, const Layout &L) {
     Ctl *ctl = at<Ctl>(ws, L.ctl);
@@ -248,7 +246,6 @@ int render_front(const gs_scene *scene, const gs_camera *camera, uint32_t layer_
     void *ws = workspace;
     Ctl *ctl = at<Ctl>(ws, L.ctl);
     const uint32_t n = static_cast<uint32_t>(sv.n);
-    const uint32_t cap = static_cast<uint32_t>(L.dup_cap);
     if ((rc = cuda_check(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st), "memset status")) != GS_OK) return rc;
     if ((rc = cuda_check(cudaMemsetAsync(at<char>(ws, L.ranges), 0, static_cast<size_t>(L.Tn) * 8, st),
                          "memset ranges")) != GS_OK)
@@ -283,43 +280,31 @@ int render_front(const gs_scene *scene, const gs_camera *camera, uint32_t layer_
         }
     }
     uint32_t *order = sv2[0];
-    uint32_t *dup_off = at<uint32_t>(ws, L.dup_off);
-    {
-        Stage sg(GS_STAGE_DUP_SCAN, st, 3);
-        if ((rc = cuda_check(launch_dup_offsets(order, tiles, n, dup_off, partials, ctl, L.dup_cap, st),
-                             "dup offsets")) != GS_OK)
-            return rc;
-    }
-    uint32_t *tk[2] = {at<uint32_t>(ws, L.tile_k[0]), at<uint32_t>(ws, L.tile_k[1])};
-    uint32_t *tv[2] = {at<uint32_t>(ws, L.tile_v[0]), at<uint32_t>(ws, L.tile_v[1])};
-    {
-        Stage sg(GS_STAGE_EMIT, st, 1);
-        if ((rc = cuda_check(launch_emit(order, dup_off, rec, n, cv.Tx, tk[0], tv[0], ctl, L.dup_cap, st), "emit")) !=
-            GS_OK)
-            return rc;
-    }
-    const int tp = tile_sort_passes(L.Tn);
-    {
-        Stage sg(GS_STAGE_TILE_SORT, st, 3 * tp);
-        for (int pass = 0; pass < tp; ++pass) {
-            const int a = pass & 1;
-            if ((rc = cuda_check(launch_radix_pass(tk[a], tv[a], tk[1 - a], tv[1 - a], &ctl->n_dup_c, cap, 8 * pass,
-                                                   hist, ctl->tile_mm, pass == 0, st),
-                                 "tile sort")) != GS_OK)
-                return rc;
-        }
-    }
-    const int fin = tp & 1;
+    uint32_t *list = at<uint32_t>(ws, L.list);
+    uint2 *rowlist = at<uint2>(ws, L.rowlist);
     uint2 *ranges = at<uint2>(ws, L.ranges);
+    {
+        Stage sg(GS_STAGE_BIN_ROWS, st, 4);
+        if ((rc = cuda_check(launch_bin_rows(order, rec, n, cv.Ty, at<uint32_t>(ws, L.bin_m), at<void>(ws, L.bin_rows),
+                                             rowlist, ctl, L.dup_cap, L.bin_piece, st),
+                             "binning rows")) != GS_OK)
+            return rc;
+    }
+    {
+        Stage sg(GS_STAGE_BIN_TILES, st, 3);
+        if ((rc = cuda_check(launch_bin_tiles(rowlist, at<void>(ws, L.bin_rows), cv.Tx, cv.Ty, L.bin_piece,
+                                              at<uint32_t>(ws, L.bin_p), list, ranges, ctl, st),
+                             "binning tiles")) != GS_OK)
+            return rc;
+    }
     const CompositeBufs cb = composite_bufs(ws, L);
     {
-        Stage sg(GS_STAGE_RANGES, st, 2);
-        if ((rc = cuda_check(launch_ranges(tk[fin], cap, ranges, ctl, st), "ranges")) != GS_OK) return rc;
+        Stage sg(GS_STAGE_COMPOSITE_SETUP, st, 1);
         if ((rc = cuda_check(launch_fwd_setup(cb, ranges, L.Tn, st), "compositor set-up")) != GS_OK) return rc;
     }
     job->order = cb.order;
     job->ranges = ranges;
-    job->list = tv[fin];
+    job->list = list;
     job->rec = rec;
     job->image = image;
     job->alpha = alpha;
@@ -394,13 +379,12 @@ int gs_render_backward(const gs_scene *scene, const gs_camera *camera, const flo
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     void *ws = workspace;
     float4 *rec_grad = at<float4>(ws, L.rec_grad);
-    const int fin = tile_sort_passes(L.Tn) & 1;
     {
     Stage sg(GS_STAGE_COMPOSITE_BWD, st, 2);
     if ((rc = cuda_check(cudaMemsetAsync(rec_grad, 0, static_cast<size_t>(sv.n) * sizeof(Rec), st), "memset grad")) !=
         GS_OK)
         return rc;
-    if ((rc = cuda_check(launch_composite_backward(composite_bufs(ws, L), at<uint2>(ws, L.ranges), at<uint32_t>(ws, L.tile_v[fin]),
+    if ((rc = cuda_check(launch_composite_backward(composite_bufs(ws, L), at<uint2>(ws, L.ranges), at<uint32_t>(ws, L.list),
                                                    at<Rec>(ws, L.rec), cv.W, cv.H, cv.Tx, cv.Ty,
                                                    make_float3(bg[0], bg[1], bg[2]), at<float>(ws, L.t_final),
                                                    at<uint32_t>(ws, L.n_contrib), dL_dimage,
@@ -420,10 +404,8 @@ int gs_workspace_layout(int64_t n, int32_t width, int32_t height, size_t ws_byte
     if (cap < 0) return fail(GS_ERR_WORKSPACE, "workspace of %zu bytes is below the fixed part", ws_bytes);
     Layout L;
     if (!make_layout(n, width, height, cap, &L)) return fail(GS_ERR_INVALID, "bad sizes");
-    const int fin = tile_sort_passes(L.Tn) & 1;
     const int64_t v[GS_LAYOUT_COUNT] = {
-        (int64_t)L.ctl, (int64_t)L.rec, (int64_t)L.tiles, (int64_t)L.depth, (int64_t)L.tile_k[fin],
-        (int64_t)L.tile_v[fin], (int64_t)L.ranges, (int64_t)L.t_final, (int64_t)L.n_contrib,
+        (int64_t)L.ctl, (int64_t)L.rec, (int64_t)L.tiles, (int64_t)L.depth, (int64_t)L.list, (int64_t)L.ranges, (int64_t)L.t_final, (int64_t)L.n_contrib,
         (int64_t)L.rec_grad, (int64_t)L.total, cap};
     for (int k = 0; k < GS_LAYOUT_COUNT; ++k) out[k] = v[k];
     return GS_OK;
@@ -475,6 +457,75 @@ int gs_profile_collect(double *ms, int64_t *calls) {
 }
 
 int64_t gs_kernel_launches(void) { return g_launches.load(); }
+
+int gs_image_loss_workspace_size(int32_t width, int32_t height, size_t *bytes) {
+    if (!bytes) return fail(GS_ERR_INVALID, "bytes is NULL");
+    if (width <= 0 || height <= 0 || width > GS_MAX_IMAGE_DIM || height > GS_MAX_IMAGE_DIM)
+        return fail(GS_ERR_INVALID, "image size %dx%d outside 1..%d", width, height, GS_MAX_IMAGE_DIM);
+    *bytes = loss_workspace_bytes(width, height);
+    return GS_OK;
+}
+
+int gs_image_loss(const float *image, const float *alpha, const float *target_rgb, const float *target_alpha,
+                  const float *bg, int32_t width, int32_t height, float lambda_dssim, float w_alpha,
+                  void *workspace, size_t ws_bytes, float *loss, float *dL_dimage, float *dL_dalpha,
+                  void *stream) {
+    size_t need = 0;
+    int rc = gs_image_loss_workspace_size(width, height, &need);
+    if (rc != GS_OK) return rc;
+    if (!image || !target_rgb || !target_alpha || !bg || !loss || !dL_dimage || !workspace)
+        return fail(GS_ERR_INVALID, "NULL argument");
+    if (ws_bytes < need) return fail(GS_ERR_WORKSPACE, "loss workspace of %zu bytes, need %zu", ws_bytes, need);
+    if (!aligned(workspace, 256)) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
+    if (!(lambda_dssim >= 0.f && lambda_dssim <= 1.f) || !(w_alpha >= 0.f))
+        return fail(GS_ERR_INVALID, "lambda_dssim must be in [0, 1] and w_alpha >= 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!alpha && dL_dalpha &&
+        (rc = cuda_check(cudaMemsetAsync(dL_dalpha, 0, static_cast<size_t>(width) * height * 4, st),
+                         "zero dL_dalpha")) != GS_OK)
+        return rc;
+    Stage sg(GS_STAGE_LOSS, st, 3);
+    return cuda_check(launch_image_loss(image, alpha, target_rgb, target_alpha, make_float3(bg[0], bg[1], bg[2]),
+                                        width, height, lambda_dssim, w_alpha, workspace, loss, dL_dimage,
+                                        alpha ? dL_dalpha : nullptr, st),
+                      "image loss");
+}
+
+int gs_adam_step(const gs_scene *scene, const gs_grads *grads, const gs_adam_state *state, const float *lr,
+                 float beta1, float beta2, float eps, int32_t step, uint32_t train_layer_mask, void *stream) {
+    SceneView sv;
+    int rc;
+    if ((rc = check_scene(scene, &sv)) != GS_OK) return rc;
+    if (!grads || !state || !lr) return fail(GS_ERR_INVALID, "NULL argument");
+    if (sv.dtype_sh != GS_DTYPE_F32 || sv.dtype_sr != GS_DTYPE_F32)
+        return fail(GS_ERR_INVALID, "Adam updates float32 parameters only");
+    if (step < 1) return fail(GS_ERR_INVALID, "step must be >= 1");
+    if (!(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps >= 0.f))
+        return fail(GS_ERR_INVALID, "bad Adam hyper-parameters");
+    if (sv.n == 0) return GS_OK;
+    const int K = (sv.sh_degree + 1) * (sv.sh_degree + 1);
+    float *p[5] = {const_cast<float *>(sv.means), static_cast<float *>(const_cast<void *>(sv.log_scales)),
+                   static_cast<float *>(const_cast<void *>(sv.quats)), const_cast<float *>(sv.opacity_logit),
+                   static_cast<float *>(const_cast<void *>(sv.sh))};
+    const float *g[5] = {grads->means, grads->log_scales, grads->quats, grads->opacity_logit, grads->sh};
+    const uint32_t width[5] = {3, 3, 4, 1, static_cast<uint32_t>(3 * K)};
+    for (int k = 0; k < 5; ++k)
+        if (!g[k] || !state->m[k] || !state->v[k]) return fail(GS_ERR_INVALID, "gradient or moment array is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Stage sg(GS_STAGE_ADAM, st, 1);
+    return cuda_check(launch_adam(p, g, state->m, state->v, width, sv.n, sv.layer, train_layer_mask, lr, beta1, beta2,
+                                  eps, step, st),
+                      "adam");
+}
+
+int gs_gather_rows(const void *src, void *dst, int64_t row_bytes, const int32_t *index, int64_t n, void *stream) {
+    if (n < 0 || row_bytes <= 0 || row_bytes > 0x7FFFFFFF) return fail(GS_ERR_INVALID, "bad row size or count");
+    if (n > 0 && (!src || !dst || !index)) return fail(GS_ERR_INVALID, "NULL argument");
+    if ((row_bytes % 2 == 0) && (!aligned(src, 2) || !aligned(dst, 2)))
+        return fail(GS_ERR_INVALID, "rows of an even byte count must be 2-byte aligned");
+    return cuda_check(launch_gather_rows(src, dst, row_bytes, index, n, static_cast<cudaStream_t>(stream)),
+                      "gather rows");
+}
 
 int gs_read_status(const void *workspace, gs_status *out, void *stream) {
     if (!workspace || !out) return fail(GS_ERR_INVALID, "NULL argument");

@@ -20,6 +20,10 @@ constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 0x1.010102p-8f;    // 1/255 rounded to float
 constexpr float kTMin = 1e-4f;
 constexpr uint32_t kSeg = 256;                 // list positions per backward segment (checkpoint stride)
+constexpr int kBinMaxDim = 256;                // tile rows and columns the binning handles (4096 px)
+constexpr int kBinBlocks = 1024;               // CTAs (of 8 chunk warps) of the row pass of the binning
+constexpr int kBinChunks = kBinBlocks * 8;     // chunks of the depth order in the row pass
+constexpr int kBinChunksPerThread = kBinChunks / 1024;
 
 // Per-Gaussian record written by the preprocess and gathered by the compositor.
 // a = (u, v, A2, beta), b = (G2, opacity, r, g), c = (b, depth, rect01, rect23)
@@ -36,14 +40,13 @@ struct __align__(16) Rec {
 struct Ctl {
     gs_status st;          // 32 bytes
     uint32_t n_vis;        // visible Gaussians (compaction total)
-    uint32_t n_dup_c;      // min(n_dup, capacity): items in the tile sort
     uint32_t scan_total;   // scratch total of the last scan
     uint32_t depth_mm[2];  // ~min and max of the depth keys (radix pass skipping)
-    uint32_t tile_mm[2];   // ~min and max of the tile keys
     uint32_t fwd_queue;    // next work item of the persistent forward compositor
     uint32_t bwd_queue;    // next work item of the persistent backward compositor
     uint32_t n_items;      // backward work items (tile, 8x8 block, segment)
-    uint32_t pad[14];
+    uint32_t n_pieces;     // row-list pieces of the binning
+    uint32_t pad[16];
 };
 static_assert(sizeof(Ctl) == 128, "Ctl layout");
 
@@ -51,8 +54,9 @@ static_assert(sizeof(Ctl) == 128, "Ctl layout");
 struct Layout {
     int64_t n = 0, dup_cap = 0;
     int W = 0, H = 0, Tx = 0, Ty = 0, Tn = 0;
-    size_t ctl = 0, rec = 0, tiles = 0, depth = 0, sort_k[2] = {0, 0}, sort_v[2] = {0, 0}, dup_off = 0,
-           tile_k[2] = {0, 0}, tile_v[2] = {0, 0}, ranges = 0, t_final = 0, n_contrib = 0,
+    uint32_t bin_piece = 0;
+    size_t ctl = 0, rec = 0, tiles = 0, depth = 0, sort_k[2] = {0, 0}, sort_v[2] = {0, 0}, bin_m = 0,
+           bin_rows = 0, bin_p = 0, rowlist = 0, list = 0, ranges = 0, t_final = 0, n_contrib = 0,
            partials = 0, hist = 0, rec_grad = 0, tile_order = 0, tile_order_bwd = 0, seg_base = 0, qwork = 0,
            ckpt = 0, items = 0, total = 0;
 };
@@ -113,14 +117,31 @@ cudaError_t launch_compact_visible(const uint32_t *tiles, const uint32_t *depth_
 cudaError_t launch_radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                               const uint32_t *n_dev, uint32_t n_cap, int shift, uint32_t *hist, uint32_t *minmax,
                               bool first, cudaStream_t st);
-// dup_off[p] = exclusive prefix of tiles[order[p]] over p < ctl->n_vis; writes n_dup,
-// n_dup_c and the overflow status.
-cudaError_t launch_dup_offsets(const uint32_t *order, const uint32_t *tiles, uint32_t n_cap, uint32_t *dup_off,
-                               uint32_t *partials, Ctl *ctl, uint64_t dup_cap, cudaStream_t st);
-cudaError_t launch_emit(const uint32_t *order, const uint32_t *dup_off, const Rec *rec, uint32_t n_cap, int Tx,
-                        uint32_t *tile_k, uint32_t *tile_v, Ctl *ctl, uint64_t dup_cap, cudaStream_t st);
-cudaError_t launch_ranges(const uint32_t *tile_k, uint32_t n_cap, uint2 *ranges, const Ctl *ctl,
-                          cudaStream_t st);
+// Tile binning (bin.cu).  Rows: splits the depth-ordered visible Gaussians
+// (order[p], p < min(ctl->n_vis, n_cap)) into per-tile-row lists of
+// (Gaussian, x0 | x1 << 16) in depth order; writes n_dup and the overflow
+// status (n_dup > cap).  M: kBinChunks * Ty words; rows_buf: bin_rows_bytes(Ty).
+cudaError_t launch_bin_rows(const uint32_t *order, const Rec *rec, uint32_t n_cap, int Ty, uint32_t *M,
+                            void *rows_buf, uint2 *rowlist, Ctl *ctl, uint64_t cap, uint32_t piece, cudaStream_t st);
+// Tiles: splits every row list into its tiles; writes the final Gaussian list
+// (tile order, depth order within a tile) and every tile's [start, end).
+// Does nothing when the status holds an error.
+// P: bin_piece_bytes(cap, Tx, Ty) bytes; piece = bin_piece_entries(cap, Tx).
+cudaError_t launch_bin_tiles(const uint2 *rowlist, const void *rows_buf, int Tx, int Ty, uint32_t piece, uint32_t *P,
+                             uint32_t *list, uint2 *ranges, const Ctl *ctl, cudaStream_t st);
+size_t bin_rows_bytes(int Ty);
+uint32_t bin_piece_entries(int64_t dup_cap, int Tx);
+size_t bin_piece_bytes(int64_t dup_cap, int Tx, int Ty);
+// Training-step kernels (train.cu).
+size_t loss_workspace_bytes(int W, int H);
+cudaError_t launch_image_loss(const float *X, const float *A, const float *Ct, const float *At, float3 bg, int W,
+                              int H, float lam, float w_a, void *ws, float *loss, float *dX, float *dA,
+                              cudaStream_t st);
+cudaError_t launch_adam(float *const p[5], const float *const g[5], float *const m[5], float *const v[5],
+                        const uint32_t width[5], int64_t n, const uint8_t *layer, uint32_t train_mask,
+                        const float lr[5], float beta1, float beta2, float eps, int step, cudaStream_t st);
+cudaError_t launch_gather_rows(const void *src, void *dst, int64_t row_bytes, const int32_t *idx, int64_t n,
+                               cudaStream_t st);
 cudaError_t launch_prune(const float *contrib_max, int n, float thr, uint8_t *keep, int32_t *keep_index,
                          int64_t *n_keep, uint32_t *partials, cudaStream_t st);
 

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) k_scan_reduce(F f, NSrc ns, uint32_t *__r
     if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
-enum ScanFinal { FIN_NONE = 0, FIN_NVIS = 1, FIN_NDUP = 2, FIN_NKEEP = 3 };
+enum ScanFinal { FIN_NONE = 0, FIN_NVIS = 1, FIN_NKEEP = 2 };
 
 __global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *__restrict__ partials, int G, int mode,
                                                         Ctl *ctl, uint64_t cap, int64_t *n_keep) {
@@ -114,11 +114,6 @@ __global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *__restrict__ p
         if (mode == FIN_NVIS) {
             ctl->n_vis = total;
             ctl->st.n_visible = total;
-        } else if (mode == FIN_NDUP) {
-            ctl->st.n_dup = total;
-            ctl->st.dup_capacity = cap;
-            ctl->n_dup_c = total < cap ? total : static_cast<uint32_t>(cap);
-            if (total > cap) ctl->st.error = GS_ERR_WORKSPACE;
         } else if (mode == FIN_NKEEP) {
             *n_keep = total;
         }
@@ -163,14 +158,6 @@ struct CompactOut {
     __device__ __forceinline__ void operator()(uint32_t i, uint32_t off, uint32_t v) const {
         if (v) { keys[off] = depth_key[i]; vals[off] = i; }
     }
-};
-struct OrderedTiles {
-    const uint32_t *order, *tiles;
-    __device__ __forceinline__ uint32_t operator()(uint32_t p) const { return tiles[order[p]]; }
-};
-struct OffsetOut {
-    uint32_t *dup_off;
-    __device__ __forceinline__ void operator()(uint32_t p, uint32_t off, uint32_t) const { dup_off[p] = off; }
 };
 struct KeepFlag {
     const float *cmax;
@@ -366,67 +353,6 @@ __global__ void __launch_bounds__(256) k_radix_down(const uint32_t *__restrict__
 
 // ---------------------------------------------------------------------------
 
-// Each warp takes 32 consecutive visible Gaussians (in depth order).  Their
-// pairs occupy one contiguous range of the pair list (the offsets are an
-// exclusive scan), which the warp writes with coalesced stores: for output
-// slot k the owning Gaussian is found by a binary search over the 32 start
-// offsets, and the tile within its rectangle by one division.
-__global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ order, const uint32_t *__restrict__ dup_off,
-                                              const Rec *__restrict__ rec, NSrc ns, int Tx,
-                                              uint32_t *__restrict__ tile_k, uint32_t *__restrict__ tile_v,
-                                              uint64_t cap) {
-    __shared__ uint32_t s_start[8][33];
-    __shared__ uint32_t s_g[8][32], s_x0[8][32], s_y0[8][32], s_w[8][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t n = ns.get();
-    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
-    for (uint32_t p0 = (blockIdx.x * (blockDim.x >> 5) + warp) * 32u; p0 < n; p0 += nwarps * 32u) {
-        const uint32_t p = p0 + lane;
-        uint32_t start = 0, cnt = 0, g = 0, x0 = 0, y0 = 0, w = 1;
-        if (p < n) {
-            g = order[p];
-            start = dup_off[p];
-            const float4 c = rec[g].c;
-            const uint32_t r0 = __float_as_uint(c.z), r1 = __float_as_uint(c.w);
-            x0 = r0 & 0xFFFFu; y0 = r0 >> 16;
-            w = (r1 & 0xFFFFu) - x0;
-            cnt = w * ((r1 >> 16) - y0);
-        }
-        // range end of the warp: the last valid lane's start + count
-        const uint32_t nvalid = min(32u, n - p0);
-        const uint32_t end = __shfl_sync(FULL, start + cnt, nvalid - 1);
-        const uint32_t first = __shfl_sync(FULL, start, 0);
-        s_start[warp][lane] = p < n ? start : end;
-        if (lane == 0) s_start[warp][32] = end;
-        s_g[warp][lane] = g; s_x0[warp][lane] = x0; s_y0[warp][lane] = y0; s_w[warp][lane] = w;
-        __syncwarp();
-        for (uint64_t k = static_cast<uint64_t>(first) + lane; k < end; k += 32) {
-            if (k >= cap) break;
-            // largest j with s_start[j] <= k (lanes with no pairs share the next start)
-            int lo = 0, hi = 31;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_start[warp][mid] <= k) lo = mid; else hi = mid - 1;
-            }
-            const uint32_t r = static_cast<uint32_t>(k) - s_start[warp][lo];
-            const uint32_t wj = s_w[warp][lo];
-            const uint32_t ty = r / wj, tx = r - ty * wj;
-            tile_k[k] = (s_y0[warp][lo] + ty) * static_cast<uint32_t>(Tx) + s_x0[warp][lo] + tx;
-            tile_v[k] = s_g[warp][lo];
-        }
-        __syncwarp();
-    }
-}
-
-__global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ tile_k, NSrc ns, uint2 *__restrict__ ranges) {
-    const uint32_t n = ns.get();
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t t = tile_k[i];
-        if (i == 0 || tile_k[i - 1] != t) ranges[t].x = i;
-        if (i == n - 1 || tile_k[i + 1] != t) ranges[t].y = i + 1;
-    }
-}
-
 }  // namespace
 
 int sort_blocks() {
@@ -461,35 +387,6 @@ cudaError_t launch_radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t
     k_radix_up<<<G, 256, 0, st>>>(kin, ns, shift, hist, minmax, first ? 1 : 0);
     k_radix_rowscan<<<256, 256, 0, st>>>(hist, G, rowtot, minmax, shift, first ? 1 : 0);
     k_radix_down<<<G, 256, 0, st>>>(kin, vin, kout, vout, ns, shift, hist, rowtot, minmax, first ? 1 : 0);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_dup_offsets(const uint32_t *order, const uint32_t *tiles, uint32_t n_cap, uint32_t *dup_off,
-                               uint32_t *partials, Ctl *ctl, uint64_t dup_cap, cudaStream_t st) {
-    const int G = sort_blocks();
-    NSrc ns{&ctl->n_vis, n_cap};
-    OrderedTiles f{order, tiles};
-    k_scan_reduce<<<G, 256, 0, st>>>(f, ns, partials);
-    k_scan_partials<<<1, 1024, 0, st>>>(partials, G, FIN_NDUP, ctl, dup_cap, nullptr);
-    k_scan_down<<<G, 256, 0, st>>>(f, ns, partials, OffsetOut{dup_off});
-    return cudaGetLastError();
-}
-
-cudaError_t launch_emit(const uint32_t *order, const uint32_t *dup_off, const Rec *rec, uint32_t n_cap, int Tx,
-                        uint32_t *tile_k, uint32_t *tile_v, Ctl *ctl, uint64_t dup_cap, cudaStream_t st) {
-    NSrc ns{&ctl->n_vis, n_cap};
-    // one warp per 32 visible Gaussians of the capacity, at most 4 CTAs of 8 warps per sort block
-    const uint32_t blocks = max(1u, min((n_cap + 255) / 256, static_cast<uint32_t>(4 * sort_blocks())));
-    k_emit<<<blocks, 256, 0, st>>>(order, dup_off, rec, ns, Tx, tile_k, tile_v, dup_cap);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_ranges(const uint32_t *tile_k, uint32_t n_cap, uint2 *ranges, const Ctl *ctl, cudaStream_t st) {
-    NSrc ns{&ctl->n_dup_c, n_cap};
-    // grid-stride over the device count with enough warps to cover memory latency
-    const uint32_t blocks = max(1u, min(static_cast<uint32_t>((n_cap + 255) / 256),
-                                        static_cast<uint32_t>(4 * sort_blocks())));
-    k_ranges<<<blocks, 256, 0, st>>>(tile_k, ns, ranges);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,321 @@
+// The training step around the rasterizer (Sec. 3.2: every layer is
+// optimised with the layers below it frozen, a random background per frame
+// and the alpha channel in the loss): the image loss with its gradient, Adam
+// on the Gaussian parameters, and the row compaction that applies a prune.
+//
+// Loss (the 3DGS image loss the paper's training builds on):
+//   Y    = C_t + (1 - A_t) bg                 target under this frame's background
+//   loss = (1 - lam) mean|X - Y| + lam (1 - mean SSIM(X, Y)) + w_a mean|A - A_t|
+// SSIM per channel with an 11x11 Gaussian window (sigma 1.5, normalised),
+// zero outside the image, C1 = 0.01^2, C2 = 0.03^2.  Its gradient is three
+// window sums of per-pixel maps (the window is symmetric):
+//   dSSIM/dx_p = (G*a)_p + 2 x_p (G*b)_p + y_p (G*c)_p,
+//   a = df/dmu_x - 2 mu_x df/dsx - mu_y df/dsxy,  b = df/dsx,  c = df/dsxy.
+// Both kernels stage a (32 + 10) x (8 + 10) halo tile in shared memory and run
+// the window as a horizontal then a vertical 11-tap pass (HBM-bound: a few
+// floats per pixel and channel in and out).
+#include <cmath>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kLW = 32, kLH = 8, kHalo = 5, kWin = 11;
+constexpr int kRW = kLW + 2 * kHalo, kRH = kLH + 2 * kHalo;   // 42 x 18 staged region
+constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
+
+struct Win {
+    float g[kWin];
+};
+
+__device__ __forceinline__ float target_at(const float *trgb, const float *talpha, float bgc, size_t pc, size_t p) {
+    return trgb[pc] + (1.f - talpha[p]) * bgc;
+}
+
+__device__ __forceinline__ float sgn(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
+
+// Pass 1: per pixel and channel, SSIM and the maps a, b, c; block sums of
+// SSIM, |X - Y| and (channel 0) |A - A_t|.
+__global__ void __launch_bounds__(kLW *kLH) k_loss_maps(const float *__restrict__ X, const float *__restrict__ A,
+                                                        const float *__restrict__ Ct, const float *__restrict__ At,
+                                                        float3 bg, int W, int H, const Win win,
+                                                        float *__restrict__ maps, float *__restrict__ partials) {
+    __shared__ float s_x[kRH][kRW], s_y[kRH][kRW];
+    __shared__ float s_h[5][kRH][kLW];
+    __shared__ float s_red[3][kLW * kLH / 32];
+    const int ch = blockIdx.z;
+    const float bgc = ch == 0 ? bg.x : (ch == 1 ? bg.y : bg.z);
+    const size_t plane = static_cast<size_t>(W) * H;
+    const int x0 = blockIdx.x * kLW - kHalo, y0 = blockIdx.y * kLH - kHalo;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kRW * kRH; i += kLW * kLH) {
+        const int ry = i / kRW, rx = i % kRW;
+        const int gx = x0 + rx, gy = y0 + ry;
+        float xv = 0.f, yv = 0.f;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+            const size_t p = static_cast<size_t>(gy) * W + gx;
+            xv = X[ch * plane + p];
+            yv = target_at(Ct, At, bgc, ch * plane + p, p);
+        }
+        s_x[ry][rx] = xv;
+        s_y[ry][rx] = yv;
+    }
+    __syncthreads();
+    for (int i = tid; i < kRH * kLW; i += kLW * kLH) {
+        const int ry = i / kLW, cx = i % kLW;
+        float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
+#pragma unroll
+        for (int j = 0; j < kWin; ++j) {
+            const float a = s_x[ry][cx + j], b = s_y[ry][cx + j], w = win.g[j];
+            mx = fmaf(w, a, mx);
+            my = fmaf(w, b, my);
+            xx = fmaf(w, a * a, xx);
+            yy = fmaf(w, b * b, yy);
+            xy = fmaf(w, a * b, xy);
+        }
+        s_h[0][ry][cx] = mx;
+        s_h[1][ry][cx] = my;
+        s_h[2][ry][cx] = xx;
+        s_h[3][ry][cx] = yy;
+        s_h[4][ry][cx] = xy;
+    }
+    __syncthreads();
+    const int lx = tid % kLW, ly = tid / kLW;
+    const int gx = blockIdx.x * kLW + lx, gy = blockIdx.y * kLH + ly;
+    float f = 0.f, l1 = 0.f, la = 0.f;
+    if (gx < W && gy < H) {
+        float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < kWin; ++i)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) m[q] = fmaf(win.g[i], s_h[q][ly + i][lx], m[q]);
+        const float mux = m[0], muy = m[1];
+        const float sx = m[2] - mux * mux, sy = m[3] - muy * muy, sxy = m[4] - mux * muy;
+        const float n1 = 2.f * mux * muy + kC1, n2 = 2.f * sxy + kC2;
+        const float d1 = mux * mux + muy * muy + kC1, d2 = sx + sy + kC2;
+        f = (n1 * n2) / (d1 * d2);
+        const float df_dmx = f * (2.f * muy / n1 - 2.f * mux / d1);
+        const float df_dsx = -f / d2;
+        const float df_dsxy = 2.f * f / n2;
+        const size_t p = static_cast<size_t>(gy) * W + gx;
+        float *mp = maps + static_cast<size_t>(ch) * 3 * plane;
+        mp[p] = df_dmx - 2.f * mux * df_dsx - muy * df_dsxy;
+        mp[plane + p] = df_dsx;
+        mp[2 * plane + p] = df_dsxy;
+        l1 = fabsf(s_x[ly + kHalo][lx + kHalo] - s_y[ly + kHalo][lx + kHalo]);
+        if (ch == 0 && A) la = fabsf(A[p] - At[p]);
+    }
+    // block sums (fixed order: deterministic)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        f += __shfl_down_sync(0xFFFFFFFFu, f, o);
+        l1 += __shfl_down_sync(0xFFFFFFFFu, l1, o);
+        la += __shfl_down_sync(0xFFFFFFFFu, la, o);
+    }
+    if ((tid & 31) == 0) {
+        s_red[0][tid >> 5] = f;
+        s_red[1][tid >> 5] = l1;
+        s_red[2][tid >> 5] = la;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        float s = 0.f;
+        for (int w = 0; w < kLW * kLH / 32; ++w) s += s_red[tid][w];
+        const size_t b = (static_cast<size_t>(blockIdx.z) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        partials[3 * b + tid] = s;
+    }
+}
+
+// Pass 2: window sums of a, b, c and the gradient of the loss.
+__global__ void __launch_bounds__(kLW *kLH) k_loss_grad(const float *__restrict__ X, const float *__restrict__ A,
+                                                        const float *__restrict__ Ct, const float *__restrict__ At,
+                                                        float3 bg, int W, int H, const Win win, float lam, float w_a,
+                                                        const float *__restrict__ maps, float *__restrict__ dX,
+                                                        float *__restrict__ dA) {
+    __shared__ float s_m[3][kRH][kRW];
+    __shared__ float s_h[3][kRH][kLW];
+    const int ch = blockIdx.z;
+    const float bgc = ch == 0 ? bg.x : (ch == 1 ? bg.y : bg.z);
+    const size_t plane = static_cast<size_t>(W) * H;
+    const float *mp = maps + static_cast<size_t>(ch) * 3 * plane;
+    const int x0 = blockIdx.x * kLW - kHalo, y0 = blockIdx.y * kLH - kHalo;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kRW * kRH; i += kLW * kLH) {
+        const int ry = i / kRW, rx = i % kRW;
+        const int gx = x0 + rx, gy = y0 + ry;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const size_t p = in ? static_cast<size_t>(gy) * W + gx : 0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) s_m[q][ry][rx] = in ? mp[q * plane + p] : 0.f;
+    }
+    __syncthreads();
+    for (int i = tid; i < kRH * kLW; i += kLW * kLH) {
+        const int ry = i / kLW, cx = i % kLW;
+        float h[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < kWin; ++j)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) h[q] = fmaf(win.g[j], s_m[q][ry][cx + j], h[q]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) s_h[q][ry][cx] = h[q];
+    }
+    __syncthreads();
+    const int lx = tid % kLW, ly = tid / kLW;
+    const int gx = blockIdx.x * kLW + lx, gy = blockIdx.y * kLH + ly;
+    if (gx >= W || gy >= H) return;
+    float s[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < kWin; ++i)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) s[q] = fmaf(win.g[i], s_h[q][ly + i][lx], s[q]);
+    const size_t p = static_cast<size_t>(gy) * W + gx;
+    const float x = X[ch * plane + p];
+    const float y = target_at(Ct, At, bgc, ch * plane + p, p);
+    const float inv_n = 1.f / (3.f * static_cast<float>(plane));
+    const float dS = s[0] + 2.f * x * s[1] + y * s[2];
+    dX[ch * plane + p] = ((1.f - lam) * sgn(x - y) - lam * dS) * inv_n;
+    if (ch == 0 && dA) dA[p] = A ? w_a * sgn(A[p] - At[p]) / static_cast<float>(plane) : 0.f;
+}
+
+// loss = (1 - lam) L1 + lam (1 - SSIM) + w_a LA from the block sums (double).
+__global__ void __launch_bounds__(256) k_loss_reduce(const float *__restrict__ partials, int nb, size_t plane,
+                                                     float lam, float w_a, float *__restrict__ loss) {
+    __shared__ double s[3][256];
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nb; b += 256)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) a[q] += partials[3 * b + q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) s[q][threadIdx.x] = a[q];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double n = 3.0 * static_cast<double>(plane);
+        *loss = static_cast<float>((1.0 - lam) * s[1][0] / n + lam * (1.0 - s[0][0] / n) +
+                                   w_a * s[2][0] / static_cast<double>(plane));
+    }
+}
+
+// Adam over the five parameter arrays seen as one index space; a Gaussian
+// whose layer is not in train_mask keeps parameters and moments.
+struct AdamArrays {
+    float *p[5];
+    const float *g[5];
+    float *m[5], *v[5];
+    uint64_t end[5];       // cumulative element counts
+    uint32_t width[5];     // elements per Gaussian
+    float step[5];         // lr / (1 - beta1^t)
+};
+
+__global__ void __launch_bounds__(256) k_adam(const AdamArrays arr, const uint8_t *__restrict__ layer,
+                                              uint32_t train_mask, float beta1, float beta2, float inv_sqrt_bc2,
+                                              float eps) {
+    const uint64_t total = arr.end[4];
+    for (uint64_t e = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        int k = 0;
+        while (e >= arr.end[k]) ++k;
+        const uint64_t i = e - (k ? arr.end[k - 1] : 0);
+        const uint64_t row = i / arr.width[k];
+        if (!((train_mask >> layer[row]) & 1u)) continue;
+        const float g = arr.g[k][i];
+        const float m = fmaf(beta1, arr.m[k][i], (1.f - beta1) * g);
+        const float v = fmaf(beta2, arr.v[k][i], (1.f - beta2) * g * g);
+        arr.m[k][i] = m;
+        arr.v[k][i] = v;
+        arr.p[k][i] -= arr.step[k] * m / (sqrtf(v) * inv_sqrt_bc2 + eps);
+    }
+}
+
+// dst row i = src row idx[i], rows of `words` words of type T.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather_rows(const T *__restrict__ src, T *__restrict__ dst, uint32_t words,
+                                                     const int32_t *__restrict__ idx, uint64_t n) {
+    const uint64_t total = n * words;
+    for (uint64_t e = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint64_t r = e / words, w = e - r * words;
+        dst[e] = src[static_cast<uint64_t>(idx[r]) * words + w];
+    }
+}
+
+}  // namespace
+
+size_t loss_workspace_bytes(int W, int H) {
+    const size_t plane = static_cast<size_t>(W) * H;
+    const size_t nb = static_cast<size_t>((W + kLW - 1) / kLW) * ((H + kLH - 1) / kLH) * 3;
+    return 9 * plane * 4 + ((3 * nb * 4 + 255) / 256) * 256;
+}
+
+cudaError_t launch_image_loss(const float *X, const float *A, const float *Ct, const float *At, float3 bg, int W,
+                              int H, float lam, float w_a, void *ws, float *loss, float *dX, float *dA,
+                              cudaStream_t st) {
+    Win win;
+    double g[kWin], sum = 0.0;
+    for (int j = 0; j < kWin; ++j) {
+        const double r = j - kHalo;
+        g[j] = std::exp(-r * r / (2.0 * 1.5 * 1.5));
+        sum += g[j];
+    }
+    for (int j = 0; j < kWin; ++j) win.g[j] = static_cast<float>(g[j] / sum);
+    const size_t plane = static_cast<size_t>(W) * H;
+    float *maps = static_cast<float *>(ws);
+    float *partials = maps + 9 * plane;
+    const dim3 grid((W + kLW - 1) / kLW, (H + kLH - 1) / kLH, 3);
+    k_loss_maps<<<grid, kLW * kLH, 0, st>>>(X, A, Ct, At, bg, W, H, win, maps, partials);
+    k_loss_grad<<<grid, kLW * kLH, 0, st>>>(X, A, Ct, At, bg, W, H, win, lam, w_a, maps, dX, dA);
+    k_loss_reduce<<<1, 256, 0, st>>>(partials, static_cast<int>(grid.x * grid.y * grid.z), plane, lam,
+                                     A ? w_a : 0.f, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float *const p[5], const float *const g[5], float *const m[5], float *const v[5],
+                        const uint32_t width[5], int64_t n, const uint8_t *layer, uint32_t train_mask,
+                        const float lr[5], float beta1, float beta2, float eps, int step, cudaStream_t st) {
+    AdamArrays a;
+    uint64_t acc = 0;
+    const double bc1 = 1.0 - std::pow(static_cast<double>(beta1), step);
+    const double bc2 = 1.0 - std::pow(static_cast<double>(beta2), step);
+    for (int k = 0; k < 5; ++k) {
+        a.p[k] = p[k];
+        a.g[k] = g[k];
+        a.m[k] = m[k];
+        a.v[k] = v[k];
+        a.width[k] = width[k];
+        acc += static_cast<uint64_t>(n) * width[k];
+        a.end[k] = acc;
+        a.step[k] = static_cast<float>(lr[k] / bc1);
+    }
+    if (acc == 0) return cudaSuccess;
+    const int blocks = static_cast<int>(std::min<uint64_t>((acc + 255) / 256, 8ull * 1024));
+    k_adam<<<blocks, 256, 0, st>>>(a, layer, train_mask, beta1, beta2, static_cast<float>(1.0 / std::sqrt(bc2)), eps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const void *src, void *dst, int64_t row_bytes, const int32_t *idx, int64_t n,
+                               cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int wb = (row_bytes % 4 == 0 && (reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) % 4 == 0)
+                       ? 4 : (row_bytes % 2 == 0 ? 2 : 1);
+    const uint32_t words = static_cast<uint32_t>(row_bytes / wb);
+    const uint64_t total = static_cast<uint64_t>(n) * words;
+    const int blocks = static_cast<int>(std::min<uint64_t>((total + 255) / 256, 8ull * 1024));
+    if (wb == 4)
+        k_gather_rows<uint32_t><<<blocks, 256, 0, st>>>(static_cast<const uint32_t *>(src), static_cast<uint32_t *>(dst),
+                                                        words, idx, static_cast<uint64_t>(n));
+    else if (wb == 2)
+        k_gather_rows<uint16_t><<<blocks, 256, 0, st>>>(static_cast<const uint16_t *>(src), static_cast<uint16_t *>(dst),
+                                                        words, idx, static_cast<uint64_t>(n));
+    else
+        k_gather_rows<uint8_t><<<blocks, 256, 0, st>>>(static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst),
+                                                       words, idx, static_cast<uint64_t>(n));
+    return cudaGetLastError();
+}
+
+}  // namespace gs

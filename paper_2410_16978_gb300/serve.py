@@ -89,13 +89,19 @@ class RenderServer:
     size) grows and the request is rendered again."""
 
     def __init__(self, models: Dict[str, DeviceScene], memory_budget: int = 8 << 30, max_views_per_batch: int = 16,
-                 max_inflight_batches: int = 2, device="cuda"):
+                 max_inflight_batches: int = 2, device="cuda", policy: str = "priority",
+                 large_view_pixels: int = 2_000_000):
+        if policy not in ("priority", "fifo"):
+            raise ValueError(policy)
         self.models = models
         self.device = torch.device(device)
         self.budget = int(memory_budget)
         self.max_views = min(int(max_views_per_batch), _lib.GS_MAX_BATCH)
         self.max_inflight = int(max_inflight_batches)
+        self.policy = policy
+        self.large_view_pixels = int(large_view_pixels)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(self.max_inflight)]
+        self.stream_hi = torch.cuda.Stream(self.device, priority=-1)
         self._cap: Dict[tuple, int] = {}
         self._free: Dict[tuple, List[_ViewBuffers]] = collections.defaultdict(list)
         self._c_scene = {k: m.c_struct() for k, m in models.items()}
@@ -189,10 +195,24 @@ class RenderServer:
         return views, imgs
 
     # -- trace replay ---------------------------------------------------------
+    def is_large(self, req: RenderRequest) -> bool:
+        return any(int(c.width) * int(c.height) >= self.large_view_pixels for c in req.cameras)
+
     def run_trace(self, requests: Sequence[RenderRequest], mode: str = "served", keep_images=False):
         """Replays the arrival trace in real time.  Returns (results, seconds
         from the first arrival to the last completion).  Completion times are
-        device event times, on the clock of the trace."""
+        device event times, on the clock of the trace.
+
+        plain:  one request at a time in arrival order, one gs_render call per
+                view, all on one stream (up to max_inflight requests queued).
+        served: continuous batching.  Waiting requests are packed, in arrival
+                order, into gs_render_batch launches of up to max_views views
+                as soon as a launch slot and the memory budget allow.  With
+                policy "priority" there are two lanes: requests with a view of
+                at least large_view_pixels go to a high-priority stream, one
+                batch at a time; the others to normal-priority streams, so
+                small requests fill the device around a large frame without
+                delaying it.  Policy "fifo" is one lane over all streams."""
         if mode not in ("served", "plain"):
             raise ValueError(mode)
         reqs = sorted(requests, key=lambda r: r.arrival)
@@ -202,46 +222,68 @@ class RenderServer:
         ref.record(self.streams[0])
         ref.synchronize()
         t0 = time.perf_counter()
-        waiting = collections.deque()
-        pending = []
-        nxt, k = 0, 0
-        slots = self.max_inflight
-        while nxt < len(reqs) or waiting or pending:
+        if mode == "plain":
+            lanes = [dict(pred=lambda r: True, streams=[self.streams[0]], slots=self.max_inflight, batch=False)]
+        elif self.policy == "fifo":
+            lanes = [dict(pred=lambda r: True, streams=self.streams, slots=self.max_inflight, batch=True)]
+        else:
+            lanes = [dict(pred=self.is_large, streams=[self.stream_hi], slots=1, batch=True),
+                     dict(pred=lambda r: not self.is_large(r), streams=self.streams, slots=self.max_inflight,
+                          batch=True)]
+        for ln in lanes:
+            ln.update(waiting=collections.deque(), pending=[], k=0)
+        nxt = 0
+
+        def lane_of(r):
+            return next(ln for ln in lanes if ln["pred"](r))
+
+        while nxt < len(reqs) or any(ln["waiting"] or ln["pending"] for ln in lanes):
             now = time.perf_counter() - t0
             while nxt < len(reqs) and reqs[nxt].arrival <= now:
-                waiting.append(reqs[nxt])
+                lane_of(reqs[nxt])["waiting"].append(reqs[nxt])
                 nxt += 1
-            self._retire(pending, results, ref, waiting)
-            if waiting and len(pending) < slots:
+            for ln in lanes:
+                redo = collections.deque()
+                self._retire(ln["pending"], results, ref, redo)
+                ln["waiting"].extendleft(reversed(redo))
+            launched = False
+            for ln in lanes:
+                waiting, pending = ln["waiting"], ln["pending"]
+                if not waiting or len(pending) >= ln["slots"]:
+                    continue
                 batch, nviews, nbytes = [], 0, 0
+                busy = any(l2["pending"] for l2 in lanes)
                 while waiting:
                     r = waiting[0]
-                    if mode == "plain" and batch:
+                    if not ln["batch"] and batch:
                         break
                     if nviews + len(r.cameras) > self.max_views:
                         break
                     rb = self.request_bytes(r)
-                    if self.in_use + nbytes + rb > self.budget and (batch or pending):
+                    if self.in_use + nbytes + rb > self.budget and (batch or busy):
                         break
                     batch.append(waiting.popleft())
                     nviews += len(r.cameras)
                     nbytes += rb
-                if batch:
-                    stream = self.streams[k % len(self.streams)] if mode == "served" else self.streams[0]
-                    k += 1
-                    st = time.perf_counter() - t0
-                    for r in batch:
-                        if math.isnan(results[r.rid].start):
-                            results[r.rid].start = st
-                    if mode == "served":
-                        views, imgs = self._launch_batch(batch, stream, keep_images)
-                    else:
-                        views, imgs = self._launch_plain(batch[0], stream, keep_images)
-                    ev = torch.cuda.Event(enable_timing=True)
-                    ev.record(stream)
-                    pending.append((ev, views, imgs))
+                if not batch:
                     continue
-            if not pending and not waiting and nxt < len(reqs):
+                stream = ln["streams"][ln["k"] % len(ln["streams"])]
+                ln["k"] += 1
+                st = time.perf_counter() - t0
+                for r in batch:
+                    if math.isnan(results[r.rid].start):
+                        results[r.rid].start = st
+                if ln["batch"]:
+                    views, imgs = self._launch_batch(batch, stream, keep_images)
+                else:
+                    views, imgs = self._launch_plain(batch[0], stream, keep_images)
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(stream)
+                pending.append((ev, views, imgs))
+                launched = True
+            if launched:
+                continue
+            if not any(ln["pending"] or ln["waiting"] for ln in lanes) and nxt < len(reqs):
                 wait = reqs[nxt].arrival - (time.perf_counter() - t0)
                 if wait > 3e-4:
                     time.sleep(wait - 2e-4)

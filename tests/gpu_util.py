@@ -35,7 +35,7 @@ def read_ws(rast):
 
     rec = region("rec", 12 * n, np.float32).reshape(n, 12)
     out = dict(status=st, rec=rec, tiles=region("tiles", n, np.uint32), depth=region("depth", n, np.uint32),
-               tile_k=region("tile_k", D, np.uint32), tile_v=region("tile_v", D, np.uint32),
+               list=region("list", D, np.uint32),
                ranges=region("ranges", 2 * Tn, np.uint32).reshape(Tn, 2),
                t_final=region("t_final", W * H, np.float32).reshape(H, W),
                n_contrib=region("n_contrib", W * H, np.uint32).reshape(H, W), D=D)
@@ -86,7 +86,7 @@ def compare_records(ws, pre32):
 
 def compare_lists(ws, ranges_or, list_or):
     assert ws["D"] == list_or.shape[0], (ws["D"], list_or.shape[0])
-    assert np.array_equal(ws["tile_v"].astype(np.int64), list_or.astype(np.int64))
+    assert np.array_equal(ws["list"].astype(np.int64), list_or.astype(np.int64))
     r = ws["ranges"].astype(np.int64)
     empty_or = ranges_or[:, 0] == ranges_or[:, 1]
     assert np.array_equal(r[~empty_or], ranges_or[~empty_or])

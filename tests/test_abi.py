@@ -38,7 +38,7 @@ def test_workspace_size_and_layout():
     b = _lib.gs_render_workspace_size(1000, 100, 70, 5000)
     lay = _lib.gs_workspace_layout(1000, 100, 70, b)
     assert lay["total"] <= b and lay["dup_capacity"] >= 5000 - 64
-    offs = [lay[k] for k in _lib.LAYOUT_NAMES[:11]]
+    offs = [lay[k] for k in _lib.LAYOUT_NAMES[:9]]     # the regions (total and capacity follow)
     assert all(o % 256 == 0 for o in offs)
     assert len(set(offs)) == len(offs)
     with pytest.raises(_lib.GsError) as e:
@@ -50,6 +50,11 @@ def test_workspace_size_and_layout():
     with pytest.raises(_lib.GsError) as e:
         _lib.gs_workspace_layout(1000, 100, 70, 1024)
     assert e.value.code == _lib.GS_ERR_WORKSPACE
+    _lib.gs_render_workspace_size(10, 4096, 4096, 10)          # the largest image
+    for w, h in ((4097, 16), (16, 4097)):
+        with pytest.raises(_lib.GsError) as e:
+            _lib.gs_render_workspace_size(10, w, h, 10)
+        assert e.value.code == _lib.GS_ERR_INVALID
 
 
 def test_render_rejects_bad_arguments_on_host():

@@ -37,7 +37,8 @@ def _alone(ds, req):
 def test_served_mix_equals_alone():
     models = _models()
     trace = make_trace(np.random.default_rng(3), list(models), n_requests=48, rate=4000.0, sizes=SIZES)
-    srv = RenderServer(models, memory_budget=64 << 20, max_views_per_batch=8)
+    # 128x96 and the stereo 80x72 views count as large: both lanes are used
+    srv = RenderServer(models, memory_budget=64 << 20, max_views_per_batch=8, large_view_pixels=5000)
     # a capacity far below the need of one model forces the overflow-and-retry path
     srv._cap[("m_big", 128, 96)] = 64
     res, wall = srv.run_trace(trace, "served", keep_images=True)
@@ -59,7 +60,7 @@ def test_served_mix_equals_alone():
 def test_plain_and_served_replays_agree():
     models = _models()
     trace = make_trace(np.random.default_rng(4), list(models), n_requests=24, rate=2000.0, sizes=SIZES)
-    srv = RenderServer(models, memory_budget=32 << 20)
+    srv = RenderServer(models, memory_budget=32 << 20, policy="fifo")
     a, _ = srv.run_trace(trace, "plain", keep_images=True)
     b, _ = srv.run_trace(trace, "served", keep_images=True)
     torch.cuda.synchronize()
