@@ -23,7 +23,18 @@ loss; the image loss is that of the 3DGS training the paper builds on):
 * Adam (Kingma & Ba 2015) with bias correction, one learning rate per
   parameter group; Gaussians of frozen layers keep parameters and moments.
 
-Parity status: ssim / loss pinned by SSIM(x, x) = 1, the interior closed form
+* Inactive pruning (Sec. 3.2.2): per trainable Gaussian and step i, p_i, c_i,
+  s_i are the Euclidean norms of the update Adam applied to its mean, its SH
+  coefficients (colour) and its log-scales; AvgSample = (1/dR) sum over dR
+  steps of (2 p_i + 0.1 c_i + 0.1 s_i); a trainable Gaussian is removed when
+  AvgSample <= T, and T is multiplied by 0.975 after each comparison (T0 =
+  0.015, dR = 100).  Reading: "norm" is the norm of the per-step update (the
+  activity of the optimisation), colour is every SH coefficient, scale is the
+  stored log-scale; Gaussians of frozen layers are not tested.
+
+Parity status: activity pinned by the constant-gradient closed form (each
+update is lr sign(g), so the norms are lr sqrt(count)) and the paper's
+constants (tests/golden/inactive_pruning.txt); ssim / loss pinned by SSIM(x, x) = 1, the interior closed form
 for constant images, an independent scipy.ndimage evaluation of the window
 sums, and central finite differences of the loss; adam pinned by the
 constant-gradient closed form (each step moves by lr sign(g)) and a
@@ -150,3 +161,21 @@ def adam_step(param, grad, m, v, t: int, lr: float, frozen_rows=None, beta1=0.9,
 def compact(arr, keep):
     """Rows of arr whose keep flag is set, in their original order."""
     return np.asarray(arr)[np.asarray(keep, bool)]
+
+
+ACT_W = (2.0, 0.1, 0.1)          # position, colour, scale weights (Sec. 3.2.2)
+
+
+def activity_sample(d_means, d_sh, d_log_scales, weights=ACT_W) -> np.ndarray:
+    """2 |d_mean| + 0.1 |d_sh| + 0.1 |d_log_scale| per Gaussian (row norms of one step's updates)."""
+    n = np.asarray(d_means).shape[0]
+    p = np.linalg.norm(np.asarray(d_means, np.float64).reshape(n, -1), axis=1)
+    c = np.linalg.norm(np.asarray(d_sh, np.float64).reshape(n, -1), axis=1)
+    s = np.linalg.norm(np.asarray(d_log_scales, np.float64).reshape(n, -1), axis=1)
+    return weights[0] * p + weights[1] * c + weights[2] * s
+
+
+def activity_prune(activity_sum, samples: int, threshold: float, trainable) -> np.ndarray:
+    """keep = not (trainable and activity_sum / samples <= threshold)."""
+    avg = np.asarray(activity_sum, np.float64) / samples
+    return ~(np.asarray(trainable, bool) & (avg <= threshold))

@@ -119,3 +119,58 @@ def test_compact_keeps_order():
     a = np.arange(20).reshape(10, 2)
     keep = np.array([1, 0, 0, 1, 1, 0, 1, 0, 0, 1], bool)
     assert np.array_equal(T.compact(a, keep), a[[0, 3, 4, 6, 9]])
+
+
+def _golden(name):
+    import os
+    vals = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+def test_activity_weights_are_the_papers():
+    g = _golden("inactive_pruning.txt")
+    assert T.ACT_W == (g["w_p"], g["w_c"], g["w_s"])
+
+
+def test_activity_constant_gradient_closed_form():
+    """With a constant gradient every Adam update is lr sign(g) per element, so
+    the step's norms are lr sqrt(elements) and the sample is their weighted sum."""
+    rng = np.random.default_rng(6)
+    n, K = 7, 16
+    lr = (1.6e-4, 2.5e-3, 5e-3)            # means, SH, log-scales
+    shapes = [(n, 3), (n, K, 3), (n, 3)]
+    p = [rng.standard_normal(s) for s in shapes]
+    g = [rng.standard_normal(s) for s in shapes]
+    m = [np.zeros(s) for s in shapes]
+    v = [np.zeros(s) for s in shapes]
+    acc = np.zeros(n)
+    for t in range(1, 6):
+        d = []
+        for k in range(3):
+            p1, m[k], v[k] = T.adam_step(p[k], g[k], m[k], v[k], t, lr[k])
+            d.append(p1 - p[k])
+            p[k] = p1
+        acc += T.activity_sample(*d)
+    per_step = 2 * lr[0] * np.sqrt(3) + 0.1 * lr[1] * np.sqrt(3 * K) + 0.1 * lr[2] * np.sqrt(3)
+    assert np.allclose(acc, 5 * per_step, rtol=1e-9)
+
+
+def test_activity_prune_threshold_and_decay():
+    g = _golden("inactive_pruning.txt")
+    dR, T0, decay = int(g["dR"]), g["T0"], g["decay"]
+    acc = np.array([0.5, 1.5, 1.4999, 0.0, 3.0]) * dR * 0.01     # averages 0.005, 0.015, 0.014999, 0, 0.03
+    trainable = np.array([1, 1, 1, 0, 1], bool)
+    keep = T.activity_prune(acc, dR, T0, trainable)
+    # <= T0 removed (equality included), frozen rows never tested
+    assert keep.tolist() == [False, False, False, True, True]
+    # the threshold after k comparisons is T0 * decay^k
+    thr = T0
+    for _ in range(10):
+        thr *= decay
+    assert abs(thr - 0.015 * 0.975 ** 10) < 1e-15
