@@ -163,6 +163,23 @@ typedef struct gs_render_request {
 } gs_render_request;
 int gs_render_batch(const gs_render_request *reqs, int32_t n, void *stream);
 
+/* Stereo pair (Sec. 3.3: a VR frame renders the scene once per eye) of one
+ * scene with the same layer mask and clip planes: each eye as gs_render on
+ * its own workspace, both eyes composited by one launch.  shared_sort != 0
+ * sorts once for both eyes, as the paper's renderer can: the Gaussians
+ * visible to either eye are ordered by their depth in the left eye (by the
+ * right eye's depth when only the right eye sees them), and both eyes bin
+ * and composite in that order.  The left image is then exactly gs_render's;
+ * the right image differs only where splats change depth order between the
+ * eyes (an approximation).  With shared_sort, the left status word's
+ * n_visible counts the Gaussians visible to either eye.  Workspaces must be
+ * distinct; either eye's pair list may overflow independently (status word
+ * of that workspace).                                                        */
+int gs_render_stereo(const gs_scene *scene, const gs_camera *left, const gs_camera *right, uint32_t layer_mask,
+                     const gs_clip_plane *planes, int32_t n_planes, const float *bg, void *ws_left,
+                     size_t ws_left_bytes, void *ws_right, size_t ws_right_bytes, float *image_left,
+                     float *alpha_left, float *image_right, float *alpha_right, int32_t shared_sort, void *stream);
+
 /* Backward of the last gs_render made with this workspace (same scene, camera
  * and bg; Sec. 3.2 layered training).
  *   dL_dimage  [3][H][W], dL_dalpha [H][W] (either may be NULL = zero)
@@ -226,6 +243,28 @@ typedef struct gs_adam_state {
  * (frozen layers).  GS_ERR_INVALID for non-float32 fields or NULL arrays.   */
 int gs_adam_step(const gs_scene *scene, const gs_grads *grads, const gs_adam_state *state, const float *lr,
                  float beta1, float beta2, float eps, int32_t step, uint32_t train_layer_mask, void *stream);
+
+/* Activity of the inactive pruning (Sec. 3.2.2), called after gs_adam_step
+ * with the same state and hyper-parameters: for every Gaussian whose layer is
+ * in train_layer_mask,
+ *   activity[g] += 2 |d mean| + 0.1 |d SH| + 0.1 |d log-scale|
+ * where d is the update that Adam step applied (recomputed from the moments
+ * in state: m[0], v[0] means, m[4], v[4] SH, m[1], v[1] log-scales).  layer
+ * u8 [n], activity f32 [n] (device, accumulated).  lr[5] as for gs_adam_step.
+ * Asynchronous; GS_ERR_INVALID for NULL arrays or bad sizes.               */
+int gs_activity_accumulate(const gs_adam_state *state, const uint8_t *layer, int64_t n, int32_t sh_degree,
+                           const float *lr, float beta1, float beta2, float eps, int32_t step,
+                           uint32_t train_layer_mask, float *activity, void *stream);
+
+/* Inactive pruning decision (Sec. 3.2.2): keep[i] = 0 when layer i is in
+ * train_layer_mask and activity[i] / samples <= threshold (the average over
+ * the samples accumulated since the last decision), else 1; keep_index and
+ * n_keep as for gs_contrib_prune, with its workspace size.  The caller
+ * multiplies the threshold by the decay (0.975 in the paper) after each
+ * decision and resets activity.                                              */
+int gs_activity_prune(const float *activity, const uint8_t *layer, int64_t n, uint32_t train_layer_mask,
+                      float samples, float threshold, uint8_t *keep, int32_t *keep_index, int64_t *n_keep,
+                      void *workspace, size_t ws_bytes, void *stream);
 
 /* Row gather for applying a prune: dst row i = src row index[i] for
  * i < n, rows of row_bytes > 0 bytes (2-byte aligned arrays when row_bytes is

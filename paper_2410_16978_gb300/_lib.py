@@ -21,9 +21,9 @@ GS_TILE = 16
 GS_MAX_PLANES = 8
 GS_MAX_BATCH = 16
 
-EXPORTED = ("gs_render_workspace_size", "gs_render", "gs_render_batch", "gs_render_backward", "gs_prune_workspace_size",
+EXPORTED = ("gs_render_workspace_size", "gs_render", "gs_render_batch", "gs_render_stereo", "gs_render_backward", "gs_prune_workspace_size",
             "gs_contrib_prune", "gs_contrib_prune_noalloc", "gs_image_loss_workspace_size", "gs_image_loss",
-            "gs_adam_step", "gs_gather_rows", "gs_workspace_layout", "gs_read_status", "gs_profile_enable",
+            "gs_adam_step", "gs_activity_accumulate", "gs_activity_prune", "gs_gather_rows", "gs_workspace_layout", "gs_read_status", "gs_profile_enable",
             "gs_profile_collect", "gs_kernel_launches", "gs_last_error_string", "gs_version")
 STAGES = ("preprocess", "compact", "depth_sort", "bin_rows", "bin_tiles", "composite_setup", "composite",
           "composite_bwd", "preprocess_bwd", "prune", "loss", "adam")
@@ -105,6 +105,10 @@ def load(build_if_missing: bool = True):
                                 ctypes.POINTER(gs_clip_plane), ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
                                 _P, ctypes.c_size_t, _P, _P, _P]
         L.gs_render_batch.argtypes = [ctypes.POINTER(gs_render_request), ctypes.c_int32, _P]
+        L.gs_render_stereo.argtypes = [ctypes.POINTER(gs_scene), ctypes.POINTER(gs_camera), ctypes.POINTER(gs_camera),
+                                       ctypes.c_uint32, ctypes.POINTER(gs_clip_plane), ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_float), _P, ctypes.c_size_t, _P, ctypes.c_size_t, _P,
+                                       _P, _P, _P, ctypes.c_int32, _P]
         L.gs_render_backward.argtypes = [ctypes.POINTER(gs_scene), ctypes.POINTER(gs_camera),
                                          ctypes.POINTER(ctypes.c_float), _P, ctypes.c_size_t, _P, _P,
                                          ctypes.c_uint32, ctypes.POINTER(gs_grads), _P, _P, _P]
@@ -119,6 +123,11 @@ def load(build_if_missing: bool = True):
                                    ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_int32, ctypes.c_uint32, _P]
         L.gs_gather_rows.argtypes = [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P]
+        L.gs_activity_accumulate.argtypes = [ctypes.POINTER(gs_adam_state), _P, ctypes.c_int64, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float,
+                                             ctypes.c_float, ctypes.c_int32, ctypes.c_uint32, _P, _P]
+        L.gs_activity_prune.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_uint32, ctypes.c_float, ctypes.c_float, _P,
+                                        _P, _P, _P, ctypes.c_size_t, _P]
         L.gs_workspace_layout.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t,
                                           ctypes.POINTER(ctypes.c_int64)]
         L.gs_profile_enable.argtypes = [ctypes.c_int]
@@ -215,6 +224,18 @@ def gs_render_batch(views, stream: int) -> None:
     del keep
 
 
+def gs_render_stereo(scene: gs_scene, left: gs_camera, right: gs_camera, layer_mask: int, planes, bg, ws_left,
+                     ws_left_bytes: int, ws_right, ws_right_bytes: int, image_left, alpha_left, image_right,
+                     alpha_right, shared_sort: bool, stream: int) -> None:
+    parr, npl = make_planes(planes)
+    bgv = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    _check(load().gs_render_stereo(ctypes.byref(scene), ctypes.byref(left), ctypes.byref(right),
+                                   int(layer_mask) & 0xFFFFFFFF, parr, npl, bgv, _ptr(ws_left), int(ws_left_bytes),
+                                   _ptr(ws_right), int(ws_right_bytes), _ptr(image_left), _ptr(alpha_left),
+                                   _ptr(image_right), _ptr(alpha_right), 1 if shared_sort else 0,
+                                   ctypes.c_void_p(stream)))
+
+
 def gs_render_backward(scene: gs_scene, camera: gs_camera, bg, workspace, ws_bytes: int, dL_dimage, dL_dalpha,
                        grad_layer_mask: int, grads: gs_grads, contrib_sum, contrib_max, stream: int) -> None:
     bgv = (ctypes.c_float * 3)(*[float(v) for v in bg])
@@ -261,6 +282,21 @@ def gs_adam_step(scene: gs_scene, grads: gs_grads, state: gs_adam_state, lr, bet
     _check(load().gs_adam_step(ctypes.byref(scene), ctypes.byref(grads), ctypes.byref(state), lrv, float(beta1),
                                float(beta2), float(eps), int(step), int(train_layer_mask) & 0xFFFFFFFF,
                                ctypes.c_void_p(stream)))
+
+
+def gs_activity_accumulate(state: gs_adam_state, layer, n: int, sh_degree: int, lr, beta1: float, beta2: float,
+                           eps: float, step: int, train_layer_mask: int, activity, stream: int) -> None:
+    lrv = (ctypes.c_float * 5)(*[float(v) for v in lr])
+    _check(load().gs_activity_accumulate(ctypes.byref(state), _ptr(layer), int(n), int(sh_degree), lrv, float(beta1),
+                                         float(beta2), float(eps), int(step), int(train_layer_mask) & 0xFFFFFFFF,
+                                         _ptr(activity), ctypes.c_void_p(stream)))
+
+
+def gs_activity_prune(activity, layer, n: int, train_layer_mask: int, samples: float, threshold: float, keep,
+                      keep_index, n_keep, workspace, ws_bytes: int, stream: int) -> None:
+    _check(load().gs_activity_prune(_ptr(activity), _ptr(layer), int(n), int(train_layer_mask) & 0xFFFFFFFF,
+                                    float(samples), float(threshold), _ptr(keep), _ptr(keep_index), _ptr(n_keep),
+                                    _ptr(workspace), int(ws_bytes), ctypes.c_void_p(stream)))
 
 
 def gs_gather_rows(src, dst, row_bytes: int, index, n: int, stream: int) -> None:

@@ -178,6 +178,19 @@ __device__ __forceinline__ void fetch_chunk(const uint32_t *__restrict__ list, c
     }
 }
 
+// The record of an id loaded one chunk earlier: list and record loads of a
+// chunk are issued a chunk apart, so the record load does not wait on the
+// list load in the same iteration.
+__device__ __forceinline__ void fetch_rec(const Rec *__restrict__ rec, uint32_t g, bool valid, Chunk &ch) {
+    if (valid) {
+        ch.g = g;
+        const Rec *r = rec + g;
+        ch.a = r->a;
+        ch.b = r->b;
+        ch.c = r->c.x;
+    }
+}
+
 struct FwdBatch {
     FwdJob job[kMaxBatch];
     int n;
@@ -218,6 +231,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_cons
         float4 *my_ckpt = J.ckpt + static_cast<size_t>(J.seg_base[tile]) * kTilePix + ly * kTile + lx;
         Chunk nxt;
         fetch_chunk(list, rec, rg.x + lane, rg.y, nxt);
+        uint32_t gid = rg.x + 32 + lane < rg.y ? list[rg.x + 32 + lane] : 0u;   // ids one chunk ahead
         for (uint32_t base = rg.x; base < rg.y; base += 32) {
             if (__all_sync(FULL, done)) break;
             const uint32_t pos0 = base - rg.x;
@@ -237,7 +251,8 @@ __global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_cons
                 s_pos[warp][slot] = pos0 + lane;
             }
             __syncwarp();
-            fetch_chunk(list, rec, base + 32 + lane, rg.y, nxt);
+            fetch_rec(rec, gid, base + 32 + lane < rg.y, nxt);
+            gid = base + 64 + lane < rg.y ? list[base + 64 + lane] : 0u;
             const int cnt = __popc(km);
             for (int k = 0; k < cnt && !done; ++k) {
                 const float4 a = s_a[warp][k], b = s_b[warp][k];

@@ -222,20 +222,32 @@ namespace {
 
 // Validates one view, launches S1 (preprocess) and S2 (binning and sorts) and
 // the compositor set-up on st, and describes the view in *job.
-int render_front(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mask, const gs_clip_plane *planes,
-                 int32_t n_planes, const float *bg, void *workspace, size_t ws_bytes, float *image, float *alpha,
-                 cudaStream_t st, FwdJob *job, uint32_t **queue) {
+// One view of a render call between its phases.
+struct FrontCtx {
     SceneView sv;
     CamView cv;
+    Layout L;
+    void *ws = nullptr;
+    Ctl *ctl = nullptr;
+    Rec *rec = nullptr;
+    uint32_t *tiles = nullptr;
+    uint32_t *depth = nullptr;
+    float *image = nullptr, *alpha = nullptr;
+    float bg[3] = {0.f, 0.f, 0.f};
+};
+
+// Phase 1: validation, status reset and S1 (preprocess).
+int front_preprocess(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mask,
+                     const gs_clip_plane *planes, int32_t n_planes, const float *bg, void *workspace,
+                     size_t ws_bytes, float *image, float *alpha, cudaStream_t st, FrontCtx *f) {
     int rc;
-    if ((rc = check_scene(scene, &sv)) != GS_OK) return rc;
-    if ((rc = check_camera(camera, &cv)) != GS_OK) return rc;
+    if ((rc = check_scene(scene, &f->sv)) != GS_OK) return rc;
+    if ((rc = check_camera(camera, &f->cv)) != GS_OK) return rc;
     if (n_planes < 0 || n_planes > GS_MAX_PLANES) return fail(GS_ERR_INVALID, "n_planes must be 0..%d", GS_MAX_PLANES);
     if (n_planes > 0 && !planes) return fail(GS_ERR_INVALID, "planes is NULL");
     if (!bg) return fail(GS_ERR_INVALID, "bg is NULL");
     if (!image) return fail(GS_ERR_INVALID, "image is NULL");
-    Layout L;
-    if ((rc = workspace_layout(scene, cv, workspace, ws_bytes, &L)) != GS_OK) return rc;
+    if ((rc = workspace_layout(scene, f->cv, workspace, ws_bytes, &f->L)) != GS_OK) return rc;
     Planes pl;
     std::memset(&pl, 0, sizeof pl);
     pl.n = n_planes;
@@ -243,57 +255,80 @@ int render_front(const gs_scene *scene, const gs_camera *camera, uint32_t layer_
         pl.p[k] = make_float4(planes[k].n[0], planes[k].n[1], planes[k].n[2], planes[k].d);
         pl.bits[k] = planes[k].layer_bits;
     }
-    void *ws = workspace;
-    Ctl *ctl = at<Ctl>(ws, L.ctl);
-    const uint32_t n = static_cast<uint32_t>(sv.n);
-    if ((rc = cuda_check(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st), "memset status")) != GS_OK) return rc;
-    if ((rc = cuda_check(cudaMemsetAsync(at<char>(ws, L.ranges), 0, static_cast<size_t>(L.Tn) * 8, st),
+    const Layout &L = f->L;
+    f->ws = workspace;
+    f->ctl = at<Ctl>(workspace, L.ctl);
+    f->rec = at<Rec>(workspace, L.rec);
+    f->tiles = at<uint32_t>(workspace, L.tiles);
+    f->depth = at<uint32_t>(workspace, L.depth);
+    f->image = image;
+    f->alpha = alpha;
+    for (int c = 0; c < 3; ++c) f->bg[c] = bg[c];
+    if ((rc = cuda_check(cudaMemsetAsync(f->ctl, 0, sizeof(Ctl), st), "memset status")) != GS_OK) return rc;
+    if ((rc = cuda_check(cudaMemsetAsync(at<char>(workspace, L.ranges), 0, static_cast<size_t>(L.Tn) * 8, st),
                          "memset ranges")) != GS_OK)
         return rc;
-    Rec *rec = at<Rec>(ws, L.rec);
-    uint32_t *tiles = at<uint32_t>(ws, L.tiles);
-    {
-        Stage sg(GS_STAGE_PREPROCESS, st, 1);
-        if ((rc = cuda_check(launch_preprocess(sv, cv, layer_mask, pl, rec, tiles, at<uint32_t>(ws, L.depth), st),
-                             "preprocess")) != GS_OK)
-            return rc;
-    }
+    Stage sg(GS_STAGE_PREPROCESS, st, 1);
+    return cuda_check(launch_preprocess(f->sv, f->cv, layer_mask, pl, f->rec, f->tiles, f->depth, st), "preprocess");
+}
+
+// Phase 2: compaction of the visible Gaussians and the depth radix sort.  With
+// `other`, a Gaussian visible to either view is kept and keyed by this view's
+// depth when this view sees it, else by the other's (shared stereo order).
+// Returns the depth order (in this view's workspace).
+int front_sort(FrontCtx &f, const FrontCtx *other, cudaStream_t st, uint32_t **order) {
+    int rc;
+    const Layout &L = f.L;
+    void *ws = f.ws;
+    const uint32_t n = static_cast<uint32_t>(f.sv.n);
     uint32_t *sk[2] = {at<uint32_t>(ws, L.sort_k[0]), at<uint32_t>(ws, L.sort_k[1])};
     uint32_t *sv2[2] = {at<uint32_t>(ws, L.sort_v[0]), at<uint32_t>(ws, L.sort_v[1])};
     uint32_t *partials = at<uint32_t>(ws, L.partials);
     uint32_t *hist = at<uint32_t>(ws, L.hist);
     {
         Stage sg(GS_STAGE_COMPACT, st, 3);
-        if ((rc = cuda_check(launch_compact_visible(tiles, at<uint32_t>(ws, L.depth), sv.n, sk[0], sv2[0], partials,
-                                                    ctl, st),
-                             "compact")) != GS_OK)
-            return rc;
+        rc = other ? cuda_check(launch_compact_visible2(f.tiles, f.depth, other->tiles, other->depth, f.sv.n, sk[0],
+                                                        sv2[0], partials, f.ctl, st),
+                                "compact (stereo)")
+                   : cuda_check(launch_compact_visible(f.tiles, f.depth, f.sv.n, sk[0], sv2[0], partials, f.ctl, st),
+                                "compact");
+        if (rc != GS_OK) return rc;
     }
     {
         Stage sg(GS_STAGE_DEPTH_SORT, st, 12);
         for (int pass = 0; pass < 4; ++pass) {
             const int a = pass & 1;
-            if ((rc = cuda_check(launch_radix_pass(sk[a], sv2[a], sk[1 - a], sv2[1 - a], &ctl->n_vis, n, 8 * pass,
-                                                   hist, ctl->depth_mm, pass == 0, st),
+            if ((rc = cuda_check(launch_radix_pass(sk[a], sv2[a], sk[1 - a], sv2[1 - a], &f.ctl->n_vis, n, 8 * pass,
+                                                   hist, f.ctl->depth_mm, pass == 0, st),
                                  "depth sort")) != GS_OK)
                 return rc;
         }
     }
-    uint32_t *order = sv2[0];
+    *order = sv2[0];
+    return GS_OK;
+}
+
+// Phase 3: binning in the given depth order (whose count is at n_vis), the
+// compositor set-up, and the forward job of the view.
+int front_bin(FrontCtx &f, const uint32_t *order, cudaStream_t st, FwdJob *job, uint32_t **queue) {
+    int rc;
+    const Layout &L = f.L;
+    void *ws = f.ws;
+    const uint32_t n = static_cast<uint32_t>(f.sv.n);
     uint32_t *list = at<uint32_t>(ws, L.list);
     uint2 *rowlist = at<uint2>(ws, L.rowlist);
     uint2 *ranges = at<uint2>(ws, L.ranges);
     {
         Stage sg(GS_STAGE_BIN_ROWS, st, 4);
-        if ((rc = cuda_check(launch_bin_rows(order, rec, n, cv.Ty, at<uint32_t>(ws, L.bin_m), at<void>(ws, L.bin_rows),
-                                             rowlist, ctl, L.dup_cap, L.bin_piece, st),
+        if ((rc = cuda_check(launch_bin_rows(order, f.rec, n, f.cv.Ty, at<uint32_t>(ws, L.bin_m),
+                                             at<void>(ws, L.bin_rows), rowlist, f.ctl, L.dup_cap, L.bin_piece, st),
                              "binning rows")) != GS_OK)
             return rc;
     }
     {
         Stage sg(GS_STAGE_BIN_TILES, st, 3);
-        if ((rc = cuda_check(launch_bin_tiles(rowlist, at<void>(ws, L.bin_rows), cv.Tx, cv.Ty, L.bin_piece,
-                                              at<uint32_t>(ws, L.bin_p), list, ranges, ctl, st),
+        if ((rc = cuda_check(launch_bin_tiles(rowlist, at<void>(ws, L.bin_rows), f.cv.Tx, f.cv.Ty, L.bin_piece,
+                                              at<uint32_t>(ws, L.bin_p), list, ranges, f.ctl, st),
                              "binning tiles")) != GS_OK)
             return rc;
     }
@@ -305,22 +340,36 @@ int render_front(const gs_scene *scene, const gs_camera *camera, uint32_t layer_
     job->order = cb.order;
     job->ranges = ranges;
     job->list = list;
-    job->rec = rec;
-    job->image = image;
-    job->alpha = alpha;
+    job->rec = f.rec;
+    job->image = f.image;
+    job->alpha = f.alpha;
     job->t_final = at<float>(ws, L.t_final);
     job->n_contrib = at<uint32_t>(ws, L.n_contrib);
     job->seg_base = cb.seg_base;
     job->ckpt = cb.ckpt;
     job->qwork = cb.qwork;
-    job->W = cv.W;
-    job->H = cv.H;
-    job->Tx = cv.Tx;
+    job->W = f.cv.W;
+    job->H = f.cv.H;
+    job->Tx = f.cv.Tx;
     job->Tn = L.Tn;
-    job->bg = make_float3(bg[0], bg[1], bg[2]);
+    job->bg = make_float3(f.bg[0], f.bg[1], f.bg[2]);
     job->item_begin = 0;
     *queue = cb.queue;
     return GS_OK;
+}
+
+// Validates one view, launches S1 (preprocess) and S2 (sort and binning) and
+// the compositor set-up, and fills the view's forward job.
+int render_front(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mask, const gs_clip_plane *planes,
+                 int32_t n_planes, const float *bg, void *workspace, size_t ws_bytes, float *image, float *alpha,
+                 cudaStream_t st, FwdJob *job, uint32_t **queue) {
+    FrontCtx f;
+    int rc = front_preprocess(scene, camera, layer_mask, planes, n_planes, bg, workspace, ws_bytes, image, alpha, st,
+                              &f);
+    if (rc != GS_OK) return rc;
+    uint32_t *order = nullptr;
+    if ((rc = front_sort(f, nullptr, st, &order)) != GS_OK) return rc;
+    return front_bin(f, order, st, job, queue);
 }
 
 }  // namespace
@@ -361,6 +410,47 @@ int gs_render_batch(const gs_render_request *reqs, int32_t n, void *stream) {
     return cuda_check(launch_composite_forward(jobs, n, queue0, st), "batched composite");
 }
 
+
+int gs_render_stereo(const gs_scene *scene, const gs_camera *left, const gs_camera *right, uint32_t layer_mask,
+                     const gs_clip_plane *planes, int32_t n_planes, const float *bg, void *ws_left,
+                     size_t ws_left_bytes, void *ws_right, size_t ws_right_bytes, float *image_left,
+                     float *alpha_left, float *image_right, float *alpha_right, int32_t shared_sort, void *stream) {
+    if (ws_left == ws_right) return fail(GS_ERR_INVALID, "the two eyes need separate workspaces");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    FrontCtx f[2];
+    int rc;
+    if ((rc = front_preprocess(scene, left, layer_mask, planes, n_planes, bg, ws_left, ws_left_bytes, image_left,
+                               alpha_left, st, &f[0])) != GS_OK)
+        return rc;
+    if ((rc = front_preprocess(scene, right, layer_mask, planes, n_planes, bg, ws_right, ws_right_bytes, image_right,
+                               alpha_right, st, &f[1])) != GS_OK)
+        return rc;
+    FwdJob jobs[2];
+    uint32_t *queue[2] = {nullptr, nullptr};
+    if (shared_sort) {
+        uint32_t *order = nullptr;
+        if ((rc = front_sort(f[0], &f[1], st, &order)) != GS_OK) return rc;
+        // the right eye bins in the shared order: it needs the shared count too
+        if ((rc = cuda_check(cudaMemcpyAsync(&f[1].ctl->n_vis, &f[0].ctl->n_vis, sizeof(uint32_t),
+                                             cudaMemcpyDeviceToDevice, st),
+                             "shared count")) != GS_OK)
+            return rc;
+        if ((rc = cuda_check(cudaMemcpyAsync(&f[1].ctl->st.n_visible, &f[0].ctl->st.n_visible, sizeof(uint32_t),
+                                             cudaMemcpyDeviceToDevice, st),
+                             "shared count")) != GS_OK)
+            return rc;
+        if ((rc = front_bin(f[0], order, st, &jobs[0], &queue[0])) != GS_OK) return rc;
+        if ((rc = front_bin(f[1], order, st, &jobs[1], &queue[1])) != GS_OK) return rc;
+    } else {
+        for (int e = 0; e < 2; ++e) {
+            uint32_t *order = nullptr;
+            if ((rc = front_sort(f[e], nullptr, st, &order)) != GS_OK) return rc;
+            if ((rc = front_bin(f[e], order, st, &jobs[e], &queue[e])) != GS_OK) return rc;
+        }
+    }
+    Stage sg(GS_STAGE_COMPOSITE, st, 1);
+    return cuda_check(launch_composite_forward(jobs, 2, queue[0], st), "stereo composite");
+}
 
 int gs_render_backward(const gs_scene *scene, const gs_camera *camera, const float *bg, void *workspace,
                        size_t ws_bytes, const float *dL_dimage, const float *dL_dalpha, uint32_t grad_layer_mask,
@@ -516,6 +606,45 @@ int gs_adam_step(const gs_scene *scene, const gs_grads *grads, const gs_adam_sta
     return cuda_check(launch_adam(p, g, state->m, state->v, width, sv.n, sv.layer, train_layer_mask, lr, beta1, beta2,
                                   eps, step, st),
                       "adam");
+}
+
+int gs_activity_accumulate(const gs_adam_state *state, const uint8_t *layer, int64_t n, int32_t sh_degree,
+                           const float *lr, float beta1, float beta2, float eps, int32_t step,
+                           uint32_t train_layer_mask, float *activity, void *stream) {
+    if (n < 0 || n > 0x7FFFFFFF) return fail(GS_ERR_INVALID, "n out of range");
+    if (sh_degree < 0 || sh_degree > 3) return fail(GS_ERR_INVALID, "sh_degree must be 0..3");
+    if (step < 1) return fail(GS_ERR_INVALID, "step must be >= 1");
+    if (!state || !lr) return fail(GS_ERR_INVALID, "NULL argument");
+    if (n == 0) return GS_OK;
+    if (!layer || !activity || !state->m[0] || !state->v[0] || !state->m[1] || !state->v[1] || !state->m[4] ||
+        !state->v[4])
+        return fail(GS_ERR_INVALID, "NULL array");
+    const float *m[3] = {state->m[0], state->m[4], state->m[1]};
+    const float *v[3] = {state->v[0], state->v[4], state->v[1]};
+    const float l3[3] = {lr[0], lr[4], lr[1]};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Stage sg(GS_STAGE_ADAM, st, 1);
+    return cuda_check(launch_activity(m, v, (sh_degree + 1) * (sh_degree + 1), n, layer, train_layer_mask, l3, beta1,
+                                      beta2, eps, step, activity, st),
+                      "activity");
+}
+
+int gs_activity_prune(const float *activity, const uint8_t *layer, int64_t n, uint32_t train_layer_mask,
+                      float samples, float threshold, uint8_t *keep, int32_t *keep_index, int64_t *n_keep,
+                      void *workspace, size_t ws_bytes, void *stream) {
+    if (n < 0 || n > 0x7FFFFFFF) return fail(GS_ERR_INVALID, "n out of range");
+    if (!n_keep) return fail(GS_ERR_INVALID, "n_keep is NULL");
+    if (n > 0 && (!activity || !layer || !keep)) return fail(GS_ERR_INVALID, "activity, layer and keep must be set");
+    if (!(samples > 0.f)) return fail(GS_ERR_INVALID, "samples must be > 0");
+    size_t need = 0;
+    gs_prune_workspace_size(n, &need);
+    if (!workspace || ws_bytes < need) return fail(GS_ERR_WORKSPACE, "prune workspace needs %zu bytes", need);
+    if (!aligned(workspace, 16)) return fail(GS_ERR_INVALID, "workspace must be 16-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Stage sg(GS_STAGE_PRUNE, st, 3);
+    return cuda_check(launch_activity_prune(activity, layer, train_layer_mask, static_cast<int>(n), samples, threshold,
+                                            keep, keep_index, n_keep, static_cast<uint32_t *>(workspace), st),
+                      "activity prune");
 }
 
 int gs_gather_rows(const void *src, void *dst, int64_t row_bytes, const int32_t *index, int64_t n, void *stream) {

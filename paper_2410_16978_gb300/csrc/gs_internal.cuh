@@ -111,6 +111,11 @@ int report(int code, const char *msg);   // sets gs_last_error_string(), returns
 // to (keys_out, vals_out) and the count to ctl->n_vis.
 cudaError_t launch_compact_visible(const uint32_t *tiles, const uint32_t *depth_key, int n, uint32_t *keys_out,
                                    uint32_t *vals_out, uint32_t *partials, Ctl *ctl, cudaStream_t st);
+// Stereo variant: Gaussians visible to view a or view b; key = depth_a where
+// view a sees the Gaussian, else depth_b (one depth order shared by two eyes).
+cudaError_t launch_compact_visible2(const uint32_t *tiles_a, const uint32_t *depth_a, const uint32_t *tiles_b,
+                                    const uint32_t *depth_b, int n, uint32_t *keys_out, uint32_t *vals_out,
+                                    uint32_t *partials, Ctl *ctl, cudaStream_t st);
 // One stable LSD pass on 8 bits at `shift` of min(*n_dev, n_cap) (key, value) pairs.
 // minmax (2 words, zeroed before the sort) receives ~min and max key in the
 // first pass; later passes whose digit is constant only copy.
@@ -142,6 +147,12 @@ cudaError_t launch_adam(float *const p[5], const float *const g[5], float *const
                         const float lr[5], float beta1, float beta2, float eps, int step, cudaStream_t st);
 cudaError_t launch_gather_rows(const void *src, void *dst, int64_t row_bytes, const int32_t *idx, int64_t n,
                                cudaStream_t st);
+cudaError_t launch_activity(const float *const m[3], const float *const v[3], int sh_coeffs, int64_t n,
+                            const uint8_t *layer, uint32_t train_mask, const float lr[3], float beta1, float beta2,
+                            float eps, int step, float *activity, cudaStream_t st);
+cudaError_t launch_activity_prune(const float *activity, const uint8_t *layer, uint32_t train_mask, int n,
+                                  float samples, float thr, uint8_t *keep, int32_t *keep_index, int64_t *n_keep,
+                                  uint32_t *partials, cudaStream_t st);
 cudaError_t launch_prune(const float *contrib_max, int n, float thr, uint8_t *keep, int32_t *keep_index,
                          int64_t *n_keep, uint32_t *partials, cudaStream_t st);
 

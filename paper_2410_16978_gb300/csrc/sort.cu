@@ -159,10 +159,36 @@ struct CompactOut {
         if (v) { keys[off] = depth_key[i]; vals[off] = i; }
     }
 };
+struct VisFlag2 {           // visible to either of two views
+    const uint32_t *tiles_a, *tiles_b;
+    __device__ __forceinline__ uint32_t operator()(uint32_t i) const {
+        return (tiles_a[i] > 0 || tiles_b[i] > 0) ? 1u : 0u;
+    }
+};
+struct CompactOut2 {        // key: view a's depth when view a sees it, else view b's
+    const uint32_t *tiles_a, *depth_a, *depth_b;
+    uint32_t *keys, *vals;
+    __device__ __forceinline__ void operator()(uint32_t i, uint32_t off, uint32_t v) const {
+        if (v) {
+            keys[off] = tiles_a[i] > 0 ? depth_a[i] : depth_b[i];
+            vals[off] = i;
+        }
+    }
+};
 struct KeepFlag {
     const float *cmax;
     float thr;
     __device__ __forceinline__ uint32_t operator()(uint32_t i) const { return cmax[i] >= thr ? 1u : 0u; }
+};
+struct ActiveFlag {         // keep unless trainable and activity / samples <= thr
+    const float *act;
+    const uint8_t *layer;
+    uint32_t mask;
+    float inv_samples, thr;
+    __device__ __forceinline__ uint32_t operator()(uint32_t i) const {
+        const bool trainable = (mask >> layer[i]) & 1u;
+        return (trainable && act[i] * inv_samples <= thr) ? 0u : 1u;
+    }
 };
 struct KeepOut {
     uint8_t *keep;
@@ -378,6 +404,18 @@ cudaError_t launch_compact_visible(const uint32_t *tiles, const uint32_t *depth_
     return cudaGetLastError();
 }
 
+cudaError_t launch_compact_visible2(const uint32_t *tiles_a, const uint32_t *depth_a, const uint32_t *tiles_b,
+                                    const uint32_t *depth_b, int n, uint32_t *keys_out, uint32_t *vals_out,
+                                    uint32_t *partials, Ctl *ctl, cudaStream_t st) {
+    const int G = sort_blocks();
+    NSrc ns{nullptr, static_cast<uint32_t>(n)};
+    VisFlag2 f{tiles_a, tiles_b};
+    k_scan_reduce<<<G, 256, 0, st>>>(f, ns, partials);
+    k_scan_partials<<<1, 1024, 0, st>>>(partials, G, FIN_NVIS, ctl, 0, nullptr);
+    k_scan_down<<<G, 256, 0, st>>>(f, ns, partials, CompactOut2{tiles_a, depth_a, depth_b, keys_out, vals_out});
+    return cudaGetLastError();
+}
+
 cudaError_t launch_radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                               const uint32_t *n_dev, uint32_t n_cap, int shift, uint32_t *hist, uint32_t *minmax,
                               bool first, cudaStream_t st) {
@@ -387,6 +425,19 @@ cudaError_t launch_radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t
     k_radix_up<<<G, 256, 0, st>>>(kin, ns, shift, hist, minmax, first ? 1 : 0);
     k_radix_rowscan<<<256, 256, 0, st>>>(hist, G, rowtot, minmax, shift, first ? 1 : 0);
     k_radix_down<<<G, 256, 0, st>>>(kin, vin, kout, vout, ns, shift, hist, rowtot, minmax, first ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_activity_prune(const float *activity, const uint8_t *layer, uint32_t train_mask, int n,
+                                  float samples, float thr, uint8_t *keep, int32_t *keep_index, int64_t *n_keep,
+                                  uint32_t *partials, cudaStream_t st) {
+    const int G = sort_blocks();
+    NSrc ns{nullptr, static_cast<uint32_t>(n)};
+    ActiveFlag f{activity, layer, train_mask, 1.f / samples, thr};
+    Ctl *ctl = reinterpret_cast<Ctl *>(partials + kMaxSortBlocks);
+    k_scan_reduce<<<G, 256, 0, st>>>(f, ns, partials);
+    k_scan_partials<<<1, 1024, 0, st>>>(partials, G, FIN_NKEEP, ctl, 0, n_keep);
+    k_scan_down<<<G, 256, 0, st>>>(f, ns, partials, KeepOut{keep, keep_index});
     return cudaGetLastError();
 }
 

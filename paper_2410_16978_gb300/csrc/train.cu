@@ -233,6 +233,36 @@ __global__ void __launch_bounds__(256) k_adam(const AdamArrays arr, const uint8_
     }
 }
 
+// Activity of the inactive pruning (Sec. 3.2.2): per trainable Gaussian,
+// activity += 2 |d mean| + 0.1 |d SH| + 0.1 |d log-scale|, the norms of the
+// update the last Adam step applied, recomputed from the new moments with
+// the same expression as k_adam.
+struct ActArgs {
+    const float *m[3], *v[3];   // means, SH, log-scales
+    uint32_t width[3];          // 3, 3K, 3
+    float step[3];              // lr / (1 - beta1^t)
+    float inv_sqrt_bc2, eps;
+};
+
+__global__ void __launch_bounds__(256) k_activity(const ActArgs a, const uint8_t *__restrict__ layer,
+                                                  uint32_t train_mask, int n, float *__restrict__ activity) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n || !((train_mask >> layer[g]) & 1u)) return;
+    float nrm[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float *m = a.m[k] + static_cast<size_t>(g) * a.width[k];
+        const float *v = a.v[k] + static_cast<size_t>(g) * a.width[k];
+        float acc = 0.f;
+        for (uint32_t e = 0; e < a.width[k]; ++e) {
+            const float d = a.step[k] * m[e] / (sqrtf(v[e]) * a.inv_sqrt_bc2 + a.eps);
+            acc = fmaf(d, d, acc);
+        }
+        nrm[k] = sqrtf(acc);
+    }
+    activity[g] += 2.f * nrm[0] + 0.1f * nrm[1] + 0.1f * nrm[2];
+}
+
 // dst row i = src row idx[i], rows of `words` words of type T.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather_rows(const T *__restrict__ src, T *__restrict__ dst, uint32_t words,
@@ -295,6 +325,26 @@ cudaError_t launch_adam(float *const p[5], const float *const g[5], float *const
     if (acc == 0) return cudaSuccess;
     const int blocks = static_cast<int>(std::min<uint64_t>((acc + 255) / 256, 8ull * 1024));
     k_adam<<<blocks, 256, 0, st>>>(a, layer, train_mask, beta1, beta2, static_cast<float>(1.0 / std::sqrt(bc2)), eps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_activity(const float *const m[3], const float *const v[3], int sh_coeffs, int64_t n,
+                            const uint8_t *layer, uint32_t train_mask, const float lr[3], float beta1, float beta2,
+                            float eps, int step, float *activity, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    ActArgs a;
+    const double bc1 = 1.0 - std::pow(static_cast<double>(beta1), step);
+    const double bc2 = 1.0 - std::pow(static_cast<double>(beta2), step);
+    const uint32_t width[3] = {3, static_cast<uint32_t>(3 * sh_coeffs), 3};
+    for (int k = 0; k < 3; ++k) {
+        a.m[k] = m[k];
+        a.v[k] = v[k];
+        a.width[k] = width[k];
+        a.step[k] = static_cast<float>(lr[k] / bc1);
+    }
+    a.inv_sqrt_bc2 = static_cast<float>(1.0 / std::sqrt(bc2));
+    a.eps = eps;
+    k_activity<<<static_cast<int>((n + 255) / 256), 256, 0, st>>>(a, layer, train_mask, static_cast<int>(n), activity);
     return cudaGetLastError();
 }
 

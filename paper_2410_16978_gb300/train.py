@@ -1,11 +1,13 @@
 """Training step of the layered model (Sec. 3.2): render through the
 autograd Function, image loss with the alpha channel against a target under a
 random background, backward with per-Gaussian contributions, Adam on the
-trainable layers, and contribution pruning.
+trainable layers, contribution pruning, and the activity-based inactive
+pruning of Sec. 3.2.2.
 
 Every step runs in libgs.so kernels (gs_render, gs_image_loss,
-gs_render_backward, gs_adam_step, gs_contrib_prune, gs_gather_rows); PyTorch
-holds the tensors and chains the two autograd Functions.
+gs_render_backward, gs_adam_step, gs_activity_accumulate, gs_activity_prune,
+gs_contrib_prune, gs_gather_rows); PyTorch holds the tensors and chains the
+two autograd Functions.
 """
 from __future__ import annotations
 
@@ -60,6 +62,10 @@ class TrainConfig:
     w_alpha: float = 0.8                 # alpha L1 weight
     train_layer_mask: int = 0xFFFFFFFF   # layers being optimised (the rest are frozen)
     prune_threshold: float = 0.005
+    activity_prune: bool = False         # inactive pruning of Sec. 3.2.2
+    activity_interval: int = 100         # dR: steps per activity average
+    activity_threshold: float = 0.015    # T0
+    activity_decay: float = 0.975
 
 
 class Trainer:
@@ -67,7 +73,9 @@ class Trainer:
     one view: forward, loss, backward (gradients of the trainable layers and
     the blend weights of every Gaussian), Adam.  ``prune()`` removes the
     Gaussians whose largest blend weight since the last prune is below the
-    threshold, with their Adam moments."""
+    threshold, with their Adam moments.  With ``activity_prune`` every step
+    also accumulates each trainable Gaussian's activity, and every
+    ``activity_interval`` steps the inactive ones are removed."""
 
     def __init__(self, scene: DeviceScene, cameras: Sequence, config: TrainConfig = TrainConfig(),
                  dup_capacity: Optional[int] = None):
@@ -87,6 +95,10 @@ class Trainer:
         self._loss_ws = {}
         self.contrib_max = torch.zeros(scene.n, device=self.device)
         self.contrib_sum = torch.zeros(scene.n, device=self.device)
+        self.activity = torch.zeros(scene.n, device=self.device)
+        self.activity_samples = 0
+        self.activity_threshold = float(config.activity_threshold)
+        self.activity_removed = 0
 
     def _rast(self, cam) -> Rasterizer:
         key = (int(cam.width), int(cam.height))
@@ -128,20 +140,55 @@ class Trainer:
                 st.v[k] = self.v[k].data_ptr()
             _lib.gs_adam_step(sc.c_struct(), g, st, self.cfg.lr, self.cfg.beta1, self.cfg.beta2, self.cfg.eps, self.t,
                               self.cfg.train_layer_mask, _stream_handle(None))
+            if self.cfg.activity_prune:
+                _lib.gs_activity_accumulate(st, sc.layer, sc.n, sc.sh_degree, self.cfg.lr, self.cfg.beta1,
+                                            self.cfg.beta2, self.cfg.eps, self.t, self.cfg.train_layer_mask,
+                                            self.activity, _stream_handle(None))
+                self.activity_samples += 1
+        if self.cfg.activity_prune and self.activity_samples == self.cfg.activity_interval:
+            self.activity_prune()
         return loss.detach()
 
-    def prune(self) -> int:
-        """Applies the contribution prune; returns the number of Gaussians kept."""
-        keep, keep_index, n_keep = contrib_prune(self.contrib_max, self.cfg.prune_threshold)
-        n = int(n_keep.item())
+    def _apply_keep(self, keep_index, n: int):
         idx = keep_index[:n]
         with torch.no_grad():
             sub = self.scene.subset(idx)
             self.m = [gather_rows(a, idx) for a in self.m]
             self.v = [gather_rows(a, idx) for a in self.v]
+            self.contrib_max = gather_rows(self.contrib_max, idx)
+            self.contrib_sum = gather_rows(self.contrib_sum, idx)
+            self.activity = gather_rows(self.activity, idx)
         self.scene = sub
         for p in sub.params():
             p.requires_grad_(True)
-        self.contrib_max = torch.zeros(n, device=self.device)
-        self.contrib_sum = torch.zeros(n, device=self.device)
+
+    def activity_prune(self) -> int:
+        """Inactive pruning (Sec. 3.2.2): removes the trainable Gaussians whose
+        average activity over the samples since the last decision is at or
+        below the threshold, then decays the threshold and restarts the
+        average.  Returns the number kept."""
+        sc = self.scene
+        keep = torch.empty(sc.n, dtype=torch.uint8, device=self.device)
+        keep_index = torch.empty(sc.n, dtype=torch.int32, device=self.device)
+        n_keep = torch.empty(1, dtype=torch.int64, device=self.device)
+        wsb = _lib.gs_prune_workspace_size(sc.n)
+        ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=self.device)
+        _lib.gs_activity_prune(self.activity, sc.layer, sc.n, self.cfg.train_layer_mask, self.activity_samples,
+                               self.activity_threshold, keep, keep_index, n_keep, ws, wsb, _stream_handle(None))
+        n = int(n_keep.item())
+        self.activity_removed += sc.n - n
+        if n < sc.n:
+            self._apply_keep(keep_index, n)
+        self.activity.zero_()
+        self.activity_samples = 0
+        self.activity_threshold *= self.cfg.activity_decay
+        return n
+
+    def prune(self) -> int:
+        """Applies the contribution prune; returns the number of Gaussians kept."""
+        keep, keep_index, n_keep = contrib_prune(self.contrib_max, self.cfg.prune_threshold)
+        n = int(n_keep.item())
+        self._apply_keep(keep_index, n)
+        self.contrib_max.zero_()
+        self.contrib_sum.zero_()
         return n

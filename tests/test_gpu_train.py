@@ -192,3 +192,75 @@ def test_training_prune_compacts_parameters_and_moments():
     for a, b in zip(tr.m, moments):
         assert np.array_equal(a.cpu().numpy(), b[keep_ref.astype(bool)])
     assert tr.scene.n == n and tr.contrib_max.shape[0] == n
+
+
+def test_activity_accumulate_and_prune_match_oracle():
+    """Activity of three Adam steps (frozen layer 0) against the oracle's norms
+    of its own updates; the prune decision bit-exact on the GPU's activity."""
+    rng = np.random.default_rng(8)
+    n, K = 257, 16
+    shapes = [(n, 3), (n, 3), (n, 4), (n,), (n, K, 3)]
+    p0 = [rng.standard_normal(s).astype(np.float32) for s in shapes]
+    layer = rng.integers(0, 3, n).astype(np.uint8)
+    mask = 0b110
+    lr = (1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3)
+    P = [torch.from_numpy(a.copy()).cuda() for a in p0]
+    M = [torch.zeros_like(a) for a in P]
+    V = [torch.zeros_like(a) for a in P]
+    L = torch.from_numpy(layer).cuda()
+    sc = DeviceScene(*P, L, 3)
+    act = torch.zeros(n, device="cuda")
+    ref = [(a.astype(np.float64), np.zeros(a.shape), np.zeros(a.shape)) for a in p0]
+    ref_act = np.zeros(n)
+    frozen = ((mask >> layer.astype(np.int64)) & 1) == 0
+    for t in range(1, 4):
+        gr = [rng.standard_normal(s).astype(np.float32) for s in shapes]
+        G = [torch.from_numpy(a).cuda() for a in gr]
+        g = _lib.gs_grads()
+        g.means, g.log_scales, g.quats, g.opacity_logit, g.sh = (x.data_ptr() for x in G)
+        st = _lib.gs_adam_state()
+        for k in range(5):
+            st.m[k], st.v[k] = M[k].data_ptr(), V[k].data_ptr()
+        _lib.gs_adam_step(sc.c_struct(), g, st, lr, 0.9, 0.999, 1e-15, t, mask, 0)
+        _lib.gs_activity_accumulate(st, L, n, 3, lr, 0.9, 0.999, 1e-15, t, mask, act, 0)
+        new = [OT.adam_step(r[0], gr[k], r[1], r[2], t, lr[k], frozen_rows=frozen) for k, r in enumerate(ref)]
+        d = [new[k][0] - ref[k][0] for k in range(5)]
+        ref_act += OT.activity_sample(d[0], d[4], d[1])
+        ref = new
+    torch.cuda.synchronize()
+    a = act.cpu().numpy().astype(np.float64)
+    assert np.all(a[frozen] == 0.0)
+    assert np.abs(a - ref_act).max() <= 1e-5 * np.abs(ref_act).max()
+    # decision on the GPU's own activity (two samples: act * 0.5 is exact in
+    # both precisions), threshold inside its range
+    thr = float(np.float32(np.median(a[~frozen]) / 2.0))
+    keep = torch.empty(n, dtype=torch.uint8, device="cuda")
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    nk = torch.empty(1, dtype=torch.int64, device="cuda")
+    wsb = _lib.gs_prune_workspace_size(n)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    _lib.gs_activity_prune(act, L, n, mask, 2.0, thr, keep, idx, nk, ws, wsb, 0)
+    torch.cuda.synchronize()
+    want = OT.activity_prune(a, 2, thr, ~frozen)
+    got = keep.cpu().numpy().astype(bool)
+    assert np.array_equal(got, want)
+    k = int(nk.item())
+    assert k == int(want.sum()) and np.array_equal(idx.cpu().numpy()[:k], np.nonzero(want)[0])
+
+
+def test_trainer_activity_prune_keeps_frozen_layers():
+    sc, cams = _small_training_case()
+    ds = DeviceScene.from_host(sc)
+    cfg = TrainConfig(train_layer_mask=0b10, activity_prune=True, activity_interval=3, activity_threshold=1e9)
+    tr = Trainer(ds, cams, cfg)
+    rng = np.random.default_rng(4)
+    n_frozen = int((sc.layer == 0).sum())
+    for v in range(3):
+        tr.step(v % 2, torch.from_numpy(rng.random((3, 56, 72)).astype(np.float32) * 0.5).cuda(),
+                torch.full((56, 72), 0.5, device="cuda"), (0.3, 0.3, 0.3))
+    torch.cuda.synchronize()
+    # a huge threshold removes every trainable Gaussian and no frozen one
+    assert tr.scene.n == n_frozen and tr.activity_removed == sc.n - n_frozen
+    assert np.all(tr.scene.layer.cpu().numpy() == 0)
+    assert tr.activity_samples == 0 and abs(tr.activity_threshold - 1e9 * 0.975) < 1e3
+    assert tr.m[0].shape[0] == n_frozen and tr.contrib_max.shape[0] == n_frozen
