@@ -43,7 +43,7 @@ enum {
     GS_ERR_OOM = 5         /* an admission/memory budget was exceeded */
 };
 
-enum { GS_DTYPE_F32 = 0, GS_DTYPE_F16 = 1, GS_DTYPE_BF16 = 2 };
+enum { GS_DTYPE_F32 = 0, GS_DTYPE_F16 = 1, GS_DTYPE_BF16 = 2, GS_DTYPE_SH_CODEBOOK = 3 };
 
 #define GS_TILE 16          /* tile edge in pixels */
 #define GS_MAX_PLANES 8     /* clip planes per call */
@@ -80,7 +80,12 @@ typedef struct gs_clip_plane {
  *   sh             [N][K][3] dtype_sh, K = (sh_degree+1)^2, real SH with the
  *                  Condon-Shortley phase, index k = l*l + l + m
  *   layer          uint8 [N], values 0..31
- * Every pointer must be 16-byte aligned.                                     */
+ * With dtype_sh = GS_DTYPE_SH_CODEBOOK (Sec. 3.3: K-means clustering of the
+ * SH coefficients; render only, sh_degree >= 1): sh is the DC coefficient
+ * float32 [N][3]; sh_index uint16 [N] selects a row of sh_table, FP16
+ * [sh_table_rows][R] with R = 3(K-1) rounded up to a multiple of 8 (the
+ * coefficients k = 1..K-1, channel fastest, then zero padding).  Both fields
+ * are ignored for the other dtypes.  Every pointer must be 16-byte aligned. */
 typedef struct gs_scene {
     const void *means;
     const void *log_scales;
@@ -91,8 +96,10 @@ typedef struct gs_scene {
     int64_t n;
     int32_t sh_degree;      /* 0..3 */
     int32_t dtype_sh;       /* GS_DTYPE_* */
-    int32_t dtype_scale_rot;/* GS_DTYPE_* */
-    int32_t _reserved;
+    int32_t dtype_scale_rot;/* GS_DTYPE_F32 / F16 / BF16 */
+    int32_t sh_table_rows;  /* codebook rows (1..65536), GS_DTYPE_SH_CODEBOOK only */
+    const uint16_t *sh_index;
+    const void *sh_table;
 } gs_scene;
 
 /* Gradient outputs (device, float32, same shapes as the scene fields).  Every
@@ -265,6 +272,24 @@ int gs_activity_accumulate(const gs_adam_state *state, const uint8_t *layer, int
 int gs_activity_prune(const float *activity, const uint8_t *layer, int64_t n, uint32_t train_layer_mask,
                       float samples, float threshold, uint8_t *keep, int32_t *keep_index, int64_t *n_keep,
                       void *workspace, size_t ws_bytes, void *stream);
+
+/* ---- SH codebook construction (Sec. 3.3, K-means; offline, before rendering)
+ * Points are rows of `dim` <= 48 floats, `stride` floats apart (device).
+ * gs_kmeans_assign: assign[i] = argmin_j |x_i - c_j|^2 over the k centroids
+ * (float32 [k][dim], device), ties to the lower index.
+ * gs_kmeans_update: every centroid with at least one assigned point becomes
+ * their mean; scratch: gs_kmeans_scratch_size bytes (device).
+ * gs_sh_codebook_encode: from a float32 scene's sh [N][K][3] and the final
+ * assignment and centroids (dim = 3(K-1), the coefficients k >= 1): dc
+ * float32 [N][3], index uint16 [N] (k <= 65536), table FP16 [k][R] as
+ * described at gs_scene.  All asynchronous.                                 */
+int gs_kmeans_scratch_size(int32_t k, int32_t dim, size_t *bytes);
+int gs_kmeans_assign(const float *points, int64_t n, int32_t dim, int64_t stride, const float *centroids, int32_t k,
+                     uint32_t *assign, void *stream);
+int gs_kmeans_update(const float *points, int64_t n, int32_t dim, int64_t stride, const uint32_t *assign, int32_t k,
+                     float *centroids, void *scratch, size_t scratch_bytes, void *stream);
+int gs_sh_codebook_encode(const float *sh, int64_t n, int32_t sh_degree, const uint32_t *assign,
+                          const float *centroids, int32_t k, float *dc, uint16_t *index, void *table, void *stream);
 
 /* Row gather for applying a prune: dst row i = src row index[i] for
  * i < n, rows of row_bytes > 0 bytes (2-byte aligned arrays when row_bytes is

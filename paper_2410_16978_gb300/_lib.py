@@ -16,6 +16,7 @@ from . import build as _build
 _P = ctypes.c_void_p
 
 GS_OK, GS_ERR_INVALID, GS_ERR_WORKSPACE, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_OOM = range(6)
+GS_DTYPE_SH_CODEBOOK = 3
 GS_DTYPE_F32, GS_DTYPE_F16, GS_DTYPE_BF16 = 0, 1, 2
 GS_TILE = 16
 GS_MAX_PLANES = 8
@@ -23,7 +24,8 @@ GS_MAX_BATCH = 16
 
 EXPORTED = ("gs_render_workspace_size", "gs_render", "gs_render_batch", "gs_render_stereo", "gs_render_backward", "gs_prune_workspace_size",
             "gs_contrib_prune", "gs_contrib_prune_noalloc", "gs_image_loss_workspace_size", "gs_image_loss",
-            "gs_adam_step", "gs_activity_accumulate", "gs_activity_prune", "gs_gather_rows", "gs_workspace_layout", "gs_read_status", "gs_profile_enable",
+            "gs_adam_step", "gs_activity_accumulate", "gs_activity_prune", "gs_gather_rows", "gs_kmeans_scratch_size",
+            "gs_kmeans_assign", "gs_kmeans_update", "gs_sh_codebook_encode", "gs_workspace_layout", "gs_read_status", "gs_profile_enable",
             "gs_profile_collect", "gs_kernel_launches", "gs_last_error_string", "gs_version")
 STAGES = ("preprocess", "compact", "depth_sort", "bin_rows", "bin_tiles", "composite_setup", "composite",
           "composite_bwd", "preprocess_bwd", "prune", "loss", "adam")
@@ -47,7 +49,8 @@ class gs_clip_plane(ctypes.Structure):
 class gs_scene(ctypes.Structure):
     _fields_ = [("means", _P), ("log_scales", _P), ("quats", _P), ("opacity_logit", _P), ("sh", _P),
                 ("layer", _P), ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32),
-                ("dtype_sh", ctypes.c_int32), ("dtype_scale_rot", ctypes.c_int32), ("_reserved", ctypes.c_int32)]
+                ("dtype_sh", ctypes.c_int32), ("dtype_scale_rot", ctypes.c_int32), ("sh_table_rows", ctypes.c_int32),
+                ("sh_index", _P), ("sh_table", _P)]
 
 
 class gs_grads(ctypes.Structure):
@@ -123,6 +126,11 @@ def load(build_if_missing: bool = True):
                                    ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_int32, ctypes.c_uint32, _P]
         L.gs_gather_rows.argtypes = [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P]
+        L.gs_kmeans_scratch_size.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+        L.gs_kmeans_assign.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P, ctypes.c_int32, _P, _P]
+        L.gs_kmeans_update.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P, ctypes.c_int32, _P, _P,
+                                       ctypes.c_size_t, _P]
+        L.gs_sh_codebook_encode.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, _P, _P]
         L.gs_activity_accumulate.argtypes = [ctypes.POINTER(gs_adam_state), _P, ctypes.c_int64, ctypes.c_int32,
                                              ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float,
                                              ctypes.c_float, ctypes.c_int32, ctypes.c_uint32, _P, _P]
@@ -297,6 +305,29 @@ def gs_activity_prune(activity, layer, n: int, train_layer_mask: int, samples: f
     _check(load().gs_activity_prune(_ptr(activity), _ptr(layer), int(n), int(train_layer_mask) & 0xFFFFFFFF,
                                     float(samples), float(threshold), _ptr(keep), _ptr(keep_index), _ptr(n_keep),
                                     _ptr(workspace), int(ws_bytes), ctypes.c_void_p(stream)))
+
+
+def gs_kmeans_scratch_size(k: int, dim: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().gs_kmeans_scratch_size(int(k), int(dim), ctypes.byref(out)))
+    return int(out.value)
+
+
+def gs_kmeans_assign(points, n: int, dim: int, stride: int, centroids, k: int, assign, stream: int) -> None:
+    _check(load().gs_kmeans_assign(_ptr(points), int(n), int(dim), int(stride), _ptr(centroids), int(k), _ptr(assign),
+                                   ctypes.c_void_p(stream)))
+
+
+def gs_kmeans_update(points, n: int, dim: int, stride: int, assign, k: int, centroids, scratch, scratch_bytes: int,
+                     stream: int) -> None:
+    _check(load().gs_kmeans_update(_ptr(points), int(n), int(dim), int(stride), _ptr(assign), int(k),
+                                   _ptr(centroids), _ptr(scratch), int(scratch_bytes), ctypes.c_void_p(stream)))
+
+
+def gs_sh_codebook_encode(sh, n: int, sh_degree: int, assign, centroids, k: int, dc, index, table,
+                          stream: int) -> None:
+    _check(load().gs_sh_codebook_encode(_ptr(sh), int(n), int(sh_degree), _ptr(assign), _ptr(centroids), int(k),
+                                        _ptr(dc), _ptr(index), _ptr(table), ctypes.c_void_p(stream)))
 
 
 def gs_gather_rows(src, dst, row_bytes: int, index, n: int, stream: int) -> None:

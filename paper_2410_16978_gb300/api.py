@@ -14,7 +14,7 @@ import torch
 from . import _lib
 
 _DT = {"f32": (_lib.GS_DTYPE_F32, torch.float32), "f16": (_lib.GS_DTYPE_F16, torch.float16),
-       "bf16": (_lib.GS_DTYPE_BF16, torch.bfloat16)}
+       "bf16": (_lib.GS_DTYPE_BF16, torch.bfloat16), "cb": (_lib.GS_DTYPE_SH_CODEBOOK, torch.float32)}
 
 
 def _require_cuda(t: torch.Tensor, name: str):
@@ -32,7 +32,7 @@ class DeviceScene:
     """
 
     def __init__(self, means, log_scales, quats, opacity_logit, sh, layer, sh_degree: int,
-                 sh_dtype: str = "f32", sr_dtype: str = "f32"):
+                 sh_dtype: str = "f32", sr_dtype: str = "f32", sh_index=None, sh_table=None):
         self.means = means
         self.log_scales = log_scales
         self.quats = quats
@@ -42,7 +42,14 @@ class DeviceScene:
         self.sh_degree = int(sh_degree)
         self.sh_dtype = sh_dtype
         self.sr_dtype = sr_dtype
-        for name in ("means", "log_scales", "quats", "opacity_logit", "sh", "layer"):
+        self.sh_index = sh_index      # codebook storage ("cb"): uint16 [N]
+        self.sh_table = sh_table      # codebook storage: float16 [rows][R]
+        names = ["means", "log_scales", "quats", "opacity_logit", "sh", "layer"]
+        if sh_dtype == "cb":
+            if sh_index is None or sh_table is None:
+                raise ValueError("codebook storage needs sh_index and sh_table")
+            names += ["sh_index", "sh_table"]
+        for name in names:
             _require_cuda(getattr(self, name), name)
 
     @classmethod
@@ -79,6 +86,10 @@ class DeviceScene:
         s.sh_degree = self.sh_degree
         s.dtype_sh = _DT[self.sh_dtype][0]
         s.dtype_scale_rot = _DT[self.sr_dtype][0]
+        if self.sh_dtype == "cb":
+            s.sh_index = self.sh_index.data_ptr()
+            s.sh_table = self.sh_table.data_ptr()
+            s.sh_table_rows = int(self.sh_table.shape[0])
         return s
 
     def subset(self, keep_index: torch.Tensor, stream=None) -> "DeviceScene":

@@ -23,7 +23,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
 # Translation units whose arithmetic must not be contracted into FMAs: the
 # preprocess evaluates its integer decisions in a fixed single-precision order.
 PER_FILE = {"preprocess.cu": ["-fmad=false"]}
-SOURCES = ["gs_api.cu", "preprocess.cu", "preprocess_bwd.cu", "sort.cu", "bin.cu", "composite.cu", "train.cu", "noalloc.cu"]
+SOURCES = ["gs_api.cu", "preprocess.cu", "preprocess_bwd.cu", "sort.cu", "bin.cu", "composite.cu", "train.cu", "codebook.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

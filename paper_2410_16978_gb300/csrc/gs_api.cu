@@ -134,9 +134,16 @@ int check_scene(const gs_scene *s, SceneView *v) {
     if (!s) return fail(GS_ERR_INVALID, "scene is NULL");
     if (s->n < 0 || s->n > 0x7FFFFFFF) return fail(GS_ERR_INVALID, "scene n out of range: %lld", (long long)s->n);
     if (s->sh_degree < 0 || s->sh_degree > 3) return fail(GS_ERR_INVALID, "sh_degree must be 0..3");
-    for (int dt : {s->dtype_sh, s->dtype_scale_rot})
-        if (dt != GS_DTYPE_F32 && dt != GS_DTYPE_F16 && dt != GS_DTYPE_BF16)
-            return fail(GS_ERR_INVALID, "unknown dtype %d", dt);
+    if (s->dtype_scale_rot != GS_DTYPE_F32 && s->dtype_scale_rot != GS_DTYPE_F16 && s->dtype_scale_rot != GS_DTYPE_BF16)
+        return fail(GS_ERR_INVALID, "unknown dtype %d", s->dtype_scale_rot);
+    if (s->dtype_sh != GS_DTYPE_F32 && s->dtype_sh != GS_DTYPE_F16 && s->dtype_sh != GS_DTYPE_BF16 &&
+        s->dtype_sh != GS_DTYPE_SH_CODEBOOK)
+        return fail(GS_ERR_INVALID, "unknown dtype %d", s->dtype_sh);
+    const bool cb = s->dtype_sh == GS_DTYPE_SH_CODEBOOK;
+    if (cb && (s->sh_degree < 1 || s->sh_table_rows < 1 || s->sh_table_rows > 65536))
+        return fail(GS_ERR_INVALID, "codebook SH needs sh_degree >= 1 and 1..65536 table rows");
+    if (cb && s->n > 0 && (!s->sh_index || !s->sh_table || !aligned(s->sh_index, 16) || !aligned(s->sh_table, 16)))
+        return fail(GS_ERR_INVALID, "codebook index and table must be set and 16-byte aligned");
     if (s->n > 0) {
         const void *ptrs[6] = {s->means, s->log_scales, s->quats, s->opacity_logit, s->sh, s->layer};
         for (const void *p : ptrs)
@@ -154,6 +161,9 @@ int check_scene(const gs_scene *s, SceneView *v) {
     v->sh_degree = s->sh_degree;
     v->dtype_sh = s->dtype_sh;
     v->dtype_sr = s->dtype_scale_rot;
+    v->sh_index = cb ? s->sh_index : nullptr;
+    v->sh_table = cb ? s->sh_table : nullptr;
+    v->sh_table_rows = cb ? s->sh_table_rows : 0;
     return GS_OK;
 }
 
@@ -460,6 +470,7 @@ int gs_render_backward(const gs_scene *scene, const gs_camera *camera, const flo
     int rc;
     if ((rc = check_scene(scene, &sv)) != GS_OK) return rc;
     if ((rc = check_camera(camera, &cv)) != GS_OK) return rc;
+    if (sv.dtype_sh == GS_DTYPE_SH_CODEBOOK) return fail(GS_ERR_INVALID, "codebook SH is render only");
     if (!bg) return fail(GS_ERR_INVALID, "bg is NULL");
     if (!grads || (sv.n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logit ||
                                 !grads->sh)))
@@ -645,6 +656,48 @@ int gs_activity_prune(const float *activity, const uint8_t *layer, int64_t n, ui
     return cuda_check(launch_activity_prune(activity, layer, train_layer_mask, static_cast<int>(n), samples, threshold,
                                             keep, keep_index, n_keep, static_cast<uint32_t *>(workspace), st),
                       "activity prune");
+}
+
+int gs_kmeans_scratch_size(int32_t k, int32_t dim, size_t *bytes) {
+    if (!bytes) return fail(GS_ERR_INVALID, "bytes is NULL");
+    if (k < 1 || dim < 1 || dim > kCbMaxDim) return fail(GS_ERR_INVALID, "k >= 1 and 1 <= dim <= %d", kCbMaxDim);
+    *bytes = static_cast<size_t>(k) * (dim + 1) * sizeof(float);
+    return GS_OK;
+}
+
+int gs_kmeans_assign(const float *points, int64_t n, int32_t dim, int64_t stride, const float *centroids, int32_t k,
+                     uint32_t *assign, void *stream) {
+    if (n < 0 || k < 1 || dim < 1 || dim > kCbMaxDim || stride < dim)
+        return fail(GS_ERR_INVALID, "bad sizes (n %lld, k %d, dim %d, stride %lld)", (long long)n, k, dim,
+                    (long long)stride);
+    if (n > 0 && (!points || !centroids || !assign)) return fail(GS_ERR_INVALID, "NULL argument");
+    return cuda_check(launch_kmeans_assign(points, n, dim, stride, centroids, k, assign,
+                                           static_cast<cudaStream_t>(stream)),
+                      "kmeans assign");
+}
+
+int gs_kmeans_update(const float *points, int64_t n, int32_t dim, int64_t stride, const uint32_t *assign, int32_t k,
+                     float *centroids, void *scratch, size_t scratch_bytes, void *stream) {
+    size_t need = 0;
+    int rc = gs_kmeans_scratch_size(k, dim, &need);
+    if (rc != GS_OK) return rc;
+    if (n < 0 || stride < dim) return fail(GS_ERR_INVALID, "bad sizes");
+    if (!centroids || !scratch || (n > 0 && (!points || !assign))) return fail(GS_ERR_INVALID, "NULL argument");
+    if (scratch_bytes < need) return fail(GS_ERR_WORKSPACE, "k-means scratch needs %zu bytes", need);
+    return cuda_check(launch_kmeans_update(points, n, dim, stride, assign, k, centroids, static_cast<float *>(scratch),
+                                           static_cast<cudaStream_t>(stream)),
+                      "kmeans update");
+}
+
+int gs_sh_codebook_encode(const float *sh, int64_t n, int32_t sh_degree, const uint32_t *assign,
+                          const float *centroids, int32_t k, float *dc, uint16_t *index, void *table, void *stream) {
+    if (n < 0 || sh_degree < 1 || sh_degree > 3 || k < 1 || k > 65536)
+        return fail(GS_ERR_INVALID, "bad sizes (n %lld, degree %d, k %d)", (long long)n, sh_degree, k);
+    if (!centroids || !table || (n > 0 && (!sh || !assign || !dc || !index))) return fail(GS_ERR_INVALID, "NULL argument");
+    const int K = (sh_degree + 1) * (sh_degree + 1);
+    return cuda_check(launch_sh_encode(sh, n, K, assign, centroids, k, dc, index, table,
+                                       static_cast<cudaStream_t>(stream)),
+                      "sh codebook encode");
 }
 
 int gs_gather_rows(const void *src, void *dst, int64_t row_bytes, const int32_t *index, int64_t n, void *stream) {

@@ -20,6 +20,7 @@ constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 0x1.010102p-8f;    // 1/255 rounded to float
 constexpr float kTMin = 1e-4f;
 constexpr uint32_t kSeg = 256;                 // list positions per backward segment (checkpoint stride)
+constexpr int kCbMaxDim = 48;                  // SH codebook: coordinates per row, 3(K-1) <= 45 padded
 constexpr int kBinMaxDim = 256;                // tile rows and columns the binning handles (4096 px)
 constexpr int kBinBlocks = 1024;               // CTAs (of 8 chunk warps) of the row pass of the binning
 constexpr int kBinChunks = kBinBlocks * 8;     // chunks of the depth order in the row pass
@@ -69,7 +70,13 @@ int64_t capacity_for(int64_t n, int W, int H, size_t ws_bytes);
 template <typename T>
 inline T *at(void *base, size_t off) { return reinterpret_cast<T *>(static_cast<char *>(base) + off); }
 
+// Halves per row of an SH codebook table: 3(K-1) rounded up to 8 (16-byte rows).
+__host__ __device__ constexpr int cb_row_halves(int K) { return (3 * (K - 1) + 7) / 8 * 8; }
+
 struct SceneView {
+    const uint16_t *sh_index;   // codebook storage: index per Gaussian
+    const void *sh_table;       // codebook storage: FP16 rows of cb_row_halves(K)
+    int sh_table_rows;
     const float *means;
     const void *log_scales;
     const void *quats;
@@ -153,6 +160,13 @@ cudaError_t launch_activity(const float *const m[3], const float *const v[3], in
 cudaError_t launch_activity_prune(const float *activity, const uint8_t *layer, uint32_t train_mask, int n,
                                   float samples, float thr, uint8_t *keep, int32_t *keep_index, int64_t *n_keep,
                                   uint32_t *partials, cudaStream_t st);
+// SH codebook (codebook.cu).
+cudaError_t launch_kmeans_assign(const float *pts, int64_t n, int dim, int64_t stride, const float *cent, int k,
+                                 uint32_t *assign, cudaStream_t st);
+cudaError_t launch_kmeans_update(const float *pts, int64_t n, int dim, int64_t stride, const uint32_t *assign, int k,
+                                 float *cent, float *scratch, cudaStream_t st);
+cudaError_t launch_sh_encode(const float *sh, int64_t n, int K, const uint32_t *assign, const float *cent, int k,
+                             float *dc, uint16_t *index, void *table, cudaStream_t st);
 cudaError_t launch_prune(const float *contrib_max, int n, float thr, uint8_t *keep, int32_t *keep_index,
                          int64_t *n_keep, uint32_t *partials, cudaStream_t st);
 

@@ -167,7 +167,26 @@ __global__ void __launch_bounds__(128) k_preprocess(SceneView s, CamView c, uint
                 sh_basis<DEG>(dx / dn, dy / dn, dz / dn, b);
                 const int64_t base = static_cast<int64_t>(i) * K * 3;
                 float shv[3 * K];
-                if (s.dtype_sh == GS_DTYPE_F32 && (3 * K) % 4 == 0) {
+                if (s.dtype_sh == GS_DTYPE_SH_CODEBOOK) {
+                    // DC per Gaussian; coefficients k >= 1 from the FP16 table row (16-byte loads from L2)
+                    const float *dcp = static_cast<const float *>(s.sh) + static_cast<int64_t>(i) * 3;
+                    shv[0] = dcp[0]; shv[1] = dcp[1]; shv[2] = dcp[2];
+                    constexpr int ROW = cb_row_halves(K);
+                    const uint4 *row = reinterpret_cast<const uint4 *>(static_cast<const __half *>(s.sh_table) +
+                                                                       static_cast<int64_t>(s.sh_index[i]) * ROW);
+#pragma unroll
+                    for (int q = 0; q < ROW / 8; ++q) {
+                        const uint4 v = row[q];
+                        const __half2 *h = reinterpret_cast<const __half2 *>(&v);
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const float2 f = __half22float2(h[r]);
+                            const int d0 = 8 * q + 2 * r;
+                            if (d0 < 3 * (K - 1)) shv[3 + d0] = f.x;
+                            if (d0 + 1 < 3 * (K - 1)) shv[3 + d0 + 1] = f.y;
+                        }
+                    }
+                } else if (s.dtype_sh == GS_DTYPE_F32 && (3 * K) % 4 == 0) {
                     // 16-byte loads of this Gaussian's coefficients (its row starts 16-byte aligned)
                     const float4 *src = reinterpret_cast<const float4 *>(static_cast<const float *>(s.sh) + base);
 #pragma unroll
