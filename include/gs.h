@@ -119,8 +119,7 @@ typedef struct gs_status {
     uint32_t n_visible;     /* Gaussians that survived every cull */
     uint64_t n_dup;         /* (tile, Gaussian) pairs the frame needs */
     uint64_t dup_capacity;  /* pairs the workspace can hold */
-    uint32_t max_tile_list; /* reserved */
-    uint32_t _reserved;
+    uint64_t n_blended;     /* (pixel, Gaussian) pairs blended by the last forward composite */
 } gs_status;
 
 /* Bytes of workspace for rendering n Gaussians at width x height with room for

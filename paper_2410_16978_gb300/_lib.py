@@ -70,8 +70,7 @@ class gs_adam_state(ctypes.Structure):
 
 class gs_status(ctypes.Structure):
     _fields_ = [("error", ctypes.c_int32), ("n_visible", ctypes.c_uint32), ("n_dup", ctypes.c_uint64),
-                ("dup_capacity", ctypes.c_uint64), ("max_tile_list", ctypes.c_uint32),
-                ("_reserved", ctypes.c_uint32)]
+                ("dup_capacity", ctypes.c_uint64), ("n_blended", ctypes.c_uint64)]
 
 
 class GsError(RuntimeError):

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_cons
         const float px = x + 0.5f, py = y + 0.5f;
         const float bx0 = (tile % Tx) * kTile + (sub & 1) * 8 + 0.5f, by0 = (tile / Tx) * kTile + (sub >> 1) * 4 + 0.5f;
         float T = 1.f, D0 = 0.f, D1 = 0.f, D2 = 0.f;     // D: colour blended in the current segment
-        uint32_t last = 0, sd = 0;
+        uint32_t last = 0, sd = 0, nb = 0;
         bool done = !inside;
         float4 *my_ckpt = J.ckpt + static_cast<size_t>(J.seg_base[tile]) * kTilePix + ly * kTile + lx;
         Chunk nxt;
@@ -271,6 +271,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_cons
                 D2 = __fmaf_rn(s_c[warp][k], w, D2);
                 T = Tnew;
                 last = s_pos[warp][k] + 1;
+                ++nb;
             }
         }
         // Checkpoint s holds (T at segment start, D of segment s-1) as written
@@ -298,6 +299,8 @@ __global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_cons
         }
         const uint32_t wm = __reduce_max_sync(FULL, last);
         if (lane == 0 && wm) atomicMax(&J.qwork[4 * tile + (sub & 1) + 2 * (sub >> 2)], wm);
+        const uint32_t wb = __reduce_add_sync(FULL, nb);
+        if (lane == 0 && wb) atomicAdd(J.n_blended, static_cast<unsigned long long>(wb));
     }
 }
 

@@ -358,6 +358,7 @@ int front_bin(FrontCtx &f, const uint32_t *order, cudaStream_t st, FwdJob *job, 
     job->seg_base = cb.seg_base;
     job->ckpt = cb.ckpt;
     job->qwork = cb.qwork;
+    job->n_blended = reinterpret_cast<unsigned long long *>(&f.ctl->st.n_blended);
     job->W = f.cv.W;
     job->H = f.cv.H;
     job->Tx = f.cv.Tx;

@@ -194,6 +194,7 @@ struct FwdJob {
     const uint32_t *seg_base;
     float4 *ckpt;
     uint32_t *qwork;
+    unsigned long long *n_blended;   // the view's status word: blended pairs
     int W, H, Tx, Tn;
     float3 bg;
     uint32_t item_begin;   // first global work item of this view (filled by the launcher)

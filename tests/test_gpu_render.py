@@ -222,3 +222,27 @@ def test_render_batch_limits_and_overflow_isolation():
     assert r_small.status().error == _lib.GS_ERR_WORKSPACE
     assert r_ok.status().error == 0
     assert torch.equal(its[1]["image"], ref_img)
+
+
+def test_blended_pair_count():
+    """The status word's blended-pair count equals the number of (pixel,
+    Gaussian) pairs the oracle blends (up to one per fragile pixel)."""
+    sc, cam, mask, planes, bg = WL["shells_ragged"]
+    _, rast, img, al = gpu_render(sc, cam, mask, planes, bg)
+    st = rast.status()
+    pre, ranges, lst, co = oracle_stage(sc, cam, mask, planes, bg)
+    W, H = cam.width, cam.height
+    Tx = (W + 15) // 16
+    count = 0
+    for y in range(H):
+        for x in range(W):
+            t = (y // 16) * Tx + x // 16
+            ids = lst[ranges[t, 0]:ranges[t, 0] + co["ncontrib"][y, x]]
+            if ids.size == 0:
+                continue
+            dx = x + 0.5 - pre["u"][ids]
+            dy = y + 0.5 - pre["v"][ids]
+            p = dx + pre["beta"][ids] * dy
+            a = np.minimum(0.99, pre["opac"][ids] * np.exp2(pre["A2"][ids] * p * p + pre["G2"][ids] * dy * dy))
+            count += int((a >= 1.0 / 255.0).sum())
+    assert abs(int(st.n_blended) - count) <= int((co["fragile"] > 0).sum()), (st.n_blended, count)
