@@ -33,6 +33,9 @@ namespace {
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr float kLn2 = 0x1.62e430p-1f;
 constexpr int kFwdThreads = 256;
+// Forward pixels per lane: 1 (an 8x4 block per warp) or 2 (8x8).  2 gives each lane two blend chains but culls
+// on a larger block and needs 70 registers; on the 1.2M-Gaussian frame it measured 0.28 ms against 0.22 ms.
+constexpr int kFwdPx = 1;
 constexpr int kBwdThreads = 128;
 // Backward pixels per lane: 2 (an 8x8 block per warp) or 4 (16x8).  4 halves the per-splat reduction and
 // atomics per pixel but needs 96 registers (5 blocks per SM instead of 7) and culls on a coarser block;
@@ -201,11 +204,13 @@ struct FwdBatch {
     uint32_t total;
 };
 
+template <int PX>
 __global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_constant__ FwdBatch batch,
                                                                uint32_t *__restrict__ queue) {
     __shared__ float4 s_a[kFwdThreads / 32][32], s_b[kFwdThreads / 32][32];
     __shared__ float s_c[kFwdThreads / 32][32];
     __shared__ uint32_t s_pos[kFwdThreads / 32][32];
+    constexpr int NB = 8 / PX;                          // blocks per tile: 8x4 (PX = 1) or 8x8 (PX = 2)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     for (;;) {
@@ -220,31 +225,49 @@ __global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_cons
         const int Tx = J.Tx, W = J.W, H = J.H;
         const uint32_t *__restrict__ list = J.list;
         const Rec *__restrict__ rec = J.rec;
-        const int tile = J.order[local >> 3];
-        const int sub = local & 7;                      // 8x4 block: column sub & 1, row sub >> 1
+        const int tile = J.order[local / NB];
+        const int sub = local % NB;                     // block column sub & 1, block row sub >> 1
+        const int ox = (sub & 1) * 8, oy = (sub >> 1) * 4 * PX;
         const uint2 rg = J.ranges[tile];
-        const int lx = (sub & 1) * 8 + (lane & 7), ly = (sub >> 1) * 4 + (lane >> 3);
-        const int x = (tile % Tx) * kTile + lx;
-        const int y = (tile / Tx) * kTile + ly;
-        const bool inside = x < W && y < H;
-        const float px = x + 0.5f, py = y + 0.5f;
-        const float bx0 = (tile % Tx) * kTile + (sub & 1) * 8 + 0.5f, by0 = (tile / Tx) * kTile + (sub >> 1) * 4 + 0.5f;
-        float T = 1.f, D0 = 0.f, D1 = 0.f, D2 = 0.f;     // D: colour blended in the current segment
-        uint32_t last = 0, sd = 0, nb = 0;
-        bool done = !inside;
-        float4 *my_ckpt = J.ckpt + static_cast<size_t>(J.seg_base[tile]) * kTilePix + ly * kTile + lx;
+        const float bx0 = (tile % Tx) * kTile + ox + 0.5f, by0 = (tile / Tx) * kTile + oy + 0.5f;
+        float px[PX], py[PX], T[PX], D0[PX], D1[PX], D2[PX];   // D: colour blended in the current segment
+        uint32_t last[PX];
+        bool done[PX], inside[PX];
+        int lyv[PX];
+        const int lx = ox + (lane & 7);
+#pragma unroll
+        for (int j = 0; j < PX; ++j) {
+            lyv[j] = oy + (lane >> 3) + 4 * j;
+            const int x = (tile % Tx) * kTile + lx, y = (tile / Tx) * kTile + lyv[j];
+            inside[j] = x < W && y < H;
+            px[j] = x + 0.5f;
+            py[j] = y + 0.5f;
+            T[j] = 1.f;
+            D0[j] = D1[j] = D2[j] = 0.f;
+            last[j] = 0;
+            done[j] = !inside[j];
+        }
+        uint32_t sd = 0, nb = 0;
+        float4 *ck0 = J.ckpt + static_cast<size_t>(J.seg_base[tile]) * kTilePix + lx;
         Chunk nxt;
         fetch_chunk(list, rec, rg.x + lane, rg.y, nxt);
         uint32_t gid = rg.x + 32 + lane < rg.y ? list[rg.x + 32 + lane] : 0u;   // ids one chunk ahead
         for (uint32_t base = rg.x; base < rg.y; base += 32) {
-            if (__all_sync(FULL, done)) break;
+            bool mine = true;
+#pragma unroll
+            for (int j = 0; j < PX; ++j) mine = mine && done[j];
+            if (__all_sync(FULL, mine)) break;
             const uint32_t pos0 = base - rg.x;
             if (pos0 != 0 && pos0 % kSeg == 0) {
                 sd = pos0 / kSeg;
-                my_ckpt[static_cast<size_t>(sd) * kTilePix] = make_float4(T, D0, D1, D2);
-                D0 = D1 = D2 = 0.f;
+#pragma unroll
+                for (int j = 0; j < PX; ++j) {
+                    ck0[static_cast<size_t>(sd) * kTilePix + lyv[j] * kTile] = make_float4(T[j], D0[j], D1[j], D2[j]);
+                    D0[j] = D1[j] = D2[j] = 0.f;
+                }
             }
-            const bool keep = base + lane < rg.y && splat_reaches_block(nxt.a, nxt.b, bx0, bx0 + 7.f, by0, by0 + 3.f);
+            const bool keep = base + lane < rg.y &&
+                              splat_reaches_block(nxt.a, nxt.b, bx0, bx0 + 7.f, by0, by0 + (4.f * PX - 1.f));
             const unsigned km = __ballot_sync(FULL, keep);
             __syncwarp();
             if (keep) {
@@ -258,47 +281,64 @@ __global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_cons
             fetch_rec(rec, gid, base + 32 + lane < rg.y, nxt);
             gid = base + 64 + lane < rg.y ? list[base + 64 + lane] : 0u;
             const int cnt = __popc(km);
-            for (int k = 0; k < cnt && !done; ++k) {
+            for (int k = 0; k < cnt && !mine; ++k) {
                 const float4 a = s_a[warp][k], b = s_b[warp][k];
-                float p, dy, ex, ao;
-                const float al = splat_alpha(px, py, a, b, p, dy, ex, ao);
-                if (al < kAlphaMin) continue;
-                const float Tnew = __fmul_rn(T, __fsub_rn(1.f, al));
-                if (Tnew < kTMin) { done = true; break; }
-                const float w = __fmul_rn(al, T);
-                D0 = __fmaf_rn(b.z, w, D0);
-                D1 = __fmaf_rn(b.w, w, D1);
-                D2 = __fmaf_rn(s_c[warp][k], w, D2);
-                T = Tnew;
-                last = s_pos[warp][k] + 1;
-                ++nb;
+                mine = true;
+#pragma unroll
+                for (int j = 0; j < PX; ++j) {
+                    if (!done[j]) {
+                        float p, dy, ex, ao;
+                        const float al = splat_alpha(px[j], py[j], a, b, p, dy, ex, ao);
+                        if (al >= kAlphaMin) {
+                            const float Tnew = __fmul_rn(T[j], __fsub_rn(1.f, al));
+                            if (Tnew < kTMin) {
+                                done[j] = true;
+                            } else {
+                                const float w = __fmul_rn(al, T[j]);
+                                D0[j] = __fmaf_rn(b.z, w, D0[j]);
+                                D1[j] = __fmaf_rn(b.w, w, D1[j]);
+                                D2[j] = __fmaf_rn(s_c[warp][k], w, D2[j]);
+                                T[j] = Tnew;
+                                last[j] = s_pos[warp][k] + 1;
+                                ++nb;
+                            }
+                        }
+                    }
+                    mine = mine && done[j];
+                }
             }
         }
-        // Checkpoint s holds (T at segment start, D of segment s-1) as written
-        // above; rewrite it, deepest segment first, to (T at segment start,
-        // F_s), F_s = colour blended at list positions >= s kSeg.  F_0 is the
-        // pixel's colour sum.
-        float C0 = D0, C1 = D1, C2 = D2;
-        for (uint32_t s = sd; s > 0; --s) {
-            float4 *slot = my_ckpt + static_cast<size_t>(s) * kTilePix;
-            const float4 raw = *slot;
-            *slot = make_float4(raw.x, C0, C1, C2);
-            C0 = __fadd_rn(raw.y, C0);
-            C1 = __fadd_rn(raw.z, C1);
-            C2 = __fadd_rn(raw.w, C2);
+        uint32_t lmax = 0;
+#pragma unroll
+        for (int j = 0; j < PX; ++j) {
+            // Checkpoint s holds (T at segment start, D of segment s-1) as written
+            // above; rewrite it, deepest segment first, to (T at segment start,
+            // F_s), F_s = colour blended at list positions >= s kSeg.  F_0 is the
+            // pixel's colour sum.
+            float C0 = D0[j], C1 = D1[j], C2 = D2[j];
+            for (uint32_t s = sd; s > 0; --s) {
+                float4 *slot = ck0 + static_cast<size_t>(s) * kTilePix + lyv[j] * kTile;
+                const float4 raw = *slot;
+                *slot = make_float4(raw.x, C0, C1, C2);
+                C0 = __fadd_rn(raw.y, C0);
+                C1 = __fadd_rn(raw.z, C1);
+                C2 = __fadd_rn(raw.w, C2);
+            }
+            if (inside[j]) {
+                const int x = (tile % Tx) * kTile + lx, y = (tile / Tx) * kTile + lyv[j];
+                const size_t plane = static_cast<size_t>(W) * H;
+                const size_t pix = static_cast<size_t>(y) * W + x;
+                J.image[pix] = __fmaf_rn(T[j], J.bg.x, C0);
+                J.image[plane + pix] = __fmaf_rn(T[j], J.bg.y, C1);
+                J.image[2 * plane + pix] = __fmaf_rn(T[j], J.bg.z, C2);
+                if (J.alpha) J.alpha[pix] = 1.f - T[j];
+                J.t_final[pix] = T[j];
+                J.n_contrib[pix] = last[j];
+            }
+            lmax = max(lmax, last[j]);
         }
-        if (inside) {
-            const size_t plane = static_cast<size_t>(W) * H;
-            const size_t pix = static_cast<size_t>(y) * W + x;
-            J.image[pix] = __fmaf_rn(T, J.bg.x, C0);
-            J.image[plane + pix] = __fmaf_rn(T, J.bg.y, C1);
-            J.image[2 * plane + pix] = __fmaf_rn(T, J.bg.z, C2);
-            if (J.alpha) J.alpha[pix] = 1.f - T;
-            J.t_final[pix] = T;
-            J.n_contrib[pix] = last;
-        }
-        const uint32_t wm = __reduce_max_sync(FULL, last);
-        if (lane == 0 && wm) atomicMax(&J.qwork[4 * tile + (sub & 1) + 2 * (sub >> 2)], wm);
+        const uint32_t wm = __reduce_max_sync(FULL, lmax);
+        if (lane == 0 && wm) atomicMax(&J.qwork[4 * tile + (sub & 1) + 2 * ((oy) >> 3)], wm);
         const uint32_t wb = __reduce_add_sync(FULL, nb);
         if (lane == 0 && wb) atomicAdd(J.n_blended, static_cast<unsigned long long>(wb));
     }
@@ -322,7 +362,6 @@ __global__ void __launch_bounds__(1024) k_bwd_setup(const uint32_t *__restrict__
         uint32_t ns[4] = {0, 0, 0, 0};
         if (r < Tn) {
             t = order[r];
-#pragma unroll
             if (PX == 2) {
                 for (int q = 0; q < 4; ++q) ns[q] = ceil_seg(qwork[4 * t + q]);
             } else {
@@ -340,23 +379,48 @@ __global__ void __launch_bounds__(1024) k_bwd_setup(const uint32_t *__restrict__
     if (threadIdx.x == 0) *n_items = carry;
 }
 
-// Reduce-scatter of 16 values across a warp: at step o (16, 8, 4, 2) each
-// lane keeps the half of its values selected by bit o of its lane id and adds
-// its partner's copy of that half; a last exchange at 1 completes the sums.
-// Afterwards lanes 2i and 2i+1 hold the warp sum of value i.
-__device__ __forceinline__ float reduce_scatter16(float v[16], int lane) {
+// Reduce-scatter of 10 values across a warp in 12 shuffles.  Halving by lane
+// bit: bit 4 splits the values 5 / 5, bit 3 splits each half 3 / 2, bit 2
+// splits those 2 / 1 and 1 / 1, bit 1 splits the remaining pair, and bit 0
+// completes the sums.  Lane l ends with the warp sum of value
+// reduce10_owner(l); value i is held by the lanes of one aligned group.
+__device__ __forceinline__ int reduce10_owner(int lane) {
+    const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1, b1 = (lane >> 1) & 1;
+    return 5 * b4 + (b3 ? 3 + b2 : (b2 ? 2 : b1));
+}
+
+// The lowest lane holding each value (lanes 0, 2, 4, 8, 12, 16, 18, 20, 24, 28).
+__device__ __forceinline__ bool reduce10_writer(int lane) {
+    return !(lane & 1) && (((lane & 12) == 0) || !(lane & 2));
+}
+
+__device__ __forceinline__ float reduce_scatter10(const float v[10], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    float a[5];
 #pragma unroll
-    for (int h = 8; h >= 1; h >>= 1) {
-        const int o = 2 * h;                    // xor distance 16, 8, 4, 2
-        const bool hi = lane & o;
-#pragma unroll
-        for (int q = 0; q < h; ++q) {
-            const float send = hi ? v[q] : v[q + h];
-            const float recv = __shfl_xor_sync(FULL, send, o);
-            v[q] = (hi ? v[q + h] : v[q]) + recv;
-        }
+    for (int i = 0; i < 5; ++i) {
+        const float keep = b4 ? v[i + 5] : v[i];
+        const float send = b4 ? v[i] : v[i + 5];
+        a[i] = keep + __shfl_xor_sync(FULL, send, 16);
     }
-    return v[0] + __shfl_xor_sync(FULL, v[0], 1);
+    float c[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float hi = i < 2 ? a[i + 3] : 0.f;
+        const float send = b3 ? a[i] : hi;
+        const float keep = b3 ? hi : a[i];
+        c[i] = keep + __shfl_xor_sync(FULL, send, 8);
+    }
+    const float s0 = b3 ? (b2 ? c[0] : c[1]) : (b2 ? c[0] : c[2]);
+    const float s1 = (!b3 && b2) ? c[1] : 0.f;
+    const float r0 = __shfl_xor_sync(FULL, s0, 4);
+    const float r1 = __shfl_xor_sync(FULL, s1, 4);
+    const float d0 = (b3 ? (b2 ? c[1] : c[0]) : (b2 ? c[2] : c[0])) + r0;
+    const float d1 = c[1] + r1;
+    const bool two = !b3 && !b2;
+    const float s2 = two ? (b1 ? d0 : d1) : d0;
+    const float e = (two ? (b1 ? d1 : d0) : d0) + __shfl_xor_sync(FULL, s2, 2);
+    return e + __shfl_xor_sync(FULL, e, 1);
 }
 
 // Backward, back to front within a segment.  With
@@ -371,11 +435,10 @@ __device__ __forceinline__ float reduce_scatter16(float v[16], int lane) {
 // is at most of the size of T there, so deep splats keep their relative
 // accuracy (a running total minus a prefix would not).
 //
-// Each splat's 10 sums are reduced over the warp and added to the record
-// gradient with vector atomics:
-//   rec_grad[3g]   += (du, dv, dA2, dbeta)
-//   rec_grad[3g+1] += (dG2, dopacity, dr, dg)
-//   rec_grad[3g+2] += (db, sum of alpha*T, 0, 0);  contrib_max[g] = max(.., alpha*T)
+// Each splat's 10 sums are reduce-scattered over the warp and added to the
+// record gradient, float 12 g + i for value i, by ten lanes at once:
+//   (du, dv, dA2, dbeta, dG2, dopacity, dr, dg, db, sum of alpha*T);
+//   contrib_max[g] = max(.., alpha*T)
 template <int PX>
 __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
     const uint2 *__restrict__ items, const uint32_t *__restrict__ n_items, uint32_t *__restrict__ queue,
@@ -390,6 +453,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
     __shared__ uint32_t s_pos[kBwdThreads / 32][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    const int own = reduce10_owner(lane);
+    const bool writer = reduce10_writer(lane);
     const uint32_t total = *n_items;
     const size_t plane = static_cast<size_t>(W) * H;
     for (;;) {
@@ -478,8 +543,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
                     any |= act[j];
                 }
                 if (!__any_sync(FULL, any)) continue;
-                // v: du, dv, dA2, dbeta, dG2, dopacity, dr, dg, db, sum of alpha*T (10..15 unused)
-                float v[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                // v: du, dv, dA2, dbeta, dG2, dopacity, dr, dg, db, sum of alpha*T
+                float v[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 float wmx = 0.f;
 #pragma unroll
                 for (int j = 0; j < PX; ++j) {
@@ -507,18 +572,13 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
                     v[9] += wgt;
                     wmx = fmaxf(wmx, wgt);
                 }
-                const float sv = reduce_scatter16(v, lane);
-                // value i sits in lane 2i: lanes 0, 8, 16 gather (i, i+1, i+2, i+3)
-                const float r1 = __shfl_down_sync(FULL, sv, 2);
-                const float r2 = __shfl_down_sync(FULL, sv, 4);
-                const float r3 = __shfl_down_sync(FULL, sv, 6);
+                const float sv = reduce_scatter10(v, lane);
                 const uint32_t smx = __reduce_max_sync(FULL, __float_as_uint(wmx));
                 const uint32_t g = s_g[warp][k];
                 const bool train = (grad_layer_mask >> layer[g]) & 1u;
-                if (lane == 0 && train) atomicAdd(&rec_grad[3 * g], make_float4(sv, r1, r2, r3));
-                if (lane == 8 && train) atomicAdd(&rec_grad[3 * g + 1], make_float4(sv, r1, r2, r3));
-                if (lane == 16)
-                    atomicAdd(reinterpret_cast<float2 *>(&rec_grad[3 * g + 2]), make_float2(train ? sv : 0.f, r1));
+                // value i is float 12 g + i of the record gradient: one atomic per value, one instruction
+                if (writer && (train || own == 9))
+                    atomicAdd(reinterpret_cast<float *>(rec_grad) + 12 * static_cast<size_t>(g) + own, sv);
                 if (lane == 1 && contrib_max) atomicMax(reinterpret_cast<unsigned int *>(&contrib_max[g]), smx);
             }
         }
@@ -551,15 +611,15 @@ cudaError_t launch_composite_forward(const FwdJob *jobs, int n, uint32_t *queue,
         if (jobs[i].Tn == 0) continue;
         batch.job[batch.n] = jobs[i];
         batch.job[batch.n].item_begin = total;
-        total += static_cast<uint32_t>(jobs[i].Tn) * 8u;
+        total += static_cast<uint32_t>(jobs[i].Tn) * (8u / kFwdPx);
         ++batch.n;
     }
     batch.total = total;
     if (total == 0) return cudaSuccess;
     static int blocks = 0;
-    if (!blocks) blocks = persistent_blocks(k_composite_fwd, kFwdThreads);
+    if (!blocks) blocks = persistent_blocks(k_composite_fwd<kFwdPx>, kFwdThreads);
     const int b = min(blocks, static_cast<int>((total + kFwdThreads / 32 - 1) / (kFwdThreads / 32)));
-    k_composite_fwd<<<b, kFwdThreads, 0, st>>>(batch, queue);
+    k_composite_fwd<kFwdPx><<<b, kFwdThreads, 0, st>>>(batch, queue);
     return cudaGetLastError();
 }
 
