@@ -12,7 +12,7 @@
 //     one list per tile row.  K = gridDim.x * 8 warps each take a contiguous
 //     chunk of the depth order; a first pass counts each chunk's entries per
 //     row in shared memory, an exclusive scan over the chunks of every row
-//     (row-major count matrix [Ty][K]) gives each chunk its place, and a
+//     (row-major count matrices [Ty][K] of entries and of pairs) gives each chunk its place, and a
 //     second pass writes the entries (Gaussian, x0 | x1 << 16) there.  Within
 //     a chunk the entries go out in depth order: a warp expands 32 Gaussians
 //     into their row pairs 32 at a time and ranks equal rows by lane
@@ -113,11 +113,15 @@ __global__ void __launch_bounds__(256) k_bin_rows(const uint32_t *__restrict__ o
     const uint32_t n = min(ctl->n_vis, n_cap);
     const uint32_t b = static_cast<uint32_t>(static_cast<uint64_t>(n) * c / K);
     const uint32_t e = static_cast<uint32_t>(static_cast<uint64_t>(n) * (c + 1) / K);
-    for (int r = lane; r <= Ty; r += 32) {
-        s_cnt[warp][r] = (SCATTER && r < Ty) ? rows[r].start + M[static_cast<size_t>(r) * K + c] : 0u;
-        if (!SCATTER) s_px[warp][r] = 0;
+    // the block's 8 chunks are 8 consecutive columns of the row-major count
+    // matrix: thread t moves (row t / 8, column t % 8), so every row segment
+    // is one 32-byte transaction
+    for (int t = threadIdx.x; t < 8 * (Ty + 1); t += blockDim.x) {
+        const int r = t >> 3, w = t & 7;
+        s_cnt[w][r] = (SCATTER && r < Ty) ? rows[r].start + M[static_cast<size_t>(r) * K + blockIdx.x * 8u + w] : 0u;
+        if (!SCATTER) s_px[w][r] = 0;
     }
-    __syncwarp();
+    __syncthreads();
     for (uint32_t p0 = b; p0 < e; p0 += 32) {
         const uint32_t p = p0 + lane;
         uint32_t g = 0, y0 = 0, x01 = 0, nrows = 0;
@@ -162,26 +166,37 @@ __global__ void __launch_bounds__(256) k_bin_rows(const uint32_t *__restrict__ o
         __syncwarp();
         warp_prefix_inplace(s_cnt[warp], Ty, lane);
         warp_prefix_inplace(s_px[warp], Ty, lane);
-        for (int r = lane; r < Ty; r += 32) {
-            M[static_cast<size_t>(r) * K + c] = s_cnt[warp][r];
-            if (s_px[warp][r]) atomicAdd(&rows[r].pairs, s_px[warp][r]);
+        __syncthreads();
+        // entries and pairs per (row, chunk), written as 32-byte row segments; the
+        // pairs matrix follows the entries matrix and is summed per row by the scan
+        for (int t = threadIdx.x; t < 8 * Ty; t += blockDim.x) {
+            const int r = t >> 3, w = t & 7;
+            const size_t at = static_cast<size_t>(r) * K + blockIdx.x * 8u + w;
+            M[at] = s_cnt[w][r];
+            M[static_cast<size_t>(Ty) * K + at] = s_px[w][r];
         }
     }
 }
 
 // Per row (one CTA each): exclusive scan of the row's K chunk counts in place.
-__global__ void __launch_bounds__(1024) k_bin_rowscan(uint32_t *__restrict__ M, int K, RowInfo *__restrict__ rows) {
+__global__ void __launch_bounds__(1024) k_bin_rowscan(uint32_t *__restrict__ M, int K, int Ty,
+                                                      RowInfo *__restrict__ rows) {
     __shared__ uint32_t s_w[32];
     uint32_t *row = M + static_cast<size_t>(blockIdx.x) * K;
+    const uint32_t *prow = M + static_cast<size_t>(Ty + blockIdx.x) * K;   // pairs of the same row
     const int per = (K + 1023) / 1024;
     uint32_t v[kBinChunksPerThread];
-    uint32_t sum = 0;
+    uint32_t sum = 0, psum = 0;
 #pragma unroll
     for (int q = 0; q < kBinChunksPerThread; ++q) {
         const int i = threadIdx.x * per + q;
         v[q] = (q < per && i < K) ? row[i] : 0u;
         sum += v[q];
+        psum += (q < per && i < K) ? prow[i] : 0u;
     }
+    uint32_t ptot;
+    block_excl_scan<1024>(psum, s_w, &ptot);
+    if (threadIdx.x == 0) rows[blockIdx.x].pairs = ptot;
     uint32_t tot;
     uint32_t run = block_excl_scan<1024>(sum, s_w, &tot);
 #pragma unroll
@@ -343,7 +358,7 @@ cudaError_t launch_bin_rows(const uint32_t *order, const Rec *rec, uint32_t n_ca
     cudaError_t e = cudaMemsetAsync(rows, 0, static_cast<size_t>(Ty) * sizeof(RowInfo), st);
     if (e != cudaSuccess) return e;
     k_bin_rows<false><<<kBinBlocks, 256, 0, st>>>(order, rec, n_cap, Ty, M, rows, rowlist, ctl);
-    k_bin_rowscan<<<Ty, 1024, 0, st>>>(M, kBinBlocks * 8, rows);
+    k_bin_rowscan<<<Ty, 1024, 0, st>>>(M, kBinBlocks * 8, Ty, rows);
     k_bin_rowstart<<<1, 256, 0, st>>>(rows, Ty, ctl, cap, piece);
     k_bin_rows<true><<<kBinBlocks, 256, 0, st>>>(order, rec, n_cap, Ty, M, rows, rowlist, ctl);
     return cudaGetLastError();

@@ -31,7 +31,7 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     o.depth = take(N * 4);
     o.sort_k[0] = take(N * 4); o.sort_k[1] = take(N * 4);
     o.sort_v[0] = take(N * 4); o.sort_v[1] = take(N * 4);
-    o.bin_m = take(static_cast<size_t>(kBinChunks) * o.Ty * 4);
+    o.bin_m = take(static_cast<size_t>(kBinChunks) * o.Ty * 8);   // entries and pairs per (row, chunk)
     o.bin_rows = take(bin_rows_bytes(o.Ty));
     o.bin_piece = bin_piece_entries(dup_cap, o.Tx);
     o.bin_p = take(bin_piece_bytes(dup_cap, o.Tx, o.Ty));
