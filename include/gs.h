@@ -342,8 +342,8 @@ int gs_read_status(const void *workspace, gs_status *out, void *stream);
  * Not thread safe: enable it in one thread at a time.                        */
 enum {
     GS_STAGE_PREPROCESS = 0,   /* S1 */
-    GS_STAGE_COMPACT,          /* S2: visible compaction (scan) */
-    GS_STAGE_DEPTH_SORT,       /* S2: 4 radix passes on depth bits */
+    GS_STAGE_COMPACT,          /* S2: visible count and digit histograms of the depth keys */
+    GS_STAGE_DEPTH_SORT,       /* S2: radix digit kernels on the depth bits (the first compacts) */
     GS_STAGE_BIN_ROWS,         /* S2: depth-ordered split of the pairs into tile rows */
     GS_STAGE_BIN_TILES,        /* S2: split of every row into its tiles, tile ranges */
     GS_STAGE_COMPOSITE_SETUP,  /* S3: heaviest-first tile order, checkpoint bases */

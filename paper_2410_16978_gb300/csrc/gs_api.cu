@@ -31,6 +31,10 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     o.depth = take(N * 4);
     o.sort_k[0] = take(N * 4); o.sort_k[1] = take(N * 4);
     o.sort_v[0] = take(N * 4); o.sort_v[1] = take(N * 4);
+    o.order = take(N * 4);
+    o.vis_index = take(N * 4);
+    o.sort_hist = take(4 * 256 * 4);
+    o.sort_status = take(sort_status_bytes(n));
     o.bin_m = take(static_cast<size_t>(kBinChunks) * o.Ty * 8);   // entries and pairs per (row, chunk)
     o.bin_rows = take(bin_rows_bytes(o.Ty));
     o.bin_piece = bin_piece_entries(dup_cap, o.Tx);
@@ -39,7 +43,6 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     o.t_final = take(P * 4);
     o.n_contrib = take(P * 4);
     o.partials = take(kMaxSortBlocks * 4);
-    o.hist = take((static_cast<size_t>(256) * kMaxSortBlocks + 256) * 4);   // + digit totals
     o.rec_grad = take(N * sizeof(Rec));
     o.tile_order = take(static_cast<size_t>(o.Tn) * 4);
     o.tile_order_bwd = take(static_cast<size_t>(o.Tn) * 4);
@@ -282,39 +285,43 @@ int front_preprocess(const gs_scene *scene, const gs_camera *camera, uint32_t la
     return cuda_check(launch_preprocess(f->sv, f->cv, layer_mask, pl, f->rec, f->tiles, f->depth, st), "preprocess");
 }
 
-// Phase 2: compaction of the visible Gaussians and the depth radix sort.  With
-// `other`, a Gaussian visible to either view is kept and keyed by this view's
-// depth when this view sees it, else by the other's (shared stereo order).
-// Returns the depth order (in this view's workspace).
+// Phase 2: the depth sort of the visible Gaussians.  With `other`, a
+// Gaussian visible to either view is kept and keyed by this view's depth when
+// this view sees it, else by the other's (shared stereo order).  Returns the
+// depth order (in this view's workspace).
+SortWork sort_work(void *ws, const Layout &L) {
+    SortWork w;
+    for (int k = 0; k < 2; ++k) {
+        w.keys[k] = at<uint32_t>(ws, L.sort_k[k]);
+        w.vals[k] = at<uint32_t>(ws, L.sort_v[k]);
+    }
+    w.order = at<uint32_t>(ws, L.order);
+    w.vis_index = at<uint32_t>(ws, L.vis_index);
+    w.ghist = at<uint32_t>(ws, L.sort_hist);
+    w.status = at<uint64_t>(ws, L.sort_status);
+    return w;
+}
+
 int front_sort(FrontCtx &f, const FrontCtx *other, cudaStream_t st, uint32_t **order) {
+    const SortWork w = sort_work(f.ws, f.L);
     int rc;
-    const Layout &L = f.L;
-    void *ws = f.ws;
-    const uint32_t n = static_cast<uint32_t>(f.sv.n);
-    uint32_t *sk[2] = {at<uint32_t>(ws, L.sort_k[0]), at<uint32_t>(ws, L.sort_k[1])};
-    uint32_t *sv2[2] = {at<uint32_t>(ws, L.sort_v[0]), at<uint32_t>(ws, L.sort_v[1])};
-    uint32_t *partials = at<uint32_t>(ws, L.partials);
-    uint32_t *hist = at<uint32_t>(ws, L.hist);
     {
-        Stage sg(GS_STAGE_COMPACT, st, 3);
-        rc = other ? cuda_check(launch_compact_visible2(f.tiles, f.depth, other->tiles, other->depth, f.sv.n, sk[0],
-                                                        sv2[0], partials, f.ctl, st),
-                                "compact (stereo)")
-                   : cuda_check(launch_compact_visible(f.tiles, f.depth, f.sv.n, sk[0], sv2[0], partials, f.ctl, st),
-                                "compact");
+        Stage sg(GS_STAGE_COMPACT, st, 1);
+        rc = other ? cuda_check(launch_sort_histograms2(f.tiles, f.depth, other->tiles, other->depth, f.sv.n, w,
+                                                        f.ctl, st),
+                                "depth histograms (stereo)")
+                   : cuda_check(launch_sort_histograms(f.tiles, f.depth, f.sv.n, w, f.ctl, st), "depth histograms");
         if (rc != GS_OK) return rc;
     }
     {
-        Stage sg(GS_STAGE_DEPTH_SORT, st, 12);
-        for (int pass = 0; pass < 4; ++pass) {
-            const int a = pass & 1;
-            if ((rc = cuda_check(launch_radix_pass(sk[a], sv2[a], sk[1 - a], sv2[1 - a], &f.ctl->n_vis, n, 8 * pass,
-                                                   hist, f.ctl->depth_mm, pass == 0, st),
-                                 "depth sort")) != GS_OK)
-                return rc;
-        }
+        Stage sg(GS_STAGE_DEPTH_SORT, st, 4);
+        rc = other ? cuda_check(launch_sort_digits2(f.tiles, f.depth, other->tiles, other->depth, f.sv.n, w, f.ctl,
+                                                    st),
+                                "depth sort (stereo)")
+                   : cuda_check(launch_sort_digits(f.tiles, f.depth, f.sv.n, w, f.ctl, st), "depth sort");
+        if (rc != GS_OK) return rc;
     }
-    *order = sv2[0];
+    *order = w.order;
     return GS_OK;
 }
 
@@ -441,7 +448,14 @@ int gs_render_stereo(const gs_scene *scene, const gs_camera *left, const gs_came
     if (shared_sort) {
         uint32_t *order = nullptr;
         if ((rc = front_sort(f[0], &f[1], st, &order)) != GS_OK) return rc;
-        // the right eye bins in the shared order: it needs the shared count too
+        // the right eye bins in the shared order: it needs the shared count, and
+        // its backward the visible list, too
+        if ((rc = cuda_check(cudaMemcpyAsync(at<uint32_t>(f[1].ws, f[1].L.vis_index),
+                                             at<uint32_t>(f[0].ws, f[0].L.vis_index),
+                                             static_cast<size_t>(f[0].sv.n) * sizeof(uint32_t),
+                                             cudaMemcpyDeviceToDevice, st),
+                             "shared visible list")) != GS_OK)
+            return rc;
         if ((rc = cuda_check(cudaMemcpyAsync(&f[1].ctl->n_vis, &f[0].ctl->n_vis, sizeof(uint32_t),
                                              cudaMemcpyDeviceToDevice, st),
                              "shared count")) != GS_OK)
@@ -495,8 +509,9 @@ int gs_render_backward(const gs_scene *scene, const gs_camera *camera, const flo
         return rc;
     }
     Stage sg(GS_STAGE_PREPROCESS_BWD, st, 1);
-    return cuda_check(launch_preprocess_backward(sv, cv, at<uint32_t>(ws, L.tiles), rec_grad, grad_layer_mask, *grads,
-                                                 contrib_sum, st),
+    return cuda_check(launch_preprocess_backward(sv, cv, at<uint32_t>(ws, L.tiles), at<uint32_t>(ws, L.vis_index),
+                                                 at<Ctl>(ws, L.ctl), rec_grad, grad_layer_mask, *grads, contrib_sum,
+                                                 st),
                       "preprocess backward");
 }
 

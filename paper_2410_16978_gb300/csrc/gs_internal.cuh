@@ -47,7 +47,8 @@ struct Ctl {
     uint32_t bwd_queue;    // next work item of the persistent backward compositor
     uint32_t n_items;      // backward work items (tile, 8x8 block, segment)
     uint32_t n_pieces;     // row-list pieces of the binning
-    uint32_t pad[16];
+    uint32_t sort_ticket[4];   // next tile of each digit kernel of the depth sort
+    uint32_t pad[12];
 };
 static_assert(sizeof(Ctl) == 128, "Ctl layout");
 
@@ -56,9 +57,10 @@ struct Layout {
     int64_t n = 0, dup_cap = 0;
     int W = 0, H = 0, Tx = 0, Ty = 0, Tn = 0;
     uint32_t bin_piece = 0;
-    size_t ctl = 0, rec = 0, tiles = 0, depth = 0, sort_k[2] = {0, 0}, sort_v[2] = {0, 0}, bin_m = 0,
+    size_t ctl = 0, rec = 0, tiles = 0, depth = 0, sort_k[2] = {0, 0}, sort_v[2] = {0, 0}, order = 0, vis_index = 0,
+           sort_hist = 0, sort_status = 0, bin_m = 0,
            bin_rows = 0, bin_p = 0, rowlist = 0, list = 0, ranges = 0, t_final = 0, n_contrib = 0,
-           partials = 0, hist = 0, rec_grad = 0, tile_order = 0, tile_order_bwd = 0, seg_base = 0, qwork = 0,
+           partials = 0, rec_grad = 0, tile_order = 0, tile_order_bwd = 0, seg_base = 0, qwork = 0,
            ckpt = 0, items = 0, total = 0;
 };
 
@@ -107,28 +109,41 @@ cudaError_t launch_preprocess(const SceneView &s, const CamView &c, uint32_t lay
                               Rec *rec, uint32_t *tiles, uint32_t *depth_key, cudaStream_t st);
 // Also adds the per-Gaussian blend-weight sums (record-gradient slot 9) to
 // contrib_sum when it is not null.
+// vis_index: the visible list of the last render (index order, ctl->n_vis
+// entries; a two-eye list may also hold Gaussians this view does not see).
 cudaError_t launch_preprocess_backward(const SceneView &s, const CamView &c, const uint32_t *tiles,
-                                       const float4 *rec_grad, uint32_t grad_layer_mask, const gs_grads &g,
-                                       float *contrib_sum, cudaStream_t st);
+                                       const uint32_t *vis_index, const Ctl *ctl, const float4 *rec_grad,
+                                       uint32_t grad_layer_mask, const gs_grads &g, float *contrib_sum,
+                                       cudaStream_t st);
 
 int sort_blocks();   // blocks of the sort / scan kernels on this device
 int report(int code, const char *msg);   // sets gs_last_error_string(), returns code
 
-// Visible compaction: for i < n with tiles[i] > 0, writes (depth_key[i], i) in index order
-// to (keys_out, vals_out) and the count to ctl->n_vis.
-cudaError_t launch_compact_visible(const uint32_t *tiles, const uint32_t *depth_key, int n, uint32_t *keys_out,
-                                   uint32_t *vals_out, uint32_t *partials, Ctl *ctl, cudaStream_t st);
-// Stereo variant: Gaussians visible to view a or view b; key = depth_a where
-// view a sees the Gaussian, else depth_b (one depth order shared by two eyes).
-cudaError_t launch_compact_visible2(const uint32_t *tiles_a, const uint32_t *depth_a, const uint32_t *tiles_b,
-                                    const uint32_t *depth_b, int n, uint32_t *keys_out, uint32_t *vals_out,
-                                    uint32_t *partials, Ctl *ctl, cudaStream_t st);
-// One stable LSD pass on 8 bits at `shift` of min(*n_dev, n_cap) (key, value) pairs.
-// minmax (2 words, zeroed before the sort) receives ~min and max key in the
-// first pass; later passes whose digit is constant only copy.
-cudaError_t launch_radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
-                              const uint32_t *n_dev, uint32_t n_cap, int shift, uint32_t *hist, uint32_t *minmax,
-                              bool first, cudaStream_t st);
+// Depth sort (sort.cu).  Buffers in the workspace:
+struct SortWork {
+    uint32_t *keys[2], *vals[2];   // ping-pong (key, Gaussian) buffers of the digit kernels, N each
+    uint32_t *order;               // out: visible Gaussians in (depth, index) order, N
+    uint32_t *vis_index;           // out: visible Gaussians in index order, N
+    uint32_t *ghist;               // 4 x 256 digit histograms
+    uint64_t *status;              // sort_status_bytes(N): look-back words of the four digit kernels
+};
+uint32_t sort_tiles(int64_t n);
+size_t sort_status_bytes(int64_t n);
+// Sorts the Gaussians i < n with tiles[i] > 0 by (depth[i], i).  Histograms:
+// the visible count (to ctl->n_vis and ctl->st.n_visible), the key range
+// (ctl->depth_mm) and the digit histograms; these control words and the
+// tickets must be zero on entry.  Digits: writes work.order and
+// work.vis_index.
+cudaError_t launch_sort_histograms(const uint32_t *tiles, const uint32_t *depth, int n, const SortWork &work,
+                                   Ctl *ctl, cudaStream_t st);
+cudaError_t launch_sort_digits(const uint32_t *tiles, const uint32_t *depth, int n, const SortWork &work, Ctl *ctl,
+                               cudaStream_t st);
+// Two eyes: Gaussians visible to view a or view b, keyed by depth_a where
+// view a sees the Gaussian, else by depth_b (one depth order for both eyes).
+cudaError_t launch_sort_histograms2(const uint32_t *tiles_a, const uint32_t *depth_a, const uint32_t *tiles_b,
+                                    const uint32_t *depth_b, int n, const SortWork &work, Ctl *ctl, cudaStream_t st);
+cudaError_t launch_sort_digits2(const uint32_t *tiles_a, const uint32_t *depth_a, const uint32_t *tiles_b,
+                                const uint32_t *depth_b, int n, const SortWork &work, Ctl *ctl, cudaStream_t st);
 // Tile binning (bin.cu).  Rows: splits the depth-ordered visible Gaussians
 // (order[p], p < min(ctl->n_vis, n_cap)) into per-tile-row lists of
 // (Gaussian, x0 | x1 << 16) in depth order; writes n_dup and the overflow

@@ -3,6 +3,13 @@
 // quaternions, opacity logit, SH), the backward of the EWA projection used by
 // the layered training (Sec. 3.2).  Gaussians that were culled or whose layer
 // is frozen (not in grad_layer_mask; Sec. 3.2: lower layers stay fixed) get 0.
+//
+// One launch with two roles.  The first blocks take the visible Gaussians
+// from the sort's index-ordered visible list, one thread each, so every warp
+// does the chain rule on 32 live Gaussians instead of the third of its lanes
+// that a pass over all indices would keep.  The other blocks write the zero
+// rows: a warp takes 32 consecutive Gaussians and stores zeros to the rows
+// that are not live, every array with coalesced stores.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -56,211 +63,276 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float *
 }
 
 constexpr int kBwdThreads = 128;
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// SH coefficients of Gaussian i as [k][channel]; 16-byte loads for float32
+// rows whose length is a multiple of 4 floats (SH degrees 1 and 3).
+template <int K>
+__device__ __forceinline__ void load_sh(const SceneView &s, int i, float *v) {
+    const int64_t base = static_cast<int64_t>(i) * 3 * K;
+    if constexpr ((3 * K) % 4 == 0) {
+        if (s.dtype_sh == GS_DTYPE_F32 && (reinterpret_cast<uintptr_t>(s.sh) & 15u) == 0) {
+            const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(s.sh) + base);
+#pragma unroll
+            for (int q = 0; q < 3 * K / 4; ++q) {
+                const float4 x = p[q];
+                v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 3 * K; ++e) v[e] = ldv(s.sh, base + e, s.dtype_sh);
+}
+
+// A gradient row of W floats; 16-byte stores where the row allows them.
+template <int W>
+__device__ __forceinline__ void store_row(float *dst, const float *v) {
+    if constexpr (W % 4 == 0) {
+        if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+#pragma unroll
+            for (int q = 0; q < W / 4; ++q)
+                reinterpret_cast<float4 *>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            return;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < W; ++e) dst[e] = v[e];
+}
+
+// Zeros of the rows r < nrows of a [32][W] block whose bit is set in `rows`.
+template <int W>
+__device__ __forceinline__ void zero_rows(float *base, unsigned rows, int nrows, int lane) {
+    if constexpr (W % 4 == 0) {
+        if ((reinterpret_cast<uintptr_t>(base) & 15u) == 0) {
+            for (int q = lane; q < nrows * (W / 4); q += 32)
+                if ((rows >> (q / (W / 4))) & 1u) reinterpret_cast<float4 *>(base)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            return;
+        }
+    }
+    for (int e = lane; e < nrows * W; e += 32)
+        if ((rows >> (e / W)) & 1u) base[e] = 0.f;
+}
+
+// The chain rule of one live Gaussian.
+template <int DEG>
+__device__ __forceinline__ void grad_one(const SceneView &s, const CamView &c, int i, const float4 *__restrict__ rec_grad,
+                                         const gs_grads &g) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const float4 ga = rec_grad[3 * i], gb = rec_grad[3 * i + 1], gc = rec_grad[3 * i + 2];
+    const float dU = ga.x, dV = ga.y, dA2 = ga.z, dBeta = ga.w, dG2 = gb.x, dOp = gb.y;
+    const float dRgb[3] = {gb.z, gb.w, gc.x};
+    const float mx = s.means[3 * i], my_ = s.means[3 * i + 1], mz = s.means[3 * i + 2];
+    const float *R = c.R;
+
+    // opacity
+    const float o = 1.f / (1.f + expf(-s.opacity_logit[i]));
+    g.opacity_logit[i] = dOp * o * (1.f - o);
+
+    // colour and the view-direction part of d(mean)
+    const float cp0 = -(R[0] * c.t[0] + R[3] * c.t[1] + R[6] * c.t[2]);
+    const float cp1 = -(R[1] * c.t[0] + R[4] * c.t[1] + R[7] * c.t[2]);
+    const float cp2 = -(R[2] * c.t[0] + R[5] * c.t[1] + R[8] * c.t[2]);
+    const float vx = mx - cp0, vy = my_ - cp1, vz = mz - cp2;
+    const float ivn = rsqrtf(vx * vx + vy * vy + vz * vz);
+    const float dx = vx * ivn, dy = vy * ivn, dz = vz * ivn;
+    float b[K];
+    float3 db[K];
+    sh_basis_grad<DEG>(dx, dy, dz, b, db);
+    float shv[3 * K];
+    load_sh<K>(s, i, shv);
+    float gch[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc += b[k] * shv[3 * k + ch];
+        gch[ch] = acc + 0.5f > 0.f ? dRgb[ch] : 0.f;
+    }
+    float ddx = 0.f, ddy = 0.f, ddz = 0.f;
+    float gsh[3 * K];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            gsh[3 * k + ch] = gch[ch] * b[k];
+            const float t = shv[3 * k + ch] * gch[ch];
+            ddx += t * db[k].x; ddy += t * db[k].y; ddz += t * db[k].z;
+        }
+    }
+    store_row<3 * K>(g.sh + static_cast<int64_t>(i) * 3 * K, gsh);
+    const float dd = ddx * dx + ddy * dy + ddz * dz;
+    float gmx = (ddx - dx * dd) * ivn, gmy = (ddy - dy * dd) * ivn, gmz = (ddz - dz * dd) * ivn;
+
+    // recompute the projection
+    const float px = R[0] * mx + R[1] * my_ + R[2] * mz + c.t[0];
+    const float py = R[3] * mx + R[4] * my_ + R[5] * mz + c.t[1];
+    const float pz = R[6] * mx + R[7] * my_ + R[8] * mz + c.t[2];
+    float sc[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sc[k] = expf(ldv(s.log_scales, 3 * (int64_t)i + k, s.dtype_sr));
+    float q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = ldv(s.quats, 4 * (int64_t)i + k, s.dtype_sr);
+    const float iqn = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const float w = q[0] * iqn, x = q[1] * iqn, y = q[2] * iqn, z = q[3] * iqn;
+    const float Rq[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
+                         2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
+                         2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
+    float M[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * a + j] = Rq[3 * a + j] * sc[j];
+    float Sg[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb)
+            Sg[3 * a + bb] = M[3 * a] * M[3 * bb] + M[3 * a + 1] * M[3 * bb + 1] + M[3 * a + 2] * M[3 * bb + 2];
+    const float limx = 1.3f * (0.5f * c.W / c.fx), limy = 1.3f * (0.5f * c.H / c.fy);
+    const float iz = 1.f / pz;
+    const float rx = px * iz, ry = py * iz;
+    const bool clx = rx < -limx || rx > limx, cly = ry < -limy || ry > limy;
+    const float cxz = fminf(limx, fmaxf(-limx, rx)), cyz = fminf(limy, fmaxf(-limy, ry));
+    const float J00 = c.fx * iz, J02 = -c.fx * cxz * iz, J11 = c.fy * iz, J12 = -c.fy * cyz * iz;
+    float T[6];
+#pragma unroll
+    for (int bb = 0; bb < 3; ++bb) {
+        T[bb] = J00 * R[bb] + J02 * R[6 + bb];
+        T[3 + bb] = J11 * R[3 + bb] + J12 * R[6 + bb];
+    }
+    float U[6];   // T Sigma
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb)
+            U[3 * a + bb] = T[3 * a] * Sg[bb] + T[3 * a + 1] * Sg[3 + bb] + T[3 * a + 2] * Sg[6 + bb];
+    const float s00 = U[0] * T[0] + U[1] * T[1] + U[2] * T[2] + 0.3f;
+    const float s01 = U[0] * T[3] + U[1] * T[4] + U[2] * T[5];
+    const float s11 = U[3] * T[3] + U[4] * T[4] + U[5] * T[5] + 0.3f;
+    const float det = s00 * s11 - s01 * s01;
+    const float NHL = -0x1.715476p-1f;
+    const float idet2 = 1.f / (det * det);
+    const float is11 = 1.f / s11;
+    const float ds00 = dA2 * (-NHL * s11 * s11 * idet2);
+    const float ds11 = dA2 * (-NHL * s01 * s01 * idet2) + dBeta * (s01 * is11 * is11) + dG2 * (-NHL * is11 * is11);
+    const float ds01 = dA2 * (2.f * NHL * s11 * s01 * idet2) - dBeta * is11;
+    const float G00 = ds00, G01 = 0.5f * ds01, G11 = ds11;
+
+    // dSigma = T^T G T (symmetric), dT = 2 G T Sigma = 2 G U
+    float dSg[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb)
+            dSg[3 * a + bb] = T[a] * (G00 * T[bb] + G01 * T[3 + bb]) + T[3 + a] * (G01 * T[bb] + G11 * T[3 + bb]);
+    float dT[6];
+#pragma unroll
+    for (int bb = 0; bb < 3; ++bb) {
+        dT[bb] = 2.f * (G00 * U[bb] + G01 * U[3 + bb]);
+        dT[3 + bb] = 2.f * (G01 * U[bb] + G11 * U[3 + bb]);
+    }
+    // dJ = dT W^T (only the entries that are not identically zero)
+    const float dJ00 = dT[0] * R[0] + dT[1] * R[1] + dT[2] * R[2];
+    const float dJ02 = dT[0] * R[6] + dT[1] * R[7] + dT[2] * R[8];
+    const float dJ11 = dT[3] * R[3] + dT[4] * R[4] + dT[5] * R[5];
+    const float dJ12 = dT[3] * R[6] + dT[4] * R[7] + dT[5] * R[8];
+    const float iz2 = iz * iz;
+    float dpx = 0.f, dpy = 0.f, dpz = 0.f;
+    dpz += -dJ00 * c.fx * iz2 + dJ02 * c.fx * cxz * iz2 - dJ11 * c.fy * iz2 + dJ12 * c.fy * cyz * iz2;
+    const float dcx = -dJ02 * c.fx * iz, dcy = -dJ12 * c.fy * iz;
+    if (!clx) { dpx += dcx * iz; dpz -= dcx * px * iz2; }
+    if (!cly) { dpy += dcy * iz; dpz -= dcy * py * iz2; }
+    dpx += dU * c.fx * iz;
+    dpy += dV * c.fy * iz;
+    dpz -= (dU * c.fx * px + dV * c.fy * py) * iz2;
+    gmx += R[0] * dpx + R[3] * dpy + R[6] * dpz;
+    gmy += R[1] * dpx + R[4] * dpy + R[7] * dpz;
+    gmz += R[2] * dpx + R[5] * dpy + R[8] * dpz;
+    g.means[3 * i] = gmx; g.means[3 * i + 1] = gmy; g.means[3 * i + 2] = gmz;
+
+    // Sigma = M M^T: dM = 2 dSigma M;  M = Rq diag(s)
+    float dR[9];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float ds = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float dM = 2.f * (dSg[3 * a] * M[j] + dSg[3 * a + 1] * M[3 + j] + dSg[3 * a + 2] * M[6 + j]);
+            ds += dM * Rq[3 * a + j];
+            dR[3 * a + j] = dM * sc[j];
+        }
+        g.log_scales[3 * i + j] = ds * sc[j];
+    }
+    // rotation matrix of the unit quaternion -> (w, x, y, z)
+    const float dw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+    const float dxq = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] +
+                             w * dR[7] - 2.f * x * dR[8]);
+    const float dyq = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] +
+                             z * dR[7] - 2.f * y * dR[8]);
+    const float dzq = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
+                             x * dR[6] + y * dR[7]);
+    const float qd = dw * w + dxq * x + dyq * y + dzq * z;
+    g.quats[4 * i] = (dw - w * qd) * iqn;
+    g.quats[4 * i + 1] = (dxq - x * qd) * iqn;
+    g.quats[4 * i + 2] = (dyq - y * qd) * iqn;
+    g.quats[4 * i + 3] = (dzq - z * qd) * iqn;
+}
 
 template <int DEG>
 __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd(SceneView s, CamView c,
                                                                 const uint32_t *__restrict__ tiles,
+                                                                const uint32_t *__restrict__ vis_index,
+                                                                const Ctl *__restrict__ ctl,
                                                                 const float4 *__restrict__ rec_grad,
                                                                 uint32_t grad_layer_mask, gs_grads g,
-                                                                float *__restrict__ contrib_sum) {
+                                                                float *__restrict__ contrib_sum, int live_blocks) {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    constexpr int KS = 3 * K + 1;                     // odd stride: conflict-free rows
-    __shared__ float s_gsh[kBwdThreads * KS];
-    const int i = blockIdx.x * kBwdThreads + threadIdx.x;
-    float *my = s_gsh + threadIdx.x * KS;
-    const bool visible = i < s.n && tiles[i] > 0;
-    if (visible && contrib_sum) contrib_sum[i] += rec_grad[3 * i + 2].y;
-    const bool live = visible && ((grad_layer_mask >> s.layer[i]) & 1u);
-    if (!live) {
-#pragma unroll
-        for (int k = 0; k < 3 * K; ++k) my[k] = 0.f;
-        if (i < s.n) {
-            for (int k = 0; k < 3; ++k) { g.means[3 * i + k] = 0.f; g.log_scales[3 * i + k] = 0.f; }
-            for (int k = 0; k < 4; ++k) g.quats[4 * i + k] = 0.f;
-            g.opacity_logit[i] = 0.f;
-        }
-    } else {
-        const float4 ga = rec_grad[3 * i], gb = rec_grad[3 * i + 1], gc = rec_grad[3 * i + 2];
-        const float dU = ga.x, dV = ga.y, dA2 = ga.z, dBeta = ga.w, dG2 = gb.x, dOp = gb.y;
-        const float dRgb[3] = {gb.z, gb.w, gc.x};
-        const float mx = s.means[3 * i], my_ = s.means[3 * i + 1], mz = s.means[3 * i + 2];
-        const float *R = c.R;
-
-        // opacity
-        const float o = 1.f / (1.f + expf(-s.opacity_logit[i]));
-        g.opacity_logit[i] = dOp * o * (1.f - o);
-
-        // colour and the view-direction part of d(mean)
-        const float cp0 = -(R[0] * c.t[0] + R[3] * c.t[1] + R[6] * c.t[2]);
-        const float cp1 = -(R[1] * c.t[0] + R[4] * c.t[1] + R[7] * c.t[2]);
-        const float cp2 = -(R[2] * c.t[0] + R[5] * c.t[1] + R[8] * c.t[2]);
-        const float vx = mx - cp0, vy = my_ - cp1, vz = mz - cp2;
-        const float ivn = rsqrtf(vx * vx + vy * vy + vz * vz);
-        const float dx = vx * ivn, dy = vy * ivn, dz = vz * ivn;
-        float b[K];
-        float3 db[K];
-        sh_basis_grad<DEG>(dx, dy, dz, b, db);
-        const int64_t base = static_cast<int64_t>(i) * K * 3;
-        float ddx = 0.f, ddy = 0.f, ddz = 0.f;
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float shv[K];
-            float acc = 0.f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                shv[k] = ldv(s.sh, base + 3 * k + ch, s.dtype_sh);
-                acc += b[k] * shv[k];
-            }
-            const float gch = acc + 0.5f > 0.f ? dRgb[ch] : 0.f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                my[3 * k + ch] = gch * b[k];
-                const float t = shv[k] * gch;
-                ddx += t * db[k].x; ddy += t * db[k].y; ddz += t * db[k].z;
-            }
-        }
-        const float dd = ddx * dx + ddy * dy + ddz * dz;
-        float gmx = (ddx - dx * dd) * ivn, gmy = (ddy - dy * dd) * ivn, gmz = (ddz - dz * dd) * ivn;
-
-        // recompute the projection
-        const float px = R[0] * mx + R[1] * my_ + R[2] * mz + c.t[0];
-        const float py = R[3] * mx + R[4] * my_ + R[5] * mz + c.t[1];
-        const float pz = R[6] * mx + R[7] * my_ + R[8] * mz + c.t[2];
-        float sc[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) sc[k] = expf(ldv(s.log_scales, 3 * (int64_t)i + k, s.dtype_sr));
-        float q[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) q[k] = ldv(s.quats, 4 * (int64_t)i + k, s.dtype_sr);
-        const float iqn = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-        const float w = q[0] * iqn, x = q[1] * iqn, y = q[2] * iqn, z = q[3] * iqn;
-        const float Rq[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
-                             2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
-                             2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
-        float M[9];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) M[3 * a + j] = Rq[3 * a + j] * sc[j];
-        float Sg[9];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int bb = 0; bb < 3; ++bb)
-                Sg[3 * a + bb] = M[3 * a] * M[3 * bb] + M[3 * a + 1] * M[3 * bb + 1] + M[3 * a + 2] * M[3 * bb + 2];
-        const float limx = 1.3f * (0.5f * c.W / c.fx), limy = 1.3f * (0.5f * c.H / c.fy);
-        const float iz = 1.f / pz;
-        const float rx = px * iz, ry = py * iz;
-        const bool clx = rx < -limx || rx > limx, cly = ry < -limy || ry > limy;
-        const float cxz = fminf(limx, fmaxf(-limx, rx)), cyz = fminf(limy, fmaxf(-limy, ry));
-        const float J00 = c.fx * iz, J02 = -c.fx * cxz * iz, J11 = c.fy * iz, J12 = -c.fy * cyz * iz;
-        float T[6];
-#pragma unroll
-        for (int bb = 0; bb < 3; ++bb) {
-            T[bb] = J00 * R[bb] + J02 * R[6 + bb];
-            T[3 + bb] = J11 * R[3 + bb] + J12 * R[6 + bb];
-        }
-        float U[6];   // T Sigma
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int bb = 0; bb < 3; ++bb)
-                U[3 * a + bb] = T[3 * a] * Sg[bb] + T[3 * a + 1] * Sg[3 + bb] + T[3 * a + 2] * Sg[6 + bb];
-        const float s00 = U[0] * T[0] + U[1] * T[1] + U[2] * T[2] + 0.3f;
-        const float s01 = U[0] * T[3] + U[1] * T[4] + U[2] * T[5];
-        const float s11 = U[3] * T[3] + U[4] * T[4] + U[5] * T[5] + 0.3f;
-        const float det = s00 * s11 - s01 * s01;
-        const float NHL = -0x1.715476p-1f;
-        const float idet2 = 1.f / (det * det);
-        const float is11 = 1.f / s11;
-        const float ds00 = dA2 * (-NHL * s11 * s11 * idet2);
-        const float ds11 = dA2 * (-NHL * s01 * s01 * idet2) + dBeta * (s01 * is11 * is11) + dG2 * (-NHL * is11 * is11);
-        const float ds01 = dA2 * (2.f * NHL * s11 * s01 * idet2) - dBeta * is11;
-        const float G00 = ds00, G01 = 0.5f * ds01, G11 = ds11;
-
-        // dSigma = T^T G T (symmetric), dT = 2 G T Sigma = 2 G U
-        float dSg[9];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int bb = 0; bb < 3; ++bb)
-                dSg[3 * a + bb] = T[a] * (G00 * T[bb] + G01 * T[3 + bb]) + T[3 + a] * (G01 * T[bb] + G11 * T[3 + bb]);
-        float dT[6];
-#pragma unroll
-        for (int bb = 0; bb < 3; ++bb) {
-            dT[bb] = 2.f * (G00 * U[bb] + G01 * U[3 + bb]);
-            dT[3 + bb] = 2.f * (G01 * U[bb] + G11 * U[3 + bb]);
-        }
-        // dJ = dT W^T (only the entries that are not identically zero)
-        const float dJ00 = dT[0] * R[0] + dT[1] * R[1] + dT[2] * R[2];
-        const float dJ02 = dT[0] * R[6] + dT[1] * R[7] + dT[2] * R[8];
-        const float dJ11 = dT[3] * R[3] + dT[4] * R[4] + dT[5] * R[5];
-        const float dJ12 = dT[3] * R[6] + dT[4] * R[7] + dT[5] * R[8];
-        const float iz2 = iz * iz;
-        float dpx = 0.f, dpy = 0.f, dpz = 0.f;
-        dpz += -dJ00 * c.fx * iz2 + dJ02 * c.fx * cxz * iz2 - dJ11 * c.fy * iz2 + dJ12 * c.fy * cyz * iz2;
-        const float dcx = -dJ02 * c.fx * iz, dcy = -dJ12 * c.fy * iz;
-        if (!clx) { dpx += dcx * iz; dpz -= dcx * px * iz2; }
-        if (!cly) { dpy += dcy * iz; dpz -= dcy * py * iz2; }
-        dpx += dU * c.fx * iz;
-        dpy += dV * c.fy * iz;
-        dpz -= (dU * c.fx * px + dV * c.fy * py) * iz2;
-        gmx += R[0] * dpx + R[3] * dpy + R[6] * dpz;
-        gmy += R[1] * dpx + R[4] * dpy + R[7] * dpz;
-        gmz += R[2] * dpx + R[5] * dpy + R[8] * dpz;
-        g.means[3 * i] = gmx; g.means[3 * i + 1] = gmy; g.means[3 * i + 2] = gmz;
-
-        // Sigma = M M^T: dM = 2 dSigma M;  M = Rq diag(s)
-        float dR[9];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            float ds = 0.f;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float dM = 2.f * (dSg[3 * a] * M[j] + dSg[3 * a + 1] * M[3 + j] + dSg[3 * a + 2] * M[6 + j]);
-                ds += dM * Rq[3 * a + j];
-                dR[3 * a + j] = dM * sc[j];
-            }
-            g.log_scales[3 * i + j] = ds * sc[j];
-        }
-        // rotation matrix of the unit quaternion -> (w, x, y, z)
-        const float dw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
-        const float dxq = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] +
-                                 w * dR[7] - 2.f * x * dR[8]);
-        const float dyq = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] +
-                                 z * dR[7] - 2.f * y * dR[8]);
-        const float dzq = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
-                                 x * dR[6] + y * dR[7]);
-        const float qd = dw * w + dxq * x + dyq * y + dzq * z;
-        g.quats[4 * i] = (dw - w * qd) * iqn;
-        g.quats[4 * i + 1] = (dxq - x * qd) * iqn;
-        g.quats[4 * i + 2] = (dyq - y * qd) * iqn;
-        g.quats[4 * i + 3] = (dzq - z * qd) * iqn;
+    if (static_cast<int>(blockIdx.x) < live_blocks) {
+        const uint32_t p = blockIdx.x * kBwdThreads + threadIdx.x;
+        if (p >= min(ctl->n_vis, static_cast<uint32_t>(s.n))) return;
+        const int i = static_cast<int>(vis_index[p]);
+        if (tiles[i] == 0) return;              // a two-eye list also holds Gaussians only the other eye sees
+        if (contrib_sum) contrib_sum[i] += rec_grad[3 * i + 2].y;
+        if (!((grad_layer_mask >> s.layer[i]) & 1u)) return;   // frozen: a zero row
+        grad_one<DEG>(s, c, i, rec_grad, g);
+        return;
     }
-    // the block's SH gradients are one contiguous slab: write it with coalesced stores
-    __syncthreads();
-    const int first = blockIdx.x * kBwdThreads;
-    const int nrows = min(kBwdThreads, s.n - first);
-    float *dst = g.sh + static_cast<int64_t>(first) * 3 * K;
-    for (int e = threadIdx.x; e < nrows * 3 * K; e += kBwdThreads) {
-        const int row = e / (3 * K), col = e - row * (3 * K);
-        dst[e] = s_gsh[row * KS + col];
-    }
+    const int lane = threadIdx.x & 31;
+    const int64_t i0 = (static_cast<int64_t>(blockIdx.x - live_blocks) * (kBwdThreads / 32) + (threadIdx.x >> 5)) * 32;
+    if (i0 >= s.n) return;
+    const int nrows = s.n - i0 < 32 ? static_cast<int>(s.n - i0) : 32;
+    const int64_t i = i0 + lane;
+    const bool live = lane < nrows && tiles[i] > 0 && ((grad_layer_mask >> s.layer[i]) & 1u);
+    const unsigned rows = ~__ballot_sync(FULL, live);
+    if ((rows & (nrows == 32 ? FULL : (1u << nrows) - 1u)) == 0) return;
+    zero_rows<3>(g.means + 3 * i0, rows, nrows, lane);
+    zero_rows<3>(g.log_scales + 3 * i0, rows, nrows, lane);
+    zero_rows<4>(g.quats + 4 * i0, rows, nrows, lane);
+    zero_rows<1>(g.opacity_logit + i0, rows, nrows, lane);
+    zero_rows<3 * K>(g.sh + 3 * K * i0, rows, nrows, lane);
 }
 
 }  // namespace
 
 cudaError_t launch_preprocess_backward(const SceneView &s, const CamView &c, const uint32_t *tiles,
-                                       const float4 *rec_grad, uint32_t grad_layer_mask, const gs_grads &g,
-                                       float *contrib_sum, cudaStream_t st) {
+                                       const uint32_t *vis_index, const Ctl *ctl, const float4 *rec_grad,
+                                       uint32_t grad_layer_mask, const gs_grads &g, float *contrib_sum,
+                                       cudaStream_t st) {
     if (s.n == 0) return cudaSuccess;
-    const int blocks = (s.n + kBwdThreads - 1) / kBwdThreads;
+    const int live_blocks = (s.n + kBwdThreads - 1) / kBwdThreads;          // the visible list is at most n long
+    const int zero_blocks = (s.n + kBwdThreads - 1) / kBwdThreads;          // 32 Gaussians per warp
+    const int blocks = live_blocks + zero_blocks;
+#define GS_PBWD(D) k_preprocess_bwd<D><<<blocks, kBwdThreads, 0, st>>>(s, c, tiles, vis_index, ctl, rec_grad, \
+                                                                       grad_layer_mask, g, contrib_sum, live_blocks)
     switch (s.sh_degree) {
-        case 0: k_preprocess_bwd<0><<<blocks, kBwdThreads, 0, st>>>(s, c, tiles, rec_grad, grad_layer_mask, g, contrib_sum); break;
-        case 1: k_preprocess_bwd<1><<<blocks, kBwdThreads, 0, st>>>(s, c, tiles, rec_grad, grad_layer_mask, g, contrib_sum); break;
-        case 2: k_preprocess_bwd<2><<<blocks, kBwdThreads, 0, st>>>(s, c, tiles, rec_grad, grad_layer_mask, g, contrib_sum); break;
-        default: k_preprocess_bwd<3><<<blocks, kBwdThreads, 0, st>>>(s, c, tiles, rec_grad, grad_layer_mask, g, contrib_sum); break;
+        case 0: GS_PBWD(0); break;
+        case 1: GS_PBWD(1); break;
+        case 2: GS_PBWD(2); break;
+        default: GS_PBWD(3); break;
     }
+#undef GS_PBWD
     return cudaGetLastError();
 }
 

@@ -1,19 +1,29 @@
-// S2 - tile binning with depth-keyed radix sorts (Sec. 3.3: the Gaussians are
-// sorted relative to the camera; the paper's renderer uses GPU radix sorts).
+// S2 - the depth sort of the visible Gaussians (Sec. 3.3: the Gaussians are
+// sorted relative to the camera; the paper's renderer uses GPU radix sorts),
+// and the scans of the prune entry points.
 //
-// Order of the tile lists: (tile, depth, Gaussian index).  It is produced by
-//   1. compacting the visible Gaussians in index order,
-//   2. a stable LSD radix sort of them by the float bits of their depth,
-//   3. an exclusive scan of their tile counts in that depth order,
-//   4. emitting one (tile id, Gaussian) pair per covered tile at the scanned
-//      offsets (so the pairs are in depth order), and
-//   5. a stable LSD radix sort of the pairs by tile id,
-// which equals a stable sort of the keys (tile << 32 | depth bits) emitted in
-// index order, with 32-bit keys and far fewer passes over the pair list.
+// The depth order is a stable LSD radix sort of the visible Gaussians, taken
+// in index order, by the float bits of their depth (so ties keep index
+// order).  It runs as
+//   1. one pass over all Gaussians that counts the visible ones, the four
+//      8-bit digit histograms of their keys and the smallest and largest key;
+//   2. one kernel per digit.  A CTA takes a tile of 2048 items by ticket,
+//      ranks them by digit in shared memory, and finds the tile's global
+//      offset of every digit by a decoupled look-back over the tiles before
+//      it (the single-pass prefix scan of Merrill and Garland, used per digit
+//      as in Adinets and Merrill's Onesweep radix sort).  The first digit
+//      kernel reads the Gaussians directly, keeps the visible ones and also
+//      writes their indices in index order (the visible list of the
+//      backward).
+// A digit at and above the highest bit where the smallest and largest key
+// differ is the same in every key: its kernel returns at once, and the last
+// digit kernel that runs writes the final order.  A tile waits only on tiles
+// with smaller tickets, whose CTAs are already running, and every wait is
+// bounded (GS_ERR_TIMEOUT in the status word when it gives up).
 //
-// Every kernel runs on a fixed grid of sort_blocks() CTAs that each own a
-// contiguous range of the items, so item counts produced on the device never
-// need to travel to the host.
+// The scans of the prune entry points keep a fixed grid of sort_blocks() CTAs
+// that each own a contiguous range of the items, so item counts produced on
+// the device never need to travel to the host.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -82,7 +92,7 @@ __global__ void __launch_bounds__(256) k_scan_reduce(F f, NSrc ns, uint32_t *__r
     if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
-enum ScanFinal { FIN_NONE = 0, FIN_NVIS = 1, FIN_NKEEP = 2 };
+enum ScanFinal { FIN_NONE = 0, FIN_NKEEP = 2 };
 
 __global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *__restrict__ partials, int G, int mode,
                                                         Ctl *ctl, uint64_t cap, int64_t *n_keep) {
@@ -111,12 +121,7 @@ __global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *__restrict__ p
     if (t < G) partials[t] = excl;
     if (t == 0) {
         const uint32_t total = s_w[31];
-        if (mode == FIN_NVIS) {
-            ctl->n_vis = total;
-            ctl->st.n_visible = total;
-        } else if (mode == FIN_NKEEP) {
-            *n_keep = total;
-        }
+        if (mode == FIN_NKEEP) *n_keep = total;
         ctl->scan_total = total;
     }
 }
@@ -148,33 +153,6 @@ __global__ void __launch_bounds__(256) k_scan_down(F f, NSrc ns, const uint32_t 
 }
 
 // --- functors ---
-struct VisFlag {
-    const uint32_t *tiles;
-    __device__ __forceinline__ uint32_t operator()(uint32_t i) const { return tiles[i] > 0 ? 1u : 0u; }
-};
-struct CompactOut {
-    const uint32_t *depth_key;
-    uint32_t *keys, *vals;
-    __device__ __forceinline__ void operator()(uint32_t i, uint32_t off, uint32_t v) const {
-        if (v) { keys[off] = depth_key[i]; vals[off] = i; }
-    }
-};
-struct VisFlag2 {           // visible to either of two views
-    const uint32_t *tiles_a, *tiles_b;
-    __device__ __forceinline__ uint32_t operator()(uint32_t i) const {
-        return (tiles_a[i] > 0 || tiles_b[i] > 0) ? 1u : 0u;
-    }
-};
-struct CompactOut2 {        // key: view a's depth when view a sees it, else view b's
-    const uint32_t *tiles_a, *depth_a, *depth_b;
-    uint32_t *keys, *vals;
-    __device__ __forceinline__ void operator()(uint32_t i, uint32_t off, uint32_t v) const {
-        if (v) {
-            keys[off] = tiles_a[i] > 0 ? depth_a[i] : depth_b[i];
-            vals[off] = i;
-        }
-    }
-};
 struct KeepFlag {
     const float *cmax;
     float thr;
@@ -200,181 +178,310 @@ struct KeepOut {
 };
 
 // ---------------------------------------------------------------------------
-// Radix sort pass: 8-bit digits, histogram per (digit, block) in digit-major
-// order.  The first pass of a sort also records min and max key (as max of
-// ~key and max of key); a later pass whose digit is the same in every key
-// (all keys agree on the bits at and above its shift) is an identity
-// permutation and only copies.
+// Depth sort.
 
-__device__ __forceinline__ bool pass_is_constant(const uint32_t *mm, int shift) {
-    const uint32_t kmin = ~mm[0], kmax = mm[1];
-    return ((kmin ^ kmax) >> shift) == 0;
+struct VisSrc {             // one view: visible where its tile count is non-zero
+    const uint32_t *tiles, *depth;
+    __device__ __forceinline__ bool visible(uint32_t i) const { return tiles[i] > 0; }
+    __device__ __forceinline__ uint32_t key(uint32_t i) const { return depth[i]; }
+};
+struct VisSrc2 {            // two eyes: visible to either; keyed by view a's depth where view a sees it
+    const uint32_t *tiles_a, *depth_a, *tiles_b, *depth_b;
+    __device__ __forceinline__ bool visible(uint32_t i) const { return tiles_a[i] > 0 || tiles_b[i] > 0; }
+    __device__ __forceinline__ uint32_t key(uint32_t i) const { return tiles_a[i] > 0 ? depth_a[i] : depth_b[i]; }
+};
+
+constexpr int kLookCounters = 256;                 // one per digit
+constexpr uint64_t kLookAgg = 1ull << 32;          // the tile's own count is published
+constexpr uint64_t kLookIncl = 2ull << 32;         // the count of every tile up to and including it
+constexpr uint32_t kSpinLimit = 1u << 20;
+
+__device__ __forceinline__ void st_volatile(uint64_t *p, uint64_t v) { *reinterpret_cast<volatile uint64_t *>(p) = v; }
+__device__ __forceinline__ uint64_t ld_volatile(const uint64_t *p) {
+    return *reinterpret_cast<const volatile uint64_t *>(p);
 }
 
-__global__ void __launch_bounds__(256) k_radix_up(const uint32_t *__restrict__ keys, NSrc ns, int shift,
-                                                  uint32_t *__restrict__ hist, uint32_t *__restrict__ mm, int first) {
-    __shared__ uint32_t s_h[8][256];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (!first && pass_is_constant(mm, shift)) return;
-    for (int k = threadIdx.x; k < 8 * 256; k += 256) (&s_h[0][0])[k] = 0;
+// Digit kernels that run: one per 8-bit digit below the highest bit where the
+// smallest and largest visible key differ, and always the first (it also
+// compacts the visible Gaussians).
+__device__ __forceinline__ int sort_passes(const Ctl *ctl) {
+    const uint32_t v = ctl->n_vis > 1 ? (~ctl->depth_mm[0]) ^ ctl->depth_mm[1] : 0u;
+    const int m = v ? (39 - __clz(v)) / 8 : 0;     // ceil((32 - clz) / 8)
+    return m > 1 ? m : 1;
+}
+
+// Exclusive prefix of counter c over the tiles before tile t (whose own count
+// `own` is already published as an aggregate unless t == 0); publishes the
+// inclusive prefix of tile t.  The predecessors are read kLookWindow at a time,
+// nearest first, so a walk over tiles that only hold aggregates costs one
+// memory latency per window instead of one per tile.
+constexpr int kLookWindow = 8;
+__device__ uint32_t look_back(uint64_t *status, uint32_t t, int c, uint32_t own, Ctl *ctl) {
+    uint32_t excl = 0;
+    int64_t j = static_cast<int64_t>(t) - 1;
+    uint32_t spins = 0;
+    while (j >= 0) {
+        uint64_t w[kLookWindow];
+#pragma unroll
+        for (int k = 0; k < kLookWindow; ++k)
+            w[k] = j - k >= 0 ? ld_volatile(status + static_cast<size_t>(j - k) * kLookCounters + c) : kLookIncl;
+        int used = 0;
+        bool incl = false, waiting = false;
+#pragma unroll
+        for (int k = 0; k < kLookWindow; ++k) {
+            if (incl || waiting) continue;
+            const uint64_t flag = w[k] & ~0xFFFFFFFFull;
+            if (flag == 0) {
+                waiting = true;
+                continue;
+            }
+            excl += static_cast<uint32_t>(w[k]);
+            ++used;
+            incl = flag == kLookIncl;
+        }
+        if (incl) break;
+        j -= used;
+        if (waiting) {
+            if (++spins > kSpinLimit) {
+                ctl->st.error = GS_ERR_TIMEOUT;
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    st_volatile(status + static_cast<size_t>(t) * kLookCounters + c, kLookIncl | (excl + own));
+    return excl;
+}
+
+template <class Src>
+__global__ void __launch_bounds__(256) k_sort_hist(Src src, uint32_t n, uint32_t *__restrict__ ghist, Ctl *ctl) {
+    __shared__ uint32_t s_h[4][256];
+    __shared__ uint32_t s_w[8];
+    const int lane = threadIdx.x & 31;
+    for (int k = threadIdx.x; k < 4 * 256; k += 256) (&s_h[0][0])[k] = 0;
     __syncthreads();
     uint32_t beg, end;
-    block_range(ns.get(), beg, end);
-    uint32_t kinv = 0, kmax = 0;
+    block_range(n, beg, end);
+    uint32_t kinv = 0, kmax = 0, cnt = 0;
     for (uint32_t t0 = beg; t0 < end; t0 += kSortTile) {
+        bool vis[kSortItems];
         uint32_t key[kSortItems];
 #pragma unroll
-        for (int r = 0; r < kSortItems; ++r) {        // issue all loads of the tile first
-            const uint32_t i = t0 + r * 256 + threadIdx.x;
-            key[r] = i < end ? keys[i] : 0;
-        }
-#pragma unroll
         for (int r = 0; r < kSortItems; ++r) {
             const uint32_t i = t0 + r * 256 + threadIdx.x;
-            const bool valid = i < end;
-            uint32_t d = 256u + lane;
-            if (valid) {
-                d = (key[r] >> shift) & 255u;
+            vis[r] = i < end && src.visible(i);
+        }
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) key[r] = vis[r] ? src.key(t0 + r * 256 + threadIdx.x) : 0u;
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            if (vis[r]) {
                 kinv = max(kinv, ~key[r]);
                 kmax = max(kmax, key[r]);
+                ++cnt;
             }
-            const unsigned peers = __match_any_sync(FULL, d);
-            if (valid && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&s_h[warp][d], __popc(peers));
+            const unsigned vm = __ballot_sync(FULL, vis[r]);
+            if (vm == 0) continue;
+            const int leader = __ffs(vm) - 1;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                // one atomic when the warp's visible keys share the digit (the high digits
+                // of depths in a narrow range), else one per key
+                const uint32_t d = (key[r] >> (8 * p)) & 255u;
+                const uint32_t dl = __shfl_sync(FULL, d, leader);
+                if (__all_sync(FULL, !vis[r] || d == dl)) {
+                    if (lane == leader) atomicAdd(&s_h[p][dl], __popc(vm));
+                } else if (vis[r]) {
+                    atomicAdd(&s_h[p][d], 1u);
+                }
+            }
         }
     }
-    if (first) {
-        kinv = __reduce_max_sync(FULL, kinv);
-        kmax = __reduce_max_sync(FULL, kmax);
-        if (lane == 0) {    // 0 is neutral for both maxima: warps without items change nothing
-            atomicMax(&mm[0], kinv);
-            atomicMax(&mm[1], kmax);
-        }
-    }
-    __syncthreads();
-    const int d = threadIdx.x;
-    uint32_t sum = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) sum += s_h[w][d];
-    hist[static_cast<size_t>(d) * gridDim.x + blockIdx.x] = sum;
-}
-
-// Per digit (one CTA each): exclusive scan of its G block counts in place and
-// the digit's total.
-__global__ void __launch_bounds__(256) k_radix_rowscan(uint32_t *__restrict__ hist, int G,
-                                                       uint32_t *__restrict__ rowtot, const uint32_t *__restrict__ mm,
-                                                       int shift, int first) {
-    __shared__ uint32_t s_w[8];
-    if (!first && pass_is_constant(mm, shift)) return;
-    uint32_t *row = hist + static_cast<size_t>(blockIdx.x) * G;
-    constexpr int per = kMaxSortBlocks / 256;
-    uint32_t v[per];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int k = 0; k < per; ++k) {
-        const int b = threadIdx.x * per + k;
-        v[k] = b < G ? row[b] : 0;
-        sum += v[k];
+    kinv = __reduce_max_sync(FULL, kinv);
+    kmax = __reduce_max_sync(FULL, kmax);
+    if (lane == 0) {        // 0 is neutral for both maxima
+        atomicMax(&ctl->depth_mm[0], kinv);
+        atomicMax(&ctl->depth_mm[1], kmax);
     }
     uint32_t tot;
-    uint32_t run = block_scan_256(sum, s_w, &tot);
-#pragma unroll
-    for (int k = 0; k < per; ++k) {
-        const int b = threadIdx.x * per + k;
-        if (b < G) row[b] = run;
-        run += v[k];
+    block_scan_256(cnt, s_w, &tot);
+    if (threadIdx.x == 0 && tot) {
+        atomicAdd(&ctl->n_vis, tot);
+        atomicAdd(&ctl->st.n_visible, tot);
     }
-    if (threadIdx.x == 0) rowtot[blockIdx.x] = tot;
+    for (int k = threadIdx.x; k < 4 * 256; k += 256) {
+        const uint32_t c = (&s_h[0][0])[k];
+        if (c) atomicAdd(&ghist[k], c);
+    }
 }
 
-// Stable scatter.  A block walks its range in tiles of 2048 items; warp w
-// ranks the contiguous run [256 w, 256 w + 256) of the tile in 8 rounds of 32
-// with warp-private digit counters, so items are ranked in (warp, round,
-// lane) = index order.  The tile is then sorted by digit in shared memory and
-// written out in that order, so consecutive threads store consecutive
-// addresses of the same digit's run.
-__global__ void __launch_bounds__(256) k_radix_down(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-                                                    uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, NSrc ns,
-                                                    int shift, const uint32_t *__restrict__ hist,
-                                                    const uint32_t *__restrict__ rowtot,
-                                                    const uint32_t *__restrict__ mm, int first) {
-    __shared__ uint32_t s_off[256];       // global offset of each digit for this block's next tile
+struct SortBufs {
+    const uint32_t *kin, *vin;       // digit kernels after the first: this pass's input
+    uint32_t *kout, *vout;           // the next digit kernel's input
+    uint32_t *final_out;             // Gaussian indices in depth order (last digit kernel)
+    uint32_t *vis_index;             // first digit kernel: visible indices in index order
+    const uint32_t *ghist;           // [4][256] digit histograms of the visible keys
+    uint64_t *status, *status_next;  // look-back words [tile][256] of this and the next pass
+};
+
+// One digit (bits 8 pass .. 8 pass + 7) of the stable LSD sort.  Warp w ranks
+// the contiguous run [256 w, 256 w + 256) of its tile in 8 rounds of 32 with
+// warp-private digit counters, so items are ranked in index order; the tile
+// is then sorted by digit in shared memory and written out in that order, so
+// consecutive threads store consecutive addresses of one digit's run.
+template <class Src, bool FIRST>
+__global__ void __launch_bounds__(256) k_sort_pass(Src src, uint32_t n_all, int pass, SortBufs B, Ctl *ctl) {
     __shared__ uint32_t s_wc[8][256];     // per-warp digit counts, then per-warp digit bases
     __shared__ uint32_t s_lstart[256];    // start of each digit's run in the locally sorted tile
+    __shared__ uint32_t s_off[256];       // global position of each digit's run
     __shared__ uint32_t s_key[kSortTile], s_val[kSortTile];
-    __shared__ uint32_t s_w[8];
+    __shared__ uint32_t s_w[8], s_vw[8];
+    __shared__ uint32_t s_ticket, s_visbase;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t beg, end;
-    block_range(ns.get(), beg, end);
-    if (!first && pass_is_constant(mm, shift)) {
-        for (uint32_t i = beg + threadIdx.x; i < end; i += 256) {
-            kout[i] = kin[i];
-            vout[i] = vin[i];
-        }
-        return;
-    }
-    {
-        uint32_t tot;
-        const uint32_t digit_base = block_scan_256(rowtot[threadIdx.x], s_w, &tot);
-        s_off[threadIdx.x] = digit_base + hist[static_cast<size_t>(threadIdx.x) * gridDim.x + blockIdx.x];
-    }
     const unsigned lt = (1u << lane) - 1u;
-    for (uint32_t t0 = beg; t0 < end; t0 += kSortTile) {
+    const int passes = sort_passes(ctl);
+    if (pass >= passes) return;
+    const bool last = pass == passes - 1;
+    const uint32_t n_vis = min(ctl->n_vis, n_all);
+    const uint32_t n = FIRST ? n_all : n_vis;
+    const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+    if (threadIdx.x == 0) s_ticket = atomicAdd(&ctl->sort_ticket[pass], 1u);
 #pragma unroll
-        for (int w = 0; w < 8; ++w) s_wc[w][threadIdx.x] = 0;
-        __syncthreads();
-        uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
-        const uint32_t run0 = t0 + warp * 256;
+    for (int w = 0; w < 8; ++w) s_wc[w][threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t t = s_ticket;
+    if (t >= ntiles) return;
+    if (!last && t < (n_vis + kSortTile - 1) / kSortTile)
+        for (int c = threadIdx.x; c < kLookCounters; c += 256)
+            B.status_next[static_cast<size_t>(t) * kLookCounters + c] = 0;
+    const int shift = 8 * pass;
+    const uint32_t run0 = t * kSortTile + warp * 256;
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems], vrank[kSortItems];
+    bool valid[kSortItems];
 #pragma unroll
-        for (int r = 0; r < kSortItems; ++r) {
-            const uint32_t i = run0 + r * 32 + lane;
-            key[r] = i < end ? kin[i] : 0u;
-            val[r] = i < end ? vin[i] : 0u;
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint32_t i = run0 + r * 32 + lane;
+        if constexpr (FIRST) {
+            valid[r] = i < n && src.visible(i);
+            val[r] = i;
+        } else {
+            valid[r] = i < n;
+            val[r] = valid[r] ? B.vin[i] : 0u;
         }
-#pragma unroll
-        for (int r = 0; r < kSortItems; ++r) {
-            const uint32_t i = run0 + r * 32 + lane;
-            const bool valid = i < end;
-            const uint32_t d = valid ? (key[r] >> shift) & 255u : 256u + lane;
-            const unsigned peers = __match_any_sync(FULL, d);
-            const uint32_t before = valid ? s_wc[warp][d] : 0;
-            rank[r] = before + __popc(peers & lt);
-            __syncwarp();
-            if (valid && (peers & lt) == 0) s_wc[warp][d] = before + __popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        // per digit d = thread: exclusive prefix over the warps and the tile total
-        const int d = threadIdx.x;
-        uint32_t acc = 0;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) {
-            const uint32_t c = s_wc[w][d];
-            s_wc[w][d] = acc;
-            acc += c;
-        }
-        uint32_t ntile;
-        s_lstart[d] = block_scan_256(acc, s_w, &ntile);
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < kSortItems; ++r) {
-            if (run0 + r * 32 + lane < end) {
-                const uint32_t dd = (key[r] >> shift) & 255u;
-                const uint32_t lpos = s_lstart[dd] + s_wc[warp][dd] + rank[r];
-                s_key[lpos] = key[r];
-                s_val[lpos] = val[r];
-            }
-        }
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < ntile; i += 256) {
-            const uint32_t k = s_key[i];
-            const uint32_t dd = (k >> shift) & 255u;
-            const uint32_t pos = s_off[dd] + (i - s_lstart[dd]);
-            kout[pos] = k;
-            vout[pos] = s_val[i];
-        }
-        __syncthreads();
-        s_off[d] += acc;
     }
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint32_t i = run0 + r * 32 + lane;
+        if constexpr (FIRST) key[r] = valid[r] ? src.key(i) : 0u;
+        else key[r] = valid[r] ? B.kin[i] : 0u;
+    }
+    uint32_t vw = 0;
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint32_t d = valid[r] ? (key[r] >> shift) & 255u : 256u + lane;
+        const unsigned peers = __match_any_sync(FULL, d);
+        const uint32_t before = valid[r] ? s_wc[warp][d] : 0;
+        rank[r] = before + __popc(peers & lt);
+        __syncwarp();
+        if (valid[r] && (peers & lt) == 0) s_wc[warp][d] = before + __popc(peers);
+        __syncwarp();
+        if constexpr (FIRST) {
+            const unsigned vb = __ballot_sync(FULL, valid[r]);
+            vrank[r] = vw + __popc(vb & lt);
+            vw += __popc(vb);
+        }
+    }
+    if constexpr (FIRST) {
+        if (lane == 0) s_vw[warp] = vw;
+    }
+    __syncthreads();
+    // per digit d = thread: exclusive prefix over the warps, the tile's count, and its publication
+    const int d = threadIdx.x;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const uint32_t c = s_wc[w][d];
+        s_wc[w][d] = acc;
+        acc += c;
+    }
+    st_volatile(B.status + static_cast<size_t>(t) * kLookCounters + d, (t == 0 ? kLookIncl : kLookAgg) | acc);
+    uint32_t ntile;
+    s_lstart[d] = block_scan_256(acc, s_w, &ntile);
+    uint32_t gtot;
+    const uint32_t gbase = block_scan_256(B.ghist[pass * 256 + d], s_w, &gtot);
+    const uint32_t excl = look_back(B.status, t, d, acc, ctl);
+    s_off[d] = gbase + excl;
+    if constexpr (FIRST) {
+        // the items of all digits in the tiles before this one are the visible Gaussians before it
+        uint32_t before;
+        block_scan_256(excl, s_w, &before);
+        if (d == 0) s_visbase = before;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        if (valid[r]) {
+            const uint32_t dd = (key[r] >> shift) & 255u;
+            const uint32_t lpos = s_lstart[dd] + s_wc[warp][dd] + rank[r];
+            s_key[lpos] = key[r];
+            s_val[lpos] = val[r];
+        }
+    }
+    if constexpr (FIRST) {
+        uint32_t vbase = s_visbase;
+        for (int w = 0; w < warp; ++w) vbase += s_vw[w];
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r)
+            if (valid[r]) B.vis_index[vbase + vrank[r]] = val[r];
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < ntile; i += 256) {
+        const uint32_t k = s_key[i];
+        const uint32_t dd = (k >> shift) & 255u;
+        const uint32_t pos = s_off[dd] + (i - s_lstart[dd]);
+        if (last) {
+            B.final_out[pos] = s_val[i];
+        } else {
+            B.kout[pos] = k;
+            B.vout[pos] = s_val[i];
+        }
+    }
+}
+
+template <class Src>
+cudaError_t sort_histograms(const Src &src, int n, const SortWork &w, Ctl *ctl, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const uint32_t nt = sort_tiles(n);
+    cudaError_t e = cudaMemsetAsync(w.ghist, 0, 4 * 256 * sizeof(uint32_t), st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(w.status, 0, static_cast<size_t>(nt) * kLookCounters * sizeof(uint64_t), st);
+    if (e != cudaSuccess) return e;
+    k_sort_hist<<<sort_blocks(), 256, 0, st>>>(src, static_cast<uint32_t>(n), w.ghist, ctl);
+    return cudaGetLastError();
+}
+
+template <class Src>
+cudaError_t sort_digits(const Src &src, int n, const SortWork &w, Ctl *ctl, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const uint32_t nt = sort_tiles(n);
+    uint32_t *A[2] = {w.keys[0], w.vals[0]}, *Bb[2] = {w.keys[1], w.vals[1]};
+    for (int p = 0; p < 4; ++p) {
+        SortBufs b;
+        uint32_t *const *in = (p & 1) ? A : Bb;       // pass p reads what pass p - 1 wrote
+        uint32_t *const *out = (p & 1) ? Bb : A;
+        b.kin = in[0];
+        b.vin = in[1];
+        b.kout = out[0];
+        b.vout = out[1];
+        b.final_out = w.order;
+        b.vis_index = w.vis_index;
+        b.ghist = w.ghist;
+        b.status = w.status + static_cast<size_t>(p) * nt * kLookCounters;
+        b.status_next = p < 3 ? b.status + static_cast<size_t>(nt) * kLookCounters : nullptr;
+        if (p == 0) k_sort_pass<Src, true><<<nt, 256, 0, st>>>(src, static_cast<uint32_t>(n), p, b, ctl);
+        else k_sort_pass<Src, false><<<nt, 256, 0, st>>>(src, static_cast<uint32_t>(n), p, b, ctl);
+    }
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -393,39 +500,30 @@ int sort_blocks() {
     return g;
 }
 
-cudaError_t launch_compact_visible(const uint32_t *tiles, const uint32_t *depth_key, int n, uint32_t *keys_out,
-                                   uint32_t *vals_out, uint32_t *partials, Ctl *ctl, cudaStream_t st) {
-    const int G = sort_blocks();
-    NSrc ns{nullptr, static_cast<uint32_t>(n)};
-    VisFlag f{tiles};
-    k_scan_reduce<<<G, 256, 0, st>>>(f, ns, partials);
-    k_scan_partials<<<1, 1024, 0, st>>>(partials, G, FIN_NVIS, ctl, 0, nullptr);
-    k_scan_down<<<G, 256, 0, st>>>(f, ns, partials, CompactOut{depth_key, keys_out, vals_out});
-    return cudaGetLastError();
+uint32_t sort_tiles(int64_t n) { return static_cast<uint32_t>((n + kSortTile - 1) / kSortTile); }
+
+size_t sort_status_bytes(int64_t n) {
+    return 4 * static_cast<size_t>(sort_tiles(n > 0 ? n : 1)) * kLookCounters * sizeof(uint64_t);
 }
 
-cudaError_t launch_compact_visible2(const uint32_t *tiles_a, const uint32_t *depth_a, const uint32_t *tiles_b,
-                                    const uint32_t *depth_b, int n, uint32_t *keys_out, uint32_t *vals_out,
-                                    uint32_t *partials, Ctl *ctl, cudaStream_t st) {
-    const int G = sort_blocks();
-    NSrc ns{nullptr, static_cast<uint32_t>(n)};
-    VisFlag2 f{tiles_a, tiles_b};
-    k_scan_reduce<<<G, 256, 0, st>>>(f, ns, partials);
-    k_scan_partials<<<1, 1024, 0, st>>>(partials, G, FIN_NVIS, ctl, 0, nullptr);
-    k_scan_down<<<G, 256, 0, st>>>(f, ns, partials, CompactOut2{tiles_a, depth_a, depth_b, keys_out, vals_out});
-    return cudaGetLastError();
+cudaError_t launch_sort_histograms(const uint32_t *tiles, const uint32_t *depth, int n, const SortWork &w, Ctl *ctl,
+                                   cudaStream_t st) {
+    return sort_histograms(VisSrc{tiles, depth}, n, w, ctl, st);
 }
 
-cudaError_t launch_radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
-                              const uint32_t *n_dev, uint32_t n_cap, int shift, uint32_t *hist, uint32_t *minmax,
-                              bool first, cudaStream_t st) {
-    const int G = sort_blocks();
-    NSrc ns{n_dev, n_cap};
-    uint32_t *rowtot = hist + static_cast<size_t>(256) * kMaxSortBlocks;
-    k_radix_up<<<G, 256, 0, st>>>(kin, ns, shift, hist, minmax, first ? 1 : 0);
-    k_radix_rowscan<<<256, 256, 0, st>>>(hist, G, rowtot, minmax, shift, first ? 1 : 0);
-    k_radix_down<<<G, 256, 0, st>>>(kin, vin, kout, vout, ns, shift, hist, rowtot, minmax, first ? 1 : 0);
-    return cudaGetLastError();
+cudaError_t launch_sort_digits(const uint32_t *tiles, const uint32_t *depth, int n, const SortWork &w, Ctl *ctl,
+                               cudaStream_t st) {
+    return sort_digits(VisSrc{tiles, depth}, n, w, ctl, st);
+}
+
+cudaError_t launch_sort_histograms2(const uint32_t *tiles_a, const uint32_t *depth_a, const uint32_t *tiles_b,
+                                    const uint32_t *depth_b, int n, const SortWork &w, Ctl *ctl, cudaStream_t st) {
+    return sort_histograms(VisSrc2{tiles_a, depth_a, tiles_b, depth_b}, n, w, ctl, st);
+}
+
+cudaError_t launch_sort_digits2(const uint32_t *tiles_a, const uint32_t *depth_a, const uint32_t *tiles_b,
+                                const uint32_t *depth_b, int n, const SortWork &w, Ctl *ctl, cudaStream_t st) {
+    return sort_digits(VisSrc2{tiles_a, depth_a, tiles_b, depth_b}, n, w, ctl, st);
 }
 
 cudaError_t launch_activity_prune(const float *activity, const uint8_t *layer, uint32_t train_mask, int n,

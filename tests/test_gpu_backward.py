@@ -110,3 +110,20 @@ def test_prune_edge_sizes():
         k_or, n_or = oracle.prune(cm.astype(np.float64), float(np.float32(0.005)))
         assert int(nk.item()) == n_or
         assert np.array_equal(keep.cpu().numpy(), k_or)
+
+
+@pytest.mark.parametrize("glm", [0xFFFFFFFF, 0b00101])
+def test_backward_overwrites_every_element(glm):
+    """Gradient buffers are outputs, not accumulators: with every element NaN
+    on entry, the backward leaves none (culled, frozen and live rows alike;
+    a scene size that is not a multiple of the 32-row zero blocks)."""
+    sc, cam, mask, planes, bg = WL["shells_ragged"]
+    assert sc.n % 32 != 0
+    ds, rast, img, al = gpu_render(sc, cam, mask, planes, bg)
+    dimg, dal = _upstream(cam.height, cam.width)
+    grads = {k: torch.full(p.shape, float("nan"), dtype=torch.float32, device="cuda")
+             for k, p in zip(FIELDS, ds.params())}
+    g = rast.backward(ds, cam, bg, torch.from_numpy(dimg).cuda(), torch.from_numpy(dal).cuda(), glm, grads=grads)
+    torch.cuda.synchronize()
+    for f in FIELDS:
+        assert bool(torch.isfinite(g[f]).all()), f

@@ -113,3 +113,35 @@ def test_image_sizes(W, H):
     sc = synth.shell_scene(rng, [3000, 2000], (0.8, 0.45), sh_degree=1)
     cam = synth.look_at_camera((0.2, -0.1, 3.4), width=W, height=H)
     _check(sc, cam, 0b11, [], (0.0, 0.5, 1.0))
+
+
+def _plane_scene(rng, n, depths, sh_degree=1):
+    """n Gaussians with means spread in x, y and their z from `depths`."""
+    m = np.stack([rng.uniform(-0.6, 0.6, n), rng.uniform(-0.6, 0.6, n), depths], 1).astype(np.float32)
+    K = (sh_degree + 1) ** 2
+    return Scene(m, rng.normal(-4.0, 0.4, (n, 3)).astype(np.float32),
+                 rng.standard_normal((n, 4)).astype(np.float32), rng.normal(0.0, 1.5, n).astype(np.float32),
+                 rng.normal(0, 0.3, (n, K, 3)).astype(np.float32), rng.integers(0, 2, n).astype(np.uint8), sh_degree)
+
+
+@pytest.mark.parametrize("kind", ["equal", "wide"])
+def test_depth_sort_digit_counts(kind):
+    """The depth sort runs one digit kernel per byte below the highest bit
+    where the smallest and largest key differ: all depths equal (only the
+    first, compacting kernel runs; ties stay in index order) and depths from
+    0.25 to 1000 (the keys differ in the top byte: all four run).  Several
+    2048-item sort tiles and a ragged last tile; lists bit-exact."""
+    rng = np.random.default_rng(17 if kind == "equal" else 18)
+    n = 9000
+    # camera on the +z axis looking at the origin: the depth of (x, y, z) is exactly 3 - z
+    if kind == "equal":
+        z = np.zeros(n)
+    else:
+        z = 3.0 - np.exp(rng.uniform(np.log(0.25), np.log(1000.0), n))
+    sc = _plane_scene(rng, n, z)
+    cam = synth.look_at_camera((0.0, 0.0, 3.0), width=96, height=80)
+    pre = _check(sc, cam, 0b11, [], (0.1, 0.1, 0.1))
+    d = pre["depth_f32"][pre["vis"] > 0].view(np.uint32) if "depth_f32" in pre else None
+    if d is not None:
+        span = int(d.min() ^ d.max())
+        assert (span == 0) if kind == "equal" else (span >> 24) != 0
