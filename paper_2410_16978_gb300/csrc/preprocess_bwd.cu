@@ -65,24 +65,68 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float *
 constexpr int kBwdThreads = 128;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
-// SH coefficients of Gaussian i as [k][channel]; 16-byte loads for float32
-// rows whose length is a multiple of 4 floats (SH degrees 1 and 3).
+// Everything the chain rule of Gaussian i reads, issued together before any
+// branch: the inline-PTX loads are volatile, so the compiler keeps them at
+// this point instead of moving them behind the visibility and layer tests.
 template <int K>
-__device__ __forceinline__ void load_sh(const SceneView &s, int i, float *v) {
+struct RowIn {
+    float4 ga, gb, gc;       // record gradient
+    float m[3], ol;
+    float ls[3], q[4];       // log-scales and quaternion, widened
+    float sh[3 * K];         // [k][channel]
+};
+
+__device__ __forceinline__ float4 ld_now4(const void *p) {
+    float4 v;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_now(const float *p) {
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+template <int K>
+__device__ __forceinline__ void load_row(const SceneView &s, int i, const float4 *rec_grad, RowIn<K> &r) {
+    r.ga = ld_now4(rec_grad + 3 * i);
+    r.gb = ld_now4(rec_grad + 3 * i + 1);
+    r.gc = ld_now4(rec_grad + 3 * i + 2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.m[k] = ld_now(s.means + 3 * static_cast<int64_t>(i) + k);
+    r.ol = ld_now(s.opacity_logit + i);
+    if (s.dtype_sr == GS_DTYPE_F32) {
+        const float *ls = static_cast<const float *>(s.log_scales) + 3 * static_cast<int64_t>(i);
+        const float *q = static_cast<const float *>(s.quats) + 4 * static_cast<int64_t>(i);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r.ls[k] = ld_now(ls + k);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) r.q[k] = ld_now(q + k);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r.ls[k] = ldv(s.log_scales, 3 * static_cast<int64_t>(i) + k, s.dtype_sr);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) r.q[k] = ldv(s.quats, 4 * static_cast<int64_t>(i) + k, s.dtype_sr);
+    }
     const int64_t base = static_cast<int64_t>(i) * 3 * K;
     if constexpr ((3 * K) % 4 == 0) {
         if (s.dtype_sh == GS_DTYPE_F32 && (reinterpret_cast<uintptr_t>(s.sh) & 15u) == 0) {
             const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(s.sh) + base);
 #pragma unroll
             for (int q = 0; q < 3 * K / 4; ++q) {
-                const float4 x = p[q];
-                v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+                const float4 x = ld_now4(p + q);
+                r.sh[4 * q] = x.x; r.sh[4 * q + 1] = x.y; r.sh[4 * q + 2] = x.z; r.sh[4 * q + 3] = x.w;
             }
             return;
         }
     }
+    if (s.dtype_sh == GS_DTYPE_F32) {
 #pragma unroll
-    for (int e = 0; e < 3 * K; ++e) v[e] = ldv(s.sh, base + e, s.dtype_sh);
+        for (int e = 0; e < 3 * K; ++e) r.sh[e] = ld_now(static_cast<const float *>(s.sh) + base + e);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 3 * K; ++e) r.sh[e] = ldv(s.sh, base + e, s.dtype_sh);
+    }
 }
 
 // A gradient row of W floats; 16-byte stores where the row allows them.
@@ -116,17 +160,17 @@ __device__ __forceinline__ void zero_rows(float *base, unsigned rows, int nrows,
 
 // The chain rule of one live Gaussian.
 template <int DEG>
-__device__ __forceinline__ void grad_one(const SceneView &s, const CamView &c, int i, const float4 *__restrict__ rec_grad,
+__device__ __forceinline__ void grad_one(const CamView &c, int i, const RowIn<(DEG + 1) * (DEG + 1)> &r,
                                          const gs_grads &g) {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    const float4 ga = rec_grad[3 * i], gb = rec_grad[3 * i + 1], gc = rec_grad[3 * i + 2];
+    const float4 ga = r.ga, gb = r.gb, gc = r.gc;
     const float dU = ga.x, dV = ga.y, dA2 = ga.z, dBeta = ga.w, dG2 = gb.x, dOp = gb.y;
     const float dRgb[3] = {gb.z, gb.w, gc.x};
-    const float mx = s.means[3 * i], my_ = s.means[3 * i + 1], mz = s.means[3 * i + 2];
+    const float mx = r.m[0], my_ = r.m[1], mz = r.m[2];
     const float *R = c.R;
 
     // opacity
-    const float o = 1.f / (1.f + expf(-s.opacity_logit[i]));
+    const float o = 1.f / (1.f + expf(-r.ol));
     g.opacity_logit[i] = dOp * o * (1.f - o);
 
     // colour and the view-direction part of d(mean)
@@ -139,8 +183,7 @@ __device__ __forceinline__ void grad_one(const SceneView &s, const CamView &c, i
     float b[K];
     float3 db[K];
     sh_basis_grad<DEG>(dx, dy, dz, b, db);
-    float shv[3 * K];
-    load_sh<K>(s, i, shv);
+    const float *shv = r.sh;
     float gch[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
@@ -170,10 +213,10 @@ __device__ __forceinline__ void grad_one(const SceneView &s, const CamView &c, i
     const float pz = R[6] * mx + R[7] * my_ + R[8] * mz + c.t[2];
     float sc[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) sc[k] = expf(ldv(s.log_scales, 3 * (int64_t)i + k, s.dtype_sr));
+    for (int k = 0; k < 3; ++k) sc[k] = expf(r.ls[k]);
     float q[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) q[k] = ldv(s.quats, 4 * (int64_t)i + k, s.dtype_sr);
+    for (int k = 0; k < 4; ++k) q[k] = r.q[k];
     const float iqn = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
     const float w = q[0] * iqn, x = q[1] * iqn, y = q[2] * iqn, z = q[3] * iqn;
     const float Rq[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
@@ -293,10 +336,14 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd(SceneView s, Cam
         const uint32_t p = blockIdx.x * kBwdThreads + threadIdx.x;
         if (p >= min(ctl->n_vis, static_cast<uint32_t>(s.n))) return;
         const int i = static_cast<int>(vis_index[p]);
-        if (tiles[i] == 0) return;              // a two-eye list also holds Gaussians only the other eye sees
-        if (contrib_sum) contrib_sum[i] += rec_grad[3 * i + 2].y;
-        if (!((grad_layer_mask >> s.layer[i]) & 1u)) return;   // frozen: a zero row
-        grad_one<DEG>(s, c, i, rec_grad, g);
+        const uint32_t tc = tiles[i];
+        const uint32_t ly = s.layer[i];
+        RowIn<K> r;
+        load_row<K>(s, i, rec_grad, r);
+        if (tc == 0) return;                    // a two-eye list also holds Gaussians only the other eye sees
+        if (contrib_sum) contrib_sum[i] += r.gc.y;
+        if (!((grad_layer_mask >> ly) & 1u)) return;   // frozen: a zero row
+        grad_one<DEG>(c, i, r, g);
         return;
     }
     const int lane = threadIdx.x & 31;
