@@ -4,12 +4,11 @@
 // the layered training (Sec. 3.2).  Gaussians that were culled or whose layer
 // is frozen (not in grad_layer_mask; Sec. 3.2: lower layers stay fixed) get 0.
 //
-// One launch with two roles.  The first blocks take the visible Gaussians
-// from the sort's index-ordered visible list, one thread each, so every warp
-// does the chain rule on 32 live Gaussians instead of the third of its lanes
-// that a pass over all indices would keep.  The other blocks write the zero
-// rows: a warp takes 32 consecutive Gaussians and stores zeros to the rows
-// that are not live, every array with coalesced stores.
+// The kernel takes the visible Gaussians from the sort's index-ordered visible
+// list, one thread each, so every warp does the chain rule on 32 live
+// Gaussians instead of the third of its lanes that a pass over all indices
+// would keep.  The zero rows of the other Gaussians are written by work items
+// of the backward compositor.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -63,7 +62,6 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float *
 }
 
 constexpr int kBwdThreads = 128;
-constexpr unsigned FULL = 0xFFFFFFFFu;
 
 // Everything the chain rule of Gaussian i reads, issued together before any
 // branch: the inline-PTX loads are volatile, so the compiler keeps them at
@@ -142,20 +140,6 @@ __device__ __forceinline__ void store_row(float *dst, const float *v) {
     }
 #pragma unroll
     for (int e = 0; e < W; ++e) dst[e] = v[e];
-}
-
-// Zeros of the rows r < nrows of a [32][W] block whose bit is set in `rows`.
-template <int W>
-__device__ __forceinline__ void zero_rows(float *base, unsigned rows, int nrows, int lane) {
-    if constexpr (W % 4 == 0) {
-        if ((reinterpret_cast<uintptr_t>(base) & 15u) == 0) {
-            for (int q = lane; q < nrows * (W / 4); q += 32)
-                if ((rows >> (q / (W / 4))) & 1u) reinterpret_cast<float4 *>(base)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            return;
-        }
-    }
-    for (int e = lane; e < nrows * W; e += 32)
-        if ((rows >> (e / W)) & 1u) base[e] = 0.f;
 }
 
 // The chain rule of one live Gaussian.
@@ -330,35 +314,19 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd(SceneView s, Cam
                                                                 const Ctl *__restrict__ ctl,
                                                                 const float4 *__restrict__ rec_grad,
                                                                 uint32_t grad_layer_mask, gs_grads g,
-                                                                float *__restrict__ contrib_sum, int live_blocks) {
+                                                                float *__restrict__ contrib_sum) {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    if (static_cast<int>(blockIdx.x) < live_blocks) {
-        const uint32_t p = blockIdx.x * kBwdThreads + threadIdx.x;
-        if (p >= min(ctl->n_vis, static_cast<uint32_t>(s.n))) return;
-        const int i = static_cast<int>(vis_index[p]);
-        const uint32_t tc = tiles[i];
-        const uint32_t ly = s.layer[i];
-        RowIn<K> r;
-        load_row<K>(s, i, rec_grad, r);
-        if (tc == 0) return;                    // a two-eye list also holds Gaussians only the other eye sees
-        if (contrib_sum) contrib_sum[i] += r.gc.y;
-        if (!((grad_layer_mask >> ly) & 1u)) return;   // frozen: a zero row
-        grad_one<DEG>(c, i, r, g);
-        return;
-    }
-    const int lane = threadIdx.x & 31;
-    const int64_t i0 = (static_cast<int64_t>(blockIdx.x - live_blocks) * (kBwdThreads / 32) + (threadIdx.x >> 5)) * 32;
-    if (i0 >= s.n) return;
-    const int nrows = s.n - i0 < 32 ? static_cast<int>(s.n - i0) : 32;
-    const int64_t i = i0 + lane;
-    const bool live = lane < nrows && tiles[i] > 0 && ((grad_layer_mask >> s.layer[i]) & 1u);
-    const unsigned rows = ~__ballot_sync(FULL, live);
-    if ((rows & (nrows == 32 ? FULL : (1u << nrows) - 1u)) == 0) return;
-    zero_rows<3>(g.means + 3 * i0, rows, nrows, lane);
-    zero_rows<3>(g.log_scales + 3 * i0, rows, nrows, lane);
-    zero_rows<4>(g.quats + 4 * i0, rows, nrows, lane);
-    zero_rows<1>(g.opacity_logit + i0, rows, nrows, lane);
-    zero_rows<3 * K>(g.sh + 3 * K * i0, rows, nrows, lane);
+    const uint32_t p = blockIdx.x * kBwdThreads + threadIdx.x;
+    if (p >= min(ctl->n_vis, static_cast<uint32_t>(s.n))) return;
+    const int i = static_cast<int>(vis_index[p]);
+    const uint32_t tc = tiles[i];
+    const uint32_t ly = s.layer[i];
+    RowIn<K> r;
+    load_row<K>(s, i, rec_grad, r);
+    if (tc == 0) return;                        // a two-eye list also holds Gaussians only the other eye sees
+    if (contrib_sum) contrib_sum[i] += r.gc.y;
+    if (!((grad_layer_mask >> ly) & 1u)) return;   // frozen: a zero row
+    grad_one<DEG>(c, i, r, g);
 }
 
 }  // namespace
@@ -368,11 +336,9 @@ cudaError_t launch_preprocess_backward(const SceneView &s, const CamView &c, con
                                        uint32_t grad_layer_mask, const gs_grads &g, float *contrib_sum,
                                        cudaStream_t st) {
     if (s.n == 0) return cudaSuccess;
-    const int live_blocks = (s.n + kBwdThreads - 1) / kBwdThreads;          // the visible list is at most n long
-    const int zero_blocks = (s.n + kBwdThreads - 1) / kBwdThreads;          // 32 Gaussians per warp
-    const int blocks = live_blocks + zero_blocks;
+    const int blocks = (s.n + kBwdThreads - 1) / kBwdThreads;      // the visible list is at most n long
 #define GS_PBWD(D) k_preprocess_bwd<D><<<blocks, kBwdThreads, 0, st>>>(s, c, tiles, vis_index, ctl, rec_grad, \
-                                                                       grad_layer_mask, g, contrib_sum, live_blocks)
+                                                                       grad_layer_mask, g, contrib_sum)
     switch (s.sh_degree) {
         case 0: GS_PBWD(0); break;
         case 1: GS_PBWD(1); break;
