@@ -423,61 +423,6 @@ __device__ __forceinline__ float reduce_scatter10(const float v[10], int lane) {
     return e + __shfl_xor_sync(FULL, e, 1);
 }
 
-// Zero gradient rows.  The gradients of the Gaussians that are not live
-// (culled, or in a frozen layer) are zeros.  They are written by extra work
-// items spread evenly through the backward compositor's queue: the
-// compositor is bound by instruction issue and moves little memory, so while
-// a warp waits on a zero item's loads and stores the other warps keep the
-// issue slots busy, and the 236 B of stores per Gaussian (SH degree 3) cost
-// little beyond their own instructions.  An item covers kZeroRows
-// consecutive Gaussians, 32 per step.
-constexpr int kZeroRows = 256;
-
-// Stores `zero` to the words of the rows r < nrows of a [32][w] block whose
-// bit is set in `rows`, one warp, 32 consecutive words per step.  The row of
-// word q is (q m) >> 20 with m = 2^20 / w + 1, exact for q < 32 w and w < 181.
-template <class V>
-__device__ __forceinline__ void zero_rows(V *base, int w, uint32_t m, unsigned rows, int nrows, int lane, V zero) {
-    const int total = nrows * w;
-    for (int q = lane; q < total; q += 32)
-        if ((rows >> ((static_cast<uint32_t>(q) * m) >> 20)) & 1u) base[q] = zero;
-}
-
-__device__ __forceinline__ void zero_item(const ZeroRows &zr, uint32_t z, const uint8_t *__restrict__ layer,
-                                          uint32_t mask, int lane) {
-    constexpr int kSteps = kZeroRows / 32;
-    constexpr uint32_t m1 = (1u << 20) + 1, m3 = (1u << 20) / 3 + 1, m4 = (1u << 20) / 4 + 1;
-    const int64_t r0 = static_cast<int64_t>(z) * kZeroRows;
-    uint32_t tc[kSteps], ly[kSteps];
-#pragma unroll
-    for (int k = 0; k < kSteps; ++k) {     // every liveness load of the item first
-        const int64_t i = r0 + 32 * k + lane;
-        tc[k] = i < zr.n ? zr.tiles[i] : 1u;
-        ly[k] = i < zr.n ? layer[i] : 0u;
-    }
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < kSteps; ++k) {
-        const int64_t i0 = r0 + 32 * k;
-        if (i0 >= zr.n) break;
-        const int nrows = zr.n - i0 < 32 ? static_cast<int>(zr.n - i0) : 32;
-        const bool live = tc[k] > 0 && ((mask >> ly[k]) & 1u);
-        unsigned rows = ~__ballot_sync(FULL, live);
-        if (nrows < 32) rows &= (1u << nrows) - 1u;
-        if (rows == 0) continue;
-        zero_rows(zr.means + 3 * i0, 3, m3, rows, nrows, lane, 0.f);
-        zero_rows(zr.log_scales + 3 * i0, 3, m3, rows, nrows, lane, 0.f);
-        if (zr.vec_q) zero_rows(reinterpret_cast<float4 *>(zr.quats + 4 * i0), 1, m1, rows, nrows, lane, z4);
-        else zero_rows(zr.quats + 4 * i0, 4, m4, rows, nrows, lane, 0.f);
-        zero_rows(zr.opacity + i0, 1, m1, rows, nrows, lane, 0.f);
-        if (zr.vec_sh)
-            zero_rows(reinterpret_cast<float4 *>(zr.sh + static_cast<int64_t>(zr.sh_row) * i0), zr.sh_w, zr.sh_m,
-                      rows, nrows, lane, z4);
-        else
-            zero_rows(zr.sh + static_cast<int64_t>(zr.sh_row) * i0, zr.sh_w, zr.sh_m, rows, nrows, lane, 0.f);
-    }
-}
-
 // Backward, back to front within a segment.  With
 //   S_i = sum_{j>i} c_j a_j T_j + T_N bg   (T_j: transmittance before splat j)
 //   dL/da_i = T_i (dC.c_i) - (dC.S_i - dA T_N) / (1 - a_i).
@@ -491,18 +436,17 @@ __device__ __forceinline__ void zero_item(const ZeroRows &zr, uint32_t z, const 
 // accuracy (a running total minus a prefix would not).
 //
 // Each splat's 10 sums are reduce-scattered over the warp and added to the
-// record gradient, float 12 g + i for value i, by ten lanes at once (every
-// zstride-th queue position is a zero-row item instead):
+// record gradient, float 12 g + i for value i, by ten lanes at once:
 //   (du, dv, dA2, dbeta, dG2, dopacity, dr, dg, db, sum of alpha*T);
 //   contrib_max[g] = max(.., alpha*T)
 template <int PX>
-__global__ void __launch_bounds__(kBwdThreads, 6) k_composite_bwd(
+__global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
     const uint2 *__restrict__ items, const uint32_t *__restrict__ n_items, uint32_t *__restrict__ queue,
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ list, const Rec *__restrict__ rec, int W, int H,
     int Tx, float3 bg, const float *__restrict__ t_final, const uint32_t *__restrict__ n_contrib,
     const uint32_t *__restrict__ seg_base, const float4 *__restrict__ ckpt, const uint32_t *__restrict__ qwork,
     const float *__restrict__ dL_dimage, const float *__restrict__ dL_dalpha, const uint8_t *__restrict__ layer,
-    uint32_t grad_layer_mask, float4 *__restrict__ rec_grad, float *__restrict__ contrib_max, const ZeroRows zr) {
+    uint32_t grad_layer_mask, float4 *__restrict__ rec_grad, float *__restrict__ contrib_max) {
     __shared__ float4 s_a[kBwdThreads / 32][32], s_b[kBwdThreads / 32][32];
     __shared__ float s_c[kBwdThreads / 32][32];
     __shared__ uint32_t s_g[kBwdThreads / 32][32];
@@ -512,20 +456,12 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_composite_bwd(
     const int own = reduce10_owner(lane);
     const bool writer = reduce10_writer(lane);
     const uint32_t total = *n_items;
-    // zero item z sits at queue position z S + S - 1, S = floor((total + items) / items) >= 1, so all of them
-    // come before position total + items and the compositing items keep their order in between
-    const uint32_t zstride = zr.items ? (total + zr.items) / zr.items : 0xFFFFFFFFu;
     const size_t plane = static_cast<size_t>(W) * H;
     for (;;) {
         uint32_t id = 0;
         if (lane == 0) id = atomicAdd(queue, 1u);
         id = __shfl_sync(FULL, id, 0);
-        if (id >= total + zr.items) break;
-        if (id % zstride == zstride - 1 && id / zstride < zr.items) {
-            zero_item(zr, id / zstride, layer, grad_layer_mask, lane);
-            continue;
-        }
-        id -= min(zr.items, (id + 1) / zstride);      // zero items before this position
+        if (id >= total) break;
         const uint2 it = items[id];
         const int tile = static_cast<int>(it.x);
         const int q = static_cast<int>(it.y >> 24);
@@ -691,22 +627,16 @@ cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *rang
                                       const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
                                       const uint32_t *n_contrib, const float *dL_dimage,
                                       const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
-                                      float4 *rec_grad, float *contrib_max, const ZeroRows &zero, cudaStream_t st) {
+                                      float4 *rec_grad, float *contrib_max, cudaStream_t st) {
     const int tiles = Tx * Ty;
     if (tiles == 0) return cudaSuccess;
-    ZeroRows zr = zero;
-    zr.items = static_cast<uint32_t>((static_cast<int64_t>(zr.n) + kZeroRows - 1) / kZeroRows);
-    zr.vec_q = (reinterpret_cast<uintptr_t>(zr.quats) & 15u) == 0;
-    zr.vec_sh = zr.sh_row % 4 == 0 && (reinterpret_cast<uintptr_t>(zr.sh) & 15u) == 0;
-    zr.sh_w = zr.vec_sh ? zr.sh_row / 4 : zr.sh_row;
-    zr.sh_m = (1u << 20) / static_cast<uint32_t>(zr.sh_w) + 1;
     k_bwd_setup<kBwdPx><<<1, 1024, 0, st>>>(cb.qwork, tiles, cb.order_bwd, cb.items, cb.n_items, cb.queue);
     static int blocks = 0;
     if (!blocks) blocks = persistent_blocks(k_composite_bwd<kBwdPx>, kBwdThreads);
     k_composite_bwd<kBwdPx><<<blocks, kBwdThreads, 0, st>>>(cb.items, cb.n_items, cb.queue, ranges, list, rec, W, H, Tx, bg,
                                                     t_final, n_contrib, cb.seg_base, cb.ckpt, cb.qwork,
                                                     dL_dimage, dL_dalpha, layer, grad_layer_mask, rec_grad,
-                                                    contrib_max, zr);
+                                                    contrib_max);
     return cudaGetLastError();
 }
 

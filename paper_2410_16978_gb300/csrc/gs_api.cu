@@ -504,12 +504,7 @@ int gs_render_backward(const gs_scene *scene, const gs_camera *camera, const flo
                                                    at<Rec>(ws, L.rec), cv.W, cv.H, cv.Tx, cv.Ty,
                                                    make_float3(bg[0], bg[1], bg[2]), at<float>(ws, L.t_final),
                                                    at<uint32_t>(ws, L.n_contrib), dL_dimage,
-                                                   dL_dalpha, sv.layer, grad_layer_mask, rec_grad, contrib_max,
-                                                   ZeroRows{grads->means, grads->log_scales, grads->quats,
-                                                            grads->opacity_logit, grads->sh, at<uint32_t>(ws, L.tiles),
-                                                            sv.n, 3 * (sv.sh_degree + 1) * (sv.sh_degree + 1), 0,
-                                                            false, false, 0, 0},
-                                                   st),
+                                                   dL_dalpha, sv.layer, grad_layer_mask, rec_grad, contrib_max, st),
                          "composite backward")) != GS_OK)
         return rc;
     }

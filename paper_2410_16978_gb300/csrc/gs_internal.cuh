@@ -111,7 +111,6 @@ cudaError_t launch_preprocess(const SceneView &s, const CamView &c, uint32_t lay
 // contrib_sum when it is not null.
 // vis_index: the visible list of the last render (index order, ctl->n_vis
 // entries; a two-eye list may also hold Gaussians this view does not see).
-// Writes the rows of the live Gaussians only (see ZeroRows).
 cudaError_t launch_preprocess_backward(const SceneView &s, const CamView &c, const uint32_t *tiles,
                                        const uint32_t *vis_index, const Ctl *ctl, const float4 *rec_grad,
                                        uint32_t grad_layer_mask, const gs_grads &g, float *contrib_sum,
@@ -221,24 +220,10 @@ cudaError_t launch_fwd_setup(const CompositeBufs &cb, const uint2 *ranges, int T
 // Composites n <= kMaxBatch views with one persistent launch; `queue` must
 // have been zeroed on the stream (launch_fwd_setup of any view does).
 cudaError_t launch_composite_forward(const FwdJob *jobs, int n, uint32_t *queue, cudaStream_t st);
-// The gradient rows of the Gaussians that are not live (tiles[i] == 0 or layer
-// not in the mask) are set to zero by work items of the backward compositor;
-// the preprocess backward writes the live rows.
-struct ZeroRows {
-    float *means, *log_scales, *quats, *opacity, *sh;
-    const uint32_t *tiles;
-    int n;
-    int sh_row;          // 3K floats per SH gradient row
-    // set by the launch: item count, 16-byte stores, SH row in stored words and its reciprocal
-    uint32_t items;
-    bool vec_q, vec_sh;
-    int sh_w;
-    uint32_t sh_m;
-};
 cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *ranges, const uint32_t *list,
                                       const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
                                       const uint32_t *n_contrib, const float *dL_dimage,
                                       const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
-                                      float4 *rec_grad, float *contrib_max, const ZeroRows &zero, cudaStream_t st);
+                                      float4 *rec_grad, float *contrib_max, cudaStream_t st);
 
 }  // namespace gs

@@ -4,11 +4,14 @@
 // the layered training (Sec. 3.2).  Gaussians that were culled or whose layer
 // is frozen (not in grad_layer_mask; Sec. 3.2: lower layers stay fixed) get 0.
 //
-// The kernel takes the visible Gaussians from the sort's index-ordered visible
-// list, one thread each, so every warp does the chain rule on 32 live
-// Gaussians instead of the third of its lanes that a pass over all indices
-// would keep.  The zero rows of the other Gaussians are written by work items
-// of the backward compositor.
+// One launch, two kinds of block.  Live blocks take the visible Gaussians
+// from the sort's index-ordered visible list, one thread each, so every warp
+// does the chain rule on 32 live Gaussians instead of the third of its lanes
+// that a pass over all indices would keep; they are bound by memory latency.
+// Zero blocks give each warp 256 consecutive Gaussians and store zeros to the
+// rows that are not live, 32 rows at a time with coalesced stores; they are
+// bound by store bandwidth.  The zero blocks are spread evenly among the live
+// blocks that have work, so the two kinds share the GPU for the whole launch.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -140,6 +143,69 @@ __device__ __forceinline__ void store_row(float *dst, const float *v) {
     }
 #pragma unroll
     for (int e = 0; e < W; ++e) dst[e] = v[e];
+}
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// The gradient rows of the Gaussians that are not live (tiles[i] == 0 or
+// layer not in the mask): the arrays, and per launch the zero-block count,
+// whether 16-byte stores apply, the SH row in stored words and its reciprocal.
+struct ZeroRows {
+    float *means, *log_scales, *quats, *opacity, *sh;
+    const uint32_t *tiles;
+    int n;
+    int sh_row;          // 3K floats per SH gradient row
+    uint32_t items;
+    bool vec_q, vec_sh;
+    int sh_w;
+    uint32_t sh_m;
+};
+
+constexpr int kZeroRows = 256;             // Gaussians per zero-block warp
+
+// Stores `zero` to the words of the rows r < nrows of a [32][w] block whose
+// bit is set in `rows`, one warp, 32 consecutive words per step.  The row of
+// word q is (q m) >> 20 with m = 2^20 / w + 1, exact for q < 32 w and w < 181.
+template <class V>
+__device__ __forceinline__ void zero_rows(V *base, int w, uint32_t m, unsigned rows, int nrows, int lane, V zero) {
+    const int total = nrows * w;
+    for (int q = lane; q < total; q += 32)
+        if ((rows >> ((static_cast<uint32_t>(q) * m) >> 20)) & 1u) base[q] = zero;
+}
+
+__device__ __forceinline__ void zero_item(const ZeroRows &zr, uint32_t z, const uint8_t *__restrict__ layer,
+                                          uint32_t mask, int lane) {
+    constexpr int kSteps = kZeroRows / 32;
+    constexpr uint32_t m1 = (1u << 20) + 1, m3 = (1u << 20) / 3 + 1, m4 = (1u << 20) / 4 + 1;
+    const int64_t r0 = static_cast<int64_t>(z) * kZeroRows;
+    uint32_t tc[kSteps], ly[kSteps];
+#pragma unroll
+    for (int k = 0; k < kSteps; ++k) {     // every liveness load of the item first
+        const int64_t i = r0 + 32 * k + lane;
+        tc[k] = i < zr.n ? zr.tiles[i] : 1u;
+        ly[k] = i < zr.n ? layer[i] : 0u;
+    }
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < kSteps; ++k) {
+        const int64_t i0 = r0 + 32 * k;
+        if (i0 >= zr.n) break;
+        const int nrows = zr.n - i0 < 32 ? static_cast<int>(zr.n - i0) : 32;
+        const bool live = tc[k] > 0 && ((mask >> ly[k]) & 1u);
+        unsigned rows = ~__ballot_sync(FULL, live);
+        if (nrows < 32) rows &= (1u << nrows) - 1u;
+        if (rows == 0) continue;
+        zero_rows(zr.means + 3 * i0, 3, m3, rows, nrows, lane, 0.f);
+        zero_rows(zr.log_scales + 3 * i0, 3, m3, rows, nrows, lane, 0.f);
+        if (zr.vec_q) zero_rows(reinterpret_cast<float4 *>(zr.quats + 4 * i0), 1, m1, rows, nrows, lane, z4);
+        else zero_rows(zr.quats + 4 * i0, 4, m4, rows, nrows, lane, 0.f);
+        zero_rows(zr.opacity + i0, 1, m1, rows, nrows, lane, 0.f);
+        if (zr.vec_sh)
+            zero_rows(reinterpret_cast<float4 *>(zr.sh + static_cast<int64_t>(zr.sh_row) * i0), zr.sh_w, zr.sh_m,
+                      rows, nrows, lane, z4);
+        else
+            zero_rows(zr.sh + static_cast<int64_t>(zr.sh_row) * i0, zr.sh_w, zr.sh_m, rows, nrows, lane, 0.f);
+    }
 }
 
 // The chain rule of one live Gaussian.
@@ -314,9 +380,18 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd(SceneView s, Cam
                                                                 const Ctl *__restrict__ ctl,
                                                                 const float4 *__restrict__ rec_grad,
                                                                 uint32_t grad_layer_mask, gs_grads g,
-                                                                float *__restrict__ contrib_sum) {
+                                                                float *__restrict__ contrib_sum, const ZeroRows zr) {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    const uint32_t p = blockIdx.x * kBwdThreads + threadIdx.x;
+    const uint32_t nl = (min(ctl->n_vis, static_cast<uint32_t>(s.n)) + kBwdThreads - 1) / kBwdThreads;
+    const uint32_t stride = zr.items ? (nl + zr.items) / zr.items : 0xFFFFFFFFu;
+    uint32_t b = blockIdx.x;
+    if (b % stride == stride - 1 && b / stride < zr.items) {
+        const uint32_t z = (b / stride) * (kBwdThreads / 32) + (threadIdx.x >> 5);
+        if (static_cast<int64_t>(z) * kZeroRows < s.n) zero_item(zr, z, s.layer, grad_layer_mask, threadIdx.x & 31);
+        return;
+    }
+    b -= min(zr.items, (b + 1) / stride);
+    const uint32_t p = b * kBwdThreads + threadIdx.x;
     if (p >= min(ctl->n_vis, static_cast<uint32_t>(s.n))) return;
     const int i = static_cast<int>(vis_index[p]);
     const uint32_t tc = tiles[i];
@@ -336,9 +411,17 @@ cudaError_t launch_preprocess_backward(const SceneView &s, const CamView &c, con
                                        uint32_t grad_layer_mask, const gs_grads &g, float *contrib_sum,
                                        cudaStream_t st) {
     if (s.n == 0) return cudaSuccess;
-    const int blocks = (s.n + kBwdThreads - 1) / kBwdThreads;      // the visible list is at most n long
+    ZeroRows zr{g.means, g.log_scales, g.quats, g.opacity_logit, g.sh, tiles, s.n,
+                3 * (s.sh_degree + 1) * (s.sh_degree + 1), 0, false, false, 0, 0};
+    const int64_t zitems = (static_cast<int64_t>(s.n) + kZeroRows - 1) / kZeroRows;
+    zr.items = static_cast<uint32_t>((zitems + kBwdThreads / 32 - 1) / (kBwdThreads / 32));   // zero blocks
+    zr.vec_q = (reinterpret_cast<uintptr_t>(zr.quats) & 15u) == 0;
+    zr.vec_sh = zr.sh_row % 4 == 0 && (reinterpret_cast<uintptr_t>(zr.sh) & 15u) == 0;
+    zr.sh_w = zr.vec_sh ? zr.sh_row / 4 : zr.sh_row;
+    zr.sh_m = (1u << 20) / static_cast<uint32_t>(zr.sh_w) + 1;
+    const int blocks = (s.n + kBwdThreads - 1) / kBwdThreads + static_cast<int>(zr.items);
 #define GS_PBWD(D) k_preprocess_bwd<D><<<blocks, kBwdThreads, 0, st>>>(s, c, tiles, vis_index, ctl, rec_grad, \
-                                                                       grad_layer_mask, g, contrib_sum)
+                                                                       grad_layer_mask, g, contrib_sum, zr)
     switch (s.sh_degree) {
         case 0: GS_PBWD(0); break;
         case 1: GS_PBWD(1); break;
