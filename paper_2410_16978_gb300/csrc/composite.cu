@@ -172,6 +172,7 @@ struct Chunk {
     float4 a, b;
     float c;
     uint32_t g;
+    uint32_t ly;      // backward: the splat's layer, consumed one chunk later
 };
 
 __device__ __forceinline__ void fetch_chunk(const uint32_t *__restrict__ list, const Rec *__restrict__ rec,
@@ -183,6 +184,14 @@ __device__ __forceinline__ void fetch_chunk(const uint32_t *__restrict__ list, c
         ch.b = r->b;
         ch.c = r->c.x;
     }
+}
+
+// The backward also needs each splat's layer (frozen layers get no gradient).
+__device__ __forceinline__ void fetch_chunk_layer(const uint32_t *__restrict__ list, const Rec *__restrict__ rec,
+                                                  const uint8_t *__restrict__ layer, uint32_t pos, uint32_t end,
+                                                  Chunk &ch) {
+    fetch_chunk(list, rec, pos, end, ch);
+    if (pos < end) ch.ly = layer[ch.g];
 }
 
 // The record of an id loaded one chunk earlier: list and record loads of a
@@ -511,7 +520,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
         }
         const uint32_t nchunk = (s1 - s0 + 31) / 32;
         Chunk nxt;
-        if (nchunk) fetch_chunk(list, rec, s0 + (nchunk - 1) * 32 + lane, s1, nxt);
+        if (nchunk) fetch_chunk_layer(list, rec, layer, s0 + (nchunk - 1) * 32 + lane, s1, nxt);
         for (uint32_t c = nchunk; c-- > 0;) {
             const uint32_t base = s0 + c * 32;
             const bool keep =
@@ -523,11 +532,11 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
                 s_a[warp][slot] = nxt.a;
                 s_b[warp][slot] = nxt.b;
                 s_c[warp][slot] = nxt.c;
-                s_g[warp][slot] = nxt.g;
+                s_g[warp][slot] = nxt.g | (((grad_layer_mask >> nxt.ly) & 1u) << 31);   // bit 31: trainable
                 s_pos[warp][slot] = base + lane - rg.x;
             }
             __syncwarp();
-            if (c > 0) fetch_chunk(list, rec, base - 32 + lane, s1, nxt);
+            if (c > 0) fetch_chunk_layer(list, rec, layer, base - 32 + lane, s1, nxt);
             const int cnt = __popc(km);
             for (int k = cnt - 1; k >= 0; --k) {
                 const uint32_t pos = s_pos[warp][k];
@@ -574,8 +583,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
                 }
                 const float sv = reduce_scatter10(v, lane);
                 const uint32_t smx = __reduce_max_sync(FULL, __float_as_uint(wmx));
-                const uint32_t g = s_g[warp][k];
-                const bool train = (grad_layer_mask >> layer[g]) & 1u;
+                const uint32_t gt = s_g[warp][k];
+                const uint32_t g = gt & 0x7FFFFFFFu;
+                const bool train = gt >> 31;
                 // value i is float 12 g + i of the record gradient: one atomic per value, one instruction
                 if (writer && (train || own == 9))
                     atomicAdd(reinterpret_cast<float *>(rec_grad) + 12 * static_cast<size_t>(g) + own, sv);

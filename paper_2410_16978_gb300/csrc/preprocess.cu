@@ -80,6 +80,22 @@ __global__ void __launch_bounds__(128) k_preprocess(SceneView s, CamView c, uint
     uint32_t dkey = 0xFFFFFFFFu;
     const int lay = s.layer[i];
     const float mx = s.means[3 * i], my = s.means[3 * i + 1], mz = s.means[3 * i + 2];
+    // the other per-Gaussian inputs but SH, loaded with these before the culling tests so that one memory
+    // latency covers them all
+    const float ls0 = ld_half(s.log_scales, 3 * (int64_t)i, s.dtype_sr);
+    const float ls1 = ld_half(s.log_scales, 3 * (int64_t)i + 1, s.dtype_sr);
+    const float ls2 = ld_half(s.log_scales, 3 * (int64_t)i + 2, s.dtype_sr);
+    float qw, qx, qy, qz;
+    if (s.dtype_sr == GS_DTYPE_F32) {
+        const float4 q = reinterpret_cast<const float4 *>(s.quats)[i];
+        qw = q.x; qx = q.y; qy = q.z; qz = q.w;
+    } else {
+        qw = ld_half(s.quats, 4 * (int64_t)i, s.dtype_sr);
+        qx = ld_half(s.quats, 4 * (int64_t)i + 1, s.dtype_sr);
+        qy = ld_half(s.quats, 4 * (int64_t)i + 2, s.dtype_sr);
+        qz = ld_half(s.quats, 4 * (int64_t)i + 3, s.dtype_sr);
+    }
+    const float ol = s.opacity_logit[i];
     bool keep = (layer_mask >> lay) & 1u;
     for (int k = 0; k < pl.n && keep; ++k) {
         if (!((pl.bits[k] >> lay) & 1u)) continue;
@@ -93,19 +109,9 @@ __global__ void __launch_bounds__(128) k_preprocess(SceneView s, CamView c, uint
     if (keep) {
         const float px = ((R[0] * mx + R[1] * my) + R[2] * mz) + c.t[0];
         const float py = ((R[3] * mx + R[4] * my) + R[5] * mz) + c.t[1];
-        const float s0 = exp_cw(ld_half(s.log_scales, 3 * (int64_t)i, s.dtype_sr));
-        const float s1 = exp_cw(ld_half(s.log_scales, 3 * (int64_t)i + 1, s.dtype_sr));
-        const float s2 = exp_cw(ld_half(s.log_scales, 3 * (int64_t)i + 2, s.dtype_sr));
-        float qw, qx, qy, qz;
-        if (s.dtype_sr == GS_DTYPE_F32) {
-            const float4 q = reinterpret_cast<const float4 *>(s.quats)[i];
-            qw = q.x; qx = q.y; qy = q.z; qz = q.w;
-        } else {
-            qw = ld_half(s.quats, 4 * (int64_t)i, s.dtype_sr);
-            qx = ld_half(s.quats, 4 * (int64_t)i + 1, s.dtype_sr);
-            qy = ld_half(s.quats, 4 * (int64_t)i + 2, s.dtype_sr);
-            qz = ld_half(s.quats, 4 * (int64_t)i + 3, s.dtype_sr);
-        }
+        const float s0 = exp_cw(ls0);
+        const float s1 = exp_cw(ls1);
+        const float s2 = exp_cw(ls2);
         const float qq = ((qw * qw + qx * qx) + qy * qy) + qz * qz;
         const float qn = sqrtf(qq);
         const float w = qw / qn, x = qx / qn, y = qy / qn, z = qz / qn;
@@ -209,7 +215,7 @@ __global__ void __launch_bounds__(128) k_preprocess(SceneView s, CamView c, uint
                 const float NHL = -0x1.715476p-1f;   // -log2(e)/2
                 Rec o;
                 o.a = make_float4(uu, vv, (c11 / det) * NHL, -(c01 / c11));
-                const float opac = 1.0f / (1.0f + exp_cw(-s.opacity_logit[i]));
+                const float opac = 1.0f / (1.0f + exp_cw(-ol));
                 o.b = make_float4(NHL / c11, opac, rgb[0], rgb[1]);
                 o.c = make_float4(rgb[2], pz, __uint_as_float(static_cast<uint32_t>(x0) | (static_cast<uint32_t>(y0) << 16)),
                                   __uint_as_float(static_cast<uint32_t>(x1) | (static_cast<uint32_t>(y1) << 16)));

@@ -12,7 +12,7 @@ import torch
 import oracle
 import synth
 from synth import Scene
-from tests.gpu_util import compare_image, compare_lists, compare_records, gpu_render, oracle_stage, read_ws
+from tests.gpu_util import compare_image, compare_lists, compare_records, f64_scene, gpu_render, oracle_stage, read_ws
 
 pytestmark = pytest.mark.gpu
 
@@ -145,3 +145,64 @@ def test_depth_sort_digit_counts(kind):
     if d is not None:
         span = int(d.min() ^ d.max())
         assert (span == 0) if kind == "equal" else (span >> 24) != 0
+
+
+def _heavy_scene(seed=23):
+    """A dense scene seen through a small image: most visible Gaussians cover
+    most tiles, so tile lists run to many thousands of positions (walks over
+    dozens of 256-position checkpoint segments), half the pixels stop early
+    and half walk their whole list."""
+    rng = np.random.default_rng(seed)
+    sc = synth.shell_scene(rng, [14000, 10000], (0.8, 0.45), sh_degree=2, log_scale_mu=-2.2,
+                           log_scale_sigma=0.4)
+    sc.opacity_logit = (sc.opacity_logit - 4.0).astype(np.float32)     # mostly faint splats: long walks
+    cam = synth.look_at_camera((0.3, 0.2, 3.2), width=96, height=64, fov_x_deg=45.0)
+    return sc, cam
+
+
+def test_long_lists_forward():
+    sc, cam = _heavy_scene()
+    _, rast, img, al = gpu_render(sc, cam, 0b11, [], (0.3, 0.2, 0.1))
+    ws = read_ws(rast)
+    assert ws["status"].error == 0
+    pre, ranges, lst, co = oracle_stage(sc, cam, 0b11, [], (0.3, 0.2, 0.1))
+    lens = ranges[:, 1] - ranges[:, 0]
+    assert (lens >= 4096).sum() >= 4 and (lens < 4096).sum() >= 1, lens
+    compare_records(ws, pre)
+    compare_lists(ws, ranges, lst)
+    st = compare_image(img.cpu().numpy(), al.cpu().numpy(), ws["n_contrib"].astype(np.int64), co, TOL)
+    assert st["n_bad"] == 0, st
+    # some pixels stop early and some walk their whole list
+    nc = ws["n_contrib"].astype(np.int64)
+    assert (co["T"] < 1e-3).any() and (co["T"] > 1e-3).any()
+    assert nc.max() > 4096
+
+
+def test_long_lists_backward():
+    """The backward walks back through dozens of checkpoint segments per
+    pixel: gradients within the field-normalised 1e-5 bar of the oracle.  These
+    splats cover most of the image, so nearly every one meets some pixel with
+    a threshold decision within rounding (fragile); the upstream gradient is
+    zero at those pixels, on both sides, and every Gaussian is compared."""
+    sc, cam = _heavy_scene()
+    bg = (0.3, 0.2, 0.1)
+    ds, rast, img, al = gpu_render(sc, cam, 0b11, [], bg)
+    pre, ranges, lst, co = oracle_stage(sc, cam, 0b11, [], bg)
+    rng = np.random.default_rng(4)
+    dimg = rng.standard_normal((3, cam.height, cam.width)).astype(np.float32)
+    dal = rng.standard_normal((cam.height, cam.width)).astype(np.float32)
+    fr = co["fragile"] > 0
+    assert fr.mean() < 0.2
+    dimg[:, fr] = 0.0
+    dal[fr] = 0.0
+    g = rast.backward(ds, cam, bg, torch.from_numpy(dimg).cuda(), torch.from_numpy(dal).cuda())
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    cb = oracle.composite_backward(pre, ranges, lst, bg, dimg, dal)
+    ref = oracle.chain(f64_scene(sc), cam, pre["vis"], cb["rec_grad"])
+    ok = cb["contrib_max"] > 0
+    assert ok.sum() > 1000
+    for f in ("means", "log_scales", "quats", "opacity_logit", "sh"):
+        a = g[f].reshape(sc.n, -1)[ok].astype(np.float64)
+        b = ref[f].reshape(sc.n, -1)[ok]
+        assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max(), f
