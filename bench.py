@@ -347,10 +347,10 @@ def run_gpu(args, rank, world, local_rank):
     cs = ds.c_struct()
     stream = torch.cuda.current_stream(dev)
 
-    def step(dimg_t, dal_t):
+    def step(dimg_t, dal_t, img_t=image, al_t=alpha):
         csum.zero_()
         cmax.zero_()
-        rast.render(ds, cam_c, w["layer_mask"], w["planes"], bg, image=image, alpha=alpha, check=False,
+        rast.render(ds, cam_c, w["layer_mask"], w["planes"], bg, image=img_t, alpha=al_t, check=False,
                     _c_scene=cs)
         rast.backward(ds, cam_c, bg, dimg_t, dal_t, 0xFFFFFFFF, csum, cmax, grads=grads, _c_scene=cs)
         return contrib_prune(cmax, 0.005, workspace=prune_ws)
@@ -382,6 +382,14 @@ def run_gpu(args, rank, world, local_rank):
             g.replay()
             torch.cuda.synchronize()
             graph, graph_note = g, "one CUDA graph per step (%d library kernels)" % step_launches
+            # a second graph of the same step on a second set of input and output buffers, for the
+            # double-buffered end-to-end loop below
+            bufs2 = (torch.empty_like(dimg), torch.empty_like(dal), torch.empty_like(image), torch.empty_like(alpha))
+            g2 = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g2):
+                _, _, nk_graph2 = step(*bufs2)
+            g2.replay()
+            torch.cuda.synchronize()
         except Exception as e:          # capture unsupported here: time the eager launches instead
             graph, graph_note = None, "eager launches (graph capture failed: %s)" % str(e).splitlines()[0][:120]
     run_step = graph.replay if graph is not None else (lambda: step(dimg, dal))
@@ -416,32 +424,65 @@ def run_gpu(args, rank, world, local_rank):
     prof = gs_profile_collect()
 
     # ---- end to end: host inputs (pinned) and host result every step ----
+    # Every step copies its upstream gradients from pinned host memory and reads its image, alpha and kept
+    # count back.  With the graphs, the copies run on their own streams into and out of two buffer sets, so
+    # step k's upload and step k-1's read-back overlap the compute of steps k-1 and k; each copy waits only
+    # for the step that produces or last used its buffers.
     dimg_pin = torch.from_numpy(dimg_h).pin_memory()
     dal_pin = torch.from_numpy(dal_h).pin_memory()
-    img_host = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
-    al_host = torch.empty((H, W), dtype=torch.float32).pin_memory()
-    nk_host = torch.empty(1, dtype=torch.int64).pin_memory()
+    img_host = [torch.empty((3, H, W), dtype=torch.float32).pin_memory() for _ in range(2)]
+    al_host = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(2)]
+    nk_host = [torch.empty(1, dtype=torch.int64).pin_memory() for _ in range(2)]
     e2e_steps = max(3, min(args.steps, 20))
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(e2e_steps):
-        dimg.copy_(dimg_pin, non_blocking=True)      # the step's own input buffers (captured by the graph)
-        dal.copy_(dal_pin, non_blocking=True)
-        if graph is not None:
-            graph.replay()
-            nk = nk_graph
-        else:
+    if graph is not None:
+        sets = [(dimg, dal, image, alpha, graph, nk_graph), bufs2[:4] + (g2, nk_graph2)]
+        up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        up.wait_event(e0)
+        down.wait_event(e0)
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_done = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
+        for k in range(e2e_steps):
+            sb = k % 2
+            di, da, im, al, gr, nk = sets[sb]
+            with torch.cuda.stream(up):
+                if k >= 2:
+                    up.wait_event(ev_done[sb])            # step k-2 has consumed this set's inputs
+                di.copy_(dimg_pin, non_blocking=True)
+                da.copy_(dal_pin, non_blocking=True)
+                ev_in[sb].record(up)
+            stream.wait_event(ev_in[sb])
+            if k >= 2:
+                stream.wait_event(ev_out[sb])              # step k-2's results are read back
+            gr.replay()
+            ev_done[sb].record(stream)
+            with torch.cuda.stream(down):
+                down.wait_event(ev_done[sb])
+                img_host[sb].copy_(im, non_blocking=True)
+                al_host[sb].copy_(al, non_blocking=True)
+                nk_host[sb].copy_(nk, non_blocking=True)
+                ev_out[sb].record(down)
+        for sb in range(2):
+            stream.wait_event(ev_out[sb])
+        e2e_note = "double-buffered: copies on two copy streams overlap the compute of neighbouring steps"
+    else:
+        for _ in range(e2e_steps):
+            dimg.copy_(dimg_pin, non_blocking=True)
+            dal.copy_(dal_pin, non_blocking=True)
             _, _, nk = step(dimg, dal)
-        img_host.copy_(image, non_blocking=True)
-        al_host.copy_(alpha, non_blocking=True)
-        nk_host.copy_(nk, non_blocking=True)
+            img_host[0].copy_(image, non_blocking=True)
+            al_host[0].copy_(alpha, non_blocking=True)
+            nk_host[0].copy_(nk, non_blocking=True)
+        e2e_note = "serial: copies and compute on one stream"
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
     e2e_value = world * (W * H) / (e2e_ms / 1e3) / 1e6
     h2d = dimg_h.nbytes + dal_h.nbytes
-    d2h = img_host.numel() * 4 + al_host.numel() * 4 + 8
+    d2h = img_host[0].numel() * 4 + al_host[0].numel() * 4 + 8
 
     # ---- roofline of the dominant kernel ----
     peaks, peaks_src = _peaks()
@@ -510,7 +551,7 @@ def run_gpu(args, rank, world, local_rank):
                 "psnr_db_vs_fp64_oracle": psnr,
                 "roofline": roof, "roofline_detail": roof_detail, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "ms_per_step": e2e_ms},
+                        "ms_per_step": e2e_ms, "copies": e2e_note},
                 "clocks": clk, "gpu_launches": int(launches), "serving": serving, "training": training,
                 "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()}}
         print(json.dumps(line), flush=True)
