@@ -149,12 +149,24 @@ __device__ void order_tiles(int Tn, uint32_t *order, uint32_t *s_cnt, uint32_t *
 // Forward set-up (one CTA): heaviest-first tile order by list length, the
 // checkpoint base of every tile (exclusive prefix of its segment count), and
 // zeroed per-block work and queue.
-__global__ void __launch_bounds__(1024) k_fwd_setup(const uint2 *__restrict__ ranges, int Tn,
+// The set-up kernels are a single CTA walking every tile several times; up to
+// kSetupSmemTiles tiles, their inputs (ranges, block work) are first staged in
+// dynamic shared memory so the later passes cost no memory round trips.
+constexpr int kSetupSmemTiles = 8192;
+
+__global__ void __launch_bounds__(1024) k_fwd_setup(const uint2 *__restrict__ g_ranges, int Tn,
                                                     uint32_t *__restrict__ order, uint32_t *__restrict__ seg_base,
                                                     uint32_t *__restrict__ qwork, uint32_t *__restrict__ queue) {
     __shared__ uint32_t s_cnt[kBuckets];
     __shared__ uint32_t s_w[32];
+    extern __shared__ uint2 s_ranges[];
     if (threadIdx.x == 0) *queue = 0;
+    const uint2 *ranges = g_ranges;
+    if (Tn <= kSetupSmemTiles) {
+        for (int t = threadIdx.x; t < Tn; t += blockDim.x) s_ranges[t] = g_ranges[t];
+        __syncthreads();
+        ranges = s_ranges;
+    }
     for (int q = threadIdx.x; q < 4 * Tn; q += blockDim.x) qwork[q] = 0;
     order_tiles(Tn, order, s_cnt, s_w, ranges, nullptr);
     uint32_t carry = 0;
@@ -356,13 +368,37 @@ __global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_cons
 // Backward set-up (one CTA): heaviest-first tile order by the longest blended
 // prefix, then one work item (tile, 8x8 block q, segment s) for every segment
 // s < ceil(qwork[tile][q] / kSeg), written tile by tile in that order.
+// CTAs after the first zero the record-gradient rows of the visible Gaussians
+// (visible list of the last render, n_vis entries), the only rows the
+// compositor adds to and the chain rule reads.
 template <int PX>
-__global__ void __launch_bounds__(1024) k_bwd_setup(const uint32_t *__restrict__ qwork, int Tn,
+__global__ void __launch_bounds__(1024) k_bwd_setup(const uint32_t *__restrict__ g_qwork, int Tn,
                                                     uint32_t *__restrict__ order, uint2 *__restrict__ items,
-                                                    uint32_t *__restrict__ n_items, uint32_t *__restrict__ queue) {
+                                                    uint32_t *__restrict__ n_items, uint32_t *__restrict__ queue,
+                                                    const uint32_t *__restrict__ vis_index,
+                                                    const uint32_t *__restrict__ n_vis, int n,
+                                                    float4 *__restrict__ rec_grad) {
     __shared__ uint32_t s_cnt[kBuckets];
     __shared__ uint32_t s_w[32];
+    extern __shared__ uint4 s_qwork[];
+    if (blockIdx.x > 0) {
+        const uint32_t nv = min(*n_vis, static_cast<uint32_t>(n));
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (uint32_t p = (blockIdx.x - 1) * blockDim.x + threadIdx.x; p < nv; p += (gridDim.x - 1) * blockDim.x) {
+            const size_t i = vis_index[p];
+            rec_grad[3 * i] = z;
+            rec_grad[3 * i + 1] = z;
+            rec_grad[3 * i + 2] = z;
+        }
+        return;
+    }
     if (threadIdx.x == 0) *queue = 0;
+    const uint32_t *qwork = g_qwork;
+    if (Tn <= kSetupSmemTiles) {
+        for (int t = threadIdx.x; t < Tn; t += blockDim.x) s_qwork[t] = reinterpret_cast<const uint4 *>(g_qwork)[t];
+        __syncthreads();
+        qwork = reinterpret_cast<const uint32_t *>(s_qwork);
+    }
     order_tiles(Tn, order, s_cnt, s_w, nullptr, qwork);
     uint32_t carry = 0;
     for (int r0 = 0; r0 < Tn; r0 += 1024) {
@@ -609,7 +645,13 @@ int persistent_blocks(K kernel, int threads) {
 
 cudaError_t launch_fwd_setup(const CompositeBufs &cb, const uint2 *ranges, int Tn, cudaStream_t st) {
     if (Tn == 0) return cudaSuccess;
-    k_fwd_setup<<<1, 1024, 0, st>>>(ranges, Tn, cb.order, cb.seg_base, cb.qwork, cb.queue);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_fwd_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, kSetupSmemTiles * 8);
+        attr = true;
+    }
+    const size_t smem = Tn <= kSetupSmemTiles ? static_cast<size_t>(Tn) * 8 : 0;
+    k_fwd_setup<<<1, 1024, smem, st>>>(ranges, Tn, cb.order, cb.seg_base, cb.qwork, cb.queue);
     return cudaGetLastError();
 }
 
@@ -637,10 +679,21 @@ cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *rang
                                       const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
                                       const uint32_t *n_contrib, const float *dL_dimage,
                                       const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
-                                      float4 *rec_grad, float *contrib_max, cudaStream_t st) {
+                                      float4 *rec_grad, float *contrib_max, const uint32_t *vis_index,
+                                      const uint32_t *n_vis, int n, cudaStream_t st) {
     const int tiles = Tx * Ty;
     if (tiles == 0) return cudaSuccess;
-    k_bwd_setup<kBwdPx><<<1, 1024, 0, st>>>(cb.qwork, tiles, cb.order_bwd, cb.items, cb.n_items, cb.queue);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_bwd_setup<kBwdPx>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSetupSmemTiles * 16);
+        attr = true;
+    }
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = tiles <= kSetupSmemTiles ? static_cast<size_t>(tiles) * 16 : 0;
+    k_bwd_setup<kBwdPx><<<1 + max(1, sms), 1024, smem, st>>>(cb.qwork, tiles, cb.order_bwd, cb.items, cb.n_items,
+                                                             cb.queue, vis_index, n_vis, n, rec_grad);
     static int blocks = 0;
     if (!blocks) blocks = persistent_blocks(k_composite_bwd<kBwdPx>, kBwdThreads);
     k_composite_bwd<kBwdPx><<<blocks, kBwdThreads, 0, st>>>(cb.items, cb.n_items, cb.queue, ranges, list, rec, W, H, Tx, bg,

@@ -215,7 +215,8 @@ struct FwdJob {
     uint32_t item_begin;   // first global work item of this view (filled by the launcher)
 };
 // Per-view set-up before compositing: tile order, checkpoint bases, zeroed
-// block work and queue.
+// block work and queue.  The backward's set-up also zeroes the record-gradient
+// rows of the visible Gaussians (vis_index, *n_vis of the n Gaussians).
 cudaError_t launch_fwd_setup(const CompositeBufs &cb, const uint2 *ranges, int Tn, cudaStream_t st);
 // Composites n <= kMaxBatch views with one persistent launch; `queue` must
 // have been zeroed on the stream (launch_fwd_setup of any view does).
@@ -224,6 +225,7 @@ cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *rang
                                       const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
                                       const uint32_t *n_contrib, const float *dL_dimage,
                                       const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
-                                      float4 *rec_grad, float *contrib_max, cudaStream_t st);
+                                      float4 *rec_grad, float *contrib_max, const uint32_t *vis_index,
+                                      const uint32_t *n_vis, int n, cudaStream_t st);
 
 }  // namespace gs
