@@ -305,39 +305,45 @@ __global__ void __launch_bounds__(256) k_bin_tiles(const uint2 *__restrict__ row
     }
 }
 
-// Per row (one CTA of 4 x 256 threads): thread (slice s, tile t) sums the
-// counts of tile t over its quarter of the row's pieces; the slice sums give
-// each tile's total and range; then every (piece, tile) count is replaced by
-// its first list position.
+// Per row (one CTA of 1024 threads): the threads form S slices of TW tiles
+// (TW the power of two at or above Tx, at least 16, so S = 1024 / TW <= 64);
+// thread (slice s, tile t) sums the counts of tile t over its share of the
+// row's pieces; the slice sums give each tile's total and range; then every
+// (piece, tile) count is replaced by its first list position.
 __global__ void __launch_bounds__(1024) k_bin_tiles_scan(const RowInfo *__restrict__ rows, int Tx, uint32_t piece,
                                                          uint32_t *__restrict__ P, uint2 *__restrict__ ranges,
                                                          const Ctl *__restrict__ ctl) {
-    __shared__ uint32_t s_sum[4][kBinMaxDim];
+    __shared__ uint32_t s_sum[1024];         // [slice][tile]
+    __shared__ uint32_t s_off[kBinMaxDim];
     __shared__ uint32_t s_w[32];
     if (ctl->st.error != GS_OK) return;
+    int TW = 16;
+    while (TW < Tx) TW <<= 1;
+    const int S = 1024 / TW;
     const int r = blockIdx.x;
-    const int t = threadIdx.x & (kBinMaxDim - 1), sl = threadIdx.x >> 8;
+    const int t = threadIdx.x & (TW - 1), sl = threadIdx.x / TW;
     const RowInfo ri = rows[r];
     const uint32_t npc = (ri.entries + piece - 1) / piece;
-    const uint32_t per = (npc + 3) / 4;
+    const uint32_t per = (npc + S - 1) / S;
     const uint32_t p0 = ri.piece_start + min(npc, sl * per), p1 = ri.piece_start + min(npc, (sl + 1) * per);
     uint32_t sum = 0;
     if (t < Tx)
         for (uint32_t p = p0; p < p1; ++p) sum += P[static_cast<size_t>(p) * Tx + t];
-    s_sum[sl][t] = sum;
+    s_sum[sl * TW + t] = sum;
     __syncthreads();
     uint32_t tot = 0, before = 0;
-    for (int q = 0; q < 4; ++q) {
-        const uint32_t v = s_sum[q][t];
-        if (q < sl) before += v;
-        tot += v;
-    }
+    if (t < Tx)
+        for (int q = 0; q < S; ++q) {
+            const uint32_t v = s_sum[q * TW + t];
+            if (q < sl) before += v;
+            tot += v;
+        }
     uint32_t all;
     const uint32_t toff = block_excl_scan<1024>(sl == 0 && t < Tx ? tot : 0u, s_w, &all);
-    if (sl == 0) s_sum[0][t] = toff;          // slice 0's tile offsets, read by every slice below
+    if (sl == 0 && t < Tx) s_off[t] = toff;   // tile offsets within the row, read by every slice below
     __syncthreads();
     if (t < Tx) {
-        const uint32_t base = ri.pair_start + s_sum[0][t];
+        const uint32_t base = ri.pair_start + s_off[t];
         if (sl == 0) ranges[static_cast<size_t>(r) * Tx + t] = make_uint2(base, base + tot);
         uint32_t run = base + before;
         for (uint32_t p = p0; p < p1; ++p) {
