@@ -69,17 +69,25 @@ def test_image_loss_autograd_and_identity():
     assert abs(float(z)) < 1e-6
 
 
-def test_adam_matches_oracle_with_frozen_layers():
+@pytest.mark.parametrize("mask,unaligned", [(0b110, False), (0xFFFFFFFF, False), (0b110, True)])
+def test_adam_matches_oracle_with_frozen_layers(mask, unaligned):
+    """Adam against the oracle: layer 0 frozen (or every layer trainable),
+    arrays whose lengths are not multiples of four, and moments 4 bytes off a
+    16-byte boundary (the element-wise path instead of the 16-byte one)."""
     rng = np.random.default_rng(3)
     n, K = 301, 16
     shapes = [(n, 3), (n, 3), (n, 4), (n,), (n, K, 3)]
     p0 = [rng.standard_normal(s).astype(np.float32) for s in shapes]
     layer = rng.integers(0, 3, n).astype(np.uint8)
-    mask = 0b110                                   # layer 0 frozen
     lr = (1e-3, 5e-3, 2e-3, 5e-2, 2.5e-3)
     P = [torch.from_numpy(a.copy()).cuda() for a in p0]
-    M = [torch.zeros_like(a) for a in P]
-    V = [torch.zeros_like(a) for a in P]
+    if unaligned:
+        M = [torch.zeros(a.numel() + 1, device="cuda")[1:].view(a.shape) for a in P]
+        V = [torch.zeros(a.numel() + 1, device="cuda")[1:].view(a.shape) for a in P]
+    else:
+        M = [torch.zeros_like(a) for a in P]
+        V = [torch.zeros_like(a) for a in P]
+    frozen = ((mask >> layer.astype(np.int64)) & 1) == 0
     sc = DeviceScene(*P, torch.from_numpy(layer).cuda(), 3)
     ref = [(a.astype(np.float64), np.zeros(a.shape), np.zeros(a.shape)) for a in p0]
     for t in range(1, 4):
@@ -91,12 +99,12 @@ def test_adam_matches_oracle_with_frozen_layers():
         for k in range(5):
             st.m[k], st.v[k] = M[k].data_ptr(), V[k].data_ptr()
         _lib.gs_adam_step(sc.c_struct(), g, st, lr, 0.9, 0.999, 1e-15, t, mask, 0)
-        ref = [OT.adam_step(r[0], gr[k], r[1], r[2], t, lr[k], frozen_rows=(layer == 0))
+        ref = [OT.adam_step(r[0], gr[k], r[1], r[2], t, lr[k], frozen_rows=frozen)
                for k, r in enumerate(ref)]
     torch.cuda.synchronize()
     for k in range(5):
         got = P[k].cpu().numpy()
-        assert np.array_equal(got[layer == 0], p0[k][layer == 0])          # frozen: untouched
+        assert np.array_equal(got[frozen], p0[k][frozen])                  # frozen: untouched
         assert np.abs(got - ref[k][0]).max() <= 1e-5 * lr[k] * 3 + 4e-7 * np.abs(ref[k][0]).max(), k
         assert np.allclose(M[k].cpu().numpy(), ref[k][1], rtol=1e-5, atol=1e-6)
         assert np.allclose(V[k].cpu().numpy(), ref[k][2], rtol=1e-5, atol=1e-7)
