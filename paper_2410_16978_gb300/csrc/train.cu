@@ -21,8 +21,8 @@
 namespace gs {
 namespace {
 
-constexpr int kLW = 32, kLH = 8, kHalo = 5, kWin = 11;
-constexpr int kRW = kLW + 2 * kHalo, kRH = kLH + 2 * kHalo;   // 42 x 18 staged region
+constexpr int kLW = 32, kLH = 16, kHalo = 5, kWin = 11;
+constexpr int kRW = kLW + 2 * kHalo, kRH = kLH + 2 * kHalo;   // 42 x 26 staged region
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
 
 struct Win {
@@ -178,18 +178,31 @@ __global__ void __launch_bounds__(kLW *kLH) k_loss_grad(const float *__restrict_
     if (ch == 0 && dA) dA[p] = A ? w_a * sgn(A[p] - At[p]) / static_cast<float>(plane) : 0.f;
 }
 
-// loss = (1 - lam) L1 + lam (1 - SSIM) + w_a LA from the block sums (double).
-__global__ void __launch_bounds__(256) k_loss_reduce(const float *__restrict__ partials, int nb, size_t plane,
-                                                     float lam, float w_a, float *__restrict__ loss) {
-    __shared__ double s[3][256];
+// loss = (1 - lam) L1 + lam (1 - SSIM) + w_a LA from the block sums (double,
+// one CTA, fixed order).  Eight block sums per thread are loaded before they
+// are added.
+constexpr int kRedThreads = 1024;
+__global__ void __launch_bounds__(kRedThreads) k_loss_reduce(const float *__restrict__ partials, int nb, size_t plane,
+                                                             float lam, float w_a, float *__restrict__ loss) {
+    __shared__ double s[3][kRedThreads];
     double a[3] = {0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < nb; b += 256)
+    for (int b0 = threadIdx.x; b0 < nb; b0 += 8 * kRedThreads) {
+        float v[8][3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) a[q] += partials[3 * b + q];
+        for (int u = 0; u < 8; ++u) {
+            const int b = b0 + u * kRedThreads;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) v[u][q] = b < nb ? partials[3 * b + q] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) a[q] += v[u][q];
+    }
 #pragma unroll
     for (int q = 0; q < 3; ++q) s[q][threadIdx.x] = a[q];
     __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o)
 #pragma unroll
             for (int q = 0; q < 3; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + o];
@@ -365,8 +378,8 @@ cudaError_t launch_image_loss(const float *X, const float *A, const float *Ct, c
     const dim3 grid((W + kLW - 1) / kLW, (H + kLH - 1) / kLH, 3);
     k_loss_maps<<<grid, kLW * kLH, 0, st>>>(X, A, Ct, At, bg, W, H, win, maps, partials);
     k_loss_grad<<<grid, kLW * kLH, 0, st>>>(X, A, Ct, At, bg, W, H, win, lam, w_a, maps, dX, dA);
-    k_loss_reduce<<<1, 256, 0, st>>>(partials, static_cast<int>(grid.x * grid.y * grid.z), plane, lam,
-                                     A ? w_a : 0.f, loss);
+    k_loss_reduce<<<1, kRedThreads, 0, st>>>(partials, static_cast<int>(grid.x * grid.y * grid.z), plane, lam,
+                                             A ? w_a : 0.f, loss);
     return cudaGetLastError();
 }
 
