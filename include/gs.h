@@ -346,7 +346,7 @@ enum {
     GS_STAGE_DEPTH_SORT,       /* S2: radix digit kernels on the depth bits (the first compacts) */
     GS_STAGE_BIN_ROWS,         /* S2: depth-ordered split of the pairs into tile rows */
     GS_STAGE_BIN_TILES,        /* S2: split of every row into its tiles, tile ranges */
-    GS_STAGE_COMPOSITE_SETUP,  /* S3: heaviest-first tile order, checkpoint bases */
+    GS_STAGE_COMPOSITE_SETUP,  /* S3/S4: compositor set-ups (tile orders, checkpoint bases, backward items) */
     GS_STAGE_COMPOSITE,        /* S3 (one launch per gs_render or gs_render_batch call) */
     GS_STAGE_COMPOSITE_BWD,    /* S4a (zeroing the record gradients, work-item set-up, compositor) */
     GS_STAGE_PREPROCESS_BWD,   /* S4b */

@@ -684,12 +684,8 @@ cudaError_t launch_composite_forward(const FwdJob *jobs, int n, uint32_t *queue,
     return cudaGetLastError();
 }
 
-cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *ranges, const uint32_t *list,
-                                      const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
-                                      const uint32_t *n_contrib, const float *dL_dimage,
-                                      const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
-                                      float4 *rec_grad, float *contrib_max, const uint32_t *vis_index,
-                                      const uint32_t *n_vis, int n, cudaStream_t st) {
+cudaError_t launch_bwd_setup(const CompositeBufs &cb, int Tx, int Ty, float4 *rec_grad, const uint32_t *vis_index,
+                             const uint32_t *n_vis, int n, cudaStream_t st) {
     const int tiles = Tx * Ty;
     if (tiles == 0) return cudaSuccess;
     static bool attr = false;
@@ -703,6 +699,15 @@ cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *rang
     const size_t smem = tiles <= kSetupSmemTiles ? static_cast<size_t>(tiles) * 16 : 0;
     k_bwd_setup<kBwdPx><<<1 + max(1, sms), 1024, smem, st>>>(cb.qwork, tiles, cb.order_bwd, cb.items, cb.n_items,
                                                              cb.queue, vis_index, n_vis, n, rec_grad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *ranges, const uint32_t *list,
+                                      const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
+                                      const uint32_t *n_contrib, const float *dL_dimage,
+                                      const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
+                                      float4 *rec_grad, float *contrib_max, cudaStream_t st) {
+    if (Tx * Ty == 0) return cudaSuccess;
     static int blocks = 0;
     if (!blocks) blocks = persistent_blocks(k_composite_bwd<kBwdPx>, kBwdThreads);
     k_composite_bwd<kBwdPx><<<blocks, kBwdThreads, 0, st>>>(cb.items, cb.n_items, cb.queue, ranges, list, rec, W, H, Tx, bg,

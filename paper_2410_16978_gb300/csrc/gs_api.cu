@@ -496,16 +496,22 @@ int gs_render_backward(const gs_scene *scene, const gs_camera *camera, const flo
     void *ws = workspace;
     float4 *rec_grad = at<float4>(ws, L.rec_grad);
     {
-    Stage sg(GS_STAGE_COMPOSITE_BWD, st, 2);   // set-up (with the record-gradient zeroing) and compositor
-    if ((rc = cuda_check(launch_composite_backward(composite_bufs(ws, L), at<uint2>(ws, L.ranges), at<uint32_t>(ws, L.list),
-                                                   at<Rec>(ws, L.rec), cv.W, cv.H, cv.Tx, cv.Ty,
-                                                   make_float3(bg[0], bg[1], bg[2]), at<float>(ws, L.t_final),
-                                                   at<uint32_t>(ws, L.n_contrib), dL_dimage,
-                                                   dL_dalpha, sv.layer, grad_layer_mask, rec_grad, contrib_max,
-                                                   at<uint32_t>(ws, L.vis_index), &at<Ctl>(ws, L.ctl)->n_vis, sv.n,
-                                                   st),
-                         "composite backward")) != GS_OK)
-        return rc;
+        Stage sg(GS_STAGE_COMPOSITE_SETUP, st, 1);     // with the record-gradient zeroing
+        if ((rc = cuda_check(launch_bwd_setup(composite_bufs(ws, L), cv.Tx, cv.Ty, rec_grad,
+                                              at<uint32_t>(ws, L.vis_index), &at<Ctl>(ws, L.ctl)->n_vis, sv.n, st),
+                             "backward set-up")) != GS_OK)
+            return rc;
+    }
+    {
+        Stage sg(GS_STAGE_COMPOSITE_BWD, st, 1);
+        if ((rc = cuda_check(launch_composite_backward(composite_bufs(ws, L), at<uint2>(ws, L.ranges),
+                                                       at<uint32_t>(ws, L.list), at<Rec>(ws, L.rec), cv.W, cv.H,
+                                                       cv.Tx, cv.Ty, make_float3(bg[0], bg[1], bg[2]),
+                                                       at<float>(ws, L.t_final), at<uint32_t>(ws, L.n_contrib),
+                                                       dL_dimage, dL_dalpha, sv.layer, grad_layer_mask, rec_grad,
+                                                       contrib_max, st),
+                             "composite backward")) != GS_OK)
+            return rc;
     }
     Stage sg(GS_STAGE_PREPROCESS_BWD, st, 1);
     return cuda_check(launch_preprocess_backward(sv, cv, at<uint32_t>(ws, L.tiles), at<uint32_t>(ws, L.vis_index),

@@ -221,11 +221,14 @@ cudaError_t launch_fwd_setup(const CompositeBufs &cb, const uint2 *ranges, int T
 // Composites n <= kMaxBatch views with one persistent launch; `queue` must
 // have been zeroed on the stream (launch_fwd_setup of any view does).
 cudaError_t launch_composite_forward(const FwdJob *jobs, int n, uint32_t *queue, cudaStream_t st);
+// Backward set-up: work items (tile order by longest blended prefix) and the
+// zeroed record-gradient rows of the visible Gaussians.
+cudaError_t launch_bwd_setup(const CompositeBufs &cb, int Tx, int Ty, float4 *rec_grad, const uint32_t *vis_index,
+                             const uint32_t *n_vis, int n, cudaStream_t st);
 cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *ranges, const uint32_t *list,
                                       const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
                                       const uint32_t *n_contrib, const float *dL_dimage,
                                       const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
-                                      float4 *rec_grad, float *contrib_max, const uint32_t *vis_index,
-                                      const uint32_t *n_vis, int n, cudaStream_t st);
+                                      float4 *rec_grad, float *contrib_max, cudaStream_t st);
 
 }  // namespace gs
