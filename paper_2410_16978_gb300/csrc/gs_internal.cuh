@@ -42,7 +42,7 @@ struct Ctl {
     gs_status st;          // 32 bytes
     uint32_t n_vis;        // visible Gaussians (compaction total)
     uint32_t scan_total;   // scratch total of the last scan
-    uint32_t depth_mm[2];  // ~min and max of the depth keys (radix pass skipping)
+    uint32_t depth_mm[2];  // ~min and max of the visible depth keys (digits the sort can skip)
     uint32_t fwd_queue;    // next work item of the persistent forward compositor
     uint32_t bwd_queue;    // next work item of the persistent backward compositor
     uint32_t n_items;      // backward work items (tile, 8x8 block, segment)
