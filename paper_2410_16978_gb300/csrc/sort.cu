@@ -324,18 +324,51 @@ struct SortBufs {
     uint64_t *status, *status_next;  // look-back words [tile][256] of this and the next pass
 };
 
-// One digit (bits 8 pass .. 8 pass + 7) of the stable LSD sort.  Warp w ranks
+// One digit (bits 8 pass .. 8 pass + 7) of the stable LSD sort, on tiles of
+// kPassTile items and CTAs of kPassThreads threads (fewer, larger tiles keep
+// the look-back chain short when every tile starts at once).  Warp w ranks
 // the contiguous run [256 w, 256 w + 256) of its tile in 8 rounds of 32 with
-// warp-private digit counters, so items are ranked in index order; the tile
-// is then sorted by digit in shared memory and written out in that order, so
-// consecutive threads store consecutive addresses of one digit's run.
+// warp-private 16-bit digit counters, so items are ranked in index order; the
+// tile is then sorted by digit in shared memory and written out in that order,
+// so consecutive threads store consecutive addresses of one digit's run.
+constexpr int kPassThreads = 512;
+constexpr int kPassWarps = kPassThreads / 32;
+constexpr int kPassTile = kPassThreads * kSortItems;
+
+// Exclusive scan over the 512 threads of a block; *total = sum of all v.
+__device__ __forceinline__ uint32_t block_scan_512(uint32_t v, uint32_t *s_w, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kPassWarps ? s_w[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < kPassWarps; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kPassWarps) s_w[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t base = warp > 0 ? s_w[warp - 1] : 0;
+    *total = s_w[kPassWarps - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
 template <class Src, bool FIRST>
-__global__ void __launch_bounds__(256) k_sort_pass(Src src, uint32_t n_all, int pass, SortBufs B, Ctl *ctl) {
-    __shared__ uint32_t s_wc[8][256];     // per-warp digit counts, then per-warp digit bases
-    __shared__ uint32_t s_lstart[256];    // start of each digit's run in the locally sorted tile
-    __shared__ uint32_t s_off[256];       // global position of each digit's run
-    __shared__ uint32_t s_key[kSortTile], s_val[kSortTile];
-    __shared__ uint32_t s_w[8], s_vw[8];
+__global__ void __launch_bounds__(kPassThreads) k_sort_pass(Src src, uint32_t n_all, int pass, SortBufs B, Ctl *ctl) {
+    __shared__ uint16_t s_wc[kPassWarps][256];   // per-warp digit counts, then per-warp digit bases
+    __shared__ uint32_t s_lstart[256];            // start of each digit's run in the locally sorted tile
+    __shared__ uint32_t s_off[256];               // global position of each digit's run
+    __shared__ uint32_t s_key[kPassTile], s_val[kPassTile];
+    __shared__ uint32_t s_w[kPassWarps], s_vw[kPassWarps];
     __shared__ uint32_t s_ticket, s_visbase;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -344,18 +377,17 @@ __global__ void __launch_bounds__(256) k_sort_pass(Src src, uint32_t n_all, int 
     const bool last = pass == passes - 1;
     const uint32_t n_vis = min(ctl->n_vis, n_all);
     const uint32_t n = FIRST ? n_all : n_vis;
-    const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+    const uint32_t ntiles = (n + kPassTile - 1) / kPassTile;
     if (threadIdx.x == 0) s_ticket = atomicAdd(&ctl->sort_ticket[pass], 1u);
-#pragma unroll
-    for (int w = 0; w < 8; ++w) s_wc[w][threadIdx.x] = 0;
+    for (int e = threadIdx.x; e < kPassWarps * 256; e += kPassThreads) (&s_wc[0][0])[e] = 0;
     __syncthreads();
     const uint32_t t = s_ticket;
     if (t >= ntiles) return;
-    if (!last && t < (n_vis + kSortTile - 1) / kSortTile)
-        for (int c = threadIdx.x; c < kLookCounters; c += 256)
+    if (!last && t < (n_vis + kPassTile - 1) / kPassTile)
+        for (int c = threadIdx.x; c < kLookCounters; c += kPassThreads)
             B.status_next[static_cast<size_t>(t) * kLookCounters + c] = 0;
     const int shift = 8 * pass;
-    const uint32_t run0 = t * kSortTile + warp * 256;
+    const uint32_t run0 = t * kPassTile + warp * 256;
     uint32_t key[kSortItems], val[kSortItems], rank[kSortItems], vrank[kSortItems];
     bool valid[kSortItems];
 #pragma unroll
@@ -383,7 +415,7 @@ __global__ void __launch_bounds__(256) k_sort_pass(Src src, uint32_t n_all, int 
         const uint32_t before = valid[r] ? s_wc[warp][d] : 0;
         rank[r] = before + __popc(peers & lt);
         __syncwarp();
-        if (valid[r] && (peers & lt) == 0) s_wc[warp][d] = before + __popc(peers);
+        if (valid[r] && (peers & lt) == 0) s_wc[warp][d] = static_cast<uint16_t>(before + __popc(peers));
         __syncwarp();
         if constexpr (FIRST) {
             const unsigned vb = __ballot_sync(FULL, valid[r]);
@@ -395,26 +427,31 @@ __global__ void __launch_bounds__(256) k_sort_pass(Src src, uint32_t n_all, int 
         if (lane == 0) s_vw[warp] = vw;
     }
     __syncthreads();
-    // per digit d = thread: exclusive prefix over the warps, the tile's count, and its publication
+    // per digit d = thread (the first 256 threads): exclusive prefix over the warps, the tile's count, and
+    // its publication
     const int d = threadIdx.x;
+    const bool dig = d < 256;
     uint32_t acc = 0;
+    if (dig) {
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        const uint32_t c = s_wc[w][d];
-        s_wc[w][d] = acc;
-        acc += c;
+        for (int w = 0; w < kPassWarps; ++w) {
+            const uint32_t c = s_wc[w][d];
+            s_wc[w][d] = static_cast<uint16_t>(acc);
+            acc += c;
+        }
+        st_volatile(B.status + static_cast<size_t>(t) * kLookCounters + d, (t == 0 ? kLookIncl : kLookAgg) | acc);
     }
-    st_volatile(B.status + static_cast<size_t>(t) * kLookCounters + d, (t == 0 ? kLookIncl : kLookAgg) | acc);
     uint32_t ntile;
-    s_lstart[d] = block_scan_256(acc, s_w, &ntile);
+    const uint32_t ls = block_scan_512(acc, s_w, &ntile);
+    if (dig) s_lstart[d] = ls;
     uint32_t gtot;
-    const uint32_t gbase = block_scan_256(B.ghist[pass * 256 + d], s_w, &gtot);
-    const uint32_t excl = look_back(B.status, t, d, acc, ctl);
-    s_off[d] = gbase + excl;
+    const uint32_t gbase = block_scan_512(dig ? B.ghist[pass * 256 + d] : 0u, s_w, &gtot);
+    const uint32_t excl = dig ? look_back(B.status, t, d, acc, ctl) : 0u;
+    if (dig) s_off[d] = gbase + excl;
     if constexpr (FIRST) {
         // the items of all digits in the tiles before this one are the visible Gaussians before it
         uint32_t before;
-        block_scan_256(excl, s_w, &before);
+        block_scan_512(excl, s_w, &before);
         if (d == 0) s_visbase = before;
     }
     __syncthreads();
@@ -435,7 +472,7 @@ __global__ void __launch_bounds__(256) k_sort_pass(Src src, uint32_t n_all, int 
             if (valid[r]) B.vis_index[vbase + vrank[r]] = val[r];
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < ntile; i += 256) {
+    for (uint32_t i = threadIdx.x; i < ntile; i += kPassThreads) {
         const uint32_t k = s_key[i];
         const uint32_t dd = (k >> shift) & 255u;
         const uint32_t pos = s_off[dd] + (i - s_lstart[dd]);
@@ -478,8 +515,8 @@ cudaError_t sort_digits(const Src &src, int n, const SortWork &w, Ctl *ctl, cuda
         b.ghist = w.ghist;
         b.status = w.status + static_cast<size_t>(p) * nt * kLookCounters;
         b.status_next = p < 3 ? b.status + static_cast<size_t>(nt) * kLookCounters : nullptr;
-        if (p == 0) k_sort_pass<Src, true><<<nt, 256, 0, st>>>(src, static_cast<uint32_t>(n), p, b, ctl);
-        else k_sort_pass<Src, false><<<nt, 256, 0, st>>>(src, static_cast<uint32_t>(n), p, b, ctl);
+        if (p == 0) k_sort_pass<Src, true><<<nt, kPassThreads, 0, st>>>(src, static_cast<uint32_t>(n), p, b, ctl);
+        else k_sort_pass<Src, false><<<nt, kPassThreads, 0, st>>>(src, static_cast<uint32_t>(n), p, b, ctl);
     }
     return cudaGetLastError();
 }
@@ -500,7 +537,7 @@ int sort_blocks() {
     return g;
 }
 
-uint32_t sort_tiles(int64_t n) { return static_cast<uint32_t>((n + kSortTile - 1) / kSortTile); }
+uint32_t sort_tiles(int64_t n) { return static_cast<uint32_t>((n + kPassTile - 1) / kPassTile); }
 
 size_t sort_status_bytes(int64_t n) {
     return 4 * static_cast<size_t>(sort_tiles(n > 0 ? n : 1)) * kLookCounters * sizeof(uint64_t);
