@@ -26,6 +26,7 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
     o.ctl = take(256);
+    o.sort_hist = take(4 * 256 * 4);     // right after the control block: one memset per render clears both
     o.rec = take(N * sizeof(Rec));
     o.tiles = take(N * 4);
     o.depth = take(N * 4);
@@ -33,7 +34,6 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     o.sort_v[0] = take(N * 4); o.sort_v[1] = take(N * 4);
     o.order = take(N * 4);
     o.vis_index = take(N * 4);
-    o.sort_hist = take(4 * 256 * 4);
     o.sort_status = take(sort_status_bytes(n));
     o.bin_m = take(static_cast<size_t>(kBinChunks) * o.Ty * 8);   // entries and pairs per (row, chunk)
     o.bin_rows = take(bin_rows_bytes(o.Ty));
@@ -277,7 +277,9 @@ int front_preprocess(const gs_scene *scene, const gs_camera *camera, uint32_t la
     f->image = image;
     f->alpha = alpha;
     for (int c = 0; c < 3; ++c) f->bg[c] = bg[c];
-    if ((rc = cuda_check(cudaMemsetAsync(f->ctl, 0, sizeof(Ctl), st), "memset status")) != GS_OK) return rc;
+    // the control block and the depth-sort histograms that follow it
+    if ((rc = cuda_check(cudaMemsetAsync(f->ctl, 0, L.sort_hist + 4 * 256 * 4 - L.ctl, st), "memset status")) != GS_OK)
+        return rc;
     if ((rc = cuda_check(cudaMemsetAsync(at<char>(workspace, L.ranges), 0, static_cast<size_t>(L.Tn) * 8, st),
                          "memset ranges")) != GS_OK)
         return rc;

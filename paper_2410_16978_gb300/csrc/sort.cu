@@ -254,10 +254,13 @@ __device__ uint32_t look_back(uint64_t *status, uint32_t t, int c, uint32_t own,
 }
 
 template <class Src>
-__global__ void __launch_bounds__(256) k_sort_hist(Src src, uint32_t n, uint32_t *__restrict__ ghist, Ctl *ctl) {
+__global__ void __launch_bounds__(256) k_sort_hist(Src src, uint32_t n, uint32_t *__restrict__ ghist, Ctl *ctl,
+                                                   uint64_t *__restrict__ status0, uint32_t status_words) {
     __shared__ uint32_t s_h[4][256];
     __shared__ uint32_t s_w[8];
     const int lane = threadIdx.x & 31;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < status_words; k += gridDim.x * blockDim.x)
+        status0[k] = 0;
     for (int k = threadIdx.x; k < 4 * 256; k += 256) (&s_h[0][0])[k] = 0;
     __syncthreads();
     uint32_t beg, end;
@@ -488,12 +491,11 @@ __global__ void __launch_bounds__(kPassThreads) k_sort_pass(Src src, uint32_t n_
 template <class Src>
 cudaError_t sort_histograms(const Src &src, int n, const SortWork &w, Ctl *ctl, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
+    // the histograms were cleared with the control block; the kernel also zeroes the first digit kernel's
+    // look-back words
     const uint32_t nt = sort_tiles(n);
-    cudaError_t e = cudaMemsetAsync(w.ghist, 0, 4 * 256 * sizeof(uint32_t), st);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(w.status, 0, static_cast<size_t>(nt) * kLookCounters * sizeof(uint64_t), st);
-    if (e != cudaSuccess) return e;
-    k_sort_hist<<<sort_blocks(), 256, 0, st>>>(src, static_cast<uint32_t>(n), w.ghist, ctl);
+    k_sort_hist<<<sort_blocks(), 256, 0, st>>>(src, static_cast<uint32_t>(n), w.ghist, ctl, w.status,
+                                               nt * kLookCounters);
     return cudaGetLastError();
 }
 
