@@ -360,9 +360,7 @@ __global__ void __launch_bounds__(1024) k_bin_tiles_scan(const RowInfo *__restri
 cudaError_t launch_bin_rows(const uint32_t *order, const Rec *rec, uint32_t n_cap, int Ty, uint32_t *M,
                             void *rows_buf, uint2 *rowlist, Ctl *ctl, uint64_t cap, uint32_t piece, cudaStream_t st) {
     if (Ty > kBinMaxDim) return cudaErrorInvalidValue;
-    RowInfo *rows = static_cast<RowInfo *>(rows_buf);
-    cudaError_t e = cudaMemsetAsync(rows, 0, static_cast<size_t>(Ty) * sizeof(RowInfo), st);
-    if (e != cudaSuccess) return e;
+    RowInfo *rows = static_cast<RowInfo *>(rows_buf);   // zero on entry (cleared with the control block)
     k_bin_rows<false><<<kBinBlocks, 256, 0, st>>>(order, rec, n_cap, Ty, M, rows, rowlist, ctl);
     k_bin_rowscan<<<Ty, 1024, 0, st>>>(M, kBinBlocks * 8, Ty, rows);
     k_bin_rowstart<<<1, 256, 0, st>>>(rows, Ty, ctl, cap, piece);

@@ -25,8 +25,12 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     const size_t N = static_cast<size_t>(n), D = static_cast<size_t>(dup_cap), P = static_cast<size_t>(W) * H;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
+    // the control block, the depth-sort histograms, the binning's per-row counters and the tile ranges are
+    // adjacent: one memset per render clears them all
     o.ctl = take(256);
-    o.sort_hist = take(4 * 256 * 4);     // right after the control block: one memset per render clears both
+    o.sort_hist = take(4 * 256 * 4);
+    o.bin_rows = take(bin_rows_bytes(o.Ty));
+    o.ranges = take(static_cast<size_t>(o.Tn) * 8);
     o.rec = take(N * sizeof(Rec));
     o.tiles = take(N * 4);
     o.depth = take(N * 4);
@@ -36,10 +40,8 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     o.vis_index = take(N * 4);
     o.sort_status = take(sort_status_bytes(n));
     o.bin_m = take(static_cast<size_t>(kBinChunks) * o.Ty * 8);   // entries and pairs per (row, chunk)
-    o.bin_rows = take(bin_rows_bytes(o.Ty));
     o.bin_piece = bin_piece_entries(dup_cap, o.Tx);
     o.bin_p = take(bin_piece_bytes(dup_cap, o.Tx, o.Ty));
-    o.ranges = take(static_cast<size_t>(o.Tn) * 8);
     o.t_final = take(P * 4);
     o.n_contrib = take(P * 4);
     o.partials = take(kMaxSortBlocks * 4);
@@ -277,11 +279,10 @@ int front_preprocess(const gs_scene *scene, const gs_camera *camera, uint32_t la
     f->image = image;
     f->alpha = alpha;
     for (int c = 0; c < 3; ++c) f->bg[c] = bg[c];
-    // the control block and the depth-sort histograms that follow it
-    if ((rc = cuda_check(cudaMemsetAsync(f->ctl, 0, L.sort_hist + 4 * 256 * 4 - L.ctl, st), "memset status")) != GS_OK)
-        return rc;
-    if ((rc = cuda_check(cudaMemsetAsync(at<char>(workspace, L.ranges), 0, static_cast<size_t>(L.Tn) * 8, st),
-                         "memset ranges")) != GS_OK)
+    // the control block and what follows it: depth-sort histograms, binning row counters, tile ranges (all empty
+    // if the binning overflows)
+    if ((rc = cuda_check(cudaMemsetAsync(f->ctl, 0, L.ranges + static_cast<size_t>(L.Tn) * 8 - L.ctl, st),
+                         "memset status")) != GS_OK)
         return rc;
     Stage sg(GS_STAGE_PREPROCESS, st, 1);
     return cuda_check(launch_preprocess(f->sv, f->cv, layer_mask, pl, f->rec, f->tiles, f->depth, st), "preprocess");

@@ -147,7 +147,8 @@ cudaError_t launch_sort_digits2(const uint32_t *tiles_a, const uint32_t *depth_a
 // Tile binning (bin.cu).  Rows: splits the depth-ordered visible Gaussians
 // (order[p], p < min(ctl->n_vis, n_cap)) into per-tile-row lists of
 // (Gaussian, x0 | x1 << 16) in depth order; writes n_dup and the overflow
-// status (n_dup > cap).  M: 2 kBinChunks Ty words; rows_buf: bin_rows_bytes(Ty).
+// status (n_dup > cap).  M: 2 kBinChunks Ty words; rows_buf: bin_rows_bytes(Ty),
+// zero on entry.
 cudaError_t launch_bin_rows(const uint32_t *order, const Rec *rec, uint32_t n_cap, int Ty, uint32_t *M,
                             void *rows_buf, uint2 *rowlist, Ctl *ctl, uint64_t cap, uint32_t piece, cudaStream_t st);
 // Tiles: splits every row list into its tiles; writes the final Gaussian list
