@@ -179,32 +179,42 @@ __global__ void __launch_bounds__(256) k_bin_rows(const uint32_t *__restrict__ o
 }
 
 // Per row (one CTA each): exclusive scan of the row's K chunk counts in place.
+// The row moves through shared memory with coalesced loads and stores (each
+// thread scans a contiguous run of kBinChunksPerThread counts); the row's pair
+// total needs only a sum, read coalesced.
 __global__ void __launch_bounds__(1024) k_bin_rowscan(uint32_t *__restrict__ M, int K, int Ty,
                                                       RowInfo *__restrict__ rows) {
     __shared__ uint32_t s_w[32];
+    __shared__ uint32_t s_row[kBinChunks];
     uint32_t *row = M + static_cast<size_t>(blockIdx.x) * K;
     const uint32_t *prow = M + static_cast<size_t>(Ty + blockIdx.x) * K;   // pairs of the same row
+    uint32_t psum = 0;
+    for (int i = threadIdx.x; i < K; i += 1024) {
+        s_row[i] = row[i];
+        psum += prow[i];
+    }
+    uint32_t ptot;
+    block_excl_scan<1024>(psum, s_w, &ptot);             // synchronises the block, so s_row is complete
+    if (threadIdx.x == 0) rows[blockIdx.x].pairs = ptot;
     const int per = (K + 1023) / 1024;
     uint32_t v[kBinChunksPerThread];
-    uint32_t sum = 0, psum = 0;
+    uint32_t sum = 0;
 #pragma unroll
     for (int q = 0; q < kBinChunksPerThread; ++q) {
         const int i = threadIdx.x * per + q;
-        v[q] = (q < per && i < K) ? row[i] : 0u;
+        v[q] = (q < per && i < K) ? s_row[i] : 0u;
         sum += v[q];
-        psum += (q < per && i < K) ? prow[i] : 0u;
     }
-    uint32_t ptot;
-    block_excl_scan<1024>(psum, s_w, &ptot);
-    if (threadIdx.x == 0) rows[blockIdx.x].pairs = ptot;
     uint32_t tot;
     uint32_t run = block_excl_scan<1024>(sum, s_w, &tot);
 #pragma unroll
     for (int q = 0; q < kBinChunksPerThread; ++q) {
         const int i = threadIdx.x * per + q;
-        if (q < per && i < K) row[i] = run;
+        if (q < per && i < K) s_row[i] = run;
         run += v[q];
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < K; i += 1024) row[i] = s_row[i];
     if (threadIdx.x == 0) rows[blockIdx.x].entries = tot;
 }
 
