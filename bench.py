@@ -2,7 +2,7 @@
 
 One step = one pass of the whole hot path over the 1.2M-Gaussian layered
 CT-like scene (5 nested shells, SH degree 3, 1024x1024, random 5-bit layer
-mask, one clip plane): S1 preprocess, S2 binning + depth/tile radix sorts, S3
+mask, one clip plane): S1 preprocess, S2 depth radix sort + tile binning, S3
 compositing, S4 backward (with per-Gaussian contributions) and S5 prune.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]

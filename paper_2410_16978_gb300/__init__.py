@@ -1,8 +1,8 @@
 """Layered Gaussian-splatting tile rasterizer for GB300 (sm_103a).
 
 Hot path (all in hand-written CUDA in csrc/, behind the C ABI of include/gs.h):
-per-Gaussian EWA projection with SH colour, tile binning with depth-keyed
-radix sorts, front-to-back compositing honouring layer masks and clip planes,
+per-Gaussian EWA projection with SH colour, tile binning after a depth-keyed
+radix sort, front-to-back compositing honouring layer masks and clip planes,
 and the backward pass with per-Gaussian contribution accumulation and prune.
 """
 from ._lib import (  # noqa: F401

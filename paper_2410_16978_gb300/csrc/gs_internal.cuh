@@ -40,7 +40,7 @@ struct __align__(16) Rec {
 // the public gs_status; the rest are counts the kernels hand to each other.
 struct Ctl {
     gs_status st;          // 32 bytes
-    uint32_t n_vis;        // visible Gaussians (compaction total)
+    uint32_t n_vis;        // visible Gaussians (counted by the depth-sort histograms)
     uint32_t scan_total;   // scratch total of the last scan
     uint32_t depth_mm[2];  // ~min and max of the visible depth keys (digits the sort can skip)
     uint32_t fwd_queue;    // next work item of the persistent forward compositor
