@@ -107,6 +107,14 @@ __global__ void __launch_bounds__(128) k_preprocess(SceneView s, CamView c, uint
     const float pz = ((R[6] * mx + R[7] * my) + R[8] * mz) + c.t[2];
     if (keep && !(pz > c.znear)) keep = false;
     if (keep) {
+        // the SH row (read only if the splat turns out visible) is brought into L2 while the projection runs
+        if (s.dtype_sh == GS_DTYPE_F32) {
+            constexpr int K = (DEG + 1) * (DEG + 1);
+            const char *row = reinterpret_cast<const char *>(static_cast<const float *>(s.sh) +
+                                                             static_cast<int64_t>(i) * 3 * K);
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(row));                  // first and last byte of the
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(row + 3 * K * 4 - 1));  // row: its one or two lines
+        }
         const float px = ((R[0] * mx + R[1] * my) + R[2] * mz) + c.t[0];
         const float py = ((R[3] * mx + R[4] * my) + R[5] * mz) + c.t[1];
         const float s0 = exp_cw(ls0);
