@@ -109,3 +109,37 @@ def test_shared_sort_full_size_quality():
     print("c4 shared-sort right eye vs exact: PSNR %.2f dB, max |diff| %.3g, pixels differing %d of %d"
           % (p, float(d.max()), int((d.amax(0) > 0).sum()), d.shape[1] * d.shape[2]))
     assert p >= 50.0
+
+
+@pytest.mark.parametrize("eye", [0, 1])
+def test_shared_sort_backward_per_eye(eye):
+    """The backward of each eye after a shared-sort stereo render (the right
+    eye's workspace holds a copy of the shared visible list): gradients within
+    the field-normalised 1e-5 bar of the oracle's backward over that eye's
+    lists (the left eye's own order, the right eye's shared order)."""
+    from tests.gpu_util import f64_scene
+    sc, cams, mask, planes = _stereo()
+    bg = (0.1, 0.2, 0.3)
+    ds, r, imgs, als = _run(sc, cams, mask, planes, bg, True)
+    cam = cams[eye]
+    rng = np.random.default_rng(11 + eye)
+    dimg = rng.standard_normal((3, cam.height, cam.width)).astype(np.float32)
+    dal = rng.standard_normal((cam.height, cam.width)).astype(np.float32)
+    g = r[eye].backward(ds, cam, bg, torch.from_numpy(dimg).cuda(), torch.from_numpy(dal).cuda())
+    torch.cuda.synchronize()
+    pre_l = oracle.preprocess(sc, cams[0], mask, planes, "f32")
+    pre = oracle.preprocess(sc, cam, mask, planes, "f32")
+    keyed = dict(pre)
+    if eye == 1:
+        keyed["depth"] = np.where(pre_l["vis"] > 0, pre_l["depth"], pre["depth"])
+    ranges, lst = oracle.bin_tiles(keyed)
+    cb = oracle.composite_backward(pre, ranges, lst, bg, dimg, dal)
+    ref = oracle.chain(f64_scene(sc), cam, pre["vis"], cb["rec_grad"])
+    ok = cb["touched_fragile"] == 0
+    assert ok.mean() > 0.6
+    for f in ("means", "log_scales", "quats", "opacity_logit", "sh"):
+        a = g[f].cpu().numpy().reshape(sc.n, -1)[ok].astype(np.float64)
+        b = ref[f].reshape(sc.n, -1)[ok]
+        assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max(), (eye, f)
+    vis = pre["vis"] > 0
+    assert np.all(g["sh"].cpu().numpy()[~vis] == 0)
