@@ -553,7 +553,7 @@ int gs_contrib_prune(const float *contrib_max, int64_t n, float threshold, uint8
     if (!workspace || ws_bytes < need) return fail(GS_ERR_WORKSPACE, "prune workspace needs %zu bytes", need);
     if (!aligned(workspace, 16)) return fail(GS_ERR_INVALID, "workspace must be 16-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    Stage sg(GS_STAGE_PRUNE, st, 3);
+    Stage sg(GS_STAGE_PRUNE, st, 2);
     return cuda_check(launch_prune(contrib_max, static_cast<int>(n), threshold, keep, keep_index, n_keep,
                                    static_cast<uint32_t *>(workspace), st),
                       "prune");
@@ -676,7 +676,7 @@ int gs_activity_prune(const float *activity, const uint8_t *layer, int64_t n, ui
     if (!workspace || ws_bytes < need) return fail(GS_ERR_WORKSPACE, "prune workspace needs %zu bytes", need);
     if (!aligned(workspace, 16)) return fail(GS_ERR_INVALID, "workspace must be 16-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    Stage sg(GS_STAGE_PRUNE, st, 3);
+    Stage sg(GS_STAGE_PRUNE, st, 2);
     return cuda_check(launch_activity_prune(activity, layer, train_layer_mask, static_cast<int>(n), samples, threshold,
                                             keep, keep_index, n_keep, static_cast<uint32_t *>(workspace), st),
                       "activity prune");

@@ -41,7 +41,7 @@ struct __align__(16) Rec {
 struct Ctl {
     gs_status st;          // 32 bytes
     uint32_t n_vis;        // visible Gaussians (counted by the depth-sort histograms)
-    uint32_t scan_total;   // scratch total of the last scan
+    uint32_t reserved;
     uint32_t depth_mm[2];  // ~min and max of the visible depth keys (digits the sort can skip)
     uint32_t fwd_queue;    // next work item of the persistent forward compositor
     uint32_t bwd_queue;    // next work item of the persistent backward compositor

@@ -8,9 +8,10 @@
 
 namespace {
 
-// Scratch of the prune's three-kernel scan: one 32-bit partial count per scan
-// block (at most kMaxSortBlocks) followed by the 64-byte control block.  The
-// partial counts are 32-bit, so at most 2^31 - 1 items fit one call.
+// Scratch of the prune's two-kernel scan: one 32-bit partial count per scan
+// block (at most kMaxSortBlocks), sized like the prune workspace, which also
+// reserves the bytes of a control block after them.  The partial counts are
+// 32-bit, so at most 2^31 - 1 items fit one call.
 constexpr size_t kNoallocScratchBytes = 8192;
 constexpr int64_t kNoallocMaxItems = 0x7FFFFFFF;
 static_assert(gs::kMaxSortBlocks * 4 + sizeof(gs::Ctl) <= kNoallocScratchBytes, "static prune scratch too small");

@@ -68,7 +68,8 @@ __device__ __forceinline__ uint32_t block_scan_256(uint32_t v, uint32_t *s_w, ui
 }
 
 // ---------------------------------------------------------------------------
-// Generic three-kernel scan: reduce per block, scan the block sums, rescan.
+// Generic two-kernel scan: reduce per block, then rescan, each block first
+// adding up the counts of the blocks before it (at most kMaxSortBlocks).
 
 struct NSrc {               // item count: min(*dev, cap) if dev, else cap
     const uint32_t *dev;
@@ -92,46 +93,16 @@ __global__ void __launch_bounds__(256) k_scan_reduce(F f, NSrc ns, uint32_t *__r
     if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
-enum ScanFinal { FIN_NONE = 0, FIN_NKEEP = 2 };
-
-__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *__restrict__ partials, int G, int mode,
-                                                        Ctl *ctl, uint64_t cap, int64_t *n_keep) {
-    __shared__ uint32_t s_w[32];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const uint32_t v = t < G ? partials[t] : 0;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_w[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = s_w[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, w, o);
-            if (lane >= o) w += y;
-        }
-        s_w[lane] = w;
-    }
-    __syncthreads();
-    const uint32_t excl = (warp > 0 ? s_w[warp - 1] : 0) + x - v;
-    if (t < G) partials[t] = excl;
-    if (t == 0) {
-        const uint32_t total = s_w[31];
-        if (mode == FIN_NKEEP) *n_keep = total;
-        ctl->scan_total = total;
-    }
-}
-
 template <class F, class Out>
-__global__ void __launch_bounds__(256) k_scan_down(F f, NSrc ns, const uint32_t *__restrict__ partials, Out out) {
+__global__ void __launch_bounds__(256) k_scan_down(F f, NSrc ns, const uint32_t *__restrict__ partials, Out out,
+                                                   int64_t *__restrict__ n_total) {
     __shared__ uint32_t s_w[8];
     uint32_t beg, end;
     block_range(ns.get(), beg, end);
-    uint32_t run = partials[blockIdx.x];
+    uint32_t before = 0;                       // the counts of the blocks before this one
+    for (uint32_t b = threadIdx.x; b < blockIdx.x; b += 256) before += partials[b];
+    uint32_t run;
+    block_scan_256(before, s_w, &run);
     for (uint32_t t0 = beg; t0 < end; t0 += kSortTile) {
         uint32_t v[kSortItems];
         uint32_t sum = 0;
@@ -150,6 +121,7 @@ __global__ void __launch_bounds__(256) k_scan_down(F f, NSrc ns, const uint32_t 
         }
         run += tot;
     }
+    if (n_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *n_total = run;   // the last block: the total
 }
 
 // --- functors ---
@@ -571,10 +543,8 @@ cudaError_t launch_activity_prune(const float *activity, const uint8_t *layer, u
     const int G = sort_blocks();
     NSrc ns{nullptr, static_cast<uint32_t>(n)};
     ActiveFlag f{activity, layer, train_mask, 1.f / samples, thr};
-    Ctl *ctl = reinterpret_cast<Ctl *>(partials + kMaxSortBlocks);
     k_scan_reduce<<<G, 256, 0, st>>>(f, ns, partials);
-    k_scan_partials<<<1, 1024, 0, st>>>(partials, G, FIN_NKEEP, ctl, 0, n_keep);
-    k_scan_down<<<G, 256, 0, st>>>(f, ns, partials, KeepOut{keep, keep_index});
+    k_scan_down<<<G, 256, 0, st>>>(f, ns, partials, KeepOut{keep, keep_index}, n_keep);
     return cudaGetLastError();
 }
 
@@ -583,10 +553,8 @@ cudaError_t launch_prune(const float *contrib_max, int n, float thr, uint8_t *ke
     const int G = sort_blocks();
     NSrc ns{nullptr, static_cast<uint32_t>(n)};
     KeepFlag f{contrib_max, thr};
-    Ctl *ctl = reinterpret_cast<Ctl *>(partials + kMaxSortBlocks);
     k_scan_reduce<<<G, 256, 0, st>>>(f, ns, partials);
-    k_scan_partials<<<1, 1024, 0, st>>>(partials, G, FIN_NKEEP, ctl, 0, n_keep);
-    k_scan_down<<<G, 256, 0, st>>>(f, ns, partials, KeepOut{keep, keep_index});
+    k_scan_down<<<G, 256, 0, st>>>(f, ns, partials, KeepOut{keep, keep_index}, n_keep);
     return cudaGetLastError();
 }
 
