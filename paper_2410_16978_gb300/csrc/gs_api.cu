@@ -25,10 +25,11 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     const size_t N = static_cast<size_t>(n), D = static_cast<size_t>(dup_cap), P = static_cast<size_t>(W) * H;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
-    // the control block, the depth-sort histograms, the binning's per-row counters and the tile ranges are
-    // adjacent: one memset per render clears them all
+    // the control block, the depth-sort histograms and group counts, the binning's per-row counters and the
+    // tile ranges are adjacent: one memset per render clears them all
     o.ctl = take(256);
     o.sort_hist = take(4 * 256 * 4);
+    o.sort_grp = take(sort_group_bytes(n));
     o.bin_rows = take(bin_rows_bytes(o.Ty));
     o.ranges = take(static_cast<size_t>(o.Tn) * 8);
     o.rec = take(N * sizeof(Rec));
@@ -38,6 +39,7 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     o.sort_v[0] = take(N * 4); o.sort_v[1] = take(N * 4);
     o.order = take(N * 4);
     o.vis_index = take(N * 4);
+    o.sort_cnt = take(sort_count_bytes(n));
     o.sort_status = take(sort_status_bytes(n));
     o.bin_m = take(static_cast<size_t>(kBinChunks) * o.Ty * 8);   // entries and pairs per (row, chunk)
     o.bin_piece = bin_piece_entries(dup_cap, o.Tx);
@@ -279,8 +281,8 @@ int front_preprocess(const gs_scene *scene, const gs_camera *camera, uint32_t la
     f->image = image;
     f->alpha = alpha;
     for (int c = 0; c < 3; ++c) f->bg[c] = bg[c];
-    // the control block and what follows it: depth-sort histograms, binning row counters, tile ranges (all empty
-    // if the binning overflows)
+    // the control block and what follows it: depth-sort histograms and group counts, binning row counters, tile
+    // ranges (all empty if the binning overflows)
     if ((rc = cuda_check(cudaMemsetAsync(f->ctl, 0, L.ranges + static_cast<size_t>(L.Tn) * 8 - L.ctl, st),
                          "memset status")) != GS_OK)
         return rc;
@@ -301,6 +303,8 @@ SortWork sort_work(void *ws, const Layout &L) {
     w.order = at<uint32_t>(ws, L.order);
     w.vis_index = at<uint32_t>(ws, L.vis_index);
     w.ghist = at<uint32_t>(ws, L.sort_hist);
+    w.cnt = at<uint32_t>(ws, L.sort_cnt);
+    w.grp = at<uint32_t>(ws, L.sort_grp);
     w.status = at<uint64_t>(ws, L.sort_status);
     return w;
 }

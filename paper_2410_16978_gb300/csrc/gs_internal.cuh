@@ -47,7 +47,7 @@ struct Ctl {
     uint32_t bwd_queue;    // next work item of the persistent backward compositor
     uint32_t n_items;      // backward work items (tile, 8x8 block, segment)
     uint32_t n_pieces;     // row-list pieces of the binning
-    uint32_t sort_ticket[4];   // next tile of each digit kernel of the depth sort
+    uint32_t sort_ticket[4];   // next tile of each digit kernel of the depth sort (after the first)
     uint32_t pad[12];
 };
 static_assert(sizeof(Ctl) == 128, "Ctl layout");
@@ -58,7 +58,7 @@ struct Layout {
     int W = 0, H = 0, Tx = 0, Ty = 0, Tn = 0;
     uint32_t bin_piece = 0;
     size_t ctl = 0, rec = 0, tiles = 0, depth = 0, sort_k[2] = {0, 0}, sort_v[2] = {0, 0}, order = 0, vis_index = 0,
-           sort_hist = 0, sort_status = 0, bin_m = 0,
+           sort_hist = 0, sort_grp = 0, sort_cnt = 0, sort_status = 0, bin_m = 0,
            bin_rows = 0, bin_p = 0, rowlist = 0, list = 0, ranges = 0, t_final = 0, n_contrib = 0,
            partials = 0, rec_grad = 0, tile_order = 0, tile_order_bwd = 0, seg_base = 0, qwork = 0,
            ckpt = 0, items = 0, total = 0;
@@ -125,15 +125,19 @@ struct SortWork {
     uint32_t *order;               // out: visible Gaussians in (depth, index) order, N
     uint32_t *vis_index;           // out: visible Gaussians in index order, N
     uint32_t *ghist;               // 4 x 256 digit histograms
-    uint64_t *status;              // sort_status_bytes(N): look-back words of the four digit kernels
+    uint32_t *cnt;                 // sort_count_bytes(N): per-tile counts of the first digit
+    uint32_t *grp;                 // sort_group_bytes(N): their sums per group of tiles
+    uint64_t *status;              // sort_status_bytes(N): look-back words of the later digit kernels
 };
 uint32_t sort_tiles(int64_t n);
+size_t sort_count_bytes(int64_t n);
+size_t sort_group_bytes(int64_t n);
 size_t sort_status_bytes(int64_t n);
 // Sorts the Gaussians i < n with tiles[i] > 0 by (depth[i], i).  Histograms:
 // the visible count (to ctl->n_vis and ctl->st.n_visible), the key range
-// (ctl->depth_mm) and the digit histograms; these control words and the
-// tickets must be zero on entry.  Digits: writes work.order and
-// work.vis_index.
+// (ctl->depth_mm), the digit histograms and the per-tile counts of the
+// first digit; these control words (with the tickets), work.ghist and
+// work.grp must be zero on entry.  Digits: writes work.order and work.vis_index.
 cudaError_t launch_sort_histograms(const uint32_t *tiles, const uint32_t *depth, int n, const SortWork &work,
                                    Ctl *ctl, cudaStream_t st);
 cudaError_t launch_sort_digits(const uint32_t *tiles, const uint32_t *depth, int n, const SortWork &work, Ctl *ctl,

@@ -7,14 +7,20 @@
 // order).  It runs as
 //   1. one pass over all Gaussians that counts the visible ones, the four
 //      8-bit digit histograms of their keys and the smallest and largest key;
-//   2. one kernel per digit.  A CTA takes a tile of 2048 items by ticket,
-//      ranks them by digit in shared memory, and finds the tile's global
-//      offset of every digit by a decoupled look-back over the tiles before
-//      it (the single-pass prefix scan of Merrill and Garland, used per digit
-//      as in Adinets and Merrill's Onesweep radix sort).  The first digit
-//      kernel reads the Gaussians directly, keeps the visible ones and also
-//      writes their indices in index order (the visible list of the
-//      backward).
+//   2. one kernel per digit.  A CTA takes a tile of 4096 items, ranks them
+//      by digit in shared memory, and places every digit's run of the tile
+//      at the count of that digit in all smaller keys (the histogram) plus
+//      its count in the tiles before this one.  The first digit kernel reads
+//      the Gaussians directly, keeps the visible ones and also writes their
+//      indices in index order (the visible list of the backward).  Its tiles
+//      are the histogram pass's, which counts the first digit per tile and
+//      per group of G consecutive tiles (G^2 at or above the tile count): a
+//      tile's prefix is the groups before its group plus the tiles before it
+//      in its group, fewer than 2 sqrt(tiles) independent loads per digit.
+//      The later digit kernels, over the visible Gaussians only, take their
+//      tiles by ticket and find the prefix by a decoupled look-back over the
+//      tiles before them (the single-pass prefix scan of Merrill and Garland,
+//      used per digit as in Adinets and Merrill's Onesweep radix sort).
 // A digit at and above the highest bit where the smallest and largest key
 // differ is the same in every key: its kernel returns at once, and the last
 // digit kernel that runs writes the final order.  A tile waits only on tiles
@@ -182,6 +188,20 @@ __device__ __forceinline__ int sort_passes(const Ctl *ctl) {
     return m > 1 ? m : 1;
 }
 
+constexpr int kPassThreads = 512;
+constexpr int kPassWarps = kPassThreads / 32;
+constexpr int kPassTile = kPassThreads * kSortItems;
+static_assert(kPassTile % kSortTile == 0, "a digit-kernel tile is whole histogram rounds");
+
+// Tile counts of the first digit kernel: cnt[tile][digit] and their sums
+// over groups of 2^lg consecutive tiles, grp[group][digit].
+struct TileCounts {
+    uint32_t *cnt, *grp;
+    int lg;
+};
+
+// One CTA per tile of the first digit kernel: the visible count, the key
+// range, the four digit histograms, and the tile's count of every first digit.
 // Exclusive prefix of counter c over the tiles before tile t (whose own count
 // `own` is already published as an aggregate unless t == 0); publishes the
 // inclusive prefix of tile t.  The predecessors are read kLookWindow at a time,
@@ -227,16 +247,14 @@ __device__ uint32_t look_back(uint64_t *status, uint32_t t, int c, uint32_t own,
 
 template <class Src>
 __global__ void __launch_bounds__(256) k_sort_hist(Src src, uint32_t n, uint32_t *__restrict__ ghist, Ctl *ctl,
-                                                   uint64_t *__restrict__ status0, uint32_t status_words) {
+                                                   TileCounts tc) {
     __shared__ uint32_t s_h[4][256];
     __shared__ uint32_t s_w[8];
     const int lane = threadIdx.x & 31;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < status_words; k += gridDim.x * blockDim.x)
-        status0[k] = 0;
+    const uint32_t t = blockIdx.x;
     for (int k = threadIdx.x; k < 4 * 256; k += 256) (&s_h[0][0])[k] = 0;
     __syncthreads();
-    uint32_t beg, end;
-    block_range(n, beg, end);
+    const uint32_t beg = t * kPassTile, end = min(n, beg + kPassTile);
     uint32_t kinv = 0, kmax = 0, cnt = 0;
     for (uint32_t t0 = beg; t0 < end; t0 += kSortTile) {
         bool vis[kSortItems];
@@ -288,6 +306,9 @@ __global__ void __launch_bounds__(256) k_sort_hist(Src src, uint32_t n, uint32_t
         const uint32_t c = (&s_h[0][0])[k];
         if (c) atomicAdd(&ghist[k], c);
     }
+    const uint32_t c0 = s_h[0][threadIdx.x];
+    tc.cnt[static_cast<size_t>(t) * kLookCounters + threadIdx.x] = c0;
+    if (c0) atomicAdd(&tc.grp[static_cast<size_t>(t >> tc.lg) * kLookCounters + threadIdx.x], c0);
 }
 
 struct SortBufs {
@@ -296,19 +317,16 @@ struct SortBufs {
     uint32_t *final_out;             // Gaussian indices in depth order (last digit kernel)
     uint32_t *vis_index;             // first digit kernel: visible indices in index order
     const uint32_t *ghist;           // [4][256] digit histograms of the visible keys
-    uint64_t *status, *status_next;  // look-back words [tile][256] of this and the next pass
+    TileCounts tc;                   // first digit kernel: tile and group counts
+    uint64_t *status, *status_next;  // look-back words [tile][256] of this (after the first) and the next pass
 };
 
 // One digit (bits 8 pass .. 8 pass + 7) of the stable LSD sort, on tiles of
-// kPassTile items and CTAs of kPassThreads threads (fewer, larger tiles keep
-// the look-back chain short when every tile starts at once).  Warp w ranks
-// the contiguous run [256 w, 256 w + 256) of its tile in 8 rounds of 32 with
+// kPassTile items and CTAs of kPassThreads threads.  Warp w ranks the
+// contiguous run [256 w, 256 w + 256) of its tile in 8 rounds of 32 with
 // warp-private 16-bit digit counters, so items are ranked in index order; the
 // tile is then sorted by digit in shared memory and written out in that order,
 // so consecutive threads store consecutive addresses of one digit's run.
-constexpr int kPassThreads = 512;
-constexpr int kPassWarps = kPassThreads / 32;
-constexpr int kPassTile = kPassThreads * kSortItems;
 
 // Exclusive scan over the 512 threads of a block; *total = sum of all v.
 __device__ __forceinline__ uint32_t block_scan_512(uint32_t v, uint32_t *s_w, uint32_t *total) {
@@ -344,6 +362,7 @@ __global__ void __launch_bounds__(kPassThreads) k_sort_pass(Src src, uint32_t n_
     __shared__ uint32_t s_off[256];               // global position of each digit's run
     __shared__ uint32_t s_key[kPassTile], s_val[kPassTile];
     __shared__ uint32_t s_w[kPassWarps], s_vw[kPassWarps];
+    __shared__ uint32_t s_part[256];               // per digit: its count in this group's tiles before this one
     __shared__ uint32_t s_ticket, s_visbase;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -353,11 +372,15 @@ __global__ void __launch_bounds__(kPassThreads) k_sort_pass(Src src, uint32_t n_
     const uint32_t n_vis = min(ctl->n_vis, n_all);
     const uint32_t n = FIRST ? n_all : n_vis;
     const uint32_t ntiles = (n + kPassTile - 1) / kPassTile;
-    if (threadIdx.x == 0) s_ticket = atomicAdd(&ctl->sort_ticket[pass], 1u);
+    uint32_t t = blockIdx.x;                       // the first digit kernel: the histogram pass's tiles
+    if (FIRST && t >= ntiles) return;
+    if (!FIRST && threadIdx.x == 0) s_ticket = atomicAdd(&ctl->sort_ticket[pass], 1u);
     for (int e = threadIdx.x; e < kPassWarps * 256; e += kPassThreads) (&s_wc[0][0])[e] = 0;
     __syncthreads();
-    const uint32_t t = s_ticket;
-    if (t >= ntiles) return;
+    if (!FIRST) {
+        t = s_ticket;
+        if (t >= ntiles) return;
+    }
     if (!last && t < (n_vis + kPassTile - 1) / kPassTile)
         for (int c = threadIdx.x; c < kLookCounters; c += kPassThreads)
             B.status_next[static_cast<size_t>(t) * kLookCounters + c] = 0;
@@ -402,10 +425,26 @@ __global__ void __launch_bounds__(kPassThreads) k_sort_pass(Src src, uint32_t n_
         if (lane == 0) s_vw[warp] = vw;
     }
     __syncthreads();
-    // per digit d = thread (the first 256 threads): exclusive prefix over the warps, the tile's count, and
-    // its publication
-    const int d = threadIdx.x;
-    const bool dig = d < 256;
+    const int d = threadIdx.x & 255;
+    const bool dig = threadIdx.x < 256;
+    uint32_t part = 0;
+    if constexpr (FIRST) {
+        // the count of digit d in the tiles before this one: the first 256 threads sum the groups before
+        // this tile's group, the others the tiles before it in its group
+        const uint32_t g0 = t >> B.tc.lg;
+        if (dig) {
+            const uint32_t *gp = B.tc.grp + d;
+#pragma unroll 8
+            for (uint32_t g = 0; g < g0; ++g) part += gp[static_cast<size_t>(g) * kLookCounters];
+        } else {
+            const uint32_t *cp = B.tc.cnt + d;
+#pragma unroll 8
+            for (uint32_t u = g0 << B.tc.lg; u < t; ++u) part += cp[static_cast<size_t>(u) * kLookCounters];
+            s_part[d] = part;
+        }
+    }
+    // per digit d (the first 256 threads): exclusive prefix over the warps, the tile's count, and (after
+    // the first digit kernel) its publication
     uint32_t acc = 0;
     if (dig) {
 #pragma unroll
@@ -414,14 +453,16 @@ __global__ void __launch_bounds__(kPassThreads) k_sort_pass(Src src, uint32_t n_
             s_wc[w][d] = static_cast<uint16_t>(acc);
             acc += c;
         }
-        st_volatile(B.status + static_cast<size_t>(t) * kLookCounters + d, (t == 0 ? kLookIncl : kLookAgg) | acc);
+        if (!FIRST)
+            st_volatile(B.status + static_cast<size_t>(t) * kLookCounters + d, (t == 0 ? kLookIncl : kLookAgg) | acc);
     }
     uint32_t ntile;
-    const uint32_t ls = block_scan_512(acc, s_w, &ntile);
+    const uint32_t ls = block_scan_512(acc, s_w, &ntile);      // synchronises: s_part is complete
     if (dig) s_lstart[d] = ls;
     uint32_t gtot;
     const uint32_t gbase = block_scan_512(dig ? B.ghist[pass * 256 + d] : 0u, s_w, &gtot);
-    const uint32_t excl = dig ? look_back(B.status, t, d, acc, ctl) : 0u;
+    uint32_t excl = 0;
+    if (dig) excl = FIRST ? part + s_part[d] : look_back(B.status, t, d, acc, ctl);
     if (dig) s_off[d] = gbase + excl;
     if constexpr (FIRST) {
         // the items of all digits in the tiles before this one are the visible Gaussians before it
@@ -460,20 +501,34 @@ __global__ void __launch_bounds__(kPassThreads) k_sort_pass(Src src, uint32_t n_
     }
 }
 
+// 2^lg tiles per group: the least with 2^(2 lg) >= tiles.
+int sort_group_log(uint32_t nt) {
+    int lg = 0;
+    while ((static_cast<uint64_t>(1) << (2 * lg)) < nt) ++lg;
+    return lg;
+}
+
+TileCounts tile_counts(const SortWork &w, int n) {
+    TileCounts tc;
+    tc.cnt = w.cnt;
+    tc.grp = w.grp;
+    tc.lg = sort_group_log(sort_tiles(n));
+    return tc;
+}
+
 template <class Src>
 cudaError_t sort_histograms(const Src &src, int n, const SortWork &w, Ctl *ctl, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    // the histograms were cleared with the control block; the kernel also zeroes the first digit kernel's
-    // look-back words
-    const uint32_t nt = sort_tiles(n);
-    k_sort_hist<<<sort_blocks(), 256, 0, st>>>(src, static_cast<uint32_t>(n), w.ghist, ctl, w.status,
-                                               nt * kLookCounters);
+    // the histograms and the group counts were cleared with the control block
+    const TileCounts tc = tile_counts(w, n);
+    k_sort_hist<<<sort_tiles(n), 256, 0, st>>>(src, static_cast<uint32_t>(n), w.ghist, ctl, tc);
     return cudaGetLastError();
 }
 
 template <class Src>
 cudaError_t sort_digits(const Src &src, int n, const SortWork &w, Ctl *ctl, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
+    const TileCounts tc = tile_counts(w, n);
     const uint32_t nt = sort_tiles(n);
     uint32_t *A[2] = {w.keys[0], w.vals[0]}, *Bb[2] = {w.keys[1], w.vals[1]};
     for (int p = 0; p < 4; ++p) {
@@ -487,8 +542,9 @@ cudaError_t sort_digits(const Src &src, int n, const SortWork &w, Ctl *ctl, cuda
         b.final_out = w.order;
         b.vis_index = w.vis_index;
         b.ghist = w.ghist;
-        b.status = w.status + static_cast<size_t>(p) * nt * kLookCounters;
-        b.status_next = p < 3 ? b.status + static_cast<size_t>(nt) * kLookCounters : nullptr;
+        b.tc = tc;
+        b.status = p > 0 ? w.status + static_cast<size_t>(p - 1) * nt * kLookCounters : nullptr;
+        b.status_next = p < 3 ? w.status + static_cast<size_t>(p) * nt * kLookCounters : nullptr;
         if (p == 0) k_sort_pass<Src, true><<<nt, kPassThreads, 0, st>>>(src, static_cast<uint32_t>(n), p, b, ctl);
         else k_sort_pass<Src, false><<<nt, kPassThreads, 0, st>>>(src, static_cast<uint32_t>(n), p, b, ctl);
     }
@@ -513,8 +569,18 @@ int sort_blocks() {
 
 uint32_t sort_tiles(int64_t n) { return static_cast<uint32_t>((n + kPassTile - 1) / kPassTile); }
 
+size_t sort_count_bytes(int64_t n) {
+    return static_cast<size_t>(sort_tiles(n > 0 ? n : 1)) * kLookCounters * sizeof(uint32_t);
+}
+
 size_t sort_status_bytes(int64_t n) {
-    return 4 * static_cast<size_t>(sort_tiles(n > 0 ? n : 1)) * kLookCounters * sizeof(uint64_t);
+    return 3 * static_cast<size_t>(sort_tiles(n > 0 ? n : 1)) * kLookCounters * sizeof(uint64_t);
+}
+
+size_t sort_group_bytes(int64_t n) {
+    const uint32_t nt = sort_tiles(n > 0 ? n : 1);
+    const int lg = sort_group_log(nt);
+    return static_cast<size_t>((nt + (1u << lg) - 1) >> lg) * kLookCounters * sizeof(uint32_t);
 }
 
 cudaError_t launch_sort_histograms(const uint32_t *tiles, const uint32_t *depth, int n, const SortWork &w, Ctl *ctl,
