@@ -318,10 +318,11 @@ int gs_workspace_layout(int64_t n, int32_t width, int32_t height, size_t ws_byte
  * must not touch the allocator at all between set-up and shutdown.  The paper
  * has no counterpart; this is an interface convenience of this library.
  * Same arguments and results as gs_contrib_prune minus the workspace.  The
- * scan scratch (8 KiB: 1024 32-bit partial counts + a 64-byte control block)
- * is a static device array in the library, held by every GPU that loads the
- * library until the process exits; no cudaMalloc/cudaFree or allocating
- * library routine is called.  n must be in 0 .. 2^31-1 (GS_ERR_INVALID
+ * scan scratch (8 KiB, of which the scan uses one 32-bit partial count per
+ * scan block, at most 1024) is a static device array in the library, held
+ * by every GPU that loads the library until the process exits; no
+ * cudaMalloc/cudaFree or allocating library routine is called.  n must be
+ * in 0 .. 2^31-1 (GS_ERR_INVALID
  * otherwise).  The first call on each device looks up the array's device
  * address with that device current; make that first call before any stream
  * capture.  Every call shares the one array, so calls that overlap on the
