@@ -390,8 +390,9 @@ cudaError_t launch_bin_tiles(const uint2 *rowlist, const void *rows_buf, int Tx,
 }
 
 uint32_t bin_piece_entries(int64_t dup_cap, int Tx) {
-    // pieces of 256 entries, doubled until the piece count matrix stays near 64 MB
-    uint32_t piece = 256;
+    // pieces of 128 entries (shorter per-warp chains in the tile pass than 256, without lengthening the
+    // per-row piece scans as 64 does), doubled until the piece count matrix stays near 64 MB
+    uint32_t piece = 128;
     while (piece < 4096 && static_cast<double>(dup_cap) / piece * Tx * 4.0 > 64.0 * (1 << 20)) piece *= 2;
     return piece;
 }
