@@ -356,11 +356,18 @@ __global__ void __launch_bounds__(1024) k_bin_tiles_scan(const RowInfo *__restri
         const uint32_t base = ri.pair_start + s_off[t];
         if (sl == 0) ranges[static_cast<size_t>(r) * Tx + t] = make_uint2(base, base + tot);
         uint32_t run = base + before;
-        for (uint32_t p = p0; p < p1; ++p) {
-            uint32_t *c = P + static_cast<size_t>(p) * Tx + t;
-            const uint32_t v = *c;
-            *c = run;
-            run += v;
+        // eight counts loaded before any of them is replaced, so the loads overlap instead of each waiting
+        // behind the previous store
+        constexpr int kB = 8;
+        for (uint32_t p = p0; p < p1; p += kB) {
+            uint32_t v[kB];
+#pragma unroll
+            for (int k = 0; k < kB; ++k) v[k] = p + k < p1 ? P[static_cast<size_t>(p + k) * Tx + t] : 0u;
+#pragma unroll
+            for (int k = 0; k < kB; ++k) {
+                if (p + k < p1) P[static_cast<size_t>(p + k) * Tx + t] = run;
+                run += v[k];
+            }
         }
     }
 }
