@@ -40,8 +40,11 @@ METRIC = "Mpixels/s & p50/p99 frame ms (served vs plain) at PSNR>=50dB vs FP64 o
 UNIT = "Mpixels/s"
 WORKLOAD = ("layered CT-like scene: 1.2M Gaussians in 5 layers (400k/300k/250k/100k/150k shells), SH degree 3, "
             "1024x1024, random 5-bit layer mask + 1 clip plane; step = forward + backward + contribution prune")
-# Per-pair arithmetic of the compositor kernels (FLOPs, an FMA counts 2)
-FLOP_EVAL = 14         # alpha of one (pixel, splat) pair
+# Per-pair arithmetic of the compositor kernels (FLOPs, an FMA counts 2).  A pair
+# is (pixel, list entry) up to the pixel's n_contrib; the roofline counts every
+# such pair as evaluated, and roofline_detail counts the blend arithmetic only
+# for the pairs that were blended (the status word's n_blended).
+FLOP_EVAL = 14         # alpha of one pair: offsets, exponent, exp2, opacity, clamp, threshold test
 FLOP_BLEND_FWD = 10    # blending a splat into a pixel
 FLOP_BLEND_BWD = 40    # gradient of one blended pair
 
