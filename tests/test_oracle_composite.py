@@ -228,3 +228,67 @@ def test_prune_definition():
     cm = np.array([0.0, 0.004999, 0.005, 0.7])
     keep, k = oracle.prune(cm, 0.005)
     assert list(keep) == [0, 0, 1, 1] and k == 2
+
+
+def _ragged_frame(seed):
+    # 40 Gaussians over a 56x40 frame: 4x3 tiles, the last column and row ragged
+    sc = random_small_scene(seed, n=40, sh_degree=1, extent=0.45, ls_mu=-2.6)
+    cam = axis_camera(2.6, 56, 40)
+    pre = oracle.preprocess(sc, cam)
+    ranges, lst = oracle.bin_tiles(pre)
+    return sc, cam, pre, ranges, lst
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_sampled_pixels_equal_the_full_composite(seed):
+    # The sampled compositor (used to check large frames one pixel at a time) is
+    # the full compositor restricted to the listed pixels: every output, in any
+    # order of the samples, bit for bit.
+    _, _, pre, ranges, lst = _ragged_frame(seed)
+    co = oracle.composite(pre, ranges, lst, BG)
+    H, W = co["alpha"].shape
+    ys, xs = np.divmod(np.random.default_rng(seed).permutation(W * H), W)
+    cp = oracle.composite_pixels(pre, ranges, lst, xs, ys, BG)
+    assert co["ncontrib"].max() > 1 and (co["alpha"] > 0).mean() > 0.3
+    assert np.array_equal(cp["rgb"], co["image"][:, ys, xs].T)
+    assert np.array_equal(cp["alpha"], co["alpha"][ys, xs])
+    assert np.array_equal(cp["ncontrib"], co["ncontrib"][ys, xs])
+    assert np.array_equal(cp["fragile"], co["fragile"][ys, xs])
+    assert np.array_equal(cp["alt_rgb"], co["alt_image"][:, ys, xs].T)
+    assert np.array_equal(cp["alt_alpha"], co["alt_alpha"][ys, xs])
+    assert np.array_equal(cp["alt_ncontrib"], co["alt_ncontrib"][ys, xs])
+
+
+@pytest.mark.parametrize("seed", [23, 24])
+def test_tile_restricted_backward(seed):
+    # The backward restricted to some tiles (how large frames are checked patch
+    # by patch): with every tile marked it is the unrestricted pass; with dL zero
+    # outside the marked tiles the record gradients are those of the full pass
+    # bit for bit (the skipped tiles only add zeros); blend weights only count
+    # the marked tiles, so they never exceed the full pass's and equal them for
+    # a Gaussian whose whole rectangle is marked.
+    _, _, pre, ranges, lst = _ragged_frame(seed)
+    H, W = pre["H"], pre["W"]
+    Tx, Ty = (W + 15) // 16, (H + 15) // 16
+    rng = np.random.default_rng(seed)
+    dimg = rng.standard_normal((3, H, W))
+    dal = rng.standard_normal((H, W))
+    full = oracle.composite_backward(pre, ranges, lst, BG, dimg, dal)
+    ones = oracle.composite_backward(pre, ranges, lst, BG, dimg, dal, np.ones(Tx * Ty, np.uint8))
+    for k in ("rec_grad", "contrib_sum", "contrib_max", "touched_fragile"):
+        assert np.array_equal(ones[k], full[k]), k
+    tm2 = np.zeros((Ty, Tx), np.uint8)
+    tm2[:2, 1:3] = 1
+    inside = np.kron(tm2, np.ones((16, 16), np.uint8))[:H, :W] > 0
+    dimg_m, dal_m = dimg * inside, dal * inside
+    full_m = oracle.composite_backward(pre, ranges, lst, BG, dimg_m, dal_m)
+    part = oracle.composite_backward(pre, ranges, lst, BG, dimg_m, dal_m, tm2.reshape(-1))
+    assert np.abs(full_m["rec_grad"]).max() > 0
+    assert np.array_equal(part["rec_grad"], full_m["rec_grad"])
+    assert np.all(part["contrib_max"] <= full["contrib_max"])
+    assert np.all(part["contrib_sum"] <= full["contrib_sum"] * (1 + 1e-12))
+    vis = np.nonzero(pre["vis"])[0]
+    whole = [i for i in vis if tm2[pre["rect"][i][1]:pre["rect"][i][3], pre["rect"][i][0]:pre["rect"][i][2]].all()]
+    assert len(whole) >= 1
+    assert np.array_equal(part["contrib_max"][whole], full["contrib_max"][whole])
+    assert np.allclose(part["contrib_sum"][whole], full["contrib_sum"][whole], rtol=1e-12, atol=0)
