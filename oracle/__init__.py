@@ -251,6 +251,8 @@ def composite_pixels(pre: dict, ranges, lst, xs, ys, bg=(0.0, 0.0, 0.0)) -> dict
     xs = np.ascontiguousarray(xs, np.int32)
     ys = np.ascontiguousarray(ys, np.int32)
     k = xs.shape[0]
+    if ys.shape != xs.shape or (k and (xs.min() < 0 or xs.max() >= pre["W"] or ys.min() < 0 or ys.max() >= pre["H"])):
+        raise ValueError("composite_pixels: pixel coordinates outside the %dx%d frame" % (pre["W"], pre["H"]))
     o = dict(rgb=np.zeros((k, 3)), alpha=np.zeros(k), ncontrib=np.zeros(k, np.int64),
              fragile=np.zeros(k, np.int32), alt_rgb=np.zeros((k, 3)), alt_alpha=np.zeros(k),
              alt_ncontrib=np.zeros(k, np.int64))
@@ -280,7 +282,9 @@ def composite_backward(pre: dict, ranges, lst, bg, dL_dimage, dL_dalpha=None, ti
         lst = np.zeros(1, np.int32)
     dli = _f64(dL_dimage).reshape(3, H, W)
     dla = _f64(dL_dalpha).reshape(H, W) if dL_dalpha is not None else np.zeros((H, W))
-    tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8)
+    tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8).reshape(-1)
+    if tm is not None and tm.size != np.asarray(ranges).shape[0]:
+        raise ValueError("composite_backward: tile_mask needs one entry per tile (%d)" % np.asarray(ranges).shape[0])
     L.or_composite_backward(W, H, n, _p(np.ascontiguousarray(ranges, np.int64)), _p(lst),
                             _p(_f64(pre["u"])), _p(_f64(pre["v"])), _p(_f64(pre["A2"])),
                             _p(_f64(pre["beta"])), _p(_f64(pre["G2"])), _p(_f64(pre["opac"])),

@@ -292,3 +292,16 @@ def test_tile_restricted_backward(seed):
     assert len(whole) >= 1
     assert np.array_equal(part["contrib_max"][whole], full["contrib_max"][whole])
     assert np.allclose(part["contrib_sum"][whole], full["contrib_sum"][whole], rtol=1e-12, atol=0)
+
+
+def test_oracle_rejects_out_of_frame_inputs():
+    # the C oracle does no bounds checks of its own: its wrappers refuse what would
+    # index outside the frame or the tile array
+    _, _, pre, ranges, lst = _ragged_frame(21)
+    with pytest.raises(ValueError):
+        oracle.composite_pixels(pre, ranges, lst, np.array([pre["W"]]), np.array([0]), BG)
+    with pytest.raises(ValueError):
+        oracle.composite_pixels(pre, ranges, lst, np.array([0]), np.array([-1]), BG)
+    with pytest.raises(ValueError):
+        oracle.composite_backward(pre, ranges, lst, BG, np.zeros((3, pre["H"], pre["W"])), None,
+                                  np.ones(ranges.shape[0] - 1, np.uint8))
