@@ -343,13 +343,14 @@ int gs_read_status(const void *workspace, gs_status *out, void *stream);
  * Not thread safe: enable it in one thread at a time.                        */
 enum {
     GS_STAGE_PREPROCESS = 0,   /* S1 */
-    GS_STAGE_COMPACT,          /* S2: visible count and digit histograms of the depth keys */
+    GS_STAGE_COMPACT,          /* S2: visible count, digit histograms and first-digit tile counts of the depth keys */
     GS_STAGE_DEPTH_SORT,       /* S2: radix digit kernels on the depth bits (the first compacts) */
     GS_STAGE_BIN_ROWS,         /* S2: depth-ordered split of the pairs into tile rows */
     GS_STAGE_BIN_TILES,        /* S2: split of every row into its tiles, tile ranges */
-    GS_STAGE_COMPOSITE_SETUP,  /* S3/S4: compositor set-ups (tile orders, checkpoint bases, backward items) */
+    GS_STAGE_COMPOSITE_SETUP,  /* S3/S4: compositor set-ups (tile orders, checkpoint bases, backward
+                                  items and the zeroed record gradients) */
     GS_STAGE_COMPOSITE,        /* S3 (one launch per gs_render or gs_render_batch call) */
-    GS_STAGE_COMPOSITE_BWD,    /* S4a (zeroing the record gradients, work-item set-up, compositor) */
+    GS_STAGE_COMPOSITE_BWD,    /* S4a: the backward compositor */
     GS_STAGE_PREPROCESS_BWD,   /* S4b */
     GS_STAGE_PRUNE,            /* S5 */
     GS_STAGE_LOSS,             /* training: image loss and its gradient */
