@@ -654,11 +654,11 @@ constexpr int kFwdBlocksPerSm = 2;
 
 cudaError_t launch_fwd_setup(const CompositeBufs &cb, const uint2 *ranges, int Tn, cudaStream_t st) {
     if (Tn == 0) return cudaSuccess;
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice attr;
+    attr.get([] {
         cudaFuncSetAttribute(k_fwd_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, kSetupSmemTiles * 8);
-        attr = true;
-    }
+        return 1;
+    });
     const size_t smem = Tn <= kSetupSmemTiles ? static_cast<size_t>(Tn) * 8 : 0;
     k_fwd_setup<<<1, 1024, smem, st>>>(ranges, Tn, cb.order, cb.seg_base, cb.qwork, cb.queue);
     return cudaGetLastError();
@@ -677,8 +677,8 @@ cudaError_t launch_composite_forward(const FwdJob *jobs, int n, uint32_t *queue,
     }
     batch.total = total;
     if (total == 0) return cudaSuccess;
-    static int blocks = 0;
-    if (!blocks) blocks = persistent_blocks(k_composite_fwd<kFwdPx>, kFwdThreads, kFwdBlocksPerSm);
+    static PerDevice cache;
+    const int blocks = cache.get([] { return persistent_blocks(k_composite_fwd<kFwdPx>, kFwdThreads, kFwdBlocksPerSm); });
     const int b = min(blocks, static_cast<int>((total + kFwdThreads / 32 - 1) / (kFwdThreads / 32)));
     k_composite_fwd<kFwdPx><<<b, kFwdThreads, 0, st>>>(batch, queue);
     return cudaGetLastError();
@@ -688,11 +688,11 @@ cudaError_t launch_bwd_setup(const CompositeBufs &cb, int Tx, int Ty, float4 *re
                              const uint32_t *n_vis, int n, cudaStream_t st) {
     const int tiles = Tx * Ty;
     if (tiles == 0) return cudaSuccess;
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice attr;
+    attr.get([] {
         cudaFuncSetAttribute(k_bwd_setup<kBwdPx>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSetupSmemTiles * 16);
-        attr = true;
-    }
+        return 1;
+    });
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -708,8 +708,8 @@ cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *rang
                                       const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
                                       float4 *rec_grad, float *contrib_max, cudaStream_t st) {
     if (Tx * Ty == 0) return cudaSuccess;
-    static int blocks = 0;
-    if (!blocks) blocks = persistent_blocks(k_composite_bwd<kBwdPx>, kBwdThreads);
+    static PerDevice cache;
+    const int blocks = cache.get([] { return persistent_blocks(k_composite_bwd<kBwdPx>, kBwdThreads); });
     k_composite_bwd<kBwdPx><<<blocks, kBwdThreads, 0, st>>>(cb.items, cb.n_items, cb.queue, ranges, list, rec, W, H, Tx, bg,
                                                     t_final, n_contrib, cb.seg_base, cb.ckpt, cb.qwork,
                                                     dL_dimage, dL_dalpha, layer, grad_layer_mask, rec_grad,

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "../../include/gs.h"
@@ -117,6 +118,26 @@ cudaError_t launch_preprocess_backward(const SceneView &s, const CamView &c, con
                                        cudaStream_t st);
 
 int sort_blocks();   // blocks of the sort / scan kernels on this device
+
+// A positive value computed once per device ordinal (SM counts, occupancy and
+// kernel attributes are properties of a device), safe to use from several
+// host threads.  Ordinals beyond the table are computed on every call.
+class PerDevice {
+public:
+    template <class F>
+    int get(F compute) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) return compute();
+        std::lock_guard<std::mutex> lock(mu_);
+        if (v_[dev] <= 0) v_[dev] = compute();
+        return v_[dev];
+    }
+
+private:
+    static constexpr int kDevices = 64;
+    std::mutex mu_;
+    int v_[kDevices] = {};
+};
 int report(int code, const char *msg);   // sets gs_last_error_string(), returns code
 
 // Depth sort (sort.cu).  Buffers in the workspace:

@@ -556,15 +556,14 @@ cudaError_t sort_digits(const Src &src, int n, const SortWork &w, Ctl *ctl, cuda
 }  // namespace
 
 int sort_blocks() {
-    static int cached = 0;
-    if (cached) return cached;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int g = 4 * (sms > 0 ? sms : 80);
-    if (g > kMaxSortBlocks) g = kMaxSortBlocks;
-    cached = g;
-    return g;
+    static PerDevice cache;
+    return cache.get([] {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int g = 4 * (sms > 0 ? sms : 80);
+        return g < kMaxSortBlocks ? g : kMaxSortBlocks;
+    });
 }
 
 uint32_t sort_tiles(int64_t n) { return static_cast<uint32_t>((n + kPassTile - 1) / kPassTile); }
