@@ -678,7 +678,8 @@ cudaError_t launch_composite_forward(const FwdJob *jobs, int n, uint32_t *queue,
     batch.total = total;
     if (total == 0) return cudaSuccess;
     static PerDevice cache;
-    const int blocks = cache.get([] { return persistent_blocks(k_composite_fwd<kFwdPx>, kFwdThreads, kFwdBlocksPerSm); });
+    const int blocks =
+        cache.get([] { return persistent_blocks(k_composite_fwd<kFwdPx>, kFwdThreads, kFwdBlocksPerSm); });
     const int b = min(blocks, static_cast<int>((total + kFwdThreads / 32 - 1) / (kFwdThreads / 32)));
     k_composite_fwd<kFwdPx><<<b, kFwdThreads, 0, st>>>(batch, queue);
     return cudaGetLastError();
