@@ -577,9 +577,12 @@ size_t sort_status_bytes(int64_t n) {
 }
 
 size_t sort_group_bytes(int64_t n) {
+    // ceil(sqrt(tiles)) groups: never fewer than the ceil(tiles / 2^lg) in use (2^lg >= sqrt(tiles)), and
+    // non-decreasing in n, so a workspace sized for n Gaussians also holds any smaller scene
     const uint32_t nt = sort_tiles(n > 0 ? n : 1);
-    const int lg = sort_group_log(nt);
-    return static_cast<size_t>((nt + (1u << lg) - 1) >> lg) * kLookCounters * sizeof(uint32_t);
+    uint32_t g = 1;
+    while (static_cast<uint64_t>(g) * g < nt) ++g;
+    return static_cast<size_t>(g) * kLookCounters * sizeof(uint32_t);
 }
 
 cudaError_t launch_sort_histograms(const uint32_t *tiles, const uint32_t *depth, int n, const SortWork &w, Ctl *ctl,

@@ -57,6 +57,20 @@ def test_workspace_size_and_layout():
         assert e.value.code == _lib.GS_ERR_INVALID
 
 
+def test_workspace_size_grows_with_the_scene():
+    # a workspace sized for n Gaussians holds any smaller scene: the size never
+    # drops as n grows, also where the depth sort's tile count (4096 Gaussians a
+    # tile) crosses the squares at which its group size doubles
+    for tiles in (1, 4, 16, 256, 1024, 4096, 16384, 65536):
+        prev = 0
+        for n in range(max(0, 4096 * tiles - 3), 4096 * tiles + 4):
+            b = _lib.gs_render_workspace_size(n, 1024, 1024, 1_000_000)
+            assert b >= prev, (n, b, prev)
+            prev = b
+    sizes = [_lib.gs_render_workspace_size(n, 512, 512, 100_000) for n in range(0, 3_000_000, 65_537)]
+    assert sizes == sorted(sizes)
+
+
 def test_render_rejects_bad_arguments_on_host():
     L = _lib.load()
     cam = _lib.gs_camera()
