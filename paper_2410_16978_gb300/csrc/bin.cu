@@ -27,6 +27,8 @@
 // Per pair this writes the row entry once (8 B, per row of the rectangle, not
 // per tile) and the final Gaussian id once (4 B); the count matrix is a few MB.
 // Requires Tx, Ty <= kBinMaxDim (images up to 4096 x 4096).
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -405,8 +407,14 @@ uint32_t bin_piece_entries(int64_t dup_cap, int Tx) {
 }
 
 size_t bin_piece_bytes(int64_t dup_cap, int Tx, int Ty) {
+    // Rows for the pieces in use, but never fewer than the budget's row count once the pieces have grown past
+    // 128 entries: the matrix would otherwise shrink where the piece size doubles, and the workspace with it,
+    // so a workspace sized for a pair capacity could hold fewer pairs than asked for.
     const uint32_t piece = bin_piece_entries(dup_cap, Tx);
-    return (static_cast<size_t>(dup_cap) / piece + Ty + 1) * Tx * 4;
+    const size_t rows = static_cast<size_t>(dup_cap) / piece;
+    const size_t budget_rows = static_cast<size_t>((16u << 20) / static_cast<uint32_t>(Tx));   // 64 MiB of counts
+    const size_t floor_rows = std::min(static_cast<size_t>(dup_cap) / 128, budget_rows);
+    return (std::max(rows, floor_rows) + Ty + 1) * Tx * 4;
 }
 
 size_t bin_rows_bytes(int Ty) { return static_cast<size_t>(Ty) * sizeof(RowInfo); }

@@ -71,6 +71,23 @@ def test_workspace_size_grows_with_the_scene():
     assert sizes == sorted(sizes)
 
 
+@pytest.mark.parametrize("W,H,n", [(1024, 1024, 1_200_000), (2064, 2208, 3_000_000)])
+def test_workspace_size_grows_with_the_pair_capacity(W, H, n):
+    # the binning's pieces double in size as the pair capacity grows (their
+    # count matrix keeps to a budget); the workspace must still grow with the
+    # capacity, so that a workspace sized for C pairs holds at least C
+    Tx = (W + 15) // 16
+    for k in (1, 2, 4):
+        t = k * ((1 << 31) // Tx)           # where pieces of 128 k entries would outgrow the budget
+        prev = 0
+        for c in range(t - 600, t + 600, 23):
+            b = _lib.gs_render_workspace_size(n, W, H, c)
+            assert b >= prev, (c, b, prev)
+            prev = b
+            if c % 5 == 0:
+                assert _lib.gs_workspace_layout(n, W, H, b)["dup_capacity"] >= c, c
+
+
 def test_render_rejects_bad_arguments_on_host():
     L = _lib.load()
     cam = _lib.gs_camera()
