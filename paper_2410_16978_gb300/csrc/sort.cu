@@ -16,7 +16,9 @@
 //      are the histogram pass's, which counts the first digit per tile and
 //      per group of G consecutive tiles (G^2 at or above the tile count): a
 //      tile's prefix is the groups before its group plus the tiles before it
-//      in its group, fewer than 2 sqrt(tiles) independent loads per digit.
+//      in its group: two threads per digit, one loading at most sqrt(tiles)
+//      group counts and the other fewer than 2 sqrt(tiles) tile counts, all
+//      independent loads.
 //      The later digit kernels, over the visible Gaussians only, take their
 //      tiles by ticket and find the prefix by a decoupled look-back over the
 //      tiles before them (the single-pass prefix scan of Merrill and Garland,
