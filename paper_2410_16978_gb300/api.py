@@ -166,6 +166,8 @@ class Rasterizer:
             if st.error != _lib.GS_ERR_WORKSPACE:
                 raise _lib.GsError(st.error, "device status")
             self._alloc(int(math.ceil(st.n_dup * 1.25)) + 1024)
+        else:
+            raise _lib.GsError(_lib.GS_ERR_WORKSPACE, "pair list still overflows after %d regrowths" % 4)
         return image, alpha
 
     def backward(self, scene: DeviceScene, camera, bg, dL_dimage=None, dL_dalpha=None,
