@@ -322,11 +322,15 @@ int gs_workspace_layout(int64_t n, int32_t width, int32_t height, size_t ws_byte
  * scan block, at most 1024) is a static device array in the library, held
  * by every GPU that loads the library until the process exits; no
  * cudaMalloc/cudaFree or allocating library routine is called.  n must be
- * in 0 .. 2^31-1 (GS_ERR_INVALID otherwise).  The first call on each device
- * looks up the array's device address with that device current; make that
- * first call before any stream capture.  Every call shares the one array, so
- * calls that overlap on the GPU (different streams, or host threads without
- * ordering) race.                                                            */
+ * in 0 .. 2^31-1 (GS_ERR_INVALID otherwise).  Every call looks up the
+ * array's device address (cudaGetSymbolAddress) with the calling thread's
+ * current device, so the address stays right after a device reset.  The
+ * first call on each device also loads the library's module on that device,
+ * and that load is when the driver backs the array with device memory: a
+ * caller that may not allocate later makes one warm-up call (n = 0 is
+ * enough) on each device at set-up, before any stream capture.  Every call
+ * shares the one array, so calls that overlap on the GPU (different streams,
+ * or host threads without ordering) race.                                    */
 int gs_contrib_prune_noalloc(const float *contrib_max, int64_t n, float threshold, uint8_t *keep,
                              int32_t *keep_index, int64_t *n_keep, void *stream);
 

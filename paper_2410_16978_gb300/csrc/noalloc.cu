@@ -2,7 +2,6 @@
 // allocate device memory (see include/gs.h).  Its scan scratch is a
 // file-scope static device array instead of a caller-provided workspace.
 #include <cstdio>
-#include <mutex>
 
 #include "gs_internal.cuh"
 
@@ -17,13 +16,6 @@ constexpr int64_t kNoallocMaxItems = 0x7FFFFFFF;
 static_assert(gs::kMaxSortBlocks * 4 + sizeof(gs::Ctl) <= kNoallocScratchBytes, "static prune scratch too small");
 
 static __device__ __align__(256) unsigned char g_prune_scratch[kNoallocScratchBytes];
-
-// Device address of g_prune_scratch per device ordinal.  In host code the
-// symbol is only a host-side stand-in, so the address is looked up once per
-// device, with that device current, by cudaGetSymbolAddress.
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {nullptr};
 
 }  // namespace
 
@@ -40,24 +32,17 @@ extern "C" int gs_contrib_prune_noalloc(const float *contrib_max, int64_t n, flo
     if (rc != GS_OK) return rc;
     if (need > kNoallocScratchBytes)
         return gs::report(GS_ERR_WORKSPACE, "gs_contrib_prune_noalloc: scan scratch exceeds the static array");
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return gs::report(GS_ERR_CUDA, cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices)
-        return gs::report(GS_ERR_INVALID, "gs_contrib_prune_noalloc: device ordinal above 63");
+    // In host code g_prune_scratch names a host-side stand-in, not device
+    // memory, so its device address is looked up on every call, with the
+    // calling thread's current device.  No address is cached: after a
+    // cudaDeviceReset (or a new primary context) the array lives elsewhere.
+    // The first lookup on a device loads this file's module there, which is
+    // when the driver backs the array with device memory; later lookups only
+    // read the loaded module's symbol table.
     void *ptr = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[dev]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_prune_scratch);
-            if (e != cudaSuccess || !p)
-                return gs::report(GS_ERR_CUDA, e != cudaSuccess ? cudaGetErrorString(e)
-                                                                : "cudaGetSymbolAddress returned NULL");
-            g_addr[dev] = p;
-        }
-        ptr = g_addr[dev];
-    }
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_prune_scratch);
+    if (e != cudaSuccess) return gs::report(GS_ERR_CUDA, cudaGetErrorString(e));
+    if (!ptr) return gs::report(GS_ERR_CUDA, "cudaGetSymbolAddress returned NULL");
     // Nothing in the scratch has to start at zero: the scan writes every
     // partial count and control field it later reads.
     return gs_contrib_prune(contrib_max, n, threshold, keep, keep_index, n_keep, ptr, kNoallocScratchBytes, stream);

@@ -43,6 +43,16 @@ def _without_workspace(cm, thr):
     return keep, idx, nk
 
 
+def test_noalloc_prune_warm_up_call_with_no_items():
+    # The set-up call a caller that may not allocate later makes once per
+    # device: it loads the module (backing the static array) and writes a
+    # count of zero.
+    keep, idx, nk = _outputs(1)
+    _lib.gs_contrib_prune_noalloc(keep, 0, 0.005, keep, idx, nk, _stream())
+    torch.cuda.synchronize()
+    assert int(nk.item()) == 0
+
+
 def test_noalloc_prune_matches_workspace_prune_on_two_calls_in_a_row():
     rng = np.random.default_rng(20241022)
     for n, thr in ((300_001, 0.005), (70_000, 0.002)):
