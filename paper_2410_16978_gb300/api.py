@@ -156,7 +156,8 @@ class Rasterizer:
             alpha = torch.empty((H, W), dtype=torch.float32, device=self.device)
         cs = _c_scene if _c_scene is not None else scene.c_struct()
         sh = _stream_handle(stream)
-        for _ in range(4):
+        attempts = 4
+        for attempt in range(attempts):
             _lib.gs_render(cs, cam, layer_mask, list(planes), bg, self.workspace, self.ws_bytes, image, alpha, sh)
             if not check:
                 break
@@ -165,9 +166,12 @@ class Rasterizer:
                 break
             if st.error != _lib.GS_ERR_WORKSPACE:
                 raise _lib.GsError(st.error, "device status")
+            if attempt + 1 == attempts:
+                # The workspace of the failed render stays, so its status word
+                # still describes that render.
+                raise _lib.GsError(_lib.GS_ERR_WORKSPACE,
+                                   "pair list still overflows after %d regrowths" % (attempts - 1))
             self._alloc(int(math.ceil(st.n_dup * 1.25)) + 1024)
-        else:
-            raise _lib.GsError(_lib.GS_ERR_WORKSPACE, "pair list still overflows after %d regrowths" % 4)
         return image, alpha
 
     def backward(self, scene: DeviceScene, camera, bg, dL_dimage=None, dL_dalpha=None,
