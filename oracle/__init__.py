@@ -60,6 +60,37 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
 
 
+def source_path() -> str:
+    """Path of the oracle's C source (read by the planted-mistake tests)."""
+    return _SRC
+
+
+class variant:
+    """``with oracle.variant(source_text, directory):`` builds a modified copy
+    of the oracle's C source in ``directory`` and makes every function of this
+    module use it until the block ends.  Only the planted-mistake tests use it:
+    they check that the pins reject a deliberately wrong oracle."""
+
+    def __init__(self, source_text: str, directory: str):
+        self.src = os.path.join(directory, "gs_oracle_variant.c")
+        self.so = os.path.join(directory, "liboracle_variant.so")
+        with open(self.src, "w") as f:
+            f.write(source_text)
+
+    def __enter__(self):
+        global _lib
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                               self.src, "-o", self.so, "-lm"])
+        self._saved = _load()
+        _lib = _declare(ctypes.CDLL(self.so))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self._saved
+        return False
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I32 = ctypes.c_int32
@@ -70,8 +101,11 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    path = build()
-    L = ctypes.CDLL(path)
+    _lib = _declare(ctypes.CDLL(build()))
+    return _lib
+
+
+def _declare(L):
     L.or_sh_basis.argtypes = [ctypes.c_int, _P, _P, _P]
     L.or_quat_to_rot.argtypes = [_P, _P]
     L.or_preprocess64.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
@@ -91,7 +125,6 @@ def _load():
                            _U32] + [_P] * 5)
     L.or_prune.argtypes = [_I64, _P, ctypes.c_double, _P]
     L.or_prune.restype = _I64
-    _lib = L
     return L
 
 

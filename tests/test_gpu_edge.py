@@ -12,6 +12,7 @@ import torch
 import oracle
 import synth
 from synth import Scene
+from tests.helpers import branch_scene
 from tests.gpu_util import compare_image, compare_lists, compare_records, f64_scene, gpu_render, oracle_stage, read_ws
 
 pytestmark = pytest.mark.gpu
@@ -103,6 +104,20 @@ def test_degenerate_gaussians():
     extra = slice(2500, sc.n)
     # the near-plane and behind-camera ones are culled exactly as the oracle culls them
     assert pre["vis"][extra].sum() > 0 and (pre["vis"][extra] == 0).sum() > 0
+
+
+def test_branch_scene_records_lists_and_pixels():
+    """The scene whose Gaussians reach every regime of the projection (beyond
+    and at the frustum clamp, just in front of the near plane, needle / line /
+    point covariances, edge-on discs, quaternions far from unit norm,
+    saturated opacities, clamped colours): records bit-exact against the
+    oracle's single-precision path (which is itself pinned to the FP64
+    definition on the same scene), lists and ranges bit-exact, every pixel
+    within 1e-5."""
+    sc, cam, planes, groups = branch_scene()
+    pre = _check(sc, cam, 0xFFFFFFFF, planes, (0.3, 0.2, 0.1))
+    for name, idx in groups.items():
+        assert pre["vis"][idx].sum() > 0, name
 
 
 @pytest.mark.parametrize("W,H", [(1, 1), (17, 1), (1, 33), (4096, 4096), (4096, 16), (31, 4095)])
