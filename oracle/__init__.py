@@ -119,7 +119,7 @@ def _declare(L):
     L.or_bin.argtypes = [_I64, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P]
     L.or_composite.argtypes = [ctypes.c_int, ctypes.c_int] + [_P] * 19
     L.or_composite_bruteforce.argtypes = [ctypes.c_int, ctypes.c_int, _I64, _P, _I64] + [_P] * 9
-    L.or_composite_backward.argtypes = [ctypes.c_int, ctypes.c_int, _I64] + [_P] * 17
+    L.or_composite_backward.argtypes = [ctypes.c_int, ctypes.c_int, _I64] + [_P] * 18
     L.or_composite_pixels.argtypes = [ctypes.c_int, ctypes.c_int] + [_P] * 10 + [_I64] + [_P] * 9
     L.or_chain.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P, _P,
                            _U32] + [_P] * 5)
@@ -301,7 +301,9 @@ def composite_pixels(pre: dict, ranges, lst, xs, ys, bg=(0.0, 0.0, 0.0)) -> dict
 
 
 def composite_backward(pre: dict, ranges, lst, bg, dL_dimage, dL_dalpha=None, tile_mask=None) -> dict:
-    """Record gradient [N,9] = d/d(u, v, A2, beta, G2, opac, r, g, b) and contributions.
+    """Record gradient [N,9] = d/d(u, v, A2, beta, G2, opac, r, g, b) and contributions
+    (contrib_sum, contrib_max, and contrib_count: the number of pixels, i.e. of
+    terms of contrib_sum, at which each Gaussian was blended).
 
     ``tile_mask`` (uint8 per tile) restricts the pass to the marked tiles."""
     L = _load()
@@ -310,6 +312,7 @@ def composite_backward(pre: dict, ranges, lst, bg, dL_dimage, dL_dalpha=None, ti
     rg = np.zeros((n, 9))
     cs, cm = np.zeros(n), np.zeros(n)
     tf = np.zeros(n, np.int32)
+    cc = np.zeros(n, np.int64)
     lst = np.ascontiguousarray(lst, np.int32)
     if lst.size == 0:
         lst = np.zeros(1, np.int32)
@@ -322,8 +325,8 @@ def composite_backward(pre: dict, ranges, lst, bg, dL_dimage, dL_dalpha=None, ti
                             _p(_f64(pre["u"])), _p(_f64(pre["v"])), _p(_f64(pre["A2"])),
                             _p(_f64(pre["beta"])), _p(_f64(pre["G2"])), _p(_f64(pre["opac"])),
                             _p(_f64(pre["rgb"])), _p(_f64(bg)), _p(dli), _p(dla), _p(tm) if tm is not None else None,
-                            _p(rg), _p(cs), _p(cm), _p(tf))
-    return dict(rec_grad=rg, contrib_sum=cs, contrib_max=cm, touched_fragile=tf)
+                            _p(rg), _p(cs), _p(cm), _p(tf), _p(cc))
+    return dict(rec_grad=rg, contrib_sum=cs, contrib_max=cm, touched_fragile=tf, contrib_count=cc)
 
 
 def chain(scene, cam, vis, rec_grad, grad_layer_mask: int = 0xFFFFFFFF) -> dict:

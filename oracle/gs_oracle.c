@@ -685,13 +685,16 @@ void or_composite_bruteforce(int W, int H, int64_t n, const int32_t *order, int6
  * contrib_sum[g] += a T and contrib_max[g] = max(.., a T) over blended pixels.
  * rec_grad layout per Gaussian: [du, dv, dA2, dbeta, dG2, dopac, dr, dg, db].
  * touched_fragile[g] is set when a fragile pixel blends or skips g.
+ * contrib_count[g] (may be NULL) is the number of pixels at which g was
+ * blended, i.e. the number of terms of contrib_sum[g].
  * tile_mask (may be NULL) restricts the pass to the marked tiles; the result
  * is then exact for every Gaussian whose tile rectangle lies in marked tiles. */
 void or_composite_backward(int W, int H, int64_t n, const int64_t *ranges, const int32_t *list,
                            const double *u, const double *v, const double *A2, const double *beta,
                            const double *G2, const double *opac, const double *rgb, const double *bg,
                            const double *dL_dimage, const double *dL_dalpha, const uint8_t *tile_mask,
-                           double *rec_grad, double *contrib_sum, double *contrib_max, int32_t *touched_fragile) {
+                           double *rec_grad, double *contrib_sum, double *contrib_max, int32_t *touched_fragile,
+                           int64_t *contrib_count) {
     int Tx = (W + TILE - 1) / TILE;
     int64_t maxlen = 0;
     int64_t ntiles = (int64_t)Tx * ((H + TILE - 1) / TILE);
@@ -701,7 +704,10 @@ void or_composite_backward(int W, int H, int64_t n, const int64_t *ranges, const
     double *Tb = (double *)malloc(sizeof(double) * (maxlen + 1));
     double *al = (double *)malloc(sizeof(double) * (maxlen + 1));
     memset(rec_grad, 0, sizeof(double) * 9 * n);
-    for (int64_t g = 0; g < n; ++g) { contrib_sum[g] = 0; contrib_max[g] = 0; touched_fragile[g] = 0; }
+    for (int64_t g = 0; g < n; ++g) {
+        contrib_sum[g] = 0; contrib_max[g] = 0; touched_fragile[g] = 0;
+        if (contrib_count) contrib_count[g] = 0;
+    }
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             int64_t t = (int64_t)(y / TILE) * Tx + (x / TILE);
@@ -744,6 +750,7 @@ void or_composite_backward(int W, int H, int64_t n, const int64_t *ranges, const
                 double w = a * T;
                 contrib_sum[g] += w;
                 if (w > contrib_max[g]) contrib_max[g] = w;
+                if (contrib_count) contrib_count[g] += 1;
                 for (int c = 0; c < 3; ++c) S[c] += rgb[3 * g + c] * w;
             }
         }

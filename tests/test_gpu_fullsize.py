@@ -113,14 +113,15 @@ def test_fullsize_parity(name):
     ref = oracle.chain(f64_scene(sq), cam, pre["vis"], cb["rec_grad"])
     keep = np.nonzero(inside & (cb["contrib_max"] > 0))[0]
     assert keep.size >= 48, keep.size
-    errs = {}
+    errs, abs_errs = {}, {}
     for f in FIELDS:
         assert np.isfinite(g[f].cpu().numpy()).all(), (name, f)
         a = g[f].cpu().numpy().reshape(sc.n, -1)[keep].astype(np.float64)
         b = ref[f].reshape(sc.n, -1)[keep]
-        errs[f] = np.abs(a - b).max() / np.abs(b).max()
-    print(name, "gradients of", keep.size, "Gaussians (%d fragile pixels zeroed), field-normalised max error"
-          % int(fr.sum()), errs)
+        abs_errs[f] = np.abs(a - b).max()
+        errs[f] = abs_errs[f] / np.abs(b).max()
+    print(name, "gradients of", keep.size, "Gaussians (%d fragile pixels zeroed), max error field-normalised"
+          % int(fr.sum()), errs, "absolute", abs_errs)
     for f in FIELDS:
         assert errs[f] <= GRAD_TOL, (name, f, errs[f])
     # blend weights: Gaussians that no fragile pixel touches
@@ -128,5 +129,7 @@ def test_fullsize_parity(name):
     assert kc.size >= 8, kc.size
     cm = cmax.cpu().numpy()[kc]
     assert np.abs(cm - cb["contrib_max"][kc]).max() <= 1e-5
+    # contrib_sum: within 1e-5 per term, i.e. per pixel at which the Gaussian was blended
     cs = csum.cpu().numpy()[kc]
-    assert np.abs(cs - cb["contrib_sum"][kc]).max() <= 1e-4 * max(1.0, cb["contrib_sum"][kc].max())
+    err_sum = np.abs(cs - cb["contrib_sum"][kc])
+    assert (err_sum <= 1e-5 * cb["contrib_count"][kc]).all(), float((err_sum / cb["contrib_count"][kc]).max())

@@ -78,3 +78,101 @@ def test_budget_bounds_memory_in_flight():
     res, _ = srv.run_trace(trace, "served")
     assert srv.batches == len(trace) + srv.retries
     assert all(np.isfinite(r.done) for r in res)
+
+
+def test_out_of_memory_fails_only_that_request():
+    """An allocation failure of one request's view buffers (injected in the
+    allocator, as the device would raise it) ends that request with
+    GS_ERR_OOM after one retry with the pools dropped; every other request
+    completes with the same images as alone."""
+    from paper_2410_16978_gb300 import _lib
+    from paper_2410_16978_gb300.serve import _ViewBuffers
+    models = _models()
+    trace = make_trace(np.random.default_rng(6), list(models), n_requests=16, rate=None, sizes=SIZES)
+    victim = next(r for r in trace if r.model == "m_mid")
+    calls = {"n": 0, "refused": 0}
+    in_victim = {"on": False}
+
+    def allocate(n, W, H, cap, device):
+        calls["n"] += 1
+        if in_victim["on"]:
+            calls["refused"] += 1
+            raise torch.cuda.OutOfMemoryError("CUDA out of memory (injected)")
+        return _ViewBuffers(n, W, H, cap, device)
+
+    srv = RenderServer(models, memory_budget=64 << 20, allocate=allocate)
+    real_acquire = srv._acquire
+
+    def acquire(req):
+        in_victim["on"] = req.rid == victim.rid
+        try:
+            return real_acquire(req)
+        finally:
+            in_victim["on"] = False
+
+    srv._acquire = acquire
+    res, wall = srv.run_trace(trace, "served", keep_images=True)
+    torch.cuda.synchronize()
+    by = {r.rid: r for r in res}
+    assert by[victim.rid].status == "failed" and by[victim.rid].error == _lib.GS_ERR_OOM
+    assert by[victim.rid].images is None
+    assert calls["refused"] == 2                  # the first attempt and the retry after the pools were dropped
+    assert srv.failed == 1 and srv.in_use == 0
+    for req in trace:
+        if req.rid == victim.rid:
+            continue
+        assert by[req.rid].status == "done"
+        for a, b in zip(by[req.rid].images, _alone(models[req.model], req)):
+            assert torch.equal(a, b), req.rid
+    s = summarize(res, trace, wall)
+    assert s["failed"] == 1 and s["requests"] == len(trace) - 1
+
+
+def test_cancelled_requests_never_launch():
+    """Requests withdrawn before launch (by cancel_at on the trace clock, and
+    by cancel() from another thread before the replay starts) end as
+    "cancelled", launch no view, and leave the other results unchanged."""
+    import dataclasses
+    import threading
+    models = _models()
+    base = make_trace(np.random.default_rng(7), list(models), n_requests=20, rate=None, sizes=SIZES)
+    # everything arrives at 0; two requests arrive late and are withdrawn before they arrive
+    trace = [dataclasses.replace(r, arrival=0.05, cancel_at=0.0) if k in (3, 11) else r for k, r in enumerate(base)]
+    srv = RenderServer(models, memory_budget=64 << 20)
+    t = threading.Thread(target=srv.cancel, args=(trace[7].rid,))
+    t.start()
+    t.join()
+    res, wall = srv.run_trace(trace, "served", keep_images=True)
+    torch.cuda.synchronize()
+    by = {r.rid: r for r in res}
+    gone = {trace[3].rid, trace[11].rid, trace[7].rid}
+    for rid in gone:
+        assert by[rid].status == "cancelled" and by[rid].images is None
+    assert srv.cancelled == 3 and srv.retries == 0
+    assert srv.views_launched == sum(len(r.cameras) for r in trace if r.rid not in gone)
+    for req in trace:
+        if req.rid in gone:
+            continue
+        assert by[req.rid].status == "done"
+        for a, b in zip(by[req.rid].images, _alone(models[req.model], req)):
+            assert torch.equal(a, b), req.rid
+    s = summarize(res, trace, wall)
+    assert s["cancelled"] == 3 and s["requests"] == len(trace) - 3
+
+
+def test_capacity_growth_drops_undersized_pooled_buffers():
+    """After an overflow grows a (model, size) capacity, no pooled buffer of
+    the old capacity is handed out again."""
+    models = _models()
+    cam = synth.look_at_camera((0.3, -0.2, 3.6), width=128, height=96)
+    srv = RenderServer(models, memory_budget=64 << 20)
+    key = ("m_big", 128, 96)
+    srv._cap[key] = 64
+    vbs = [srv._take("m_big", cam) for _ in range(3)]
+    for vb in vbs:
+        srv._give("m_big", cam, vb)
+    assert len(srv._free[key]) == 3
+    srv._cap[key] = 1 << 20                      # the capacity grew after these were pooled
+    vb = srv._take("m_big", cam)
+    assert vb.cap == 1 << 20 and len(srv._free[key]) == 0
+    srv._give("m_big", cam, vb)

@@ -102,6 +102,13 @@ def test_contribution_of_a_lone_splat():
     cb = oracle.render_backward(sc, cam, fwd, np.zeros(3), np.zeros((3, 33, 33)))
     assert abs(cb["contrib_sum"][0] - fwd["alpha"].sum()) < 1e-12
     assert cb["contrib_max"][0] == fwd["alpha"].max()
+    # terms of the sum: the pixels where the closed form o exp(-|d|^2 / (2 s'^2)),
+    # s'^2 = (fx s / z0)^2 + 0.3, reaches 1/255 (the 3x3 pixels around the centre)
+    o = 1 / (1 + math.exp(-0.8))
+    s2 = (cam.fx * 0.03 / 4.0) ** 2 + 0.3
+    gy, gx = np.mgrid[0:33, 0:33] + 0.5
+    a = o * np.exp(-((gx - 16.5) ** 2 + (gy - 16.5) ** 2) / (2 * s2))
+    assert cb["contrib_count"][0] == (a >= 1 / 255).sum() == 9
 
 
 def test_contribution_of_a_covered_splat():
@@ -114,6 +121,11 @@ def test_contribution_of_a_covered_splat():
     o = 1 / (1 + math.exp(-1.0))
     assert abs(cb["contrib_max"][0] - o) < 1e-12
     assert abs(cb["contrib_max"][1] - o * (1 - o)) < 1e-12
+    # the near splat is larger on screen, so it is blended wherever the far one
+    # is: the terms are the pixels with any blend plus those whose last blended
+    # list entry is the far splat (n_contrib = 2)
+    assert cb["contrib_count"][0] > 0 and cb["contrib_count"][1] > 0
+    assert cb["contrib_count"].sum() == ((fwd["alpha"] > 0).sum() + (fwd["ncontrib"] >= 2).sum())
 
 
 def test_gradients_through_clamps():
