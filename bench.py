@@ -164,68 +164,206 @@ def build_workload():
 
 # ----------------------------------------------------------------------------- oracle (CPU) timing
 
-def oracle_sample(w, gpu_image=None, band_rows=8):
-    """FP64 oracle on a bounded sample of the workload: full preprocess + binning
-    of all Gaussians, forward and backward compositing of `band_rows` tile rows
-    through the image centre, chain rule for every visible Gaussian.  The
-    compositing time is scaled to the full frame.  Returns (Mpixels/s, detail)."""
+def host_threads() -> int:
+    return max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1))
+
+
+def _oracle_map(fn, items, threads):
+    """fn over items on `threads` host threads (the oracle's C functions run
+    without the Python lock, so the threads run on separate cores)."""
+    if threads <= 1:
+        return [fn(x) for x in items]
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        return list(ex.map(fn, items))
+
+
+def _chunks(n, parts):
+    step = -(-n // max(1, parts))
+    return [slice(a, min(n, a + step)) for a in range(0, n, step)]
+
+
+def oracle_preprocess(sc, cam, mask, planes, threads):
+    """FP64 preprocess of all Gaussians, split into contiguous chunks (each
+    Gaussian is independent)."""
+    import oracle
+    parts = _oracle_map(lambda sl: oracle.preprocess(sc.subset(sl), cam, mask, planes, "f64"),
+                        _chunks(sc.n, 4 * threads), threads)
+    pre = {k: np.concatenate([p[k] for p in parts]) for k in parts[0] if isinstance(parts[0][k], np.ndarray)}
+    pre["W"], pre["H"] = int(cam.width), int(cam.height)
+    return pre
+
+
+def _row_bands(H, bands):
+    """Tile rows dealt round-robin into `bands` sets (so each set mixes heavy
+    central rows and light edge rows)."""
+    Ty = (H + 15) // 16
+    return [np.arange(k, Ty, bands) for k in range(min(bands, Ty))]
+
+
+def oracle_forward(pre, ranges, lst, bg, threads):
+    """FP64 compositing of every pixel, tile rows spread over the threads."""
+    import oracle
+    W, H = pre["W"], pre["H"]
+    img = np.zeros((3, H, W))
+    alpha = np.zeros((H, W))
+    info = {"fragile": 0, "multi_fragile": 0}
+
+    def band(rows):
+        ys = np.concatenate([np.arange(r * 16, min(H, r * 16 + 16)) for r in rows])
+        gy, gx = np.meshgrid(ys, np.arange(W), indexing="ij")
+        cp = oracle.composite_pixels(pre, ranges, lst, gx.ravel(), gy.ravel(), bg)
+        return gx.ravel(), gy.ravel(), cp
+
+    for xs, ys, cp in _oracle_map(band, _row_bands(H, 4 * threads), threads):
+        img[:, ys, xs] = cp["rgb"].T
+        alpha[ys, xs] = cp["alpha"]
+        info["fragile"] += int((cp["fragile"] > 0).sum())
+        info["multi_fragile"] += int((cp["fragile"] > 1).sum())
+    return img, alpha, info
+
+
+def oracle_backward(pre, ranges, lst, bg, dimg, dal, threads):
+    """FP64 compositing backward over every pixel: each thread takes a set of
+    tile rows; record gradients and blend weights add up (the max for
+    contrib_max) over the sets."""
+    import oracle
+    W, H = pre["W"], pre["H"]
+    Tx = (W + 15) // 16
+
+    def band(rows):
+        tm = np.zeros(len(ranges), np.uint8)
+        for r in rows:
+            tm[r * Tx:(r + 1) * Tx] = 1
+        return oracle.composite_backward(pre, ranges, lst, bg, dimg, dal, tm)
+
+    out = None
+    for cb in _oracle_map(band, _row_bands(H, threads), threads):
+        if out is None:
+            out = dict(rec_grad=cb["rec_grad"].copy(), contrib_sum=cb["contrib_sum"].copy(),
+                       contrib_max=cb["contrib_max"].copy())
+        else:
+            out["rec_grad"] += cb["rec_grad"]
+            out["contrib_sum"] += cb["contrib_sum"]
+            np.maximum(out["contrib_max"], cb["contrib_max"], out=out["contrib_max"])
+    return out
+
+
+def oracle_chain(sc, cam, vis, rec_grad, threads):
+    import oracle
+    parts = _oracle_map(lambda sl: oracle.chain(sc.subset(sl), cam, vis[sl], rec_grad[sl]),
+                        _chunks(sc.n, 4 * threads), threads)
+    return {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
+
+
+def oracle_step(w, dimg, dal, threads, backward=True):
+    """One pass of the hot path on the FP64 oracle over the whole frame:
+    preprocess, binning, compositing of every pixel, and (backward=True) the
+    compositing backward of every pixel, the chain rule and the prune.
+    Returns (seconds per stage, image, detail)."""
     import oracle
     oracle.build()
     sc, cam = w["scene"], w["cameras"][0]
-    W, H = cam.width, cam.height
-    Tx, Ty = (W + 15) // 16, (H + 15) // 16
     bg = tuple(float(v) for v in w["bg"])
-    t0 = time.perf_counter()
-    pre = oracle.preprocess(sc, cam, w["layer_mask"], w["planes"], "f64")
+    t = [time.perf_counter()]
+    pre = oracle_preprocess(sc, cam, w["layer_mask"], w["planes"], threads)
+    t.append(time.perf_counter())
     ranges, lst = oracle.bin_tiles(pre)
-    t1 = time.perf_counter()
-    r0 = Ty // 2 - band_rows // 2
-    ys, xs = np.mgrid[r0 * 16:(r0 + band_rows) * 16, 0:W]
-    cp = oracle.composite_pixels(pre, ranges, lst, xs.ravel(), ys.ravel(), bg)
-    t2 = time.perf_counter()
-    tm = np.zeros(Tx * Ty, np.uint8)
-    tm[r0 * Tx:(r0 + band_rows) * Tx] = 1
-    rng = np.random.default_rng(1)
-    dimg = rng.standard_normal((3, H, W))
-    cb = oracle.composite_backward(pre, ranges, lst, bg, dimg, None, tm)
-    t3 = time.perf_counter()
-    oracle.chain(sc, cam, pre["vis"], cb["rec_grad"])
-    t4 = time.perf_counter()
-    frac = (band_rows * 16 * W) / float(W * H)
-    full = (t1 - t0) + (t4 - t3) + ((t2 - t1) + (t3 - t2)) / frac
-    detail = {"preprocess_bin_s": t1 - t0, "band_forward_s": t2 - t1, "band_backward_s": t3 - t2,
-              "chain_s": t4 - t3, "frame_s_extrapolated": full}
-    psnr = None
-    if gpu_image is not None:
-        g = gpu_image[:, ys.ravel(), xs.ravel()].T.astype(np.float64)
-        mse = float(((g - cp["rgb"]) ** 2).mean())
-        psnr = float("inf") if mse == 0 else 10 * math.log10(1.0 / mse)
-    return (W * H) / full / 1e6, detail, psnr, (t4 - t0)
+    t.append(time.perf_counter())
+    img, alpha, info = oracle_forward(pre, ranges, lst, bg, threads)
+    t.append(time.perf_counter())
+    names = ["preprocess", "binning", "forward"]
+    if backward:
+        cb = oracle_backward(pre, ranges, lst, bg, dimg, dal, threads)
+        t.append(time.perf_counter())
+        oracle_chain(sc, cam, pre["vis"], cb["rec_grad"], threads)
+        t.append(time.perf_counter())
+        oracle.prune(cb["contrib_max"], 0.005)
+        t.append(time.perf_counter())
+        names += ["backward", "chain", "prune"]
+    stages = {k: t[i + 1] - t[i] for i, k in enumerate(names)}
+    info.update(visible=int(pre["vis"].sum()), pairs=int(lst.shape[0]))
+    return stages, img, info
+
+
+def _workload_config(w, world):
+    """The `config` object of both arms (the workload, nothing about the implementation)."""
+    sc, cam = w["scene"], w["cameras"][0]
+    scene_mb = sum(a.nbytes for a in (sc.means, sc.log_scales, sc.quats, sc.opacity_logit, sc.sh)) / 1e6
+    return {"workload": WORKLOAD, "gaussians": sc.n, "width": cam.width, "height": cam.height,
+            "l2": "inputs larger than L2 (scene %.0f MB)" % scene_mb,
+            "parallelism": "replicas x%d" % world if world > 1 else "single device"}
+
+
+def _upstream_grads(W, H):
+    rng = np.random.default_rng(7)
+    dimg = rng.standard_normal((3, H, W)).astype(np.float32) / (3 * W * H)
+    dal = rng.standard_normal((H, W)).astype(np.float32) / (W * H)
+    return dimg, dal
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: every step is the whole c2 step (full
+    frame, forward + backward + prune) in FP64 on all host cores; its measured
+    wall time is the step time."""
     if rank != 0:
         return
     w = build_workload()
-    sample = "full FP64 preprocess + binning of 1.2M Gaussians, compositing fwd+bwd of 2 central tile rows " \
-             "(32x1024 px) scaled to the frame, FP64 chain rule of every visible Gaussian"
-    args_band = 2
-    vals = []
+    cam = w["cameras"][0]
+    threads = host_threads()
+    dimg, dal = _upstream_grads(cam.width, cam.height)
     for _ in range(args.warmup):
-        pass    # the oracle has no warm-up state; warm-up steps are not repeated on the CPU
+        oracle_step(w, dimg, dal, threads)
+    walls, stage_sum, info = [], {}, None
     for _ in range(max(1, args.steps)):
-        v, detail, _, wall = oracle_sample(w, band_rows=args_band)
-        vals.append(v)
-    v = statistics.median(vals)
-    frame_ms = 1e3 * (w["cameras"][0].width * w["cameras"][0].height) / (v * 1e6)
+        t0 = time.perf_counter()
+        stages, _, info = oracle_step(w, dimg, dal, threads)
+        walls.append(time.perf_counter() - t0)
+        for k, v in stages.items():
+            stage_sum[k] = stage_sum.get(k, 0.0) + v
+    ms = 1e3 * statistics.mean(walls)
+    v = cam.width * cam.height / (ms / 1e3) / 1e6
+    sample = ("the whole step on the full %dx%d frame: FP64 preprocess of all %d Gaussians, binning, compositing "
+              "and compositing backward of every pixel, chain rule, prune; %d host threads over tile rows and "
+              "Gaussian chunks" % (cam.width, cam.height, w["scene"].n, threads))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": frame_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "mode": "oracle (FP64 C, single thread)"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _workload_config(w, world),
+            "mode": "FP64 CPU oracle (C), %d threads" % threads,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "detail": detail}
+            "stages_s_per_step": {k: round(x / len(walls), 4) for k, x in stage_sum.items()},
+            "wall_s_min_max": [round(min(walls), 4), round(max(walls), 4)],
+            "visible": info["visible"], "pairs": info["pairs"]}
     print(json.dumps(line), flush=True)
+
+
+def oracle_baselines(w, gpu_image, threads):
+    """The oracle timed beside the GPU (rank 0, N = 1): the whole c2 step on
+    all host threads (full frame), with the PSNR of the GPU image against its
+    FP64 image over every pixel; the 128x128 workload's full frame on one and
+    on all threads."""
+    import synth
+    cam = w["cameras"][0]
+    dimg, dal = _upstream_grads(cam.width, cam.height)
+    t0 = time.perf_counter()
+    stages, img, info = oracle_step(w, dimg, dal, threads)
+    wall = time.perf_counter() - t0
+    mse = float(((gpu_image.astype(np.float64) - img) ** 2).mean())
+    psnr = float("inf") if mse == 0 else 10 * math.log10(1.0 / mse)
+    err = np.abs(gpu_image.astype(np.float64) - img).max(0)
+    w1 = synth.scene_c1()
+    c1 = {}
+    for th in (1, threads):
+        t1 = time.perf_counter()
+        oracle_step(w1, *_upstream_grads(128, 128), th, backward=False)
+        c1["forward_ms_%d_thread%s" % (th, "s" if th > 1 else "")] = round(1e3 * (time.perf_counter() - t1), 3)
+    detail = {"c2_step_s": round(wall, 4), "c2_stages_s": {k: round(v, 4) for k, v in stages.items()},
+              "c1_full_frame": c1, "threads": threads}
+    parity = {"psnr_db_full_frame": psnr, "max_abs_err": float(err.max()),
+              "fragile_pixels": info["fragile"], "multi_fragile_pixels": info["multi_fragile"],
+              "pixels": int(cam.width * cam.height)}
+    return cam.width * cam.height / wall / 1e6, wall, detail, parity
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -234,40 +372,92 @@ SERVE_MODELS = (("0.5M", 0.5 / 1.2), ("1.5M", 1.25), ("3M", None))
 SERVE_SIZES = ((512, 512, 1), (1024, 1024, 1), (2064, 2208, 2))
 
 
-def run_serving(dev, n_requests=512, rate=300.0, budget=8 << 30):
+def run_serving(dev, n_requests=512, rate=300.0, budget=8 << 30, replays=3):
     """Three resident layered models (0.5M, 1.5M, 3M Gaussians, SH degree 3)
     and a Poisson trace of mixed requests, replayed in real time through the
-    served path (continuous batching, 2 streams) and through the plain path
-    (one request per gs_render sequence, FIFO), then replayed saturated (all
-    requests at t = 0) for peak throughput."""
+    served path (continuous batching) and through the plain path (one request
+    per gs_render sequence, FIFO), then replayed saturated (all requests at
+    t = 0) for peak throughput.
+
+    Both modes start every replay from the same calibration: the pair
+    capacities are sized once (36 random views, then one saturated pass of
+    the trace itself), and before each replay the capacities are restored,
+    the buffer pools dropped and re-filled by a short warm-up in that mode.
+    The 300 req/s trace is replayed `replays` times per mode in alternating
+    order (plain, served, served, plain, ...); medians and ranges are
+    reported with the retries of every replay.  One served request is
+    rendered again and compared with the FP64 oracle."""
     import synth
+    import torch
     from paper_2410_16978_gb300 import DeviceScene
     from paper_2410_16978_gb300.serve import RenderServer, make_trace, summarize
 
-    models = {}
+    models, hosts = {}, {}
     for name, scale in SERVE_MODELS:
         sc = synth.scene_c4()["scene"] if scale is None else synth.scene_c2(scale=scale)["scene"]
+        hosts[name] = sc
         models[name] = DeviceScene.from_host(sc, device=dev)
     srv = RenderServer(models, memory_budget=budget, device=dev)
-    rng = np.random.default_rng(synth.config_seed(4))
+    rng = np.random.default_rng(synth.config_seed(5))
     cal = make_trace(np.random.default_rng(1), list(models), n_requests=36, rate=None, sizes=SERVE_SIZES)
     for req in cal:
         srv.calibrate(req.model, req.cameras, req.layer_mask, req.planes)
     trace = make_trace(rng, list(models), n_requests=n_requests, rate=rate, sizes=SERVE_SIZES)
     sat = [dataclasses.replace(r, arrival=0.0) for r in trace]
+    srv.run_trace(sat, "served")                  # sizes the capacities of every (model, size) of the trace
+    caps = srv.capacities()
     out = {"models": {k: m.n for k, m in models.items()}, "requests": n_requests, "rate_rps": rate,
            "memory_budget_gib": budget / 2 ** 30, "sizes": ["%dx%dx%d" % s for s in SERVE_SIZES],
-           "mpixels_total": sum(r.pixels for r in trace) / 1e6}
+           "mpixels_total": sum(r.pixels for r in trace) / 1e6, "replays_per_mode": replays,
+           "calibration": "36 random views + one saturated served pass of the trace; restored before every replay"}
+
+    def replay(tr, mode):
+        srv.set_capacities(caps)
+        srv.run_trace(sat[:64], mode)             # refills the pools in this mode
+        r0, b0, v0 = srv.retries, srv.batches, srv.views_launched
+        res, wall = srv.run_trace(tr, mode)
+        s = summarize(res, tr, wall)
+        s.update(retries=srv.retries - r0, launches=(srv.batches - b0) if mode == "served" else None,
+                 views=srv.views_launched - v0)
+        return s
+
+    order = [("plain", "served")[(k // 2 + k) % 2] for k in range(2 * replays)]   # ABBAAB...
+    runs = {"plain": [], "served": []}
+    for mode in order:
+        runs[mode].append(replay(trace, mode))
+    for mode, rs in runs.items():
+        med = {k: statistics.median(r[k] for r in rs) for k in ("mpix_s", "p50_ms", "p99_ms", "mean_ms")}
+        med.update({k + "_range": [round(min(r[k] for r in rs), 4), round(max(r[k] for r in rs), 4)]
+                    for k in ("mpix_s", "p50_ms", "p99_ms")})
+        med["retries"] = [r["retries"] for r in rs]
+        med["by_size_p50_p99_ms"] = rs[len(rs) // 2]["by_size_p50_p99_ms"]
+        med["views"] = rs[0]["views"]
+        if mode == "served":
+            med["launches"] = [r["launches"] for r in rs]
+        out["trace_%s" % mode] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in med.items()}
     for mode in ("plain", "served"):
-        srv.run_trace(sat[:64], mode)            # warm-up: fills the buffer pools
-    for label, tr in (("trace", trace), ("saturated", sat)):
-        for mode in ("plain", "served"):
-            r0, b0, v0 = srv.retries, srv.batches, srv.views_launched
-            res, wall = srv.run_trace(tr, mode)
-            s = summarize(res, tr, wall)
-            s.update(retries=srv.retries - r0, launches=(srv.batches - b0) if mode == "served" else None,
-                     views=srv.views_launched - v0)
-            out["%s_%s" % (label, mode)] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()}
+        s = replay(sat, mode)
+        out["saturated_%s" % mode] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()}
+    out["order"] = order
+
+    # one served request (a 1024x1024 view of the 1.5M model) against the FP64 oracle
+    import oracle
+    req = next(r for r in trace if r.model == "1.5M" and r.cameras[0].width == 1024)
+    srv.set_capacities(caps)
+    res, _ = srv.run_trace([dataclasses.replace(req, arrival=0.0)], "served", keep_images=True)
+    torch.cuda.synchronize()
+    img = res[0].images[0].cpu().numpy().astype(np.float64)
+    cam = req.cameras[0]
+    prng = np.random.default_rng(3)
+    xs = prng.integers(0, cam.width, 16384).astype(np.int32)
+    ys = prng.integers(0, cam.height, 16384).astype(np.int32)
+    pre = oracle.preprocess(hosts[req.model], cam, req.layer_mask, req.planes, "f64")
+    ranges, lst = oracle.bin_tiles(pre)
+    cp = oracle.composite_pixels(pre, ranges, lst, xs, ys, req.bg)
+    mse = float(((img[:, ys, xs].T - cp["rgb"]) ** 2).mean())
+    out["served_view_psnr_db_vs_fp64_oracle"] = float("inf") if mse == 0 else 10 * math.log10(1.0 / mse)
+    out["served_view"] = "request %d: 1.5M model, 1024x1024, mask %d, %d plane(s); 16384 random pixels" % (
+        req.rid, req.layer_mask, len(req.planes))
     return out
 
 
@@ -321,6 +511,98 @@ def run_training(dev, steps=24):
             "targets": "rendered on the GPU from the perturbed scene (the parity tests use oracle renders)"}
 
 
+def run_stereo(dev, frames=20, warmup=3):
+    """The mixed-precision stereo workload's frame (3M Gaussians, 2 x
+    2064x2208, FP32 storage): gs_render_stereo with a depth sort per eye and
+    with the shared-eye sort (paper Sec. 3.3), CUDA events over `frames`
+    frames after `warmup`; the right eye of the shared sort against the exact
+    right eye."""
+    import torch
+    import synth
+    from paper_2410_16978_gb300 import DeviceScene, Rasterizer, _lib
+    w = synth.scene_c4()
+    sc, cams, mask, planes = w["scene"], w["cameras"], w["layer_mask"], w["planes"]
+    bg = (0.0, 0.0, 0.0)
+    ds = DeviceScene.from_host(sc, device=dev)
+    rs = [Rasterizer(sc.n, c.width, c.height, device=dev) for c in cams]
+    for r, c in zip(rs, cams):
+        r.render(ds, c, mask, planes, bg, check=True)
+        r._alloc(int(r.dup_capacity * 1.1) + 4096)      # the shared order adds the other eye's Gaussians
+    imgs = [torch.empty((3, c.height, c.width), device=dev) for c in cams]
+    als = [torch.empty((c.height, c.width), device=dev) for c in cams]
+    cs, cl, cr = ds.c_struct(), _lib.make_camera(cams[0]), _lib.make_camera(cams[1])
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "3M Gaussians in 5 layers, SH3 FP32, stereo 2 x 2064x2208 (64 mm), frames of both eyes"}
+    right = {}
+    for shared in (False, True):
+        def frame():
+            _lib.gs_render_stereo(cs, cl, cr, mask, list(planes), bg, rs[0].workspace, rs[0].ws_bytes,
+                                  rs[1].workspace, rs[1].ws_bytes, imgs[0], als[0], imgs[1], als[1], shared,
+                                  int(stream.cuda_stream))
+        for _ in range(warmup):
+            frame()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(frames)]
+        for e0, e1 in ev:
+            e0.record(stream)
+            frame()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = sorted(a.elapsed_time(b) for a, b in ev)
+        assert rs[0].status().error == 0 and rs[1].status().error == 0
+        right[shared] = imgs[1].clone()
+        out["shared_sort" if shared else "per_eye_sort"] = {"ms_p50": round(ms[len(ms) // 2], 4),
+                                                             "ms_min": round(ms[0], 4),
+                                                             "mpix_s": round(2 * cams[0].width * cams[0].height /
+                                                                             (ms[len(ms) // 2] / 1e3) / 1e6, 1)}
+    d = (right[True] - right[False]).double()
+    mse = float((d * d).mean())
+    out["right_eye_psnr_shared_vs_per_eye_db"] = float("inf") if mse == 0 else 10 * math.log10(1.0 / mse)
+    out["right_eye_max_abs_diff"] = float(d.abs().max())
+    out["speedup"] = round(out["per_eye_sort"]["ms_p50"] / out["shared_sort"]["ms_p50"], 4)
+    return out
+
+
+def stage_work(rast, sc, st, W, H):
+    """Algorithmic bytes (or FLOPs) of each step of the hot path for the
+    rendered frame, from the counts in its workspace: N Gaussians, V visible,
+    R (Gaussian, tile row) entries, D (tile, Gaussian) pairs, the depth
+    digits the sort needs, E evaluated and B blended (pixel, list entry)
+    pairs.  Per-unit figures as in the kernel table of the design notes."""
+    import torch
+    from paper_2410_16978_gb300 import _lib
+    lay = _lib.gs_workspace_layout(rast.n, W, H, rast.ws_bytes)
+    ws = rast.workspace
+    N, V, D = sc.n, int(st.n_visible), int(st.n_dup)
+    rec = ws[lay["rec"]:lay["rec"] + 48 * N].view(torch.int32).view(N, 12)
+    vis = ws[lay["tiles"]:lay["tiles"] + 4 * N].view(torch.int32) > 0
+    rows = ((rec[:, 11] >> 16) & 0xFFFF) - ((rec[:, 10] >> 16) & 0xFFFF)
+    R = int(rows[vis].sum().item())
+    keys = ws[lay["depth"]:lay["depth"] + 4 * N].view(torch.int32)[vis].to(torch.int64) & 0xFFFFFFFF
+    x = int((keys ^ keys.min()).max().item()) | int((keys ^ keys.max()).max().item()) if V else 0
+    digits = max(1, (x.bit_length() + 7) // 8)
+    ncon = ws[lay["n_contrib"]:lay["n_contrib"] + 4 * W * H].view(torch.int32)
+    E = float(ncon.double().sum().item())
+    B = float(st.n_blended)
+    K = (sc.sh_degree + 1) ** 2
+    small = 12 + 12 + 16 + 4 + 1                     # mean, log-scales, quaternion, opacity, layer (FP32)
+    Tn = ((W + 15) // 16) * ((H + 15) // 16)
+    work = {
+        "preprocess": ("hbm", N * (small + 8) + V * (12 * K + 48)),
+        "compact": ("hbm", 4 * N + 4 * V),
+        "depth_sort": ("hbm", 4 * N + 16 * V + 16 * V * (digits - 1)),
+        "bin_rows": ("hbm", 20 * V + 8 * R),
+        "bin_tiles": ("hbm", 16 * R + 4 * D + 8 * Tn),
+        "composite": ("alu", E * FLOP_EVAL + B * FLOP_BLEND_FWD),
+        "composite_bwd": ("alu", E * FLOP_EVAL + B * FLOP_BLEND_BWD),
+        "preprocess_bwd": ("hbm", V * (48 + small + 12 * K) + N * (small - 1 + 12 * K)),
+        "prune": ("hbm", 9 * N),
+    }
+    counts = {"gaussians": N, "visible": V, "row_entries": R, "pairs": D, "depth_digits": digits,
+              "evaluated_pairs": int(E), "blended_pairs": int(B)}
+    return work, counts
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -338,9 +620,7 @@ def run_gpu(args, rank, world, local_rank):
     image, alpha = rast.render(ds, cam, w["layer_mask"], w["planes"], bg, check=True)   # sizes the pair list
     torch.cuda.synchronize()
     st = rast.status()
-    rng = np.random.default_rng(7)
-    dimg_h = rng.standard_normal((3, H, W)).astype(np.float32) / (3 * W * H)
-    dal_h = rng.standard_normal((H, W)).astype(np.float32) / (W * H)
+    dimg_h, dal_h = _upstream_grads(W, H)
     dimg = torch.from_numpy(dimg_h).to(dev)
     dal = torch.from_numpy(dal_h).to(dev)
     csum = torch.zeros(sc.n, device=dev)
@@ -525,19 +805,46 @@ def run_gpu(args, rank, world, local_rank):
         roof = {"kernel": "k_" + dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks_src}
 
+    # ---- every step's fraction of its roofline (warm eager stage times) ----
+    work, counts = stage_work(rast, sc, st, W, H)
+    roof_all = {}
+    for k, (bound, amount) in work.items():
+        ms = stage_ms.get(k, 0.0)
+        if ms <= 0:
+            continue
+        if bound == "hbm":
+            ach = amount / (ms / 1e3) / 1e9
+            roof_all[k] = {"ms": round(ms, 4), "bound": "hbm", "bytes": int(amount), "achieved": round(ach, 1),
+                           "unit": "GB/s", "peak": peaks["hbm_gbs"], "frac": round(ach / peaks["hbm_gbs"], 4)}
+        else:
+            ach = amount / (ms / 1e3) / 1e12
+            roof_all[k] = {"ms": round(ms, 4), "bound": "alu", "flop": int(amount), "achieved": round(ach, 3),
+                           "unit": "TFLOP/s", "peak": round(fp32_peak_tflops, 3),
+                           "frac": round(ach / fp32_peak_tflops, 4),
+                           "note": "evaluated pairs x %d FLOP + blended pairs x %d" % (
+                               FLOP_EVAL, FLOP_BLEND_FWD if k == "composite" else FLOP_BLEND_BWD)}
+        tr = profiled_traffic("k_" + k)
+        if tr is not None:
+            roof_all[k]["traffic_over_algorithmic"] = round(tr / amount, 3) if bound == "hbm" else None
+    if "composite_setup" in stage_ms:
+        roof_all["composite_setup"] = {"ms": round(stage_ms["composite_setup"], 4), "bound": "latency"}
+
     # ---- CPU oracle baseline and PSNR check (rank 0, N = 1 only) ----
-    cpu = None
-    psnr = None
+    cpu, parity, oracle_detail = None, None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        img_np = image.cpu().numpy()
-        v, detail, psnr, wall = oracle_sample(w, img_np)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "full FP64 preprocess + binning, fwd+bwd compositing of 8 central tile rows scaled to "
-                         "the frame, chain rule of all visible Gaussians; %.1f s wall" % wall}
+        threads = host_threads()
+        v, wall, oracle_detail, parity = oracle_baselines(w, image.cpu().numpy(), threads)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "one whole step on the full frame (FP64 preprocess of all Gaussians, binning, "
+                         "compositing and its backward at every pixel, chain rule, prune) on %d host threads "
+                         "over tile rows and Gaussian chunks; %.1f s wall" % (threads, wall)}
 
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         serving = run_serving(dev)
+    stereo = None
+    if rank == 0 and world == 1 and not args.no_stereo:
+        stereo = run_stereo(dev)
     training = None
     if rank == 0 and world == 1 and not args.no_training:
         training = run_training(dev)
@@ -547,18 +854,26 @@ def run_gpu(args, rank, world, local_rank):
                 "warmup": max(3, args.warmup), "ms_per_step": ms_step, "p50_ms": per[len(per) // 2],
                 "p99_ms": per[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic",
-                "config": {"workload": WORKLOAD, "mode": "plain (one frame per launch sequence)",
-                           "gaussians": sc.n, "visible": int(st.n_visible), "pairs": int(st.n_dup),
-                           "width": W, "height": H, "l2": "inputs larger than L2 (scene %.0f MB)" % (
-                               sum(p.numel() * p.element_size() for p in ds.params()) / 1e6),
-                           "parallelism": "replicas" if world > 1 else "single GPU", "launch": graph_note},
-                "psnr_db_vs_fp64_oracle": psnr,
-                "roofline": roof, "roofline_detail": roof_detail, "cpu_baseline": cpu,
+                "data": "synthetic", "config": _workload_config(w, world),
+                "mode": "plain step (one frame per launch sequence): render, backward, prune",
+                "launch": graph_note, "counts": counts,
+                "psnr_db_vs_fp64_oracle": parity["psnr_db_full_frame"] if parity else None,
+                "parity": parity,
+                "roofline": roof, "roofline_detail": roof_detail, "roofline_all": roof_all,
+                "cpu_baseline": cpu, "oracle_timings": oracle_detail,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "ms_per_step": e2e_ms, "copies": e2e_note},
-                "clocks": clk, "gpu_launches": int(launches), "serving": serving, "training": training,
-                "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()}}
+                "clocks": clk, "gpu_launches": int(launches), "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()}}
+        if serving:
+            tp, ts = serving["trace_plain"], serving["trace_served"]
+            line["served"] = {"mpix_s": ts["mpix_s"], "p50_ms": ts["p50_ms"], "p99_ms": ts["p99_ms"],
+                              "saturated_mpix_s": serving["saturated_served"]["mpix_s"],
+                              "saturated_p99_ms": serving["saturated_served"]["p99_ms"],
+                              "psnr_db_vs_fp64_oracle": serving["served_view_psnr_db_vs_fp64_oracle"]}
+            line["plain"] = {"mpix_s": tp["mpix_s"], "p50_ms": tp["p50_ms"], "p99_ms": tp["p99_ms"],
+                             "saturated_mpix_s": serving["saturated_plain"]["mpix_s"],
+                             "saturated_p99_ms": serving["saturated_plain"]["p99_ms"]}
+        line.update(serving=serving, stereo=stereo, training=training)
         print(json.dumps(line), flush=True)
 
 
@@ -571,6 +886,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-training", action="store_true")
+    ap.add_argument("--no-stereo", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of one CUDA graph per step")
     args = ap.parse_args()
     world = _env_int("WORLD_SIZE", 1)

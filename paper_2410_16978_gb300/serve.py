@@ -15,8 +15,9 @@ import collections
 import ctypes
 import dataclasses
 import math
+import threading
 import time
-from typing import Dict, List, Optional, Sequence
+from typing import Callable, Dict, List, Optional, Sequence
 
 import numpy as np
 import torch
@@ -36,6 +37,7 @@ class RenderRequest:
     planes: tuple = ()
     bg: tuple = (0.0, 0.0, 0.0)
     arrival: float = 0.0           # seconds from the start of the trace
+    cancel_at: Optional[float] = None   # trace time at which the client withdraws it (if not yet launched)
 
     @property
     def pixels(self) -> int:
@@ -47,8 +49,10 @@ class RequestResult:
     rid: int
     arrival: float
     start: float = math.nan        # host time the request was launched
-    done: float = math.nan         # device completion time
+    done: float = math.nan         # device completion time (or the time it was cancelled / failed)
     images: Optional[list] = None
+    status: str = "pending"        # "done", "cancelled" (withdrawn before launch) or "failed"
+    error: int = 0                 # GS_ERR_* of a failed request (GS_ERR_OOM: no device memory for its views)
 
     @property
     def latency(self) -> float:
@@ -86,11 +90,20 @@ class RenderServer:
     (model, width, height) and reused, so the steady state allocates nothing.
     A view whose (tile, Gaussian) pairs overflowed its workspace is detected
     from its status word when its batch retires; the capacity of that (model,
-    size) grows and the request is rendered again."""
+    size) grows and the request is rendered again.
+
+    Failures and withdrawals.  When the device cannot hold a request's view
+    buffers (the allocation raises), the server drops its buffer pools and
+    tries once more; if that fails too, that request alone ends with status
+    "failed" and error GS_ERR_OOM and the others go on.  ``cancel(rid)`` (any
+    thread) or a request's ``cancel_at`` withdraws a request that has not been
+    launched yet; it ends with status "cancelled" and nothing of it runs on
+    the device.  ``allocate(n, W, H, capacity, device)`` makes a view's
+    buffers (``_ViewBuffers`` by default; tests inject failures there)."""
 
     def __init__(self, models: Dict[str, DeviceScene], memory_budget: int = 8 << 30, max_views_per_batch: int = 16,
                  max_inflight_batches: int = 2, device="cuda", policy: str = "priority",
-                 large_view_pixels: int = 2_000_000):
+                 large_view_pixels: int = 2_000_000, allocate: Optional[Callable] = None):
         if policy not in ("priority", "fifo"):
             raise ValueError(policy)
         self.models = models
@@ -105,10 +118,15 @@ class RenderServer:
         self._cap: Dict[tuple, int] = {}
         self._free: Dict[tuple, List[_ViewBuffers]] = collections.defaultdict(list)
         self._c_scene = {k: m.c_struct() for k, m in models.items()}
+        self._allocate = allocate if allocate is not None else _ViewBuffers
+        self._cancel_lock = threading.Lock()
+        self._cancelled = set()
         self.in_use = 0
         self.retries = 0
         self.batches = 0
         self.views_launched = 0
+        self.failed = 0
+        self.cancelled = 0
 
     # -- sizing ---------------------------------------------------------------
     def calibrate(self, model: str, cameras, layer_mask=0xFFFFFFFF, planes=()) -> int:
@@ -138,10 +156,36 @@ class RenderServer:
     def request_bytes(self, req: RenderRequest) -> int:
         return sum(self.view_bytes(req.model, c) for c in req.cameras)
 
+    def capacities(self) -> Dict[tuple, int]:
+        """The pair capacity per (model, width, height), e.g. to restore a
+        calibration later with ``set_capacities``."""
+        return dict(self._cap)
+
+    def set_capacities(self, caps: Dict[tuple, int]):
+        """Replaces the pair capacities and drops the pooled buffers."""
+        self._cap = dict(caps)
+        self.release_pool()
+
+    def cancel(self, rid: int):
+        """Withdraws request ``rid`` if it has not been launched yet (callable
+        from any thread; a launched request completes normally)."""
+        with self._cancel_lock:
+            self._cancelled.add(int(rid))
+
     def _take(self, model, cam) -> _ViewBuffers:
         key = self._key(model, cam)
-        vb = self._free[key].pop() if self._free[key] else \
-            _ViewBuffers(self.models[model].n, cam.width, cam.height, self._cap_of(key), self.device)
+        cap = self._cap_of(key)
+        pool = self._free[key]
+        while pool and pool[-1].cap < cap:        # sized before the capacity last grew
+            pool.pop()
+        if pool:
+            vb = pool.pop()
+        else:
+            try:
+                vb = self._allocate(self.models[model].n, cam.width, cam.height, cap, self.device)
+            except torch.cuda.OutOfMemoryError as e:
+                raise _lib.GsError(_lib.GS_ERR_OOM, "view buffers of %s %dx%d: %s" % (
+                    model, cam.width, cam.height, str(e).splitlines()[0] if str(e) else "out of memory")) from e
         self.in_use += vb.bytes
         return vb
 
@@ -151,36 +195,48 @@ class RenderServer:
         if vb.cap >= self._cap_of(key):
             self._free[key].append(vb)
 
+    def _acquire(self, req: RenderRequest):
+        """The view buffers of every view of ``req``; on GS_ERR_OOM the pools
+        are dropped and the allocation is tried once more.  Raises GsError
+        (GS_ERR_OOM) when that fails too, holding nothing."""
+        for attempt in range(2):
+            got = []
+            try:
+                for cam in req.cameras:
+                    got.append((req, cam, self._take(req.model, cam)))
+                return got
+            except _lib.GsError as e:
+                for r, cam, vb in got:
+                    self._give(r.model, cam, vb)
+                if e.code != _lib.GS_ERR_OOM or attempt == 1:
+                    raise
+                self.release_pool()
+                torch.cuda.empty_cache()
+
     def release_pool(self):
         self._free.clear()
 
     # -- launches -------------------------------------------------------------
-    def _launch_plain(self, req: RenderRequest, stream: torch.cuda.Stream, keep_images: bool):
-        """The plain path: one gs_render call per view of one request."""
-        views = []
-        cs = self._c_scene[req.model]
+    def _launch_plain(self, views, stream: torch.cuda.Stream, keep_images: bool):
+        """The plain path: one gs_render call per view of one request
+        (``views``: its (request, camera, buffers) triples)."""
         with torch.cuda.stream(stream):
-            for cam in req.cameras:
-                vb = self._take(req.model, cam)
-                _lib.gs_render(cs, _lib.make_camera(cam), req.layer_mask, list(req.planes), req.bg, vb.workspace,
-                               vb.ws_bytes, vb.image, vb.alpha, int(stream.cuda_stream))
+            for req, cam, vb in views:
+                _lib.gs_render(self._c_scene[req.model], _lib.make_camera(cam), req.layer_mask, list(req.planes),
+                               req.bg, vb.workspace, vb.ws_bytes, vb.image, vb.alpha, int(stream.cuda_stream))
                 vb.fetch_status()
-                views.append((req, cam, vb))
-            imgs = {req.rid: [vb.image.clone() for _, _, vb in views]} if keep_images else None
+            imgs = {views[0][0].rid: [vb.image.clone() for _, _, vb in views]} if keep_images else None
         self.views_launched += len(views)
         return views, imgs
 
-    def _launch_batch(self, reqs: Sequence[RenderRequest], stream: torch.cuda.Stream, keep_images: bool):
-        """All views of ``reqs`` in one gs_render_batch call."""
-        items, views = [], []
-        for req in reqs:
-            cs = self._c_scene[req.model]
-            for cam in req.cameras:
-                vb = self._take(req.model, cam)
-                views.append((req, cam, vb))
-                items.append(dict(scene=cs, camera=_lib.make_camera(cam), layer_mask=req.layer_mask,
-                                  planes=list(req.planes), bg=req.bg, workspace=vb.workspace, ws_bytes=vb.ws_bytes,
-                                  image=vb.image, alpha=vb.alpha))
+    def _launch_batch(self, views, stream: torch.cuda.Stream, keep_images: bool):
+        """All ``views`` ((request, camera, buffers) triples of several
+        requests) in one gs_render_batch call."""
+        items = []
+        for req, cam, vb in views:
+            items.append(dict(scene=self._c_scene[req.model], camera=_lib.make_camera(cam), layer_mask=req.layer_mask,
+                              planes=list(req.planes), bg=req.bg, workspace=vb.workspace, ws_bytes=vb.ws_bytes,
+                              image=vb.image, alpha=vb.alpha))
         _lib.gs_render_batch(items, int(stream.cuda_stream))
         imgs = None
         with torch.cuda.stream(stream):
@@ -246,12 +302,13 @@ class RenderServer:
                 redo = collections.deque()
                 self._retire(ln["pending"], results, ref, redo)
                 ln["waiting"].extendleft(reversed(redo))
+            self._withdraw(lanes, results, now)
             launched = False
             for ln in lanes:
                 waiting, pending = ln["waiting"], ln["pending"]
                 if not waiting or len(pending) >= ln["slots"]:
                     continue
-                batch, nviews, nbytes = [], 0, 0
+                batch, views, nviews, nbytes = [], [], 0, 0
                 busy = any(l2["pending"] for l2 in lanes)
                 while waiting:
                     r = waiting[0]
@@ -262,7 +319,16 @@ class RenderServer:
                     rb = self.request_bytes(r)
                     if self.in_use + nbytes + rb > self.budget and (batch or busy):
                         break
-                    batch.append(waiting.popleft())
+                    waiting.popleft()
+                    try:
+                        got = self._acquire(r)
+                    except _lib.GsError as e:
+                        res = results[r.rid]
+                        res.status, res.error, res.done = "failed", e.code, time.perf_counter() - t0
+                        self.failed += 1
+                        continue
+                    batch.append(r)
+                    views += got
                     nviews += len(r.cameras)
                     nbytes += rb
                 if not batch:
@@ -274,9 +340,9 @@ class RenderServer:
                     if math.isnan(results[r.rid].start):
                         results[r.rid].start = st
                 if ln["batch"]:
-                    views, imgs = self._launch_batch(batch, stream, keep_images)
+                    views, imgs = self._launch_batch(views, stream, keep_images)
                 else:
-                    views, imgs = self._launch_plain(batch[0], stream, keep_images)
+                    views, imgs = self._launch_plain(views, stream, keep_images)
                 ev = torch.cuda.Event(enable_timing=True)
                 ev.record(stream)
                 pending.append((ev, views, imgs))
@@ -287,8 +353,25 @@ class RenderServer:
                 wait = reqs[nxt].arrival - (time.perf_counter() - t0)
                 if wait > 3e-4:
                     time.sleep(wait - 2e-4)
-        last = max(r.done for r in results.values())
+        ends = [r.done for r in results.values() if r.status == "done"]
+        last = max(ends) if ends else reqs[0].arrival
         return [results[r.rid] for r in reqs], last - reqs[0].arrival
+
+    def _withdraw(self, lanes, results, now):
+        """Drops waiting (not yet launched) requests that were cancelled."""
+        with self._cancel_lock:
+            ids = set(self._cancelled)
+        for ln in lanes:
+            keep = collections.deque()
+            for r in ln["waiting"]:
+                if r.rid in ids or (r.cancel_at is not None and r.cancel_at <= now):
+                    res = results[r.rid]
+                    if res.status == "pending":
+                        res.status, res.done = "cancelled", now
+                        self.cancelled += 1
+                    continue
+                keep.append(r)
+            ln["waiting"] = keep
 
     def _retire(self, pending, results, ref, waiting):
         keep = []
@@ -303,12 +386,14 @@ class RenderServer:
                 if stt.error == _lib.GS_ERR_WORKSPACE:
                     key = self._key(req.model, cam)
                     self._cap[key] = max(self._cap_of(key), int(stt.n_dup * SCENE_MARGIN) + 4096)
+                    self._free[key].clear()          # pooled buffers of the old capacity would overflow again
                     redo[req.rid] = req
                 elif stt.error != _lib.GS_OK:
                     raise _lib.GsError(stt.error, "device status of request %d" % req.rid)
             for req, cam, vb in views:
                 if req.rid not in redo:
                     results[req.rid].done = t
+                    results[req.rid].status = "done"
                     if imgs:
                         results[req.rid].images = imgs.get(req.rid)
                 self._give(req.model, cam, vb)
@@ -319,16 +404,22 @@ class RenderServer:
 
 
 def summarize(results: Sequence[RequestResult], requests: Sequence[RenderRequest], wall: float) -> dict:
-    """Throughput over the replay and latency percentiles, overall and per
-    request size ("WxHxeyes")."""
-    lat = np.array([r.latency for r in results]) * 1e3
-    px = sum(r.pixels for r in requests)
+    """Throughput over the replay and latency percentiles of the completed
+    requests, overall and per request size ("WxHxeyes"), with the counts of
+    cancelled and failed ones."""
+    done = [r for r in results if r.status == "done" or (r.status == "pending" and np.isfinite(r.done))]
+    lat = np.array([r.latency for r in done]) * 1e3
+    done_ids = {r.rid for r in done}
+    px = sum(q.pixels for q in requests if q.rid in done_ids)
     size_of = {q.rid: "%dx%dx%d" % (q.cameras[0].width, q.cameras[0].height, len(q.cameras)) for q in requests}
     by = collections.defaultdict(list)
-    for r in results:
+    for r in done:
         by[size_of[r.rid]].append(r.latency * 1e3)
-    return {"mpix_s": px / wall / 1e6, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "requests": len(results), "wall_s": wall, "mpixels": px / 1e6,
+    pct = (lambda a, q: float(np.percentile(a, q))) if lat.size else (lambda a, q: math.nan)
+    return {"mpix_s": px / wall / 1e6 if wall > 0 else 0.0, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+            "mean_ms": float(lat.mean()) if lat.size else math.nan, "requests": len(done), "wall_s": wall,
+            "mpixels": px / 1e6, "cancelled": sum(r.status == "cancelled" for r in results),
+            "failed": sum(r.status == "failed" for r in results),
             "by_size_p50_p99_ms": {k: [round(float(np.percentile(v, 50)), 4), round(float(np.percentile(v, 99)), 4)]
                                    for k, v in sorted(by.items())}}
 

@@ -29,6 +29,12 @@ def test_reference_arm_prints_one_contract_line():
     assert d["value"] > 0 and d["ms_per_step"] > 0
     assert d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 0
     assert d["config"]["workload"] == bench.WORKLOAD
+    # the config names the workload only, so both arms print the same object
+    assert set(d["config"]) == {"workload", "gaussians", "width", "height", "l2", "parallelism"}
+    assert d["config"]["gaussians"] == 1_200_000 and d["config"]["width"] == d["config"]["height"] == 1024
+    # the step time is the measured wall time of a full-frame step, not an extrapolation
+    lo, hi = d["wall_s_min_max"]
+    assert lo * 1e3 - 1 <= d["ms_per_step"] <= hi * 1e3 + 1      # the range is rounded to 0.1 ms
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     e2e = d["e2e"]
