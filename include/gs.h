@@ -40,7 +40,8 @@ enum {
     GS_ERR_WORKSPACE = 2,  /* workspace too small (host check) or duplicate-list overflow (device status) */
     GS_ERR_CUDA = 3,       /* a CUDA runtime call or launch failed */
     GS_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up */
-    GS_ERR_OOM = 5         /* an admission/memory budget was exceeded */
+    GS_ERR_OOM = 5,        /* an admission/memory budget was exceeded */
+    GS_ERR_BOUNDS = 6      /* a bounds check of a GS_DEBUG build failed (device status; the access was skipped) */
 };
 
 enum { GS_DTYPE_F32 = 0, GS_DTYPE_F16 = 1, GS_DTYPE_BF16 = 2, GS_DTYPE_SH_CODEBOOK = 3 };
@@ -365,6 +366,58 @@ int gs_profile_enable(int on);
 int gs_profile_collect(double *ms, int64_t *calls);
 /* Kernels launched by the library since it was loaded (all entry points). */
 int64_t gs_kernel_launches(void);
+
+/* The method's constants as this library applies them (Sec. 3.3 renders the
+ * splats as the cited 3DGS renderer does; these are its values): tile edge,
+ * EWA dilation of the 2D covariance (px^2), alpha clamp and skip threshold,
+ * early-stop transmittance, frustum clamp factor, radius in standard
+ * deviations and the eigenvalue floor, the backward checkpoint stride, and
+ * the limits of one call.  Host only.                                        */
+typedef struct gs_settings {
+    int32_t tile;                 /* 16 */
+    float dilation;               /* 0.3 */
+    float alpha_max;              /* 0.99 */
+    float alpha_min;              /* 1/255 */
+    float t_min;                  /* 1e-4 */
+    float frustum_clamp;          /* 1.3 */
+    float radius_sigmas;          /* 3 */
+    float eigen_floor;            /* 0.1 */
+    int32_t checkpoint_stride;    /* list positions between backward checkpoints (256) */
+    int32_t max_sh_degree;        /* 3 */
+    int32_t max_planes;           /* GS_MAX_PLANES */
+    int32_t max_image_dim;        /* GS_MAX_IMAGE_DIM */
+    int32_t max_batch;            /* GS_MAX_BATCH */
+    int32_t debug_build;          /* 1 when compiled with GS_DEBUG */
+} gs_settings;
+int gs_get_settings(gs_settings *out);
+
+/* ---- GS_DEBUG builds (libgs_debug.so; the paper has no counterpart) ----
+ * A library compiled with GS_DEBUG checks, inside its kernels, the indices it
+ * writes and reads against the sizes they index: tile rectangles against the
+ * tile grid, depth-sort scatter positions against the visible count, row-list
+ * and pair-list positions against the pair capacity, tile ranges against the
+ * pair count, Gaussian ids read from the lists against the Gaussian count,
+ * checkpoint segments against the checkpoint area.  A failed check skips the
+ * access, sets GS_ERR_BOUNDS in the workspace status word (first failure
+ * wins) and records which check failed; it never traps.  In a release build
+ * the checks compile to nothing.
+ *   gs_debug_build():  1 in a GS_DEBUG build, 0 otherwise.
+ *   gs_debug_site():   copies the number of the first failed check of the
+ *                      workspace's last render to *site (host; 0 = none) and
+ *                      synchronises the stream.  GS_ERR_INVALID in release.
+ *   gs_debug_sort_wait(): test hook of the depth sort's bounded look-back
+ *                      wait.  spin_limit replaces its iteration limit
+ *                      (0 restores the default); withhold_pass >= 1 makes the
+ *                      first tile of that digit kernel never publish its
+ *                      counts, so the tiles after it wait until the limit
+ *                      runs out and write GS_ERR_TIMEOUT to the status word
+ *                      (-1 disables).  After a timeout the binning does not
+ *                      read the unfinished order: the render draws nothing
+ *                      and the status holds the error.  Process-wide, not
+ *                      thread safe; GS_ERR_INVALID in release builds.        */
+int gs_debug_build(void);
+int gs_debug_site(const void *workspace, uint32_t *site, void *stream);
+int gs_debug_sort_wait(uint32_t spin_limit, int32_t withhold_pass);
 
 /* Message of the calling thread's last error ("" if none). */
 const char *gs_last_error_string(void);

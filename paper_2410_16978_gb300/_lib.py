@@ -15,7 +15,7 @@ from . import build as _build
 
 _P = ctypes.c_void_p
 
-GS_OK, GS_ERR_INVALID, GS_ERR_WORKSPACE, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_OOM = range(6)
+GS_OK, GS_ERR_INVALID, GS_ERR_WORKSPACE, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_OOM, GS_ERR_BOUNDS = range(7)
 GS_DTYPE_SH_CODEBOOK = 3
 GS_DTYPE_F32, GS_DTYPE_F16, GS_DTYPE_BF16 = 0, 1, 2
 GS_TILE = 16
@@ -26,7 +26,8 @@ EXPORTED = ("gs_render_workspace_size", "gs_render", "gs_render_batch", "gs_rend
             "gs_contrib_prune", "gs_contrib_prune_noalloc", "gs_image_loss_workspace_size", "gs_image_loss",
             "gs_adam_step", "gs_activity_accumulate", "gs_activity_prune", "gs_gather_rows", "gs_kmeans_scratch_size",
             "gs_kmeans_assign", "gs_kmeans_update", "gs_sh_codebook_encode", "gs_workspace_layout", "gs_read_status", "gs_profile_enable",
-            "gs_profile_collect", "gs_kernel_launches", "gs_last_error_string", "gs_version")
+            "gs_profile_collect", "gs_kernel_launches", "gs_get_settings", "gs_debug_build", "gs_debug_site",
+            "gs_debug_sort_wait", "gs_last_error_string", "gs_version")
 STAGES = ("preprocess", "compact", "depth_sort", "bin_rows", "bin_tiles", "composite_setup", "composite",
           "composite_bwd", "preprocess_bwd", "prune", "loss", "adam")
 GS_LAYOUT_COUNT = 11
@@ -73,6 +74,15 @@ class gs_status(ctypes.Structure):
                 ("dup_capacity", ctypes.c_uint64), ("n_blended", ctypes.c_uint64)]
 
 
+class gs_settings(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("dilation", ctypes.c_float), ("alpha_max", ctypes.c_float),
+                ("alpha_min", ctypes.c_float), ("t_min", ctypes.c_float), ("frustum_clamp", ctypes.c_float),
+                ("radius_sigmas", ctypes.c_float), ("eigen_floor", ctypes.c_float),
+                ("checkpoint_stride", ctypes.c_int32), ("max_sh_degree", ctypes.c_int32),
+                ("max_planes", ctypes.c_int32), ("max_image_dim", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("debug_build", ctypes.c_int32)]
+
+
 class GsError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("gs error %d: %s" % (code, msg))
@@ -100,54 +110,99 @@ def load(build_if_missing: bool = True):
             _build.build()
         if not os.path.exists(path):
             raise RuntimeError("CUDA rasterizer library not built: %s" % path)
-        L = ctypes.CDLL(path)
-        L.gs_render_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
-                                               ctypes.POINTER(ctypes.c_size_t)]
-        L.gs_render.argtypes = [ctypes.POINTER(gs_scene), ctypes.POINTER(gs_camera), ctypes.c_uint32,
-                                ctypes.POINTER(gs_clip_plane), ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
-                                _P, ctypes.c_size_t, _P, _P, _P]
-        L.gs_render_batch.argtypes = [ctypes.POINTER(gs_render_request), ctypes.c_int32, _P]
-        L.gs_render_stereo.argtypes = [ctypes.POINTER(gs_scene), ctypes.POINTER(gs_camera), ctypes.POINTER(gs_camera),
-                                       ctypes.c_uint32, ctypes.POINTER(gs_clip_plane), ctypes.c_int32,
-                                       ctypes.POINTER(ctypes.c_float), _P, ctypes.c_size_t, _P, ctypes.c_size_t, _P,
-                                       _P, _P, _P, ctypes.c_int32, _P]
-        L.gs_render_backward.argtypes = [ctypes.POINTER(gs_scene), ctypes.POINTER(gs_camera),
-                                         ctypes.POINTER(ctypes.c_float), _P, ctypes.c_size_t, _P, _P,
-                                         ctypes.c_uint32, ctypes.POINTER(gs_grads), _P, _P, _P]
-        L.gs_prune_workspace_size.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]
-        L.gs_contrib_prune.argtypes = [_P, ctypes.c_int64, ctypes.c_float, _P, _P, _P, _P, ctypes.c_size_t, _P]
-        L.gs_read_status.argtypes = [_P, ctypes.POINTER(gs_status), _P]
-        L.gs_contrib_prune_noalloc.argtypes = [_P, ctypes.c_int64, ctypes.c_float, _P, _P, _P, _P]
-        L.gs_image_loss_workspace_size.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
-        L.gs_image_loss.argtypes = [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.c_int32,
-                                    ctypes.c_float, ctypes.c_float, _P, ctypes.c_size_t, _P, _P, _P, _P]
-        L.gs_adam_step.argtypes = [ctypes.POINTER(gs_scene), ctypes.POINTER(gs_grads), ctypes.POINTER(gs_adam_state),
-                                   ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float, ctypes.c_float,
-                                   ctypes.c_int32, ctypes.c_uint32, _P]
-        L.gs_gather_rows.argtypes = [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P]
-        L.gs_kmeans_scratch_size.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
-        L.gs_kmeans_assign.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P, ctypes.c_int32, _P, _P]
-        L.gs_kmeans_update.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P, ctypes.c_int32, _P, _P,
-                                       ctypes.c_size_t, _P]
-        L.gs_sh_codebook_encode.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, _P, _P]
-        L.gs_activity_accumulate.argtypes = [ctypes.POINTER(gs_adam_state), _P, ctypes.c_int64, ctypes.c_int32,
-                                             ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float,
-                                             ctypes.c_float, ctypes.c_int32, ctypes.c_uint32, _P, _P]
-        L.gs_activity_prune.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_uint32, ctypes.c_float, ctypes.c_float, _P,
-                                        _P, _P, _P, ctypes.c_size_t, _P]
-        L.gs_workspace_layout.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t,
-                                          ctypes.POINTER(ctypes.c_int64)]
-        L.gs_profile_enable.argtypes = [ctypes.c_int]
-        L.gs_profile_collect.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
-        L.gs_kernel_launches.argtypes = []
-        L.gs_last_error_string.restype = ctypes.c_char_p
-        L.gs_version.restype = ctypes.c_char_p
-        for name in EXPORTED:
-            if name not in ("gs_last_error_string", "gs_version"):
-                getattr(L, name).restype = ctypes.c_int
-        L.gs_kernel_launches.restype = ctypes.c_int64
-        _lib = L
-        return L
+        _lib = _declare(ctypes.CDLL(path))
+        return _lib
+
+
+_debug_lib = None
+
+
+def load_debug(build_if_missing: bool = True):
+    """Loads libgs_debug.so, the GS_DEBUG build (bounds checks that report
+    GS_ERR_BOUNDS through the status word, and the sort-wait test hook).  It is
+    a separate library; ``use(load_debug())`` routes this module's calls to it."""
+    global _debug_lib
+    with _lock:
+        if _debug_lib is None:
+            path = _build.DEBUG_LIB
+            if build_if_missing and (not os.path.exists(path) or _build._stale(path)):
+                _build.build(debug=True)
+            if not os.path.exists(path):
+                raise RuntimeError("GS_DEBUG library not built: %s" % path)
+            _debug_lib = _declare(ctypes.CDLL(path))
+        return _debug_lib
+
+
+class use:
+    """``with _lib.use(lib):`` makes every function of this module call `lib`
+    (e.g. the GS_DEBUG build) until the block ends."""
+
+    def __init__(self, lib):
+        self.lib = lib
+
+    def __enter__(self):
+        global _lib
+        self.saved = load()
+        _lib = self.lib
+        return self.lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def _declare(L):
+    L.gs_render_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                           ctypes.POINTER(ctypes.c_size_t)]
+    L.gs_render.argtypes = [ctypes.POINTER(gs_scene), ctypes.POINTER(gs_camera), ctypes.c_uint32,
+                            ctypes.POINTER(gs_clip_plane), ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
+                            _P, ctypes.c_size_t, _P, _P, _P]
+    L.gs_render_batch.argtypes = [ctypes.POINTER(gs_render_request), ctypes.c_int32, _P]
+    L.gs_render_stereo.argtypes = [ctypes.POINTER(gs_scene), ctypes.POINTER(gs_camera), ctypes.POINTER(gs_camera),
+                                   ctypes.c_uint32, ctypes.POINTER(gs_clip_plane), ctypes.c_int32,
+                                   ctypes.POINTER(ctypes.c_float), _P, ctypes.c_size_t, _P, ctypes.c_size_t, _P,
+                                   _P, _P, _P, ctypes.c_int32, _P]
+    L.gs_render_backward.argtypes = [ctypes.POINTER(gs_scene), ctypes.POINTER(gs_camera),
+                                     ctypes.POINTER(ctypes.c_float), _P, ctypes.c_size_t, _P, _P,
+                                     ctypes.c_uint32, ctypes.POINTER(gs_grads), _P, _P, _P]
+    L.gs_prune_workspace_size.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]
+    L.gs_contrib_prune.argtypes = [_P, ctypes.c_int64, ctypes.c_float, _P, _P, _P, _P, ctypes.c_size_t, _P]
+    L.gs_read_status.argtypes = [_P, ctypes.POINTER(gs_status), _P]
+    L.gs_contrib_prune_noalloc.argtypes = [_P, ctypes.c_int64, ctypes.c_float, _P, _P, _P, _P]
+    L.gs_image_loss_workspace_size.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+    L.gs_image_loss.argtypes = [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.c_int32,
+                                ctypes.c_float, ctypes.c_float, _P, ctypes.c_size_t, _P, _P, _P, _P]
+    L.gs_adam_step.argtypes = [ctypes.POINTER(gs_scene), ctypes.POINTER(gs_grads), ctypes.POINTER(gs_adam_state),
+                               ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_int32, ctypes.c_uint32, _P]
+    L.gs_gather_rows.argtypes = [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P]
+    L.gs_kmeans_scratch_size.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+    L.gs_kmeans_assign.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P, ctypes.c_int32, _P, _P]
+    L.gs_kmeans_update.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P, ctypes.c_int32, _P, _P,
+                                   ctypes.c_size_t, _P]
+    L.gs_sh_codebook_encode.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, _P, _P]
+    L.gs_activity_accumulate.argtypes = [ctypes.POINTER(gs_adam_state), _P, ctypes.c_int64, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float,
+                                         ctypes.c_float, ctypes.c_int32, ctypes.c_uint32, _P, _P]
+    L.gs_activity_prune.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_uint32, ctypes.c_float, ctypes.c_float, _P,
+                                    _P, _P, _P, ctypes.c_size_t, _P]
+    L.gs_workspace_layout.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t,
+                                      ctypes.POINTER(ctypes.c_int64)]
+    L.gs_profile_enable.argtypes = [ctypes.c_int]
+    L.gs_profile_collect.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    L.gs_kernel_launches.argtypes = []
+    L.gs_last_error_string.restype = ctypes.c_char_p
+    L.gs_version.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("gs_last_error_string", "gs_version"):
+            getattr(L, name).restype = ctypes.c_int
+    L.gs_kernel_launches.restype = ctypes.c_int64
+    L.gs_get_settings.argtypes = [ctypes.POINTER(gs_settings)]
+    L.gs_debug_build.argtypes = []
+    L.gs_debug_site.argtypes = [_P, ctypes.POINTER(ctypes.c_uint32), _P]
+    L.gs_debug_sort_wait.argtypes = [ctypes.c_uint32, ctypes.c_int32]
+    return L
 
 
 def _check(rc: int):
@@ -367,3 +422,23 @@ def gs_last_error_string() -> str:
 
 def gs_version() -> str:
     return load().gs_version().decode()
+
+
+def gs_get_settings() -> gs_settings:
+    out = gs_settings()
+    _check(load().gs_get_settings(ctypes.byref(out)))
+    return out
+
+
+def gs_debug_build() -> bool:
+    return bool(load().gs_debug_build())
+
+
+def gs_debug_site(workspace, stream: int) -> int:
+    out = ctypes.c_uint32(0)
+    _check(load().gs_debug_site(_ptr(workspace), ctypes.byref(out), ctypes.c_void_p(stream)))
+    return int(out.value)
+
+
+def gs_debug_sort_wait(spin_limit: int, withhold_pass: int) -> None:
+    _check(load().gs_debug_sort_wait(int(spin_limit), int(withhold_pass)))

@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(256) k_bin_rows(const uint32_t *__restrict__ o
                                                   const Ctl *__restrict__ ctl) {
     __shared__ uint32_t s_cnt[8][kBinMaxDim + 1];
     __shared__ uint32_t s_px[SCATTER ? 1 : 8][kBinMaxDim + 1];
-    if (SCATTER && ctl->st.error != GS_OK) return;
+    // an error before the binning (a depth sort that timed out) leaves the order unfinished: do not read it
+    if (ctl->st.error != GS_OK) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t K = gridDim.x * 8u, c = blockIdx.x * 8u + warp;
@@ -160,7 +161,8 @@ __global__ void __launch_bounds__(256) k_bin_rows(const uint32_t *__restrict__ o
             const uint32_t before = act ? s_cnt[warp][r] : 0u;
             __syncwarp();
             if (act && (peers & lt) == 0) s_cnt[warp][r] = before + __popc(peers);
-            if (act) rowlist[before + __popc(peers & lt)] = make_uint2(gj, xj);
+            if (act && GS_CHECK(before + __popc(peers & lt) < ctl->st.dup_capacity, ctl, kSiteRowList))
+                rowlist[before + __popc(peers & lt)] = make_uint2(gj, xj);
             __syncwarp();
         }
     }
@@ -185,9 +187,10 @@ __global__ void __launch_bounds__(256) k_bin_rows(const uint32_t *__restrict__ o
 // thread scans a contiguous run of kBinChunksPerThread counts); the row's pair
 // total needs only a sum, read coalesced.
 __global__ void __launch_bounds__(1024) k_bin_rowscan(uint32_t *__restrict__ M, int K, int Ty,
-                                                      RowInfo *__restrict__ rows) {
+                                                      RowInfo *__restrict__ rows, const Ctl *__restrict__ ctl) {
     __shared__ uint32_t s_w[32];
     __shared__ uint32_t s_row[kBinChunks];
+    if (ctl->st.error != GS_OK) return;
     uint32_t *row = M + static_cast<size_t>(blockIdx.x) * K;
     const uint32_t *prow = M + static_cast<size_t>(Ty + blockIdx.x) * K;   // pairs of the same row
     uint32_t psum = 0;
@@ -225,6 +228,7 @@ __global__ void __launch_bounds__(1024) k_bin_rowscan(uint32_t *__restrict__ M, 
 __global__ void __launch_bounds__(256) k_bin_rowstart(RowInfo *__restrict__ rows, int Ty, Ctl *__restrict__ ctl,
                                                       uint64_t cap, uint32_t piece) {
     __shared__ uint32_t s_w[8];
+    if (ctl->st.error != GS_OK) return;   // uniform: the status is not written in this kernel before this test
     const int r = threadIdx.x;
     uint32_t te, tp, tq;
     const uint32_t ent = r < Ty ? rows[r].entries : 0u;
@@ -304,7 +308,8 @@ __global__ void __launch_bounds__(256) k_bin_tiles(const uint2 *__restrict__ row
                 const uint32_t before = act ? s_cnt[warp][t] : 0u;
                 __syncwarp();
                 if (act && (peers & lt) == 0) s_cnt[warp][t] = before + __popc(peers);
-                if (SCATTER && act) list[before + __popc(peers & lt)] = gj;
+                if (SCATTER && act && GS_CHECK(before + __popc(peers & lt) < ctl->st.n_dup, ctl, kSitePairList))
+                    list[before + __popc(peers & lt)] = gj;
                 __syncwarp();
             }
         }
@@ -356,7 +361,8 @@ __global__ void __launch_bounds__(1024) k_bin_tiles_scan(const RowInfo *__restri
     __syncthreads();
     if (t < Tx) {
         const uint32_t base = ri.pair_start + s_off[t];
-        if (sl == 0) ranges[static_cast<size_t>(r) * Tx + t] = make_uint2(base, base + tot);
+        if (sl == 0 && GS_CHECK(base + tot <= ctl->st.n_dup, ctl, kSiteRange))
+            ranges[static_cast<size_t>(r) * Tx + t] = make_uint2(base, base + tot);
         uint32_t run = base + before;
         // eight counts loaded before any of them is replaced, so the loads overlap instead of each waiting
         // behind the previous store
@@ -381,7 +387,7 @@ cudaError_t launch_bin_rows(const uint32_t *order, const Rec *rec, uint32_t n_ca
     if (Ty > kBinMaxDim) return cudaErrorInvalidValue;
     RowInfo *rows = static_cast<RowInfo *>(rows_buf);   // zero on entry (cleared with the control block)
     k_bin_rows<false><<<kBinBlocks, 256, 0, st>>>(order, rec, n_cap, Ty, M, rows, rowlist, ctl);
-    k_bin_rowscan<<<Ty, 1024, 0, st>>>(M, kBinBlocks * 8, Ty, rows);
+    k_bin_rowscan<<<Ty, 1024, 0, st>>>(M, kBinBlocks * 8, Ty, rows, ctl);
     k_bin_rowstart<<<1, 256, 0, st>>>(rows, Ty, ctl, cap, piece);
     k_bin_rows<true><<<kBinBlocks, 256, 0, st>>>(order, rec, n_cap, Ty, M, rows, rowlist, ctl);
     return cudaGetLastError();

@@ -187,10 +187,18 @@ struct Chunk {
     uint32_t ly;      // backward: the splat's layer, consumed one chunk later
 };
 
+// n, ctl, site: the Gaussian count and the bounds check of GS_DEBUG builds
+// (nothing in release builds).
 __device__ __forceinline__ void fetch_chunk(const uint32_t *__restrict__ list, const Rec *__restrict__ rec,
-                                            uint32_t pos, uint32_t end, Chunk &ch) {
+                                            uint32_t pos, uint32_t end, Chunk &ch, uint32_t n, const Ctl *ctl,
+                                            uint32_t site) {
     if (pos < end) {
-        ch.g = list[pos];
+        const uint32_t g = list[pos];
+        if (!GS_CHECK(g < n, ctl, site)) {
+            ch = Chunk{};          // an inert splat (opacity 0): no block keeps it
+            return;
+        }
+        ch.g = g;
         const Rec *r = rec + ch.g;
         ch.a = r->a;
         ch.b = r->b;
@@ -201,9 +209,9 @@ __device__ __forceinline__ void fetch_chunk(const uint32_t *__restrict__ list, c
 // The backward also needs each splat's layer (frozen layers get no gradient).
 __device__ __forceinline__ void fetch_chunk_layer(const uint32_t *__restrict__ list, const Rec *__restrict__ rec,
                                                   const uint8_t *__restrict__ layer, uint32_t pos, uint32_t end,
-                                                  Chunk &ch) {
-    fetch_chunk(list, rec, pos, end, ch);
-    if (pos < end) ch.ly = layer[ch.g];
+                                                  Chunk &ch, uint32_t n, const Ctl *ctl) {
+    fetch_chunk(list, rec, pos, end, ch, n, ctl, kSiteBwdId);
+    if (pos < end && GS_CHECK(ch.g < n, ctl, kSiteBwdId)) ch.ly = layer[ch.g];
 }
 
 // The record of an id loaded one chunk earlier: list and record loads of a
@@ -217,6 +225,16 @@ __device__ __forceinline__ void fetch_rec(const Rec *__restrict__ rec, uint32_t 
         ch.b = r->b;
         ch.c = r->c.x;
     }
+}
+
+__device__ __forceinline__ void fetch_rec_layer(const Rec *__restrict__ rec, const uint8_t *__restrict__ layer,
+                                                uint32_t g, bool valid, Chunk &ch, uint32_t n, const Ctl *ctl) {
+    if (valid && !GS_CHECK(g < n, ctl, kSiteBwdId)) {
+        ch = Chunk{};              // an inert splat (opacity 0): no block keeps it
+        return;
+    }
+    fetch_rec(rec, g, valid, ch);
+    if (valid) ch.ly = layer[g];
 }
 
 struct FwdBatch {
@@ -271,7 +289,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_cons
         uint32_t sd = 0, nb = 0;
         float4 *ck0 = J.ckpt + static_cast<size_t>(J.seg_base[tile]) * kTilePix + lx;
         Chunk nxt;
-        fetch_chunk(list, rec, rg.x + lane, rg.y, nxt);
+        fetch_chunk(list, rec, rg.x + lane, rg.y, nxt, J.n, J.ctl, kSiteFwdId);
         uint32_t gid = rg.x + 32 + lane < rg.y ? list[rg.x + 32 + lane] : 0u;   // ids one chunk ahead
         for (uint32_t base = rg.x; base < rg.y; base += 32) {
             bool mine = true;
@@ -281,6 +299,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_cons
             const uint32_t pos0 = base - rg.x;
             if (pos0 != 0 && pos0 % kSeg == 0) {
                 sd = pos0 / kSeg;
+                if (!GS_CHECK(J.seg_base[tile] + sd < J.n_segs, J.ctl, kSiteCkpt)) break;
 #pragma unroll
                 for (int j = 0; j < PX; ++j) {
                     ck0[static_cast<size_t>(sd) * kTilePix + lyv[j] * kTile] = make_float4(T[j], D0[j], D1[j], D2[j]);
@@ -299,7 +318,10 @@ __global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_cons
                 s_pos[warp][slot] = pos0 + lane;
             }
             __syncwarp();
-            fetch_rec(rec, gid, base + 32 + lane < rg.y, nxt);
+            if (base + 32 + lane < rg.y && !GS_CHECK(gid < J.n, J.ctl, kSiteFwdId))
+                nxt = Chunk{};     // an inert splat (opacity 0): no block keeps it
+            else
+                fetch_rec(rec, gid, base + 32 + lane < rg.y, nxt);
             gid = base + 64 + lane < rg.y ? list[base + 64 + lane] : 0u;
             const int cnt = __popc(km);
             for (int k = 0; k < cnt && !mine; ++k) {
@@ -483,15 +505,19 @@ __device__ __forceinline__ float reduce_scatter10(const float v[10], int lane) {
 // Each splat's 10 sums are reduce-scattered over the warp and added to the
 // record gradient, float 12 g + i for value i, by ten lanes at once:
 //   (du, dv, dA2, dbeta, dG2, dopacity, dr, dg, db, sum of alpha*T);
-//   contrib_max[g] = max(.., alpha*T)
+//   contrib_max[g] = max(.., alpha*T).
+// The five geometric values are summed as moments of dL/de' (e' the natural
+// exponent) and scaled by the splat's constants once, after the warp sum.
+// Six CTAs per SM (80 registers) measured faster than five at 89.
 template <int PX>
-__global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
+__global__ void __launch_bounds__(kBwdThreads, 6) k_composite_bwd(
     const uint2 *__restrict__ items, const uint32_t *__restrict__ n_items, uint32_t *__restrict__ queue,
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ list, const Rec *__restrict__ rec, int W, int H,
     int Tx, float3 bg, const float *__restrict__ t_final, const uint32_t *__restrict__ n_contrib,
     const uint32_t *__restrict__ seg_base, const float4 *__restrict__ ckpt, const uint32_t *__restrict__ qwork,
     const float *__restrict__ dL_dimage, const float *__restrict__ dL_dalpha, const uint8_t *__restrict__ layer,
-    uint32_t grad_layer_mask, float4 *__restrict__ rec_grad, float *__restrict__ contrib_max) {
+    uint32_t grad_layer_mask, float4 *__restrict__ rec_grad, float *__restrict__ contrib_max, uint32_t n_rec,
+    const Ctl *__restrict__ ctl) {
     __shared__ float4 s_a[kBwdThreads / 32][32], s_b[kBwdThreads / 32][32];
     __shared__ float s_c[kBwdThreads / 32][32];
     __shared__ uint32_t s_g[kBwdThreads / 32][32];
@@ -500,6 +526,11 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
     const unsigned lt = (1u << lane) - 1u;
     const int own = reduce10_owner(lane);
     const bool writer = reduce10_writer(lane);
+    // per-lane factors of the value it holds after the reduce-scatter:
+    //   du = -2 ln2 A2 S0, dv = -2 ln2 (A2 beta S0 + G2 S1), dA2 = ln2 S2, dbeta = 2 ln2 A2 S3, dG2 = ln2 S4
+    const float cA = own == 0 ? -2.f * kLn2 : (own == 3 ? 2.f * kLn2 : 0.f);
+    const float cB = own == 1 ? -2.f * kLn2 : 0.f;
+    const float cC = (own == 2 || own == 4) ? kLn2 : (own >= 5 ? 1.f : 0.f);
     const uint32_t total = *n_items;
     const size_t plane = static_cast<size_t>(W) * H;
     for (;;) {
@@ -556,7 +587,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
         }
         const uint32_t nchunk = (s1 - s0 + 31) / 32;
         Chunk nxt;
-        if (nchunk) fetch_chunk_layer(list, rec, layer, s0 + (nchunk - 1) * 32 + lane, s1, nxt);
+        if (nchunk) fetch_chunk_layer(list, rec, layer, s0 + (nchunk - 1) * 32 + lane, s1, nxt, n_rec, ctl);
+        // ids one chunk ahead of the records (the walk goes back to front; every chunk below the last is full)
+        uint32_t gid = nchunk >= 2 ? list[s0 + (nchunk - 2) * 32 + lane] : 0u;
         for (uint32_t c = nchunk; c-- > 0;) {
             const uint32_t base = s0 + c * 32;
             const bool keep =
@@ -572,7 +605,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
                 s_pos[warp][slot] = base + lane - rg.x;
             }
             __syncwarp();
-            if (c > 0) fetch_chunk_layer(list, rec, layer, base - 32 + lane, s1, nxt);
+            fetch_rec_layer(rec, layer, gid, c > 0, nxt, n_rec, ctl);
+            if (c > 1) gid = list[base - 64 + lane];
             const int cnt = __popc(km);
             for (int k = cnt - 1; k >= 0; --k) {
                 const uint32_t pos = s_pos[warp][k];
@@ -605,19 +639,24 @@ __global__ void __launch_bounds__(kBwdThreads) k_composite_bwd(
                     v[7] += wgt * dC1[j];
                     v[8] += wgt * dC2[j];
                     if (ao[j] < kAlphaMax) {
-                        const float dLde = dLda * al[j] * kLn2;
-                        const float A2p = a.z * p[j];
+                        // moments of dL/de' = dL/da alpha (e' = e ln 2 = ln(alpha / o)); the splat's
+                        // constant factors are applied once to the warp sums (see below)
+                        const float dLde = dLda * al[j];
+                        const float tp = dLde * p[j], td = dLde * dy[j];
                         v[5] += dLda * ex[j];
-                        v[2] += dLde * p[j] * p[j];
-                        v[3] += dLde * 2.f * A2p * dy[j];
-                        v[4] += dLde * dy[j] * dy[j];
-                        v[0] -= dLde * 2.f * A2p;
-                        v[1] -= dLde * (2.f * A2p * a.w + 2.f * b.x * dy[j]);
+                        v[0] += tp;
+                        v[1] += td;
+                        v[2] += tp * p[j];
+                        v[3] += tp * dy[j];
+                        v[4] += td * dy[j];
                     }
                     v[9] += wgt;
                     wmx = fmaxf(wmx, wgt);
                 }
-                const float sv = reduce_scatter10(v, lane);
+                const float sv0 = reduce_scatter10(v, lane);
+                // sum of tp, for the lanes holding the sum of td (dv needs both)
+                const float stp = __shfl_sync(FULL, sv0, lane & ~2);
+                const float sv = sv0 * (cA * a.z + cC) + cB * (a.z * a.w * stp + b.x * sv0);
                 const uint32_t smx = __reduce_max_sync(FULL, __float_as_uint(wmx));
                 const uint32_t gt = s_g[warp][k];
                 const uint32_t g = gt & 0x7FFFFFFFu;
@@ -707,14 +746,15 @@ cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *rang
                                       const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
                                       const uint32_t *n_contrib, const float *dL_dimage,
                                       const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
-                                      float4 *rec_grad, float *contrib_max, cudaStream_t st) {
+                                      float4 *rec_grad, float *contrib_max, uint32_t n, const Ctl *ctl,
+                                      cudaStream_t st) {
     if (Tx * Ty == 0) return cudaSuccess;
     static PerDevice cache;
     const int blocks = cache.get([] { return persistent_blocks(k_composite_bwd<kBwdPx>, kBwdThreads); });
     k_composite_bwd<kBwdPx><<<blocks, kBwdThreads, 0, st>>>(cb.items, cb.n_items, cb.queue, ranges, list, rec, W, H, Tx, bg,
                                                     t_final, n_contrib, cb.seg_base, cb.ckpt, cb.qwork,
                                                     dL_dimage, dL_dalpha, layer, grad_layer_mask, rec_grad,
-                                                    contrib_max);
+                                                    contrib_max, n, ctl);
     return cudaGetLastError();
 }
 

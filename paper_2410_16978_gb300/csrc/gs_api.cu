@@ -8,6 +8,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -102,18 +104,27 @@ struct Profiler {
 Profiler g_prof;
 std::atomic<int64_t> g_launches{0};
 
+// NVTX range names of the stages (shown by profilers that record NVTX; the
+// calls cost next to nothing when no tool is attached).
+const char *const kStageNames[GS_STAGE_COUNT] = {
+    "gs preprocess", "gs depth histograms", "gs depth sort", "gs bin rows", "gs bin tiles",
+    "gs compositor set-up", "gs composite", "gs composite backward", "gs preprocess backward", "gs prune",
+    "gs image loss", "gs adam"};
+
 struct Stage {
     int stage;
     cudaStream_t st;
     size_t idx = 0;
     Stage(int s, cudaStream_t stream, int kernels) : stage(s), st(stream) {
         g_launches += kernels;
+        nvtxRangePushA(kStageNames[s]);
         if (!g_prof.on) return;
         idx = g_prof.used;
         cudaEventRecord(g_prof.get(), st);
         g_prof.get();
     }
     ~Stage() {
+        nvtxRangePop();
         if (!g_prof.on) return;
         cudaEventRecord(g_prof.pool[idx + 1], st);
         g_prof.marks.emplace_back(stage, idx);
@@ -223,7 +234,57 @@ extern "C" {
 
 const char *gs_last_error_string(void) { return g_err.c_str(); }
 
-const char *gs_version(void) { return "gs-layered-gb300 0.1 (sm_103a)"; }
+const char *gs_version(void) {
+#ifdef GS_DEBUG
+    return "gs-layered-gb300 0.2 (sm_103a, GS_DEBUG bounds checks)";
+#else
+    return "gs-layered-gb300 0.2 (sm_103a)";
+#endif
+}
+
+int gs_debug_build(void) {
+#ifdef GS_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int gs_get_settings(gs_settings *out) {
+    if (!out) return fail(GS_ERR_INVALID, "out is NULL");
+    out->tile = kTile;
+    out->dilation = kDilation;
+    out->alpha_max = kAlphaMax;
+    out->alpha_min = kAlphaMin;
+    out->t_min = kTMin;
+    out->frustum_clamp = kFrustumClamp;
+    out->radius_sigmas = kRadiusSigmas;
+    out->eigen_floor = kEigenFloor;
+    out->checkpoint_stride = static_cast<int32_t>(kSeg);
+    out->max_sh_degree = 3;
+    out->max_planes = GS_MAX_PLANES;
+    out->max_image_dim = GS_MAX_IMAGE_DIM;
+    out->max_batch = GS_MAX_BATCH;
+    out->debug_build = gs_debug_build();
+    return GS_OK;
+}
+
+int gs_debug_site(const void *workspace, uint32_t *site, void *stream) {
+#ifdef GS_DEBUG
+    if (!workspace || !site) return fail(GS_ERR_INVALID, "NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = cuda_check(cudaMemcpyAsync(site, &static_cast<const Ctl *>(workspace)->dbg_site, sizeof(uint32_t),
+                                        cudaMemcpyDeviceToHost, st),
+                        "debug site copy");
+    if (rc != GS_OK) return rc;
+    return cuda_check(cudaStreamSynchronize(st), "debug site sync");
+#else
+    (void)workspace;
+    (void)site;
+    (void)stream;
+    return fail(GS_ERR_INVALID, "gs_debug_site: only in GS_DEBUG builds");
+#endif
+}
 
 int gs_render_workspace_size(int64_t n, int32_t width, int32_t height, int64_t dup_capacity, size_t *bytes) {
     if (!bytes) return fail(GS_ERR_INVALID, "bytes is NULL");
@@ -287,7 +348,8 @@ int front_preprocess(const gs_scene *scene, const gs_camera *camera, uint32_t la
                          "memset status")) != GS_OK)
         return rc;
     Stage sg(GS_STAGE_PREPROCESS, st, 1);
-    return cuda_check(launch_preprocess(f->sv, f->cv, layer_mask, pl, f->rec, f->tiles, f->depth, st), "preprocess");
+    return cuda_check(launch_preprocess(f->sv, f->cv, layer_mask, pl, f->rec, f->tiles, f->depth, f->ctl, st),
+                      "preprocess");
 }
 
 // Phase 2: the depth sort of the visible Gaussians.  With `other`, a
@@ -373,6 +435,9 @@ int front_bin(FrontCtx &f, const uint32_t *order, cudaStream_t st, FwdJob *job, 
     job->ckpt = cb.ckpt;
     job->qwork = cb.qwork;
     job->n_blended = reinterpret_cast<unsigned long long *>(&f.ctl->st.n_blended);
+    job->ctl = f.ctl;
+    job->n = n;
+    job->n_segs = static_cast<uint32_t>(L.dup_cap / kSeg + L.Tn + 1);
     job->W = f.cv.W;
     job->H = f.cv.H;
     job->Tx = f.cv.Tx;
@@ -516,7 +581,8 @@ int gs_render_backward(const gs_scene *scene, const gs_camera *camera, const flo
                                                        cv.Tx, cv.Ty, make_float3(bg[0], bg[1], bg[2]),
                                                        at<float>(ws, L.t_final), at<uint32_t>(ws, L.n_contrib),
                                                        dL_dimage, dL_dalpha, sv.layer, grad_layer_mask, rec_grad,
-                                                       contrib_max, st),
+                                                       contrib_max, static_cast<uint32_t>(sv.n), at<Ctl>(ws, L.ctl),
+                                                       st),
                              "composite backward")) != GS_OK)
             return rc;
     }

@@ -20,6 +20,10 @@ constexpr int kMaxSortBlocks = 1024;           // histogram rows reserved in the
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 0x1.010102p-8f;    // 1/255 rounded to float
 constexpr float kTMin = 1e-4f;
+constexpr float kDilation = 0.3f;              // EWA low-pass filter added to the 2D covariance (px^2)
+constexpr float kFrustumClamp = 1.3f;          // x/z and y/z clamped to this multiple of the half field of view
+constexpr float kRadiusSigmas = 3.0f;          // splat radius in standard deviations of the larger eigenvalue
+constexpr float kEigenFloor = 0.1f;            // floor of (mid^2 - det) under the eigenvalue square root
 constexpr uint32_t kSeg = 256;                 // list positions per backward segment (checkpoint stride)
 constexpr int kCbMaxDim = 48;                  // SH codebook: coordinates per row, 3(K-1) <= 45 padded
 constexpr int kBinMaxDim = 256;                // tile rows and columns the binning handles (4096 px)
@@ -42,7 +46,7 @@ struct __align__(16) Rec {
 struct Ctl {
     gs_status st;          // 32 bytes
     uint32_t n_vis;        // visible Gaussians (counted by the depth-sort histograms)
-    uint32_t reserved;
+    uint32_t dbg_site;     // GS_DEBUG builds: number of the first failed bounds check (0: none)
     uint32_t depth_mm[2];  // ~min and max of the visible depth keys (digits the sort can skip)
     uint32_t fwd_queue;    // next work item of the persistent forward compositor
     uint32_t bwd_queue;    // next work item of the persistent backward compositor
@@ -52,6 +56,35 @@ struct Ctl {
     uint32_t pad[12];
 };
 static_assert(sizeof(Ctl) == 128, "Ctl layout");
+
+// Bounds checks of GS_DEBUG builds.  GS_CHECK(ok, ctl, site) is `ok` in a
+// debug build, where a false `ok` also sets GS_ERR_BOUNDS in the status word
+// (unless an error is already there) and the site number of the first failed
+// check; callers skip the access when it is false.  In release builds it is
+// the constant true and the check compiles away.  Site numbers:
+enum DebugSite : uint32_t {
+    kSiteRect = 1,          // preprocess: tile rectangle inside the tile grid
+    kSiteSortScatter = 2,   // depth sort: scatter position below the item count
+    kSiteRowList = 3,       // binning: row-list position below the pair capacity
+    kSitePairList = 4,      // binning: pair-list position below the pair capacity
+    kSiteRange = 5,         // binning: tile range inside the pair count
+    kSiteFwdId = 6,         // forward compositor: Gaussian id from the list below n
+    kSiteCkpt = 7,          // forward compositor: checkpoint segment inside the checkpoint area
+    kSiteBwdId = 8,         // backward compositor: Gaussian id from the list below n
+};
+#ifdef GS_DEBUG
+__device__ __forceinline__ bool gs_check(bool ok, const Ctl *ctl, uint32_t site) {
+    if (!ok) {
+        Ctl *c = const_cast<Ctl *>(ctl);
+        atomicCAS(reinterpret_cast<int *>(&c->st.error), GS_OK, GS_ERR_BOUNDS);
+        atomicCAS(&c->dbg_site, 0u, site);
+    }
+    return ok;
+}
+#define GS_CHECK(ok, ctl, site) ::gs::gs_check((ok), (ctl), (site))
+#else
+#define GS_CHECK(ok, ctl, site) true
+#endif
 
 // Workspace carve-up.  Every region starts on a 256-byte boundary.
 struct Layout {
@@ -107,7 +140,7 @@ struct Planes {
 
 // ---- launches (each returns cudaGetLastError() of its launches) ----
 cudaError_t launch_preprocess(const SceneView &s, const CamView &c, uint32_t layer_mask, const Planes &pl,
-                              Rec *rec, uint32_t *tiles, uint32_t *depth_key, cudaStream_t st);
+                              Rec *rec, uint32_t *tiles, uint32_t *depth_key, const Ctl *ctl, cudaStream_t st);
 // Also adds the per-Gaussian blend-weight sums (record-gradient slot 9) to
 // contrib_sum when it is not null.
 // vis_index: the visible list of the last render (index order, ctl->n_vis
@@ -236,6 +269,9 @@ struct FwdJob {
     float4 *ckpt;
     uint32_t *qwork;
     unsigned long long *n_blended;   // the view's status word: blended pairs
+    const Ctl *ctl;                  // the view's control block (bounds checks of GS_DEBUG builds)
+    uint32_t n;                      // Gaussians of the view's scene
+    uint32_t n_segs;                 // checkpoint segments the workspace holds
     int W, H, Tx, Tn;
     float3 bg;
     uint32_t item_begin;   // first global work item of this view (filled by the launcher)
@@ -255,6 +291,7 @@ cudaError_t launch_composite_backward(const CompositeBufs &cb, const uint2 *rang
                                       const Rec *rec, int W, int H, int Tx, int Ty, float3 bg, const float *t_final,
                                       const uint32_t *n_contrib, const float *dL_dimage,
                                       const float *dL_dalpha, const uint8_t *layer, uint32_t grad_layer_mask,
-                                      float4 *rec_grad, float *contrib_max, cudaStream_t st);
+                                      float4 *rec_grad, float *contrib_max, uint32_t n, const Ctl *ctl,
+                                      cudaStream_t st);
 
 }  // namespace gs

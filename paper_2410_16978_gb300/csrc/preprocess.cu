@@ -73,7 +73,7 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float *b) {
 template <int DEG>
 __global__ void __launch_bounds__(128) k_preprocess(SceneView s, CamView c, uint32_t layer_mask, Planes pl,
                                                     Rec *__restrict__ rec, uint32_t *__restrict__ tiles,
-                                                    uint32_t *__restrict__ depth_key) {
+                                                    uint32_t *__restrict__ depth_key, const Ctl *__restrict__ ctl) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
     uint32_t ntiles = 0;
@@ -136,8 +136,8 @@ __global__ void __launch_bounds__(128) k_preprocess(SceneView s, CamView c, uint
         const float S12 = (m10 * m20 + m11 * m21) + m12 * m22;
         const float S22 = (m20 * m20 + m21 * m21) + m22 * m22;
 
-        const float limx = 1.3f * ((0.5f * static_cast<float>(c.W)) / c.fx);
-        const float limy = 1.3f * ((0.5f * static_cast<float>(c.H)) / c.fy);
+        const float limx = kFrustumClamp * ((0.5f * static_cast<float>(c.W)) / c.fx);
+        const float limy = kFrustumClamp * ((0.5f * static_cast<float>(c.H)) / c.fy);
         const float izx = px / pz, izy = py / pz;
         const float cxz = fminf(limx, fmaxf(-limx, izx));
         const float cyz = fminf(limy, fmaxf(-limy, izy));
@@ -151,15 +151,15 @@ __global__ void __launch_bounds__(128) k_preprocess(SceneView s, CamView c, uint
         const float u10 = (t10 * S00 + t11 * S01) + t12 * S02;
         const float u11 = (t10 * S01 + t11 * S11) + t12 * S12;
         const float u12 = (t10 * S02 + t11 * S12) + t12 * S22;
-        const float c00 = ((u00 * t00 + u01 * t01) + u02 * t02) + 0.3f;
+        const float c00 = ((u00 * t00 + u01 * t01) + u02 * t02) + kDilation;
         const float c01 = (u00 * t10 + u01 * t11) + u02 * t12;
-        const float c11 = ((u10 * t10 + u11 * t11) + u12 * t12) + 0.3f;
+        const float c11 = ((u10 * t10 + u11 * t11) + u12 * t12) + kDilation;
         const float det = c00 * c11 - c01 * c01;
         if (det > 0.0f) {
             const float mid = 0.5f * (c00 + c11);
-            const float disc = fmaxf(0.1f, mid * mid - det);
+            const float disc = fmaxf(kEigenFloor, mid * mid - det);
             const float lam = mid + sqrtf(disc);
-            const float r = ceilf(3.0f * sqrtf(lam));
+            const float r = ceilf(kRadiusSigmas * sqrtf(lam));
             const float uu = c.fx * izx + c.cx, vv = c.fy * izy + c.cy;
             const float fTx = static_cast<float>(c.Tx), fTy = static_cast<float>(c.Ty);
             const float fx0 = fminf(fTx, fmaxf(0.0f, truncf((uu - r) * 0.0625f)));
@@ -168,7 +168,9 @@ __global__ void __launch_bounds__(128) k_preprocess(SceneView s, CamView c, uint
             const float fy1 = fminf(fTy, fmaxf(0.0f, truncf(((vv + r) + 15.0f) * 0.0625f)));
             const int x0 = static_cast<int>(fx0), y0 = static_cast<int>(fy0);
             const int x1 = static_cast<int>(fx1), y1 = static_cast<int>(fy1);
-            ntiles = static_cast<uint32_t>((x1 - x0) * (y1 - y0));
+            ntiles = GS_CHECK(x0 <= x1 && y0 <= y1 && x1 <= c.Tx && y1 <= c.Ty, ctl, kSiteRect)
+                         ? static_cast<uint32_t>((x1 - x0) * (y1 - y0))
+                         : 0u;
             if (ntiles > 0) {
                 // view-dependent colour
                 const float campos0 = -((R[0] * c.t[0] + R[3] * c.t[1]) + R[6] * c.t[2]);
@@ -239,14 +241,14 @@ __global__ void __launch_bounds__(128) k_preprocess(SceneView s, CamView c, uint
 }  // namespace
 
 cudaError_t launch_preprocess(const SceneView &s, const CamView &c, uint32_t layer_mask, const Planes &pl, Rec *rec,
-                              uint32_t *tiles, uint32_t *depth_key, cudaStream_t st) {
+                              uint32_t *tiles, uint32_t *depth_key, const Ctl *ctl, cudaStream_t st) {
     if (s.n == 0) return cudaSuccess;
     const int threads = 128, blocks = (s.n + threads - 1) / threads;
     switch (s.sh_degree) {
-        case 0: k_preprocess<0><<<blocks, threads, 0, st>>>(s, c, layer_mask, pl, rec, tiles, depth_key); break;
-        case 1: k_preprocess<1><<<blocks, threads, 0, st>>>(s, c, layer_mask, pl, rec, tiles, depth_key); break;
-        case 2: k_preprocess<2><<<blocks, threads, 0, st>>>(s, c, layer_mask, pl, rec, tiles, depth_key); break;
-        default: k_preprocess<3><<<blocks, threads, 0, st>>>(s, c, layer_mask, pl, rec, tiles, depth_key); break;
+        case 0: k_preprocess<0><<<blocks, threads, 0, st>>>(s, c, layer_mask, pl, rec, tiles, depth_key, ctl); break;
+        case 1: k_preprocess<1><<<blocks, threads, 0, st>>>(s, c, layer_mask, pl, rec, tiles, depth_key, ctl); break;
+        case 2: k_preprocess<2><<<blocks, threads, 0, st>>>(s, c, layer_mask, pl, rec, tiles, depth_key, ctl); break;
+        default: k_preprocess<3><<<blocks, threads, 0, st>>>(s, c, layer_mask, pl, rec, tiles, depth_key, ctl); break;
     }
     return cudaGetLastError();
 }

@@ -175,6 +175,12 @@ constexpr int kLookCounters = 256;                 // one per digit
 constexpr uint64_t kLookAgg = 1ull << 32;          // the tile's own count is published
 constexpr uint64_t kLookIncl = 2ull << 32;         // the count of every tile up to and including it
 constexpr uint32_t kSpinLimit = 1u << 20;
+#ifdef GS_DEBUG
+// Test hooks of the look-back wait (gs_debug_sort_wait): its iteration limit,
+// and a digit kernel whose first tile never publishes its counts.
+uint32_t g_dbg_spin_limit = kSpinLimit;
+int g_dbg_withhold_pass = -1;
+#endif
 
 __device__ __forceinline__ void st_volatile(uint64_t *p, uint64_t v) { *reinterpret_cast<volatile uint64_t *>(p) = v; }
 __device__ __forceinline__ uint64_t ld_volatile(const uint64_t *p) {
@@ -210,7 +216,8 @@ struct TileCounts {
 // nearest first, so a walk over tiles that only hold aggregates costs one
 // memory latency per window instead of one per tile.
 constexpr int kLookWindow = 8;
-__device__ uint32_t look_back(uint64_t *status, uint32_t t, int c, uint32_t own, Ctl *ctl) {
+__device__ uint32_t look_back(uint64_t *status, uint32_t t, int c, uint32_t own, Ctl *ctl, uint32_t spin_limit,
+                              bool publish) {
     uint32_t excl = 0;
     int64_t j = static_cast<int64_t>(t) - 1;
     uint32_t spins = 0;
@@ -236,14 +243,14 @@ __device__ uint32_t look_back(uint64_t *status, uint32_t t, int c, uint32_t own,
         if (incl) break;
         j -= used;
         if (waiting) {
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 ctl->st.error = GS_ERR_TIMEOUT;
                 break;
             }
             __nanosleep(64);
         }
     }
-    st_volatile(status + static_cast<size_t>(t) * kLookCounters + c, kLookIncl | (excl + own));
+    if (publish) st_volatile(status + static_cast<size_t>(t) * kLookCounters + c, kLookIncl | (excl + own));
     return excl;
 }
 
@@ -321,6 +328,8 @@ struct SortBufs {
     const uint32_t *ghist;           // [4][256] digit histograms of the visible keys
     TileCounts tc;                   // first digit kernel: tile and group counts
     uint64_t *status, *status_next;  // look-back words [tile][256] of this (after the first) and the next pass
+    uint32_t spin_limit;             // iterations a look-back waits for a predecessor before GS_ERR_TIMEOUT
+    int withhold;                    // GS_DEBUG test hook: this kernel's first tile publishes nothing (-1: off)
 };
 
 // One digit (bits 8 pass .. 8 pass + 7) of the stable LSD sort, on tiles of
@@ -383,6 +392,11 @@ __global__ void __launch_bounds__(kPassThreads) k_sort_pass(Src src, uint32_t n_
         t = s_ticket;
         if (t >= ntiles) return;
     }
+#ifdef GS_DEBUG
+    const bool publish = !(pass == B.withhold && t == 0);
+#else
+    constexpr bool publish = true;
+#endif
     if (!last && t < (n_vis + kPassTile - 1) / kPassTile)
         for (int c = threadIdx.x; c < kLookCounters; c += kPassThreads)
             B.status_next[static_cast<size_t>(t) * kLookCounters + c] = 0;
@@ -455,7 +469,7 @@ __global__ void __launch_bounds__(kPassThreads) k_sort_pass(Src src, uint32_t n_
             s_wc[w][d] = static_cast<uint16_t>(acc);
             acc += c;
         }
-        if (!FIRST)
+        if (!FIRST && publish)
             st_volatile(B.status + static_cast<size_t>(t) * kLookCounters + d, (t == 0 ? kLookIncl : kLookAgg) | acc);
     }
     uint32_t ntile;
@@ -464,7 +478,7 @@ __global__ void __launch_bounds__(kPassThreads) k_sort_pass(Src src, uint32_t n_
     uint32_t gtot;
     const uint32_t gbase = block_scan_512(dig ? B.ghist[pass * 256 + d] : 0u, s_w, &gtot);
     uint32_t excl = 0;
-    if (dig) excl = FIRST ? part + s_part[d] : look_back(B.status, t, d, acc, ctl);
+    if (dig) excl = FIRST ? part + s_part[d] : look_back(B.status, t, d, acc, ctl, B.spin_limit, publish);
     if (dig) s_off[d] = gbase + excl;
     if constexpr (FIRST) {
         // the items of all digits in the tiles before this one are the visible Gaussians before it
@@ -494,6 +508,7 @@ __global__ void __launch_bounds__(kPassThreads) k_sort_pass(Src src, uint32_t n_
         const uint32_t k = s_key[i];
         const uint32_t dd = (k >> shift) & 255u;
         const uint32_t pos = s_off[dd] + (i - s_lstart[dd]);
+        if (!GS_CHECK(pos < n_vis, ctl, kSiteSortScatter)) continue;
         if (last) {
             B.final_out[pos] = s_val[i];
         } else {
@@ -547,6 +562,13 @@ cudaError_t sort_digits(const Src &src, int n, const SortWork &w, Ctl *ctl, cuda
         b.tc = tc;
         b.status = p > 0 ? w.status + static_cast<size_t>(p - 1) * nt * kLookCounters : nullptr;
         b.status_next = p < 3 ? w.status + static_cast<size_t>(p) * nt * kLookCounters : nullptr;
+#ifdef GS_DEBUG
+        b.spin_limit = g_dbg_spin_limit;
+        b.withhold = g_dbg_withhold_pass;
+#else
+        b.spin_limit = kSpinLimit;
+        b.withhold = -1;
+#endif
         if (p == 0) k_sort_pass<Src, true><<<nt, kPassThreads, 0, st>>>(src, static_cast<uint32_t>(n), p, b, ctl);
         else k_sort_pass<Src, false><<<nt, kPassThreads, 0, st>>>(src, static_cast<uint32_t>(n), p, b, ctl);
     }
@@ -629,3 +651,17 @@ cudaError_t launch_prune(const float *contrib_max, int n, float thr, uint8_t *ke
 }
 
 }  // namespace gs
+
+extern "C" int gs_debug_sort_wait(uint32_t spin_limit, int32_t withhold_pass) {
+#ifdef GS_DEBUG
+    if (withhold_pass != -1 && (withhold_pass < 1 || withhold_pass > 3))
+        return gs::report(GS_ERR_INVALID, "gs_debug_sort_wait: withhold_pass must be -1 or 1..3");
+    gs::g_dbg_spin_limit = spin_limit ? spin_limit : gs::kSpinLimit;
+    gs::g_dbg_withhold_pass = withhold_pass;
+    return GS_OK;
+#else
+    (void)spin_limit;
+    (void)withhold_pass;
+    return gs::report(GS_ERR_INVALID, "gs_debug_sort_wait: only in GS_DEBUG builds");
+#endif
+}

@@ -34,6 +34,36 @@ def test_version_and_empty_error():
     assert "sm_103a" in _lib.gs_version()
 
 
+def test_settings_are_the_methods_constants():
+    s = _lib.gs_get_settings()
+    f32 = lambda x: float(ctypes.c_float(x).value)
+    assert s.tile == 16 and s.checkpoint_stride == 256 and s.max_sh_degree == 3
+    assert s.dilation == f32(0.3) and s.alpha_max == f32(0.99) and s.t_min == f32(1e-4)
+    assert s.alpha_min == f32(1.0 / 255.0) and s.frustum_clamp == f32(1.3)
+    assert s.radius_sigmas == 3.0 and s.eigen_floor == f32(0.1)
+    assert (s.max_planes, s.max_image_dim, s.max_batch) == (_lib.GS_MAX_PLANES, 4096, _lib.GS_MAX_BATCH)
+    assert s.debug_build == 0
+
+
+def test_debug_library_exports_the_same_boundary():
+    """libgs_debug.so (GS_DEBUG) has every entry point, says it is the debug
+    build, and its hooks are refused by the release library."""
+    D = _lib.load_debug()
+    for name in _declared():
+        assert hasattr(D, name), name
+    assert D.gs_debug_build() == 1 and _lib.load().gs_debug_build() == 0
+    with _lib.use(D):
+        assert _lib.gs_get_settings().debug_build == 1
+        _lib.gs_debug_sort_wait(0, -1)                  # host-only: resets the hook
+        with pytest.raises(_lib.GsError) as e:
+            _lib.gs_debug_sort_wait(100, 0)             # the first digit kernel has no wait
+        assert e.value.code == _lib.GS_ERR_INVALID
+    for call in (lambda: _lib.gs_debug_sort_wait(100, 1), lambda: _lib.gs_debug_site(None, 0)):
+        with pytest.raises(_lib.GsError) as e:
+            call()
+        assert e.value.code == _lib.GS_ERR_INVALID
+
+
 def test_workspace_size_and_layout():
     b = _lib.gs_render_workspace_size(1000, 100, 70, 5000)
     lay = _lib.gs_workspace_layout(1000, 100, 70, b)
