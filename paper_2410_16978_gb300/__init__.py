@@ -23,5 +23,6 @@ from ._lib import (  # noqa: F401
     make_camera,
 )
 from .api import DeviceScene, Rasterizer, RenderFunction, contrib_prune, render  # noqa: F401
+from .checkpoint import load_ply, load_scene, load_trainer, merge_layers, save_ply, save_scene, save_trainer  # noqa: F401
 
-__version__ = "0.1.0"
+__version__ = "0.2.0"
