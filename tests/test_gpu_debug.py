@@ -71,12 +71,14 @@ def test_failed_bounds_check_reports_and_skips(dbg):
         ncon = r.workspace[lay["n_contrib"]:lay["n_contrib"] + 4 * cam.width * cam.height].view(torch.int32)
         ncon = ncon.view(cam.height, cam.width).cpu().numpy()
         Tx = (cam.width + 15) // 16
-        # a tile whose pixels blend its first list entry, so the backward reads that entry
+        # a tile with blended splats: every entry of its blended prefix is overwritten, so the backward
+        # reads at least one bad id (an entry that some pixel blended)
         tile = next(t for t in range(Tn) if ranges[t, 1] > ranges[t, 0] and
                     ncon[(t // Tx) * 16:(t // Tx) * 16 + 16, (t % Tx) * 16:(t % Tx) * 16 + 16].max() >= 1)
         pos = int(ranges[tile, 0])
-        bad = torch.tensor([0xFFFFFFF0], dtype=torch.int64).to(torch.int32).view(torch.uint8).cuda()
-        r.workspace[lay["list"] + 4 * pos:lay["list"] + 4 * pos + 4].copy_(bad)
+        k = int(ncon[(tile // Tx) * 16:(tile // Tx) * 16 + 16, (tile % Tx) * 16:(tile % Tx) * 16 + 16].max())
+        bad = torch.full((k,), 0xFFFFFFF0, dtype=torch.int64).to(torch.int32).view(torch.uint8).cuda()
+        r.workspace[lay["list"] + 4 * pos:lay["list"] + 4 * (pos + k)].copy_(bad)
         g = r.backward(ds, cam, bg, torch.ones((3, cam.height, cam.width), device="cuda"))
         torch.cuda.synchronize()
         st = r.status()
