@@ -91,13 +91,19 @@ __device__ __forceinline__ void warp_prefix_inplace(uint32_t *a, int n, int lane
     __syncwarp();
 }
 
+// The per-row scan of the row pass splits every row's kBinChunks chunk
+// counts into kRowParts parts, one CTA each.
+constexpr int kRowParts = 4;
+constexpr int kPartChunks = kBinChunks / kRowParts;
+static_assert(kPartChunks % 1024 == 0 && kPartChunks / 1024 <= kBinChunksPerThread, "row-scan part shape");
+
 struct RowInfo {           // per tile row, in the workspace
     uint32_t start;        // first row-list entry of the row
     uint32_t entries;      // row-list entries of the row
     uint32_t pair_start;   // first pair (final list position) of the row
     uint32_t pairs;        // pairs of the row
     uint32_t piece_start;  // first piece of the row (pieces: kPiece-entry parts of row lists)
-    uint32_t pad[3];
+    uint32_t part_base[kRowParts - 1];   // entries of the row in the chunk parts before parts 1, 2, 3
 };
 
 // Pass 1 (SCATTER = false: count, true: write) over the chunks of the depth order.
@@ -121,7 +127,10 @@ __global__ void __launch_bounds__(256) k_bin_rows(const uint32_t *__restrict__ o
     // is one 32-byte transaction
     for (int t = threadIdx.x; t < 8 * (Ty + 1); t += blockDim.x) {
         const int r = t >> 3, w = t & 7;
-        s_cnt[w][r] = (SCATTER && r < Ty) ? rows[r].start + M[static_cast<size_t>(r) * K + blockIdx.x * 8u + w] : 0u;
+        const uint32_t ch = blockIdx.x * 8u + w, part = ch / (K / kRowParts);
+        s_cnt[w][r] = (SCATTER && r < Ty)
+                          ? rows[r].start + (part ? rows[r].part_base[part - 1] : 0u) + M[static_cast<size_t>(r) * K + ch]
+                          : 0u;
         if (!SCATTER) s_px[w][r] = 0;
     }
     __syncthreads();
@@ -182,65 +191,81 @@ __global__ void __launch_bounds__(256) k_bin_rows(const uint32_t *__restrict__ o
     }
 }
 
-// Per row (one CTA each): exclusive scan of the row's K chunk counts in place.
-// The row moves through shared memory with coalesced loads and stores (each
-// thread scans a contiguous run of kBinChunksPerThread counts); the row's pair
-// total needs only a sum, read coalesced.
+// Per (row, part) (one CTA each, kRowParts parts of K / kRowParts chunks per
+// row): exclusive scan of the part's chunk counts in place, and the part's
+// entry and pair totals.  The part moves through shared memory with
+// coalesced loads and stores (each thread scans a contiguous run of counts);
+// the pair total needs only a sum, read coalesced.  The last CTA to finish
+// (a counter in the control block) then does the per-row work for the whole
+// frame: part bases, row totals, the row, pair and piece starts, the pair
+// total and the capacity check.
 __global__ void __launch_bounds__(1024) k_bin_rowscan(uint32_t *__restrict__ M, int K, int Ty,
-                                                      RowInfo *__restrict__ rows, const Ctl *__restrict__ ctl) {
+                                                      RowInfo *__restrict__ rows, uint2 *__restrict__ part_tot,
+                                                      Ctl *__restrict__ ctl, uint64_t cap, uint32_t piece) {
     __shared__ uint32_t s_w[32];
-    __shared__ uint32_t s_row[kBinChunks];
-    if (ctl->st.error != GS_OK) return;
-    uint32_t *row = M + static_cast<size_t>(blockIdx.x) * K;
-    const uint32_t *prow = M + static_cast<size_t>(Ty + blockIdx.x) * K;   // pairs of the same row
+    __shared__ uint32_t s_row[kPartChunks];
+    __shared__ bool s_last;
+    if (ctl->st.error != GS_OK) return;      // uniform: an error set before this kernel (a sort that timed out)
+    const int r = blockIdx.x / kRowParts, part = blockIdx.x % kRowParts;
+    const int KP = K / kRowParts;
+    uint32_t *row = M + static_cast<size_t>(r) * K + static_cast<size_t>(part) * KP;
+    const uint32_t *prow = M + static_cast<size_t>(Ty + r) * K + static_cast<size_t>(part) * KP;   // pairs
     uint32_t psum = 0;
-    for (int i = threadIdx.x; i < K; i += 1024) {
+    for (int i = threadIdx.x; i < KP; i += 1024) {
         s_row[i] = row[i];
         psum += prow[i];
     }
     uint32_t ptot;
     block_excl_scan<1024>(psum, s_w, &ptot);             // synchronises the block, so s_row is complete
-    if (threadIdx.x == 0) rows[blockIdx.x].pairs = ptot;
-    const int per = (K + 1023) / 1024;
+    const int per = KP / 1024;
     uint32_t v[kBinChunksPerThread];
     uint32_t sum = 0;
 #pragma unroll
     for (int q = 0; q < kBinChunksPerThread; ++q) {
-        const int i = threadIdx.x * per + q;
-        v[q] = (q < per && i < K) ? s_row[i] : 0u;
+        v[q] = q < per ? s_row[threadIdx.x * per + q] : 0u;
         sum += v[q];
     }
     uint32_t tot;
     uint32_t run = block_excl_scan<1024>(sum, s_w, &tot);
 #pragma unroll
     for (int q = 0; q < kBinChunksPerThread; ++q) {
-        const int i = threadIdx.x * per + q;
-        if (q < per && i < K) s_row[i] = run;
+        if (q < per) s_row[threadIdx.x * per + q] = run;
         run += v[q];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < K; i += 1024) row[i] = s_row[i];
-    if (threadIdx.x == 0) rows[blockIdx.x].entries = tot;
-}
-
-// One CTA: row starts, pair starts, piece starts, the pair total and the
-// capacity check.
-__global__ void __launch_bounds__(256) k_bin_rowstart(RowInfo *__restrict__ rows, int Ty, Ctl *__restrict__ ctl,
-                                                      uint64_t cap, uint32_t piece) {
-    __shared__ uint32_t s_w[8];
-    if (ctl->st.error != GS_OK) return;   // uniform: the status is not written in this kernel before this test
-    const int r = threadIdx.x;
-    uint32_t te, tp, tq;
-    const uint32_t ent = r < Ty ? rows[r].entries : 0u;
-    const uint32_t s0 = block_excl_scan<256>(ent, s_w, &te);
-    const uint32_t s1 = block_excl_scan<256>(r < Ty ? rows[r].pairs : 0u, s_w, &tp);
-    const uint32_t s2 = block_excl_scan<256>((ent + piece - 1) / piece, s_w, &tq);
-    if (r < Ty) {
-        rows[r].start = s0;
-        rows[r].pair_start = s1;
-        rows[r].piece_start = s2;
+    for (int i = threadIdx.x; i < KP; i += 1024) row[i] = s_row[i];
+    if (threadIdx.x == 0) {
+        part_tot[blockIdx.x] = make_uint2(tot, ptot);
+        __threadfence();
+        s_last = atomicAdd(&ctl->bin_scan_done, 1u) == gridDim.x - 1;
     }
-    if (r == 0) {
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // the last CTA: per row (thread r < Ty <= 256) the part bases and totals, then the starts
+    const volatile uint2 *pt = part_tot;
+    uint32_t ent = 0, prs = 0;
+    if (threadIdx.x < Ty) {
+        for (int p = 0; p < kRowParts; ++p) {
+            const uint32_t e = pt[threadIdx.x * kRowParts + p].x;
+            if (p > 0) rows[threadIdx.x].part_base[p - 1] = ent;
+            ent += e;
+            prs += pt[threadIdx.x * kRowParts + p].y;
+        }
+        rows[threadIdx.x].entries = ent;
+        rows[threadIdx.x].pairs = prs;
+    }
+    uint32_t te, tp, tq;
+    const bool in = threadIdx.x < Ty;
+    const uint32_t s0 = block_excl_scan<1024>(in ? ent : 0u, s_w, &te);
+    const uint32_t s1 = block_excl_scan<1024>(in ? prs : 0u, s_w, &tp);
+    const uint32_t s2 = block_excl_scan<1024>(in ? (ent + piece - 1) / piece : 0u, s_w, &tq);
+    if (in) {
+        rows[threadIdx.x].start = s0;
+        rows[threadIdx.x].pair_start = s1;
+        rows[threadIdx.x].piece_start = s2;
+    }
+    if (threadIdx.x == 0) {
         ctl->st.n_dup = tp;
         ctl->st.dup_capacity = cap;
         ctl->n_pieces = tq;
@@ -386,9 +411,10 @@ cudaError_t launch_bin_rows(const uint32_t *order, const Rec *rec, uint32_t n_ca
                             void *rows_buf, uint2 *rowlist, Ctl *ctl, uint64_t cap, uint32_t piece, cudaStream_t st) {
     if (Ty > kBinMaxDim) return cudaErrorInvalidValue;
     RowInfo *rows = static_cast<RowInfo *>(rows_buf);   // zero on entry (cleared with the control block)
+    uint2 *part_tot = reinterpret_cast<uint2 *>(static_cast<char *>(rows_buf) + bin_rows_bytes(Ty) -
+                                                 static_cast<size_t>(Ty) * kRowParts * sizeof(uint2));
     k_bin_rows<false><<<kBinBlocks, 256, 0, st>>>(order, rec, n_cap, Ty, M, rows, rowlist, ctl);
-    k_bin_rowscan<<<Ty, 1024, 0, st>>>(M, kBinBlocks * 8, Ty, rows, ctl);
-    k_bin_rowstart<<<1, 256, 0, st>>>(rows, Ty, ctl, cap, piece);
+    k_bin_rowscan<<<Ty * kRowParts, 1024, 0, st>>>(M, kBinBlocks * 8, Ty, rows, part_tot, ctl, cap, piece);
     k_bin_rows<true><<<kBinBlocks, 256, 0, st>>>(order, rec, n_cap, Ty, M, rows, rowlist, ctl);
     return cudaGetLastError();
 }
@@ -423,7 +449,10 @@ size_t bin_piece_bytes(int64_t dup_cap, int Tx, int Ty) {
     return (std::max(rows, floor_rows) + Ty + 1) * Tx * 4;
 }
 
-size_t bin_rows_bytes(int Ty) { return static_cast<size_t>(Ty) * sizeof(RowInfo); }
+// The RowInfo of every row, then the (entries, pairs) totals of every (row, part) of the row scan.
+size_t bin_rows_bytes(int Ty) {
+    return static_cast<size_t>(Ty) * sizeof(RowInfo) + static_cast<size_t>(Ty) * kRowParts * sizeof(uint2);
+}
 static_assert(sizeof(RowInfo) == 32, "RowInfo layout");
 
 }  // namespace gs

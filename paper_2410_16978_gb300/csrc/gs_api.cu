@@ -405,7 +405,7 @@ int front_bin(FrontCtx &f, const uint32_t *order, cudaStream_t st, FwdJob *job, 
     uint2 *rowlist = at<uint2>(ws, L.rowlist);
     uint2 *ranges = at<uint2>(ws, L.ranges);
     {
-        Stage sg(GS_STAGE_BIN_ROWS, st, 4);
+        Stage sg(GS_STAGE_BIN_ROWS, st, 3);
         if ((rc = cuda_check(launch_bin_rows(order, f.rec, n, f.cv.Ty, at<uint32_t>(ws, L.bin_m),
                                              at<void>(ws, L.bin_rows), rowlist, f.ctl, L.dup_cap, L.bin_piece, st),
                              "binning rows")) != GS_OK)

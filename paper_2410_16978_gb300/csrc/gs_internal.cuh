@@ -53,7 +53,8 @@ struct Ctl {
     uint32_t n_items;      // backward work items (tile, 8x8 block, segment)
     uint32_t n_pieces;     // row-list pieces of the binning
     uint32_t sort_ticket[4];   // next tile of each digit kernel of the depth sort (after the first)
-    uint32_t pad[12];
+    uint32_t bin_scan_done;    // CTAs of the binning's per-row scan that have finished (the last one finishes)
+    uint32_t pad[11];
 };
 static_assert(sizeof(Ctl) == 128, "Ctl layout");
 
