@@ -35,6 +35,10 @@ __device__ __forceinline__ float target_at(const float *trgb, const float *talph
 
 __device__ __forceinline__ float sgn(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
 
+// SSIM's window moments are taken of x - kSsimShift and y - kSsimShift (image
+// values lie in [0, 1]); zero padding outside the image enters as -kSsimShift.
+constexpr float kSsimShift = 0.5f;
+
 // Pass 1: per pixel and channel, SSIM and the maps a, b, c; block sums of
 // SSIM, |X - Y| and (channel 0) |A - A_t|.
 __global__ void __launch_bounds__(kLW *kLH) k_loss_maps(const float *__restrict__ X, const float *__restrict__ A,
@@ -67,7 +71,7 @@ __global__ void __launch_bounds__(kLW *kLH) k_loss_maps(const float *__restrict_
         float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
 #pragma unroll
         for (int j = 0; j < kWin; ++j) {
-            const float a = s_x[ry][cx + j], b = s_y[ry][cx + j], w = win.g[j];
+            const float a = s_x[ry][cx + j] - kSsimShift, b = s_y[ry][cx + j] - kSsimShift, w = win.g[j];
             mx = fmaf(w, a, mx);
             my = fmaf(w, b, my);
             xx = fmaf(w, a * a, xx);
@@ -90,8 +94,11 @@ __global__ void __launch_bounds__(kLW *kLH) k_loss_maps(const float *__restrict_
         for (int i = 0; i < kWin; ++i)
 #pragma unroll
             for (int q = 0; q < 5; ++q) m[q] = fmaf(win.g[i], s_h[q][ly + i][lx], m[q]);
-        const float mux = m[0], muy = m[1];
-        const float sx = m[2] - mux * mux, sy = m[3] - muy * muy, sxy = m[4] - mux * muy;
+        // moments of the shifted values x - kSsimShift, y - kSsimShift: the (co)variances are shift
+        // invariant, and the shift takes most of E[x^2] - mu^2's cancellation out for values in [0, 1]
+        const float mcx = m[0], mcy = m[1];
+        const float sx = m[2] - mcx * mcx, sy = m[3] - mcy * mcy, sxy = m[4] - mcx * mcy;
+        const float mux = mcx + kSsimShift, muy = mcy + kSsimShift;
         const float n1 = 2.f * mux * muy + kC1, n2 = 2.f * sxy + kC2;
         const float d1 = mux * mux + muy * muy + kC1, d2 = sx + sy + kC2;
         f = (n1 * n2) / (d1 * d2);
@@ -100,7 +107,7 @@ __global__ void __launch_bounds__(kLW *kLH) k_loss_maps(const float *__restrict_
         const float df_dsxy = 2.f * f / n2;
         const size_t p = static_cast<size_t>(gy) * W + gx;
         float *mp = maps + static_cast<size_t>(ch) * 3 * plane;
-        mp[p] = df_dmx - 2.f * mux * df_dsx - muy * df_dsxy;
+        mp[p] = df_dmx - 2.f * mcx * df_dsx - mcy * df_dsxy;
         mp[plane + p] = df_dsx;
         mp[2 * plane + p] = df_dsxy;
         l1 = fabsf(s_x[ly + kHalo][lx + kHalo] - s_y[ly + kHalo][lx + kHalo]);
@@ -173,7 +180,7 @@ __global__ void __launch_bounds__(kLW *kLH) k_loss_grad(const float *__restrict_
     const float x = X[ch * plane + p];
     const float y = target_at(Ct, At, bgc, ch * plane + p, p);
     const float inv_n = 1.f / (3.f * static_cast<float>(plane));
-    const float dS = s[0] + 2.f * x * s[1] + y * s[2];
+    const float dS = s[0] + 2.f * (x - kSsimShift) * s[1] + (y - kSsimShift) * s[2];
     dX[ch * plane + p] = ((1.f - lam) * sgn(x - y) - lam * dS) * inv_n;
     if (ch == 0 && dA) dA[p] = A ? w_a * sgn(A[p] - At[p]) / static_cast<float>(plane) : 0.f;
 }

@@ -3,9 +3,10 @@ image loss and its gradient, Adam with frozen layers, the row gather of the
 prune, and one whole step (render, loss, backward, Adam) through the autograd
 Functions.
 
-Tolerances: the loss within 1e-5 relative; its gradient within 1e-4 of the
-largest |dL/dX|, from single-precision SSIM moments (E[x^2] - mu^2 loses
-about eps * E[x^2] / sigma^2 relative); Adam within 1e-5 of the step size."""
+Tolerances: the loss within 1e-5 relative; its gradient within 1e-5 of the
+largest |dL/dX| (measured 1e-7 to 6e-7: the SSIM window moments are taken of
+the values shifted by 0.5, which keeps E[x^2] - mu^2's single-precision
+cancellation small for values in [0, 1]); Adam within 1e-5 of the step size."""
 import numpy as np
 import pytest
 import torch
@@ -44,7 +45,8 @@ def test_image_loss_matches_oracle(H, W, lam, w_a):
     torch.cuda.synchronize()
     assert abs(float(loss) - L) <= 1e-5 * abs(L)
     e = np.abs(gX.cpu().numpy() - dX).max() / np.abs(dX).max()
-    assert e <= 1e-4, e
+    print("loss gradient error (of max |dL/dX|):", e)
+    assert e <= 1e-5, e
     if w_a:
         assert np.abs(gA.cpu().numpy() - dA).max() <= 1e-6 * np.abs(dA).max()
     else:
@@ -62,7 +64,7 @@ def test_image_loss_autograd_and_identity():
     loss = image_loss(x, a, t[2], t[3], bg, 0.2, 0.8)
     loss.backward()
     _, dX, dA = OT.loss_grad(X, A, Ct, At, bg, 0.2, 0.8)
-    assert np.abs(x.grad.cpu().numpy() - dX).max() <= 1e-4 * np.abs(dX).max()
+    assert np.abs(x.grad.cpu().numpy() - dX).max() <= 1e-5 * np.abs(dX).max()
     assert np.abs(a.grad.cpu().numpy() - dA).max() <= 1e-6 * np.abs(dA).max()
     # image equal to the target (and alpha to its alpha): SSIM 1, loss 0
     z = image_loss(torch.from_numpy(Y).cuda(), t[3], t[2], t[3], bg, 0.2, 0.8)
