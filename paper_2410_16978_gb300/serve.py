@@ -103,7 +103,7 @@ class RenderServer:
 
     def __init__(self, models: Dict[str, DeviceScene], memory_budget: int = 8 << 30, max_views_per_batch: int = 16,
                  max_inflight_batches: int = 2, device="cuda", policy: str = "priority",
-                 large_view_pixels: int = 2_000_000, allocate: Optional[Callable] = None):
+                 large_view_pixels: int = 2_000_000, allocate: Optional[Callable] = None, large_slots: int = 2):
         if policy not in ("priority", "fifo"):
             raise ValueError(policy)
         self.models = models
@@ -114,7 +114,9 @@ class RenderServer:
         self.policy = policy
         self.large_view_pixels = int(large_view_pixels)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(self.max_inflight)]
-        self.stream_hi = torch.cuda.Stream(self.device, priority=-1)
+        self.large_slots = max(1, int(large_slots))
+        self.streams_hi = [torch.cuda.Stream(self.device, priority=-1) for _ in range(self.large_slots)]
+        self.stream_hi = self.streams_hi[0]
         self._cap: Dict[tuple, int] = {}
         self._free: Dict[tuple, List[_ViewBuffers]] = collections.defaultdict(list)
         self._c_scene = {k: m.c_struct() for k, m in models.items()}
@@ -265,10 +267,12 @@ class RenderServer:
                 order, into gs_render_batch launches of up to max_views views
                 as soon as a launch slot and the memory budget allow.  With
                 policy "priority" there are two lanes: requests with a view of
-                at least large_view_pixels go to a high-priority stream, one
-                batch at a time; the others to normal-priority streams, so
-                small requests fill the device around a large frame without
-                delaying it.  Policy "fifo" is one lane over all streams."""
+                at least large_view_pixels go to large_slots high-priority
+                streams, one batch in flight on each (two let one large frame's
+                preprocess and sorts overlap another's compositing); the others
+                to normal-priority streams, so small requests fill the device
+                around the large frames without delaying them.  Policy "fifo"
+                is one lane over all streams."""
         if mode not in ("served", "plain"):
             raise ValueError(mode)
         reqs = sorted(requests, key=lambda r: r.arrival)
@@ -283,7 +287,7 @@ class RenderServer:
         elif self.policy == "fifo":
             lanes = [dict(pred=lambda r: True, streams=self.streams, slots=self.max_inflight, batch=True)]
         else:
-            lanes = [dict(pred=self.is_large, streams=[self.stream_hi], slots=1, batch=True),
+            lanes = [dict(pred=self.is_large, streams=self.streams_hi, slots=self.large_slots, batch=True),
                      dict(pred=lambda r: not self.is_large(r), streams=self.streams, slots=self.max_inflight,
                           batch=True)]
         for ln in lanes:
