@@ -41,9 +41,14 @@ UNIT = "Mpixels/s"
 WORKLOAD = ("layered CT-like scene: 1.2M Gaussians in 5 layers (400k/300k/250k/100k/150k shells), SH degree 3, "
             "1024x1024, random 5-bit layer mask + 1 clip plane; step = forward + backward + contribution prune")
 # Per-pair arithmetic of the compositor kernels (FLOPs, an FMA counts 2).  A pair
-# is (pixel, list entry) up to the pixel's n_contrib; the roofline counts every
-# such pair as evaluated, and roofline_detail counts the blend arithmetic only
-# for the pairs that were blended (the status word's n_blended).
+# is (pixel, list entry) up to the pixel's n_contrib.  The roofline uses the
+# scope table's per-pair figures for every such pair: about 20 FLOP for the
+# forward (alpha and blend) and 2.5 times that for the backward.
+# roofline_detail and roofline_all count the evaluation of every pair and the
+# blend arithmetic only for the pairs that were blended (the status word's
+# n_blended).
+FLOP_S3_PAIR = 20      # forward compositing per evaluated pair
+FLOP_S4_PAIR = 50      # backward compositing per evaluated pair (2.5 x forward)
 FLOP_EVAL = 14         # alpha of one pair: offsets, exponent, exp2, opacity, clamp, threshold test
 FLOP_BLEND_FWD = 10    # blending a splat into a pixel
 FLOP_BLEND_BWD = 40    # gradient of one blended pair
@@ -788,8 +793,8 @@ def run_gpu(args, rank, world, local_rank):
     roof_detail = None
     if dom in ("composite", "composite_bwd"):
         blend = FLOP_BLEND_BWD if dom == "composite_bwd" else FLOP_BLEND_FWD
-        # per evaluated (pixel, list entry) pair up to n_contrib: alpha plus the blend's arithmetic
-        flops = pairs_bwd * (FLOP_EVAL + blend)
+        # per evaluated (pixel, list entry) pair up to n_contrib: the scope table's per-pair figure
+        flops = pairs_bwd * (FLOP_S4_PAIR if dom == "composite_bwd" else FLOP_S3_PAIR)
         achieved = flops / (stage_ms[dom] / 1e3) / 1e12
         roof = {"kernel": "k_" + dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": profiled_traffic("k_" + dom),
@@ -799,6 +804,7 @@ def run_gpu(args, rank, world, local_rank):
         blended = float(st.n_blended)
         cons = (pairs_bwd * FLOP_EVAL + blended * blend) / (stage_ms[dom] / 1e3) / 1e12
         roof_detail = {"evaluated_pairs": int(pairs_bwd), "blended_pairs": int(blended),
+                       "flop_per_evaluated_pair": FLOP_S4_PAIR if dom == "composite_bwd" else FLOP_S3_PAIR,
                        "achieved_blend_only_tflops": cons, "frac_blend_only": cons / fp32_peak_tflops}
     else:
         K = (sc.sh_degree + 1) ** 2
