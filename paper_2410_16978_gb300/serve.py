@@ -103,7 +103,8 @@ class RenderServer:
 
     def __init__(self, models: Dict[str, DeviceScene], memory_budget: int = 8 << 30, max_views_per_batch: int = 16,
                  max_inflight_batches: int = 2, device="cuda", policy: str = "priority",
-                 large_view_pixels: int = 2_000_000, allocate: Optional[Callable] = None, large_slots: int = 2):
+                 large_view_pixels: int = 2_000_000, allocate: Optional[Callable] = None, large_slots: int = 2,
+                 split_large: bool = True):
         if policy not in ("priority", "fifo"):
             raise ValueError(policy)
         self.models = models
@@ -115,8 +116,12 @@ class RenderServer:
         self.large_view_pixels = int(large_view_pixels)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(self.max_inflight)]
         self.large_slots = max(1, int(large_slots))
+        self.split_large = bool(split_large)
         self.streams_hi = [torch.cuda.Stream(self.device, priority=-1) for _ in range(self.large_slots)]
         self.stream_hi = self.streams_hi[0]
+        # a second stream per high-priority stream: the views of a large batch are split between the two,
+        # so the two eyes of a stereo request render side by side
+        self.split_hi = {hs.cuda_stream: torch.cuda.Stream(self.device, priority=-1) for hs in self.streams_hi}
         self._cap: Dict[tuple, int] = {}
         self._free: Dict[tuple, List[_ViewBuffers]] = collections.defaultdict(list)
         self._c_scene = {k: m.c_struct() for k, m in models.items()}
@@ -231,18 +236,32 @@ class RenderServer:
         self.views_launched += len(views)
         return views, imgs
 
-    def _launch_batch(self, views, stream: torch.cuda.Stream, keep_images: bool):
+    def _launch_batch(self, views, stream: torch.cuda.Stream, keep_images: bool, split: bool = False):
         """All ``views`` ((request, camera, buffers) triples of several
-        requests) in one gs_render_batch call."""
-        items = []
-        for req, cam, vb in views:
-            items.append(dict(scene=self._c_scene[req.model], camera=_lib.make_camera(cam), layer_mask=req.layer_mask,
-                              planes=list(req.planes), bg=req.bg, workspace=vb.workspace, ws_bytes=vb.ws_bytes,
-                              image=vb.image, alpha=vb.alpha))
-        _lib.gs_render_batch(items, int(stream.cuda_stream))
+        requests) in one gs_render_batch call on ``stream``; with ``split``
+        (and two views or more) the second half of the views goes to the
+        stream's companion stream in a second call, and ``stream`` waits for
+        it, so both halves render side by side and one event on ``stream``
+        still marks the end of the batch."""
+        def items_of(vs):
+            return [dict(scene=self._c_scene[req.model], camera=_lib.make_camera(cam), layer_mask=req.layer_mask,
+                         planes=list(req.planes), bg=req.bg, workspace=vb.workspace, ws_bytes=vb.ws_bytes,
+                         image=vb.image, alpha=vb.alpha) for req, cam, vb in vs]
+        aux = self.split_hi.get(stream.cuda_stream) if split and len(views) >= 2 else None
+        if aux is not None:
+            half = (len(views) + 1) // 2
+            aux.wait_stream(stream)                     # the companion starts after what the lane queued before
+            _lib.gs_render_batch(items_of(views[:half]), int(stream.cuda_stream))
+            _lib.gs_render_batch(items_of(views[half:]), int(aux.cuda_stream))
+            with torch.cuda.stream(aux):
+                for _, _, vb in views[half:]:
+                    vb.fetch_status()
+            stream.wait_stream(aux)
+        else:
+            _lib.gs_render_batch(items_of(views), int(stream.cuda_stream))
         imgs = None
         with torch.cuda.stream(stream):
-            for _, _, vb in views:
+            for _, _, vb in (views if aux is None else views[:half]):
                 vb.fetch_status()
             if keep_images:
                 imgs = {}
@@ -287,7 +306,8 @@ class RenderServer:
         elif self.policy == "fifo":
             lanes = [dict(pred=lambda r: True, streams=self.streams, slots=self.max_inflight, batch=True)]
         else:
-            lanes = [dict(pred=self.is_large, streams=self.streams_hi, slots=self.large_slots, batch=True),
+            lanes = [dict(pred=self.is_large, streams=self.streams_hi, slots=self.large_slots, batch=True,
+                          split=self.split_large),
                      dict(pred=lambda r: not self.is_large(r), streams=self.streams, slots=self.max_inflight,
                           batch=True)]
         for ln in lanes:
@@ -344,7 +364,7 @@ class RenderServer:
                     if math.isnan(results[r.rid].start):
                         results[r.rid].start = st
                 if ln["batch"]:
-                    views, imgs = self._launch_batch(views, stream, keep_images)
+                    views, imgs = self._launch_batch(views, stream, keep_images, ln.get("split", False))
                 else:
                     views, imgs = self._launch_plain(views, stream, keep_images)
                 ev = torch.cuda.Event(enable_timing=True)
