@@ -104,7 +104,7 @@ class RenderServer:
     def __init__(self, models: Dict[str, DeviceScene], memory_budget: int = 8 << 30, max_views_per_batch: int = 16,
                  max_inflight_batches: int = 2, device="cuda", policy: str = "priority",
                  large_view_pixels: int = 2_000_000, allocate: Optional[Callable] = None, large_slots: int = 2,
-                 split_large: bool = True):
+                 split_large: bool = True, split_small: bool = True):
         if policy not in ("priority", "fifo"):
             raise ValueError(policy)
         self.models = models
@@ -117,11 +117,13 @@ class RenderServer:
         self.streams = [torch.cuda.Stream(self.device) for _ in range(self.max_inflight)]
         self.large_slots = max(1, int(large_slots))
         self.split_large = bool(split_large)
+        self.split_small = bool(split_small)
         self.streams_hi = [torch.cuda.Stream(self.device, priority=-1) for _ in range(self.large_slots)]
         self.stream_hi = self.streams_hi[0]
-        # a second stream per high-priority stream: the views of a large batch are split between the two,
-        # so the two eyes of a stereo request render side by side
+        # a companion stream per stream: the views of a batch are split between the two, so the two eyes of
+        # a stereo request (or two halves of a batch of small views) render side by side
         self.split_hi = {hs.cuda_stream: torch.cuda.Stream(self.device, priority=-1) for hs in self.streams_hi}
+        self.split_hi.update({ns.cuda_stream: torch.cuda.Stream(self.device) for ns in self.streams})
         self._cap: Dict[tuple, int] = {}
         self._free: Dict[tuple, List[_ViewBuffers]] = collections.defaultdict(list)
         self._c_scene = {k: m.c_struct() for k, m in models.items()}
@@ -309,7 +311,7 @@ class RenderServer:
             lanes = [dict(pred=self.is_large, streams=self.streams_hi, slots=self.large_slots, batch=True,
                           split=self.split_large),
                      dict(pred=lambda r: not self.is_large(r), streams=self.streams, slots=self.max_inflight,
-                          batch=True)]
+                          batch=True, split=self.split_small)]
         for ln in lanes:
             ln.update(waiting=collections.deque(), pending=[], k=0)
         nxt = 0
