@@ -381,6 +381,41 @@ SERVE_MODELS = (("0.5M", 0.5 / 1.2), ("1.5M", 1.25), ("3M", None))
 SERVE_SIZES = ((512, 512, 1), (1024, 1024, 1), (2064, 2208, 2))
 
 
+def per_view_forward(models, dev, renders=20, warmup=3):
+    """Forward time of one view of every serving model at every view size:
+    one gs_render per view through the public Rasterizer (camera at
+    (0.3, -0.2, 3.6) looking at the origin, every layer, no plane), CUDA
+    events over `renders` renders after `warmup` (workspace sized by the
+    first, checked render)."""
+    import synth
+    import torch
+    from paper_2410_16978_gb300 import Rasterizer
+
+    out = {}
+    st = torch.cuda.current_stream(dev)
+    for name, ds in models.items():
+        row = {}
+        for W, H, _ in SERVE_SIZES:
+            cam = synth.look_at_camera((0.3, -0.2, 3.6), width=W, height=H)
+            r = Rasterizer(ds.n, W, H, device=dev)
+            img, al = r.render(ds, cam, check=True)
+            for _ in range(warmup):
+                r.render(ds, cam, image=img, alpha=al, check=False)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(st)
+            for _ in range(renders):
+                r.render(ds, cam, image=img, alpha=al, check=False)
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            if r.status().error != 0:
+                raise RuntimeError("per-view render of %s %dx%d failed" % (name, W, H))
+            row["%dx%d" % (W, H)] = round(e0.elapsed_time(e1) / renders, 4)
+            del r, img, al
+        out[name] = row
+    return out
+
+
 def run_serving(dev, n_requests=512, rate=300.0, budget=8 << 30, replays=3):
     """Three resident layered models (0.5M, 1.5M, 3M Gaussians, SH degree 3)
     and a Poisson trace of mixed requests, replayed in real time through the
@@ -448,6 +483,7 @@ def run_serving(dev, n_requests=512, rate=300.0, budget=8 << 30, replays=3):
         s = replay(sat, mode)
         out["saturated_%s" % mode] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()}
     out["order"] = order
+    out["per_view_forward_ms"] = per_view_forward(models, dev)
 
     # one served request (a 1024x1024 view of the 1.5M model) against the FP64 oracle
     import oracle
