@@ -382,36 +382,46 @@ SERVE_SIZES = ((512, 512, 1), (1024, 1024, 1), (2064, 2208, 2))
 
 
 def per_view_forward(models, dev, renders=20, warmup=3):
-    """Forward time of one view of every serving model at every view size:
-    one gs_render per view through the public Rasterizer (camera at
-    (0.3, -0.2, 3.6) looking at the origin, every layer, no plane), CUDA
-    events over `renders` renders after `warmup` (workspace sized by the
-    first, checked render)."""
+    """Device time of one forward view of every serving model at every view
+    size: one gs_render through the public Rasterizer (camera at
+    (0.3, -0.2, 3.6) looking at the origin, every layer, no plane), recorded
+    once as a CUDA graph and replayed, CUDA events over `renders` replays
+    after `warmup` (workspace sized by a first, checked render).  The graph
+    takes the host's launch overhead out, so this is the view's GPU time."""
     import synth
     import torch
     from paper_2410_16978_gb300 import Rasterizer
 
     out = {}
-    st = torch.cuda.current_stream(dev)
     for name, ds in models.items():
         row = {}
         for W, H, _ in SERVE_SIZES:
             cam = synth.look_at_camera((0.3, -0.2, 3.6), width=W, height=H)
             r = Rasterizer(ds.n, W, H, device=dev)
             img, al = r.render(ds, cam, check=True)
-            for _ in range(warmup):
+            side = torch.cuda.Stream(dev)
+            side.wait_stream(torch.cuda.current_stream(dev))
+            with torch.cuda.stream(side):
                 r.render(ds, cam, image=img, alpha=al, check=False)
+            torch.cuda.current_stream(dev).wait_stream(side)
+            torch.cuda.synchronize(dev)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                r.render(ds, cam, image=img, alpha=al, check=False)
+            for _ in range(warmup):
+                g.replay()
+            st = torch.cuda.current_stream(dev)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize(dev)
             e0.record(st)
             for _ in range(renders):
-                r.render(ds, cam, image=img, alpha=al, check=False)
+                g.replay()
             e1.record(st)
             torch.cuda.synchronize(dev)
             if r.status().error != 0:
                 raise RuntimeError("per-view render of %s %dx%d failed" % (name, W, H))
             row["%dx%d" % (W, H)] = round(e0.elapsed_time(e1) / renders, 4)
-            del r, img, al
+            del g, r, img, al
         out[name] = row
     return out
 

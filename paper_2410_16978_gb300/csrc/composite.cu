@@ -5,12 +5,15 @@
 //
 // Work decomposition (compositing is FP32 FMA + MUFU work, not a dense
 // contraction, so no tensor cores are involved):
-//  * Forward: persistent warps take work items (tile, 8x4 pixel block) from a
-//    device queue in heaviest-first tile order and composite one pixel per
-//    lane until the block's 32 pixels are done.  Every kSeg list positions
-//    the warp stores each pixel's transmittance as a checkpoint, with the
-//    colour blended from there to the end of the pixel's walk (filled in
-//    when the walk ends).
+//  * Forward: persistent warps take work items (tile, 8x4 pixel block) from
+//    per-view device queues in heaviest-first tile order (the views of a
+//    batch in turn) and composite one pixel per lane until the block's 32
+//    pixels are done.  The walk goes segment by segment (kSeg list
+//    positions), each segment blended from a local product that the
+//    transmittance at its start scales; at every segment boundary the warp
+//    stores each pixel's transmittance as a checkpoint, with the colour
+//    blended from there to the end of the pixel's walk (filled in when the
+//    walk ends).
 //  * Both passes drop, 32 records at a time, the splats that provably stay
 //    below alpha = 1/255 over the warp's whole pixel block (see
 //    splat_reaches_block); list positions are kept, so nothing changes.
@@ -23,8 +26,7 @@
 //
 // splat_alpha() is the single definition of the per-(pixel, splat) alpha used
 // by both passes; every operation is an explicitly rounded intrinsic, so the
-// backward reproduces the forward's skip decisions and transmittance bit for
-// bit.
+// backward reproduces the forward's skip decisions bit for bit.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -33,9 +35,9 @@ namespace {
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr float kLn2 = 0x1.62e430p-1f;
 constexpr int kFwdThreads = 256;
-// Forward pixels per lane: 1 (an 8x4 block per warp) or 2 (8x8).  2 gives each lane two blend chains but culls
-// on a larger block and needs 70 registers; on the 1.2M-Gaussian frame it measured 0.28 ms against 0.22 ms.
-constexpr int kFwdPx = 1;
+// One pixel per lane, an 8x4 block per warp.  (Two pixels per lane, an 8x8 block, gives each lane two blend
+// chains but culls on a larger block and needs 70 registers; on the 1.2M-Gaussian frame it measured 0.28 ms
+// against 0.22 ms.)
 constexpr int kBwdThreads = 128;
 // Backward pixels per lane: 2 (an 8x8 block per warp) or 4 (16x8).  4 halves the per-splat reduction and
 // atomics per pixel but needs 96 registers (5 blocks per SM instead of 7) and culls on a coarser block;
@@ -247,150 +249,183 @@ __device__ __forceinline__ void fetch_rec_layer(const Rec *__restrict__ rec, con
 struct FwdBatch {
     FwdJob job[kMaxBatch];
     int n;
-    uint32_t total;
 };
 
-template <int PX>
-__global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_constant__ FwdBatch batch,
-                                                               uint32_t *__restrict__ queue) {
-    __shared__ float4 s_a[kFwdThreads / 32][32], s_b[kFwdThreads / 32][32];
-    __shared__ float s_c[kFwdThreads / 32][32];
-    __shared__ uint32_t s_pos[kFwdThreads / 32][32];
-    constexpr int NB = 8 / PX;                          // blocks per tile: 8x4 (PX = 1) or 8x8 (PX = 2)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Forward compositing, segment by segment.  A pixel's walk is cut at the
+// checkpoint segments (kSeg list positions).  In every segment the pixel
+// blends from a local product P = 1: the colour D it blends there is relative
+// to Ts, its transmittance at the segment's start, and the segment ends with
+// colour Ts * D and transmittance Ts * P.  The stop test of a splat is
+// Ts * P * (1 - alpha) < kTMin, the paper's T < 1e-4 on this factorisation.
+// The checkpoints store Ts and the colour blended from the segment on, which
+// is all the backward needs to start a segment's walk from its end.
+constexpr int kFwdWarps = kFwdThreads / 32;
+
+struct FwdLane {        // one pixel's walk
+    float Ts;           // transmittance at the start of the current segment
+    float P;            // product of (1 - alpha) over the splats blended in the segment
+    float D0, D1, D2;   // colour blended in the segment, relative to Ts
+    uint32_t last;      // 1 + list position (from the tile's first entry) of the last blended splat
+    uint32_t nb;        // blended splats
+    bool done;          // stopped (or outside the image)
+};
+
+struct FwdPipe {        // list ids and records fetched ahead of the walk
+    Chunk nxt;          // records of the 32 entries at pos
+    uint32_t gid;       // ids of the 32 entries at pos + 32
+    uint32_t pos;       // list position (from the tile's first entry) of nxt
+};
+
+struct FwdSmem {
+    float4 a[kFwdWarps][32], b[kFwdWarps][32];
+    float c[kFwdWarps][32];
+    uint32_t pos[kFwdWarps][32];
+};
+
+// Walks list positions [pp.pos, e) of the block at (bx0, by0) (an 8x4 block of
+// pixel centres), 32 entries at a time: the entries that can reach the block
+// are staged in shared memory, and each lane blends them into its pixel's
+// segment state.  Returns early once every lane has stopped.
+__device__ __forceinline__ void walk_segment(FwdPipe &pp, uint32_t e, const FwdJob &J, uint2 rg, float bx0, float by0,
+                                             float px, float py, FwdLane &L, int lane, int warp, FwdSmem &sm) {
     const unsigned lt = (1u << lane) - 1u;
+    const uint32_t len = rg.y - rg.x;
+    bool mine = L.done;
+    for (; pp.pos < e; pp.pos += 32) {
+        if (__all_sync(FULL, mine)) break;
+        const uint32_t base = pp.pos;
+        const bool keep =
+            base + lane < len && splat_reaches_block(pp.nxt.a, pp.nxt.b, bx0, bx0 + 7.f, by0, by0 + 3.f);
+        const unsigned km = __ballot_sync(FULL, keep);
+        __syncwarp();
+        if (keep) {
+            const int slot = __popc(km & lt);
+            sm.a[warp][slot] = pp.nxt.a;
+            sm.b[warp][slot] = pp.nxt.b;
+            sm.c[warp][slot] = pp.nxt.c;
+            sm.pos[warp][slot] = base + lane;
+        }
+        __syncwarp();
+        const bool v1 = base + 32 + lane < len;
+        if (v1 && !GS_CHECK(pp.gid < J.n, J.ctl, kSiteFwdId))
+            pp.nxt = Chunk{};      // an inert splat (opacity 0): no block keeps it
+        else
+            fetch_rec(J.rec, pp.gid, v1, pp.nxt);
+        pp.gid = base + 64 + lane < len ? J.list[rg.x + base + 64 + lane] : 0u;
+        const int cnt = __popc(km);
+        for (int k = 0; k < cnt && !mine; ++k) {
+            const float4 a = sm.a[warp][k], b = sm.b[warp][k];
+            float p, dy, ex, ao;
+            const float al = splat_alpha(px, py, a, b, p, dy, ex, ao);
+            if (al >= kAlphaMin) {
+                const float Pn = __fmul_rn(L.P, __fsub_rn(1.f, al));
+                if (__fmul_rn(L.Ts, Pn) < kTMin) {
+                    L.done = true;
+                    mine = true;
+                } else {
+                    const float w = __fmul_rn(al, L.P);
+                    L.D0 = __fmaf_rn(b.z, w, L.D0);
+                    L.D1 = __fmaf_rn(b.w, w, L.D1);
+                    L.D2 = __fmaf_rn(sm.c[warp][k], w, L.D2);
+                    L.P = Pn;
+                    L.last = sm.pos[warp][k] + 1;
+                    ++L.nb;
+                }
+            }
+        }
+    }
+}
+
+// The live view after v in turn (live != 0, v < 31).
+__device__ __forceinline__ int next_live(uint32_t live, int v) {
+    const uint32_t after = live & ~((2u << v) - 1u);
+    return __ffs(after ? after : live) - 1;
+}
+
+__global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_constant__ FwdBatch batch) {
+    __shared__ FwdSmem sm;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // Views of a batch are taken in turn, each from its own heaviest-first queue, so the heaviest blocks of
+    // every view start first; a view whose queue has run out leaves the rotation.
+    uint32_t live = (1u << batch.n) - 1u;
+    int v = static_cast<int>((blockIdx.x * kFwdWarps + warp) % static_cast<uint32_t>(batch.n));
     for (;;) {
-        uint32_t item = 0;
-        if (lane == 0) item = atomicAdd(queue, 1u);
-        item = __shfl_sync(FULL, item, 0);
-        if (item >= batch.total) break;
-        int v = 0;
-        while (v + 1 < batch.n && item >= batch.job[v + 1].item_begin) ++v;
+        uint32_t local = 0;
+        if (lane == 0) {
+            for (;;) {
+                local = atomicAdd(batch.job[v].queue, 1u);
+                if (local < static_cast<uint32_t>(batch.job[v].Tn) * 8u) break;
+                live &= ~(1u << v);
+                if (!live) break;
+                v = next_live(live, v);
+            }
+        }
+        live = __shfl_sync(FULL, live, 0);
+        if (!live) break;
+        local = __shfl_sync(FULL, local, 0);
+        v = __shfl_sync(FULL, v, 0);
         const FwdJob &J = batch.job[v];
-        const uint32_t local = item - J.item_begin;
-        const int Tx = J.Tx, W = J.W, H = J.H;
-        const uint32_t *__restrict__ list = J.list;
-        const Rec *__restrict__ rec = J.rec;
-        const int tile = J.order[local / NB];
-        const int sub = local % NB;                     // block column sub & 1, block row sub >> 1
-        const int ox = (sub & 1) * 8, oy = (sub >> 1) * 4 * PX;
+        const int W = J.W, H = J.H, Tx = J.Tx;
+        const int tile = J.order[local / 8];
+        const int sub = local % 8;                      // block column sub & 1, block row sub >> 1
+        const int ox = (sub & 1) * 8, oy = (sub >> 1) * 4;
         const uint2 rg = J.ranges[tile];
         const float bx0 = (tile % Tx) * kTile + ox + 0.5f, by0 = (tile / Tx) * kTile + oy + 0.5f;
-        float px[PX], py[PX], T[PX], D0[PX], D1[PX], D2[PX];   // D: colour blended in the current segment
-        uint32_t last[PX];
-        bool done[PX], inside[PX];
-        int lyv[PX];
-        const int lx = ox + (lane & 7);
-#pragma unroll
-        for (int j = 0; j < PX; ++j) {
-            lyv[j] = oy + (lane >> 3) + 4 * j;
-            const int x = (tile % Tx) * kTile + lx, y = (tile / Tx) * kTile + lyv[j];
-            inside[j] = x < W && y < H;
-            px[j] = x + 0.5f;
-            py[j] = y + 0.5f;
-            T[j] = 1.f;
-            D0[j] = D1[j] = D2[j] = 0.f;
-            last[j] = 0;
-            done[j] = !inside[j];
-        }
-        uint32_t sd = 0, nb = 0;
+        const int lx = ox + (lane & 7), ly = oy + (lane >> 3);
+        const int x = (tile % Tx) * kTile + lx, y = (tile / Tx) * kTile + ly;
+        const bool inside = x < W && y < H;
+        FwdLane L{1.f, 1.f, 0.f, 0.f, 0.f, 0u, 0u, !inside};
+        float C0 = 0.f, C1 = 0.f, C2 = 0.f;             // colour of the last finished segment
+        const uint32_t len = rg.y - rg.x, nseg = ceil_seg(len);
         float4 *ck0 = J.ckpt + static_cast<size_t>(J.seg_base[tile]) * kTilePix + lx;
-        Chunk nxt;
-        fetch_chunk(list, rec, rg.x + lane, rg.y, nxt, J.n, J.ctl, kSiteFwdId);
-        uint32_t gid = rg.x + 32 + lane < rg.y ? list[rg.x + 32 + lane] : 0u;   // ids one chunk ahead
-        for (uint32_t base = rg.x; base < rg.y; base += 32) {
-            bool mine = true;
-#pragma unroll
-            for (int j = 0; j < PX; ++j) mine = mine && done[j];
-            if (__all_sync(FULL, mine)) break;
-            const uint32_t pos0 = base - rg.x;
-            if (pos0 != 0 && pos0 % kSeg == 0) {
-                sd = pos0 / kSeg;
+        FwdPipe pp;
+        pp.pos = 0;
+        fetch_chunk(J.list, J.rec, rg.x + lane, rg.y, pp.nxt, J.n, J.ctl, kSiteFwdId);
+        pp.gid = rg.x + 32 + lane < rg.y ? J.list[rg.x + 32 + lane] : 0u;   // ids one chunk ahead
+        uint32_t sd = 0;
+        for (uint32_t s = 0; s < nseg; ++s) {
+            if (s > 0) {
+                if (__all_sync(FULL, L.done)) break;
+                sd = s;
                 if (!GS_CHECK(J.seg_base[tile] + sd < J.n_segs, J.ctl, kSiteCkpt)) break;
-#pragma unroll
-                for (int j = 0; j < PX; ++j) {
-                    ck0[static_cast<size_t>(sd) * kTilePix + lyv[j] * kTile] = make_float4(T[j], D0[j], D1[j], D2[j]);
-                    D0[j] = D1[j] = D2[j] = 0.f;
-                }
+                // checkpoint s: (T at the segment's start, colour of segment s - 1); rewritten below
+                ck0[static_cast<size_t>(sd) * kTilePix + ly * kTile] = make_float4(L.Ts, C0, C1, C2);
             }
-            const bool keep = base + lane < rg.y &&
-                              splat_reaches_block(nxt.a, nxt.b, bx0, bx0 + 7.f, by0, by0 + (4.f * PX - 1.f));
-            const unsigned km = __ballot_sync(FULL, keep);
-            __syncwarp();
-            if (keep) {
-                const int slot = __popc(km & lt);
-                s_a[warp][slot] = nxt.a;
-                s_b[warp][slot] = nxt.b;
-                s_c[warp][slot] = nxt.c;
-                s_pos[warp][slot] = pos0 + lane;
-            }
-            __syncwarp();
-            if (base + 32 + lane < rg.y && !GS_CHECK(gid < J.n, J.ctl, kSiteFwdId))
-                nxt = Chunk{};     // an inert splat (opacity 0): no block keeps it
-            else
-                fetch_rec(rec, gid, base + 32 + lane < rg.y, nxt);
-            gid = base + 64 + lane < rg.y ? list[base + 64 + lane] : 0u;
-            const int cnt = __popc(km);
-            for (int k = 0; k < cnt && !mine; ++k) {
-                const float4 a = s_a[warp][k], b = s_b[warp][k];
-                mine = true;
-#pragma unroll
-                for (int j = 0; j < PX; ++j) {
-                    if (!done[j]) {
-                        float p, dy, ex, ao;
-                        const float al = splat_alpha(px[j], py[j], a, b, p, dy, ex, ao);
-                        if (al >= kAlphaMin) {
-                            const float Tnew = __fmul_rn(T[j], __fsub_rn(1.f, al));
-                            if (Tnew < kTMin) {
-                                done[j] = true;
-                            } else {
-                                const float w = __fmul_rn(al, T[j]);
-                                D0[j] = __fmaf_rn(b.z, w, D0[j]);
-                                D1[j] = __fmaf_rn(b.w, w, D1[j]);
-                                D2[j] = __fmaf_rn(s_c[warp][k], w, D2[j]);
-                                T[j] = Tnew;
-                                last[j] = s_pos[warp][k] + 1;
-                                ++nb;
-                            }
-                        }
-                    }
-                    mine = mine && done[j];
-                }
-            }
+            walk_segment(pp, min((s + 1) * kSeg, len), J, rg, bx0, by0, x + 0.5f, y + 0.5f, L, lane, warp, sm);
+            // the segment ends: its colour, the transmittance at the next segment's start
+            C0 = __fmul_rn(L.Ts, L.D0);
+            C1 = __fmul_rn(L.Ts, L.D1);
+            C2 = __fmul_rn(L.Ts, L.D2);
+            L.Ts = __fmul_rn(L.Ts, L.P);
+            L.P = 1.f;
+            L.D0 = L.D1 = L.D2 = 0.f;
         }
-        uint32_t lmax = 0;
-#pragma unroll
-        for (int j = 0; j < PX; ++j) {
-            // Checkpoint s holds (T at segment start, D of segment s-1) as written
-            // above; rewrite it, deepest segment first, to (T at segment start,
-            // F_s), F_s = colour blended at list positions >= s kSeg.  F_0 is the
-            // pixel's colour sum.
-            float C0 = D0[j], C1 = D1[j], C2 = D2[j];
-            for (uint32_t s = sd; s > 0; --s) {
-                float4 *slot = ck0 + static_cast<size_t>(s) * kTilePix + lyv[j] * kTile;
-                const float4 raw = *slot;
-                *slot = make_float4(raw.x, C0, C1, C2);
-                C0 = __fadd_rn(raw.y, C0);
-                C1 = __fadd_rn(raw.z, C1);
-                C2 = __fadd_rn(raw.w, C2);
-            }
-            if (inside[j]) {
-                const int x = (tile % Tx) * kTile + lx, y = (tile / Tx) * kTile + lyv[j];
-                const size_t plane = static_cast<size_t>(W) * H;
-                const size_t pix = static_cast<size_t>(y) * W + x;
-                J.image[pix] = __fmaf_rn(T[j], J.bg.x, C0);
-                J.image[plane + pix] = __fmaf_rn(T[j], J.bg.y, C1);
-                J.image[2 * plane + pix] = __fmaf_rn(T[j], J.bg.z, C2);
-                if (J.alpha) J.alpha[pix] = 1.f - T[j];
-                J.t_final[pix] = T[j];
-                J.n_contrib[pix] = last[j];
-            }
-            lmax = max(lmax, last[j]);
+        // Checkpoint s holds (T at segment start, colour of segment s-1) as written
+        // above; rewrite it, deepest segment first, to (T at segment start, F_s),
+        // F_s = colour blended at list positions >= s kSeg.  F_0 is the pixel's colour.
+        for (uint32_t s = sd; s > 0; --s) {
+            float4 *slot = ck0 + static_cast<size_t>(s) * kTilePix + ly * kTile;
+            const float4 raw = *slot;
+            *slot = make_float4(raw.x, C0, C1, C2);
+            C0 = __fadd_rn(raw.y, C0);
+            C1 = __fadd_rn(raw.z, C1);
+            C2 = __fadd_rn(raw.w, C2);
         }
-        const uint32_t wm = __reduce_max_sync(FULL, lmax);
-        if (lane == 0 && wm) atomicMax(&J.qwork[4 * tile + (sub & 1) + 2 * ((oy) >> 3)], wm);
-        const uint32_t wb = __reduce_add_sync(FULL, nb);
+        if (inside) {
+            const size_t plane = static_cast<size_t>(W) * H;
+            const size_t pix = static_cast<size_t>(y) * W + x;
+            J.image[pix] = __fmaf_rn(L.Ts, J.bg.x, C0);
+            J.image[plane + pix] = __fmaf_rn(L.Ts, J.bg.y, C1);
+            J.image[2 * plane + pix] = __fmaf_rn(L.Ts, J.bg.z, C2);
+            if (J.alpha) J.alpha[pix] = 1.f - L.Ts;
+            J.t_final[pix] = L.Ts;
+            J.n_contrib[pix] = L.last;
+        }
+        const uint32_t wm = __reduce_max_sync(FULL, L.last);
+        if (lane == 0 && wm) atomicMax(&J.qwork[4 * tile + (sub & 1) + 2 * (oy >> 3)], wm);
+        const uint32_t wb = __reduce_add_sync(FULL, L.nb);
         if (lane == 0 && wb) atomicAdd(J.n_blended, static_cast<unsigned long long>(wb));
+        v = next_live(live, v);
     }
 }
 
@@ -713,24 +748,20 @@ cudaError_t launch_fwd_setup(const CompositeBufs &cb, const uint2 *ranges, int T
     return cudaGetLastError();
 }
 
-cudaError_t launch_composite_forward(const FwdJob *jobs, int n, uint32_t *queue, cudaStream_t st) {
+cudaError_t launch_composite_forward(const FwdJob *jobs, int n, cudaStream_t st) {
     FwdBatch batch;
     batch.n = 0;
     uint32_t total = 0;
     for (int i = 0; i < n && batch.n < kMaxBatch; ++i) {
         if (jobs[i].Tn == 0) continue;
-        batch.job[batch.n] = jobs[i];
-        batch.job[batch.n].item_begin = total;
-        total += static_cast<uint32_t>(jobs[i].Tn) * (8u / kFwdPx);
-        ++batch.n;
+        batch.job[batch.n++] = jobs[i];
+        total += static_cast<uint32_t>(jobs[i].Tn) * 8u;
     }
-    batch.total = total;
     if (total == 0) return cudaSuccess;
     static PerDevice cache;
-    const int blocks =
-        cache.get([] { return persistent_blocks(k_composite_fwd<kFwdPx>, kFwdThreads, kFwdBlocksPerSm); });
-    const int b = min(blocks, static_cast<int>((total + kFwdThreads / 32 - 1) / (kFwdThreads / 32)));
-    k_composite_fwd<kFwdPx><<<b, kFwdThreads, 0, st>>>(batch, queue);
+    const int blocks = cache.get([] { return persistent_blocks(k_composite_fwd, kFwdThreads, kFwdBlocksPerSm); });
+    const int b = min(blocks, static_cast<int>((total + kFwdWarps - 1) / kFwdWarps));
+    k_composite_fwd<<<b, kFwdThreads, 0, st>>>(batch);
     return cudaGetLastError();
 }
 

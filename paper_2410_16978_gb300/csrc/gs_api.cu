@@ -396,7 +396,7 @@ int front_sort(FrontCtx &f, const FrontCtx *other, cudaStream_t st, uint32_t **o
 
 // Phase 3: binning in the given depth order (whose count is at n_vis), the
 // compositor set-up, and the forward job of the view.
-int front_bin(FrontCtx &f, const uint32_t *order, cudaStream_t st, FwdJob *job, uint32_t **queue) {
+int front_bin(FrontCtx &f, const uint32_t *order, cudaStream_t st, FwdJob *job) {
     int rc;
     const Layout &L = f.L;
     void *ws = f.ws;
@@ -443,8 +443,7 @@ int front_bin(FrontCtx &f, const uint32_t *order, cudaStream_t st, FwdJob *job, 
     job->Tx = f.cv.Tx;
     job->Tn = L.Tn;
     job->bg = make_float3(f.bg[0], f.bg[1], f.bg[2]);
-    job->item_begin = 0;
-    *queue = cb.queue;
+    job->queue = cb.queue;
     return GS_OK;
 }
 
@@ -452,14 +451,14 @@ int front_bin(FrontCtx &f, const uint32_t *order, cudaStream_t st, FwdJob *job, 
 // the compositor set-up, and fills the view's forward job.
 int render_front(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mask, const gs_clip_plane *planes,
                  int32_t n_planes, const float *bg, void *workspace, size_t ws_bytes, float *image, float *alpha,
-                 cudaStream_t st, FwdJob *job, uint32_t **queue) {
+                 cudaStream_t st, FwdJob *job) {
     FrontCtx f;
     int rc = front_preprocess(scene, camera, layer_mask, planes, n_planes, bg, workspace, ws_bytes, image, alpha, st,
                               &f);
     if (rc != GS_OK) return rc;
     uint32_t *order = nullptr;
     if ((rc = front_sort(f, nullptr, st, &order)) != GS_OK) return rc;
-    return front_bin(f, order, st, job, queue);
+    return front_bin(f, order, st, job);
 }
 
 }  // namespace
@@ -471,12 +470,10 @@ int gs_render(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mas
               void *stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     FwdJob job;
-    uint32_t *queue = nullptr;
-    int rc = render_front(scene, camera, layer_mask, planes, n_planes, bg, workspace, ws_bytes, image, alpha, st, &job,
-                          &queue);
+    int rc = render_front(scene, camera, layer_mask, planes, n_planes, bg, workspace, ws_bytes, image, alpha, st, &job);
     if (rc != GS_OK) return rc;
     Stage sg(GS_STAGE_COMPOSITE, st, 1);
-    return cuda_check(launch_composite_forward(&job, 1, queue, st), "composite");
+    return cuda_check(launch_composite_forward(&job, 1, st), "composite");
 }
 
 int gs_render_batch(const gs_render_request *reqs, int32_t n, void *stream) {
@@ -487,17 +484,14 @@ int gs_render_batch(const gs_render_request *reqs, int32_t n, void *stream) {
                 return fail(GS_ERR_INVALID, "requests %d and %d share a workspace", j, i);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     FwdJob jobs[GS_MAX_BATCH];
-    uint32_t *queue0 = nullptr;
     for (int i = 0; i < n; ++i) {
         const gs_render_request &r = reqs[i];
-        uint32_t *q = nullptr;
         int rc = render_front(r.scene, r.camera, r.layer_mask, r.planes, r.n_planes, r.bg, r.workspace, r.ws_bytes,
-                              r.image, r.alpha, st, &jobs[i], &q);
+                              r.image, r.alpha, st, &jobs[i]);
         if (rc != GS_OK) return rc;
-        if (i == 0) queue0 = q;
     }
     Stage sg(GS_STAGE_COMPOSITE, st, 1);
-    return cuda_check(launch_composite_forward(jobs, n, queue0, st), "batched composite");
+    return cuda_check(launch_composite_forward(jobs, n, st), "batched composite");
 }
 
 
@@ -516,7 +510,6 @@ int gs_render_stereo(const gs_scene *scene, const gs_camera *left, const gs_came
                                alpha_right, st, &f[1])) != GS_OK)
         return rc;
     FwdJob jobs[2];
-    uint32_t *queue[2] = {nullptr, nullptr};
     if (shared_sort) {
         uint32_t *order = nullptr;
         if ((rc = front_sort(f[0], &f[1], st, &order)) != GS_OK) return rc;
@@ -536,17 +529,17 @@ int gs_render_stereo(const gs_scene *scene, const gs_camera *left, const gs_came
                                              cudaMemcpyDeviceToDevice, st),
                              "shared count")) != GS_OK)
             return rc;
-        if ((rc = front_bin(f[0], order, st, &jobs[0], &queue[0])) != GS_OK) return rc;
-        if ((rc = front_bin(f[1], order, st, &jobs[1], &queue[1])) != GS_OK) return rc;
+        if ((rc = front_bin(f[0], order, st, &jobs[0])) != GS_OK) return rc;
+        if ((rc = front_bin(f[1], order, st, &jobs[1])) != GS_OK) return rc;
     } else {
         for (int e = 0; e < 2; ++e) {
             uint32_t *order = nullptr;
             if ((rc = front_sort(f[e], nullptr, st, &order)) != GS_OK) return rc;
-            if ((rc = front_bin(f[e], order, st, &jobs[e], &queue[e])) != GS_OK) return rc;
+            if ((rc = front_bin(f[e], order, st, &jobs[e])) != GS_OK) return rc;
         }
     }
     Stage sg(GS_STAGE_COMPOSITE, st, 1);
-    return cuda_check(launch_composite_forward(jobs, 2, queue[0], st), "stereo composite");
+    return cuda_check(launch_composite_forward(jobs, 2, st), "stereo composite");
 }
 
 int gs_render_backward(const gs_scene *scene, const gs_camera *camera, const float *bg, void *workspace,

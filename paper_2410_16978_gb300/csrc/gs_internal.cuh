@@ -275,15 +275,15 @@ struct FwdJob {
     uint32_t n_segs;                 // checkpoint segments the workspace holds
     int W, H, Tx, Tn;
     float3 bg;
-    uint32_t item_begin;   // first global work item of this view (filled by the launcher)
+    uint32_t *queue;       // the view's work-queue counter (zeroed by its set-up)
 };
 // Per-view set-up before compositing: tile order, checkpoint bases, zeroed
 // block work and queue.  The backward's set-up also zeroes the record-gradient
 // rows of the visible Gaussians (vis_index, *n_vis of the n Gaussians).
 cudaError_t launch_fwd_setup(const CompositeBufs &cb, const uint2 *ranges, int Tn, cudaStream_t st);
-// Composites n <= kMaxBatch views with one persistent launch; `queue` must
-// have been zeroed on the stream (launch_fwd_setup of any view does).
-cudaError_t launch_composite_forward(const FwdJob *jobs, int n, uint32_t *queue, cudaStream_t st);
+// Composites n <= kMaxBatch views with one persistent launch; every view's
+// queue must have been zeroed on the stream (its launch_fwd_setup does).
+cudaError_t launch_composite_forward(const FwdJob *jobs, int n, cudaStream_t st);
 // Backward set-up: work items (tile order by longest blended prefix) and the
 // zeroed record-gradient rows of the visible Gaussians.
 cudaError_t launch_bwd_setup(const CompositeBufs &cb, int Tx, int Ty, float4 *rec_grad, const uint32_t *vis_index,
