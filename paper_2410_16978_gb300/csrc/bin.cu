@@ -16,7 +16,7 @@
 //     second pass writes the entries (Gaussian, x0 | x1 << 16) there.  Within
 //     a chunk the entries go out in depth order: a warp expands 32 Gaussians
 //     into their row pairs 32 at a time and ranks equal rows by lane
-//     (__match_any_sync), and lanes hold consecutive pairs in depth order.
+//     (__match_any_sync or ballots), and lanes hold consecutive pairs in depth order.
 //  2. Tiles.  Every row list is cut into pieces of a fixed number of entries
 //     (thousands of pieces per frame, so heavy rows spread over all SMs); a
 //     warp per piece counts its pairs per tile, a per-row scan over the
@@ -27,8 +27,6 @@
 // Per pair this writes the row entry once (8 B, per row of the rectangle, not
 // per tile) and the final Gaussian id once (4 B); the count matrix is a few MB.
 // Requires Tx, Ty <= kBinMaxDim (images up to 4096 x 4096).
-#include <algorithm>
-
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -66,6 +64,11 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_w, u
     return base + x - v;
 }
 
+__device__ __forceinline__ uint32_t shfl_payload(uint32_t v, int j) { return __shfl_sync(FULL, v, j); }
+__device__ __forceinline__ uint2 shfl_payload(uint2 v, int j) {
+    return make_uint2(__shfl_sync(FULL, v.x, j), __shfl_sync(FULL, v.y, j));
+}
+
 // Lanes hold 32 consecutive list entries in order (the valid ones first),
 // entry j covering slots [start_j, start_j + w_j) of the expanded sequence.
 // Returns the entry that owns slot k0 + lane: entries starting before k0 plus
@@ -75,6 +78,56 @@ __device__ __forceinline__ int window_owner(uint32_t start, uint32_t w, uint32_t
     const bool in = w > 0 && start >= k0 && start - k0 < 32u;
     const unsigned mask = __reduce_or_sync(FULL, in ? 1u << (start - k0) : 0u);
     return __popc(before) - 1 + __popc(mask & (0xFFFFFFFFu >> (31 - lane)));
+}
+
+// Lanes with equal keys of nb bits (among the active ones), from nb + 1 ballots.
+__device__ __forceinline__ unsigned match_keyn(uint32_t key, bool act, int lane, int nb) {
+    unsigned m = __ballot_sync(FULL, act);
+#pragma unroll 8
+    for (int b = 0; b < nb; ++b) {
+        const unsigned bb = __ballot_sync(FULL, (key >> b) & 1u);
+        m &= ((key >> b) & 1u) ? bb : ~bb;
+    }
+    return act ? m : (1u << lane);
+}
+
+// The 32 lanes hold consecutive list entries in order; entry j covers the
+// buckets [b0_j, b0_j + n_j) (n_j = 0: no entry) and carries the payload v_j.
+// The (bucket, payload) items are expanded in that order, 32 per window, and
+// each is stored at its bucket's running position s_pos[bucket] (per-warp
+// counters in shared memory), so every bucket receives its items in order:
+// the lanes of a window that share a bucket are ranked by lane, and the first
+// of them moves the counter.  Windows go in pairs whose rankings run on
+// different pipes, __match_any_sync for the first and ballots on the nb key
+// bits for the second; either alone saturates its pipe on large frames.
+// store(pos, payload) writes one item.
+template <class V, class Store>
+__device__ __forceinline__ void expand_scatter(uint32_t b0, uint32_t n, V v, uint32_t *s_pos, int lane, int nb,
+                                               Store store) {
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t incl = warp_incl_scan(n, lane);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    const uint32_t start = incl - n;
+    for (uint32_t k0 = 0; k0 < total; k0 += 64) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint32_t kw = k0 + 32u * u;
+            const uint32_t k = kw + lane;
+            const bool act = k < total;
+            const int j = window_owner(start, n, kw, lane);
+            const uint32_t sj = __shfl_sync(FULL, start, j), bj = __shfl_sync(FULL, b0, j);
+            const V vj = shfl_payload(v, j);
+            const uint32_t bk = act ? bj + (k - sj) : 0u;
+            // the two windows rank on different pipes: __match_any_sync and ballots
+            const unsigned peers = u == 0 ? __match_any_sync(FULL, act ? bk : 0x10000u + lane)
+                                          : match_keyn(bk, act, lane, nb);
+            const uint32_t before = act ? s_pos[bk] : 0u;
+            __syncwarp();
+            if (act && (peers & lt) == 0) s_pos[bk] = before + __popc(peers);
+            if (act) store(before + __popc(peers & lt), vj);
+            __syncwarp();
+        }
+    }
 }
 
 // In-place inclusive prefix sum of a[0..n) (shared memory) by one warp.
@@ -117,7 +170,6 @@ __global__ void __launch_bounds__(256) k_bin_rows(const uint32_t *__restrict__ o
     // an error before the binning (a depth sort that timed out) leaves the order unfinished: do not read it
     if (ctl->st.error != GS_OK) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
     const uint32_t K = gridDim.x * 8u, c = blockIdx.x * 8u + warp;
     const uint32_t n = min(ctl->n_vis, n_cap);
     const uint32_t b = static_cast<uint32_t>(static_cast<uint64_t>(n) * c / K);
@@ -134,12 +186,21 @@ __global__ void __launch_bounds__(256) k_bin_rows(const uint32_t *__restrict__ o
         if (!SCATTER) s_px[w][r] = 0;
     }
     __syncthreads();
+    // ids two groups ahead and records one group ahead of the group being binned, so the gathers overlap
+    // the binning of the groups before them
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t g_nx = b + lane < e ? order[b + lane] : 0u;
+    float4 c_nx = b + lane < e ? rec[g_nx].c : z4;
+    uint32_t gid = b + 32 + lane < e ? order[b + 32 + lane] : 0u;
     for (uint32_t p0 = b; p0 < e; p0 += 32) {
-        const uint32_t p = p0 + lane;
-        uint32_t g = 0, y0 = 0, x01 = 0, nrows = 0;
-        if (p < e) {
-            g = order[p];
-            const float4 cc = rec[g].c;
+        const bool valid = p0 + lane < e;
+        const uint32_t g = g_nx;
+        const float4 cc = c_nx;
+        g_nx = gid;
+        c_nx = p0 + 32 + lane < e ? rec[g_nx].c : z4;
+        gid = p0 + 64 + lane < e ? order[p0 + 64 + lane] : 0u;
+        uint32_t y0 = 0, x01 = 0, nrows = 0;
+        if (valid) {
             const uint32_t r0 = __float_as_uint(cc.z), r1 = __float_as_uint(cc.w);
             y0 = r0 >> 16;
             nrows = (r1 >> 16) - y0;
@@ -156,24 +217,9 @@ __global__ void __launch_bounds__(256) k_bin_rows(const uint32_t *__restrict__ o
             }
             continue;
         }
-        const uint32_t incl = warp_incl_scan(nrows, lane);
-        const uint32_t total = __shfl_sync(FULL, incl, 31);
-        const uint32_t start = incl - nrows;
-        for (uint32_t k0 = 0; k0 < total; k0 += 32) {
-            const uint32_t k = k0 + lane;
-            const bool act = k < total;
-            const int j = window_owner(start, nrows, k0, lane);
-            const uint32_t sj = __shfl_sync(FULL, start, j), yj = __shfl_sync(FULL, y0, j);
-            const uint32_t gj = __shfl_sync(FULL, g, j), xj = __shfl_sync(FULL, x01, j);
-            const uint32_t r = act ? yj + (k - sj) : 0u;
-            const unsigned peers = __match_any_sync(FULL, act ? r : 0x10000u + lane);
-            const uint32_t before = act ? s_cnt[warp][r] : 0u;
-            __syncwarp();
-            if (act && (peers & lt) == 0) s_cnt[warp][r] = before + __popc(peers);
-            if (act && GS_CHECK(before + __popc(peers & lt) < ctl->st.dup_capacity, ctl, kSiteRowList))
-                rowlist[before + __popc(peers & lt)] = make_uint2(gj, xj);
-            __syncwarp();
-        }
+        expand_scatter(y0, nrows, make_uint2(g, x01), s_cnt[warp], lane, 32 - __clz(max(Ty - 1, 1)), [&](uint32_t pos, uint2 en) {
+            if (GS_CHECK(pos < ctl->st.dup_capacity, ctl, kSiteRowList)) rowlist[pos] = en;
+        });
     }
     if (!SCATTER) {
         __syncwarp();
@@ -284,7 +330,6 @@ __global__ void __launch_bounds__(256) k_bin_tiles(const uint2 *__restrict__ row
     __shared__ uint32_t s_ps[kBinMaxDim + 1];
     if (ctl->st.error != GS_OK) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
     const uint32_t npieces = ctl->n_pieces;
     for (int r = threadIdx.x; r < Ty; r += blockDim.x) s_ps[r] = rows[r].piece_start;
     if (threadIdx.x == 0) s_ps[Ty] = npieces;
@@ -302,11 +347,12 @@ __global__ void __launch_bounds__(256) k_bin_tiles(const uint2 *__restrict__ row
         uint32_t *Pp = P + static_cast<size_t>(p) * Tx;
         for (int t = lane; t <= Tx; t += 32) s_cnt[warp][t] = (SCATTER && t < Tx) ? Pp[t] : 0u;
         __syncwarp();
+        uint2 en_nx = e0 + lane < e1 ? rowlist[e0 + lane] : make_uint2(0u, 0u);   // entries one group ahead
         for (uint32_t q0 = e0; q0 < e1; q0 += 32) {
-            const uint32_t q = q0 + lane;
+            const uint2 en = en_nx;
+            en_nx = q0 + 32 + lane < e1 ? rowlist[q0 + 32 + lane] : make_uint2(0u, 0u);
             uint32_t g = 0, x0 = 0, w = 0;
-            if (q < e1) {
-                const uint2 en = rowlist[q];
+            if (q0 + lane < e1) {
                 g = en.x;
                 x0 = en.y & 0xFFFFu;
                 w = (en.y >> 16) - x0;
@@ -319,24 +365,9 @@ __global__ void __launch_bounds__(256) k_bin_tiles(const uint2 *__restrict__ row
                 }
                 continue;
             }
-            const uint32_t incl = warp_incl_scan(w, lane);
-            const uint32_t total = __shfl_sync(FULL, incl, 31);
-            const uint32_t start = incl - w;
-            for (uint32_t k0 = 0; k0 < total; k0 += 32) {
-                const uint32_t k = k0 + lane;
-                const bool act = k < total;
-                const int j = window_owner(start, w, k0, lane);
-                const uint32_t sj = __shfl_sync(FULL, start, j), xj = __shfl_sync(FULL, x0, j);
-                const uint32_t gj = __shfl_sync(FULL, g, j);
-                const uint32_t t = act ? xj + (k - sj) : 0u;
-                const unsigned peers = __match_any_sync(FULL, act ? t : 0x10000u + lane);
-                const uint32_t before = act ? s_cnt[warp][t] : 0u;
-                __syncwarp();
-                if (act && (peers & lt) == 0) s_cnt[warp][t] = before + __popc(peers);
-                if (SCATTER && act && GS_CHECK(before + __popc(peers & lt) < ctl->st.n_dup, ctl, kSitePairList))
-                    list[before + __popc(peers & lt)] = gj;
-                __syncwarp();
-            }
+            expand_scatter(x0, w, g, s_cnt[warp], lane, 32 - __clz(max(Tx - 1, 1)), [&](uint32_t pos, uint32_t id) {
+                if (GS_CHECK(pos < ctl->st.n_dup, ctl, kSitePairList)) list[pos] = id;
+            });
         }
         if (!SCATTER) {
             __syncwarp();
@@ -431,22 +462,21 @@ cudaError_t launch_bin_tiles(const uint2 *rowlist, const void *rows_buf, int Tx,
 }
 
 uint32_t bin_piece_entries(int64_t dup_cap, int Tx) {
-    // pieces of 128 entries (shorter per-warp chains in the tile pass than 256, without lengthening the
-    // per-row piece scans as 64 does), doubled until the piece count matrix stays near 64 MB
-    uint32_t piece = 128;
-    while (piece < 4096 && static_cast<double>(dup_cap) / piece * Tx * 4.0 > 64.0 * (1 << 20)) piece *= 2;
-    return piece;
+    // Pieces of 256 entries at every size: measured against 128, 512 and 1024 on the 1.2M-Gaussian 1024 x 1024
+    // frame and on 3M-Gaussian views of 1024 x 1024 and 2064 x 2208 (40M and 123M pairs), 256 was fastest or
+    // within 1% of it.  (Growing the pieces with the capacity, to keep the count matrix near 64 MB, made the pieces
+    // of the 2064 x 2208 view 2048 entries long and its tile pass 1.3 times slower.)  The count matrix then takes
+    // at most 4 B per pair of capacity.
+    (void)dup_cap;
+    (void)Tx;
+    return 256u;
 }
 
 size_t bin_piece_bytes(int64_t dup_cap, int Tx, int Ty) {
-    // Rows for the pieces in use, but never fewer than the budget's row count once the pieces have grown past
-    // 128 entries: the matrix would otherwise shrink where the piece size doubles, and the workspace with it,
-    // so a workspace sized for a pair capacity could hold fewer pairs than asked for.
+    // A row list of E entries has ceil(E / piece) pieces and the row lists hold at most dup_cap entries, so
+    // dup_cap / piece + Ty rows of counts always suffice; the size grows with the capacity.
     const uint32_t piece = bin_piece_entries(dup_cap, Tx);
-    const size_t rows = static_cast<size_t>(dup_cap) / piece;
-    const size_t budget_rows = static_cast<size_t>((16u << 20) / static_cast<uint32_t>(Tx));   // 64 MiB of counts
-    const size_t floor_rows = std::min(static_cast<size_t>(dup_cap) / 128, budget_rows);
-    return (std::max(rows, floor_rows) + Ty + 1) * Tx * 4;
+    return (static_cast<size_t>(dup_cap) / piece + Ty + 1) * Tx * 4;
 }
 
 // The RowInfo of every row, then the (entries, pairs) totals of every (row, part) of the row scan.

@@ -103,9 +103,10 @@ def test_workspace_size_grows_with_the_scene():
 
 @pytest.mark.parametrize("W,H,n", [(1024, 1024, 1_200_000), (2064, 2208, 3_000_000)])
 def test_workspace_size_grows_with_the_pair_capacity(W, H, n):
-    # the binning's pieces double in size as the pair capacity grows (their
-    # count matrix keeps to a budget); the workspace must still grow with the
-    # capacity, so that a workspace sized for C pairs holds at least C
+    # the workspace must grow with the pair capacity, so that a workspace
+    # sized for C pairs holds at least C (checked across the capacities where
+    # pieces of 128 k entries would outgrow a 64 MiB count matrix, the points
+    # where an earlier sizing rule doubled the pieces)
     Tx = (W + 15) // 16
     for k in (1, 2, 4):
         t = k * ((1 << 31) // Tx)           # where pieces of 128 k entries would outgrow the budget
