@@ -732,7 +732,14 @@ int persistent_blocks(K kernel, int threads, int max_per = 1 << 30) {
 // slots.  Sixteen warps per SM still keep the SM issuing, and give those items
 // twice the share that the 32 resident warps allowed: on the 1.2M-Gaussian
 // frame the kernel took 0.19 ms instead of 0.22 (one block per SM: 0.27).
+// A launch of many pixels has many more items per warp than its longest item
+// is long, so the tail weighs less and a third CTA per SM pays: a 2064 x 2208
+// view of 3M Gaussians took 0.606 ms instead of 0.666 (the 1.2M-Gaussian
+// 1024 x 1024 frame 0.20 ms instead of 0.176, a 3M-Gaussian one 0.294 either
+// way).
 constexpr int kFwdBlocksPerSm = 2;
+constexpr int kFwdBlocksPerSmWide = 3;
+constexpr uint64_t kFwdWidePixels = 2u << 20;   // pixels of a launch from which it takes kFwdBlocksPerSmWide
 
 }  // namespace
 
@@ -752,14 +759,20 @@ cudaError_t launch_composite_forward(const FwdJob *jobs, int n, cudaStream_t st)
     FwdBatch batch;
     batch.n = 0;
     uint32_t total = 0;
+    uint64_t pixels = 0;
     for (int i = 0; i < n && batch.n < kMaxBatch; ++i) {
         if (jobs[i].Tn == 0) continue;
         batch.job[batch.n++] = jobs[i];
         total += static_cast<uint32_t>(jobs[i].Tn) * 8u;
+        pixels += static_cast<uint64_t>(jobs[i].W) * jobs[i].H;
     }
     if (total == 0) return cudaSuccess;
-    static PerDevice cache;
-    const int blocks = cache.get([] { return persistent_blocks(k_composite_fwd, kFwdThreads, kFwdBlocksPerSm); });
+    static PerDevice cache, cache_wide;
+    const int blocks = pixels >= kFwdWidePixels
+                           ? cache_wide.get([] {
+                                 return persistent_blocks(k_composite_fwd, kFwdThreads, kFwdBlocksPerSmWide);
+                             })
+                           : cache.get([] { return persistent_blocks(k_composite_fwd, kFwdThreads, kFwdBlocksPerSm); });
     const int b = min(blocks, static_cast<int>((total + kFwdWarps - 1) / kFwdWarps));
     k_composite_fwd<<<b, kFwdThreads, 0, st>>>(batch);
     return cudaGetLastError();
