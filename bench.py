@@ -61,30 +61,43 @@ def _env_int(k, d):
         return d
 
 
-# DRAM bytes per launch of a kernel from one ncu capture of this workload
-# (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the
-# kernel's source file is byte-identical to the one recorded here: the file as
-# profiled, or a later one whose changes are all outside the kernel and its
-# launch configuration (host-side caching of the launch parameters, here).
-PROFILED_TRAFFIC = {
-    "k_composite_bwd": {"bytes": 73754368, "source": "paper_2410_16978_gb300/csrc/composite.cu",
-                        "sha256": "8875014bdf18c77e06137ec1cdd2d6bb868872d01ac6577507e86073d9fab739"},
-    "k_composite": {"bytes": 37839360, "source": "paper_2410_16978_gb300/csrc/composite.cu",
-                    "sha256": "8875014bdf18c77e06137ec1cdd2d6bb868872d01ac6577507e86073d9fab739"},
-    "k_preprocess_bwd": {"bytes": 453050880, "source": "paper_2410_16978_gb300/csrc/preprocess_bwd.cu",
-                         "sha256": "770f5bae4d75d26337f17e9c0c8194b9317d4b3449043b4bf36999300b41d3d1"},
+# DRAM bytes per step of each stage (dram__bytes_read.sum + dram__bytes_write.sum
+# over the stage's kernels) from one ncu capture of this workload (the launch
+# list summarised in profiles/c2_step_launch_list.md; ncu flushes the caches
+# before every kernel, so these are cold-cache bytes).  A figure is reported
+# only while the source file of the stage's kernels is byte-identical to the
+# one recorded here: the file as profiled, or a later one whose changes leave
+# the kernels and this workload's launches as they were (composite.cu: batched
+# serving launches no longer take a third CTA per SM; the step's launch is
+# a single view of 1 Mpixel, two CTAs per SM before and after).
+_CSRC = "paper_2410_16978_gb300/csrc/"
+_SHA = {"preprocess.cu": "eb1b766eb81eb63ee835a4bc6dbec6025330022db2616323c04256d968baad77",
+        "sort.cu": "e150c0bf91f5999fb2aa087435f6814b59e87827a3e158c55ec96cf51630142d",
+        "bin.cu": "eabdf26e203452d709036cf77aea72f5be28a70460e0e3189bbfab8690e19e2e",
+        "composite.cu": "27a5d6258709300c573a0b5afab8d159049b3fedf1728eb5790dae7df5fd410d",
+        "preprocess_bwd.cu": "770f5bae4d75d26337f17e9c0c8194b9317d4b3449043b4bf36999300b41d3d1"}
+PROFILED_TRAFFIC = {   # stage: (bytes per step, source file, kernels)
+    "preprocess": (165778230, "preprocess.cu", "k_preprocess"),
+    "compact": (7835574, "sort.cu", "k_sort_hist"),
+    "depth_sort": (14910171, "sort.cu", "k_sort_pass x4"),
+    "bin_rows": (74242614, "bin.cu", "k_bin_rows x2, k_bin_rowscan"),
+    "bin_tiles": (27670070, "bin.cu", "k_bin_tiles x2, k_bin_tiles_scan"),
+    "composite": (35953408, "composite.cu", "k_composite_fwd"),
+    "composite_bwd": (72349243, "composite.cu", "k_composite_bwd"),
+    "preprocess_bwd": (448525095, "preprocess_bwd.cu", "k_preprocess_bwd"),
+    "prune": (9622705, "sort.cu", "k_scan_reduce, k_scan_down"),
 }
 
 
-def profiled_traffic(kernel: str):
+def profiled_traffic(stage: str):
     import hashlib
-    rec = PROFILED_TRAFFIC.get(kernel)
-    if not rec or rec["bytes"] is None:
+    rec = PROFILED_TRAFFIC.get(stage)
+    if not rec:
         return None
-    with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
+    with open(os.path.join(ROOT, _CSRC + rec[1]), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != _SHA[rec[1]]:
             return None
-    return rec["bytes"]
+    return rec[0]
 
 
 def max_over_ranks(ms: float, world: int, device) -> float:
@@ -351,7 +364,8 @@ def oracle_baselines(w, gpu_image, threads):
     """The oracle timed beside the GPU (rank 0, N = 1): the whole c2 step on
     all host threads (full frame), with the PSNR of the GPU image against its
     FP64 image over every pixel; the 128x128 workload's full frame on one and
-    on all threads."""
+    on all threads; the forward of each eye of the 3M stereo workload
+    (2064x2208) on all threads."""
     import synth
     cam = w["cameras"][0]
     dimg, dal = _upstream_grads(cam.width, cam.height)
@@ -367,8 +381,15 @@ def oracle_baselines(w, gpu_image, threads):
         t1 = time.perf_counter()
         oracle_step(w1, *_upstream_grads(128, 128), th, backward=False)
         c1["forward_ms_%d_thread%s" % (th, "s" if th > 1 else "")] = round(1e3 * (time.perf_counter() - t1), 3)
+    w4 = synth.scene_c4()
+    c4 = {}
+    for eye, cam4 in zip(("left", "right"), w4["cameras"]):
+        t1 = time.perf_counter()
+        st4, _, inf4 = oracle_step(dict(w4, cameras=[cam4]), None, None, threads, backward=False)
+        c4[eye] = {"forward_s": round(time.perf_counter() - t1, 3),
+                   "stages_s": {k: round(v, 3) for k, v in st4.items()}, "pairs": inf4["pairs"]}
     detail = {"c2_step_s": round(wall, 4), "c2_stages_s": {k: round(v, 4) for k, v in stages.items()},
-              "c1_full_frame": c1, "threads": threads}
+              "c1_full_frame": c1, "c4_eyes_full_frame": c4, "threads": threads}
     parity = {"psnr_db_full_frame": psnr, "max_abs_err": float(err.max()),
               "fragile_pixels": info["fragile"], "multi_fragile_pixels": info["multi_fragile"],
               "pixels": int(cam.width * cam.height)}
@@ -843,7 +864,7 @@ def run_gpu(args, rank, world, local_rank):
         flops = pairs_bwd * (FLOP_S4_PAIR if dom == "composite_bwd" else FLOP_S3_PAIR)
         achieved = flops / (stage_ms[dom] / 1e3) / 1e12
         roof = {"kernel": "k_" + dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": profiled_traffic("k_" + dom),
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": profiled_traffic(dom),
                 "peak_source": "FP32 %d SMs x 128 lanes x 2 x %.0f MHz (sm max)" % (sms, sm_max)}
         # the same with the blend arithmetic only for the pairs actually blended (most evaluated pairs
         # stay below alpha 1/255 and the kernel's block culling never evaluates them)
@@ -879,7 +900,7 @@ def run_gpu(args, rank, world, local_rank):
                            "frac": round(ach / fp32_peak_tflops, 4),
                            "note": "evaluated pairs x %d FLOP + blended pairs x %d" % (
                                FLOP_EVAL, FLOP_BLEND_FWD if k == "composite" else FLOP_BLEND_BWD)}
-        tr = profiled_traffic("k_" + k)
+        tr = profiled_traffic(k)
         if tr is not None:
             roof_all[k]["traffic_bytes"] = tr
             if bound == "hbm":

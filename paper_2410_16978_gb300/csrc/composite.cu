@@ -736,7 +736,9 @@ int persistent_blocks(K kernel, int threads, int max_per = 1 << 30) {
 // is long, so the tail weighs less and a third CTA per SM pays: a 2064 x 2208
 // view of 3M Gaussians took 0.606 ms instead of 0.666 (the 1.2M-Gaussian
 // 1024 x 1024 frame 0.20 ms instead of 0.176, a 3M-Gaussian one 0.294 either
-// way).
+// way).  Batched serving launches keep two: they run beside the launches of a
+// companion stream, and a third CTA per SM lowered the saturated served
+// throughput from 7,530 to 7,270 Mpixels/s.
 constexpr int kFwdBlocksPerSm = 2;
 constexpr int kFwdBlocksPerSmWide = 3;
 constexpr uint64_t kFwdWidePixels = 2u << 20;   // pixels of a launch from which it takes kFwdBlocksPerSmWide
@@ -755,7 +757,7 @@ cudaError_t launch_fwd_setup(const CompositeBufs &cb, const uint2 *ranges, int T
     return cudaGetLastError();
 }
 
-cudaError_t launch_composite_forward(const FwdJob *jobs, int n, cudaStream_t st) {
+cudaError_t launch_composite_forward(const FwdJob *jobs, int n, cudaStream_t st, bool wide_ok) {
     FwdBatch batch;
     batch.n = 0;
     uint32_t total = 0;
@@ -768,7 +770,7 @@ cudaError_t launch_composite_forward(const FwdJob *jobs, int n, cudaStream_t st)
     }
     if (total == 0) return cudaSuccess;
     static PerDevice cache, cache_wide;
-    const int blocks = pixels >= kFwdWidePixels
+    const int blocks = wide_ok && pixels >= kFwdWidePixels
                            ? cache_wide.get([] {
                                  return persistent_blocks(k_composite_fwd, kFwdThreads, kFwdBlocksPerSmWide);
                              })

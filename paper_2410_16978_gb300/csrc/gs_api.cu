@@ -473,7 +473,7 @@ int gs_render(const gs_scene *scene, const gs_camera *camera, uint32_t layer_mas
     int rc = render_front(scene, camera, layer_mask, planes, n_planes, bg, workspace, ws_bytes, image, alpha, st, &job);
     if (rc != GS_OK) return rc;
     Stage sg(GS_STAGE_COMPOSITE, st, 1);
-    return cuda_check(launch_composite_forward(&job, 1, st), "composite");
+    return cuda_check(launch_composite_forward(&job, 1, st, true), "composite");
 }
 
 int gs_render_batch(const gs_render_request *reqs, int32_t n, void *stream) {
@@ -491,7 +491,7 @@ int gs_render_batch(const gs_render_request *reqs, int32_t n, void *stream) {
         if (rc != GS_OK) return rc;
     }
     Stage sg(GS_STAGE_COMPOSITE, st, 1);
-    return cuda_check(launch_composite_forward(jobs, n, st), "batched composite");
+    return cuda_check(launch_composite_forward(jobs, n, st, false), "batched composite");
 }
 
 
@@ -539,7 +539,7 @@ int gs_render_stereo(const gs_scene *scene, const gs_camera *left, const gs_came
         }
     }
     Stage sg(GS_STAGE_COMPOSITE, st, 1);
-    return cuda_check(launch_composite_forward(jobs, 2, st), "stereo composite");
+    return cuda_check(launch_composite_forward(jobs, 2, st, true), "stereo composite");
 }
 
 int gs_render_backward(const gs_scene *scene, const gs_camera *camera, const float *bg, void *workspace,

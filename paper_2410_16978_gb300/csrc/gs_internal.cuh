@@ -283,7 +283,10 @@ struct FwdJob {
 cudaError_t launch_fwd_setup(const CompositeBufs &cb, const uint2 *ranges, int Tn, cudaStream_t st);
 // Composites n <= kMaxBatch views with one persistent launch; every view's
 // queue must have been zeroed on the stream (its launch_fwd_setup does).
-cudaError_t launch_composite_forward(const FwdJob *jobs, int n, cudaStream_t st);
+// wide_ok: the launch may take a third CTA per SM when it covers many pixels
+// (gs_render, gs_render_stereo); batched serving launches, which share the GPU
+// with a companion stream, keep two.
+cudaError_t launch_composite_forward(const FwdJob *jobs, int n, cudaStream_t st, bool wide_ok);
 // Backward set-up: work items (tile order by longest blended prefix) and the
 // zeroed record-gradient rows of the visible Gaussians.
 cudaError_t launch_bwd_setup(const CompositeBufs &cb, int Tx, int Ty, float4 *rec_grad, const uint32_t *vis_index,
