@@ -22,7 +22,9 @@
 //    of the whole kernel.  The checkpoints cut every 8x8 block's walk into
 //    segments of at most kSeg positions; persistent warps take (tile, block,
 //    segment) items from a queue and each walks its segment back to front
-//    from the checkpoint at the segment's end.
+//    from the checkpoint at the segment's end.  The forward writes the items:
+//    the second 8x4 block of an 8x8 block to finish knows the block's longest
+//    blended prefix, so no ordering pass runs between the two.
 //
 // splat_alpha() is the single definition of the per-(pixel, splat) alpha used
 // by both passes; every operation is an explicitly rounded intrinsic, so the
@@ -43,6 +45,8 @@ constexpr int kBwdThreads = 128;
 // atomics per pixel but needs 96 registers (5 blocks per SM instead of 7) and culls on a coarser block;
 // on the 1.2M-Gaussian frame it measured 0.403 ms against 0.362 ms for 2.
 constexpr int kBwdPx = 2;
+// The forward writes the backward's work items per 8x8 block (two pixels per lane).
+static_assert(kBwdPx == 2, "backward work items are 8x8 blocks");
 
 // 1/x to about 1 ulp (the hardware reciprocal approximation; x = 1 - alpha is in [0.01, 1]).
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -128,20 +132,13 @@ __device__ __forceinline__ int work_bucket(uint32_t w) {
     return (kBuckets - 2) - (lz * 16 + static_cast<int>(sub));
 }
 
-// Tile work: list length (qwork == nullptr) or the longest blended prefix of
-// its four 8x8 blocks.
-__device__ __forceinline__ uint32_t tile_work(int t, const uint2 *ranges, const uint32_t *qwork) {
-    if (qwork) return max(max(qwork[4 * t], qwork[4 * t + 1]), max(qwork[4 * t + 2], qwork[4 * t + 3]));
-    return ranges[t].y - ranges[t].x;
-}
-
-// One CTA (1024 threads) sorts the tiles heaviest first into order[] (ties in
-// no particular order: tiles are independent, so the order changes no result).
-__device__ void order_tiles(int Tn, uint32_t *order, uint32_t *s_cnt, uint32_t *s_w, const uint2 *ranges,
-                            const uint32_t *qwork) {
+// One CTA (1024 threads) sorts the tiles heaviest first (by list length) into
+// order[] (ties in no particular order: tiles are independent, so the order
+// changes no result).
+__device__ void order_tiles(int Tn, uint32_t *order, uint32_t *s_cnt, uint32_t *s_w, const uint2 *ranges) {
     for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) s_cnt[b] = 0;
     __syncthreads();
-    for (int t = threadIdx.x; t < Tn; t += blockDim.x) atomicAdd(&s_cnt[work_bucket(tile_work(t, ranges, qwork))], 1u);
+    for (int t = threadIdx.x; t < Tn; t += blockDim.x) atomicAdd(&s_cnt[work_bucket(ranges[t].y - ranges[t].x)], 1u);
     __syncthreads();
     {
         const uint32_t c = threadIdx.x < kBuckets ? s_cnt[threadIdx.x] : 0;
@@ -151,21 +148,22 @@ __device__ void order_tiles(int Tn, uint32_t *order, uint32_t *s_cnt, uint32_t *
     }
     __syncthreads();
     for (int t = threadIdx.x; t < Tn; t += blockDim.x)
-        order[atomicAdd(&s_cnt[work_bucket(tile_work(t, ranges, qwork))], 1u)] = t;
+        order[atomicAdd(&s_cnt[work_bucket(ranges[t].y - ranges[t].x)], 1u)] = t;
     __syncthreads();
 }
 
 // Forward set-up (one CTA): heaviest-first tile order by list length, the
 // checkpoint base of every tile (exclusive prefix of its segment count), and
 // zeroed per-block work and queue.
-// The set-up kernels are a single CTA walking every tile several times; up to
-// kSetupSmemTiles tiles, their inputs (ranges, block work) are first staged in
-// dynamic shared memory so the later passes cost no memory round trips.
+// The set-up is a single CTA walking every tile several times; up to
+// kSetupSmemTiles tiles, the tile ranges are first staged in dynamic shared
+// memory so the later passes cost no memory round trips.
 constexpr int kSetupSmemTiles = 8192;
 
 __global__ void __launch_bounds__(1024) k_fwd_setup(const uint2 *__restrict__ g_ranges, int Tn,
                                                     uint32_t *__restrict__ order, uint32_t *__restrict__ seg_base,
-                                                    uint32_t *__restrict__ qwork, uint32_t *__restrict__ queue) {
+                                                    uint32_t *__restrict__ qwork, uint32_t *__restrict__ queue,
+                                                    uint32_t *__restrict__ qdone) {
     __shared__ uint32_t s_cnt[kBuckets];
     __shared__ uint32_t s_w[32];
     extern __shared__ uint2 s_ranges[];
@@ -177,7 +175,8 @@ __global__ void __launch_bounds__(1024) k_fwd_setup(const uint2 *__restrict__ g_
         ranges = s_ranges;
     }
     for (int q = threadIdx.x; q < 4 * Tn; q += blockDim.x) qwork[q] = 0;
-    order_tiles(Tn, order, s_cnt, s_w, ranges, nullptr);
+    for (int t = threadIdx.x; t < Tn; t += blockDim.x) qdone[t] = 0;
+    order_tiles(Tn, order, s_cnt, s_w, ranges);
     uint32_t carry = 0;
     for (int t0 = 0; t0 < Tn; t0 += 1024) {
         const int t = t0 + threadIdx.x;
@@ -313,6 +312,7 @@ __device__ __forceinline__ void walk_segment(FwdPipe &pp, uint32_t e, const FwdJ
             fetch_rec(J.rec, pp.gid, v1, pp.nxt);
         pp.gid = base + 64 + lane < len ? J.list[rg.x + base + 64 + lane] : 0u;
         const int cnt = __popc(km);
+        int lastk = -1;
         for (int k = 0; k < cnt && !mine; ++k) {
             const float4 a = sm.a[warp][k], b = sm.b[warp][k];
             float p, dy, ex, ao;
@@ -328,11 +328,12 @@ __device__ __forceinline__ void walk_segment(FwdPipe &pp, uint32_t e, const FwdJ
                     L.D1 = __fmaf_rn(b.w, w, L.D1);
                     L.D2 = __fmaf_rn(sm.c[warp][k], w, L.D2);
                     L.P = Pn;
-                    L.last = sm.pos[warp][k] + 1;
+                    lastk = k;
                     ++L.nb;
                 }
             }
         }
+        if (lastk >= 0) L.last = sm.pos[warp][lastk] + 1;    // position of the chunk's last blend, read once
     }
 }
 
@@ -422,70 +423,49 @@ __global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_cons
             J.n_contrib[pix] = L.last;
         }
         const uint32_t wm = __reduce_max_sync(FULL, L.last);
-        if (lane == 0 && wm) atomicMax(&J.qwork[4 * tile + (sub & 1) + 2 * (oy >> 3)], wm);
+        const int qd = (sub & 1) + 2 * (oy >> 3);      // the 8x8 block of the tile this 8x4 block is half of
+        if (lane == 0 && wm) atomicMax(&J.qwork[4 * tile + qd], wm);
         const uint32_t wb = __reduce_add_sync(FULL, L.nb);
         if (lane == 0 && wb) atomicAdd(J.n_blended, static_cast<unsigned long long>(wb));
+        // The second of the two 8x4 blocks of an 8x8 block to finish knows that block's longest blended prefix
+        // and appends its backward work items, one per kSeg positions of the prefix.  They come out in the
+        // order the forward finishes them, the heaviest tiles last; the backward takes them from the end.
+        uint32_t nsg = 0, ibase = 0;
+        if (lane == 0) {
+            __threadfence();
+            const uint32_t prev = atomicAdd(&J.qdone[tile], 1u << (8 * qd));
+            if (((prev >> (8 * qd)) & 0xFFu) == 1u) {
+                __threadfence();
+                nsg = ceil_seg(atomicOr(&J.qwork[4 * tile + qd], 0u));
+                if (nsg) ibase = atomicAdd(J.n_items, nsg);
+            }
+        }
+        nsg = __shfl_sync(FULL, nsg, 0);
+        ibase = __shfl_sync(FULL, ibase, 0);
+        for (uint32_t sg = lane; sg < nsg; sg += 32)
+            J.items[ibase + sg] = make_uint2(static_cast<uint32_t>(tile), (static_cast<uint32_t>(qd) << 24) | sg);
         v = next_live(live, v);
     }
 }
 
-// Backward set-up (one CTA): heaviest-first tile order by the longest blended
-// prefix, then one work item (tile, 8x8 block q, segment s) for every segment
-// s < ceil(qwork[tile][q] / kSeg), written tile by tile in that order.
-// CTAs after the first zero the record-gradient rows of the visible Gaussians
-// (visible list of the last render, n_vis entries), the only rows the
-// compositor adds to and the chain rule reads.
-template <int PX>
-__global__ void __launch_bounds__(1024) k_bwd_setup(const uint32_t *__restrict__ g_qwork, int Tn,
-                                                    uint32_t *__restrict__ order, uint2 *__restrict__ items,
-                                                    uint32_t *__restrict__ n_items, uint32_t *__restrict__ queue,
+// Backward set-up: the work items (tile, 8x8 block q, segment s) were written
+// by the forward as it finished each 8x8 block; this kernel restarts the work
+// queue and zeroes the record-gradient rows of the visible Gaussians (visible
+// list of the last render, n_vis entries), the only rows the compositor adds
+// to and the chain rule reads.
+__global__ void __launch_bounds__(1024) k_bwd_setup(uint32_t *__restrict__ queue,
                                                     const uint32_t *__restrict__ vis_index,
                                                     const uint32_t *__restrict__ n_vis, int n,
                                                     float4 *__restrict__ rec_grad) {
-    __shared__ uint32_t s_cnt[kBuckets];
-    __shared__ uint32_t s_w[32];
-    extern __shared__ uint4 s_qwork[];
-    if (blockIdx.x > 0) {
-        const uint32_t nv = min(*n_vis, static_cast<uint32_t>(n));
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (uint32_t p = (blockIdx.x - 1) * blockDim.x + threadIdx.x; p < nv; p += (gridDim.x - 1) * blockDim.x) {
-            const size_t i = vis_index[p];
-            rec_grad[3 * i] = z;
-            rec_grad[3 * i + 1] = z;
-            rec_grad[3 * i + 2] = z;
-        }
-        return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *queue = 0;
+    const uint32_t nv = min(*n_vis, static_cast<uint32_t>(n));
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < nv; p += gridDim.x * blockDim.x) {
+        const size_t i = vis_index[p];
+        rec_grad[3 * i] = z;
+        rec_grad[3 * i + 1] = z;
+        rec_grad[3 * i + 2] = z;
     }
-    if (threadIdx.x == 0) *queue = 0;
-    const uint32_t *qwork = g_qwork;
-    if (Tn <= kSetupSmemTiles) {
-        for (int t = threadIdx.x; t < Tn; t += blockDim.x) s_qwork[t] = reinterpret_cast<const uint4 *>(g_qwork)[t];
-        __syncthreads();
-        qwork = reinterpret_cast<const uint32_t *>(s_qwork);
-    }
-    order_tiles(Tn, order, s_cnt, s_w, nullptr, qwork);
-    uint32_t carry = 0;
-    for (int r0 = 0; r0 < Tn; r0 += 1024) {
-        const int r = r0 + threadIdx.x;
-        uint32_t t = 0;
-        uint32_t ns[4] = {0, 0, 0, 0};
-        if (r < Tn) {
-            t = order[r];
-            if (PX == 2) {
-                for (int q = 0; q < 4; ++q) ns[q] = ceil_seg(qwork[4 * t + q]);
-            } else {
-                for (int h = 0; h < 2; ++h) ns[h] = ceil_seg(max(qwork[4 * t + 2 * h], qwork[4 * t + 2 * h + 1]));
-            }
-        }
-        uint32_t tot;
-        uint32_t at = carry + block_scan_1024(ns[0] + ns[1] + ns[2] + ns[3], s_w, &tot);
-        if (r < Tn)
-#pragma unroll
-            for (uint32_t q = 0; q < 4; ++q)
-                for (uint32_t sg = 0; sg < ns[q]; ++sg) items[at++] = make_uint2(t, (q << 24) | sg);
-        carry += tot;
-    }
-    if (threadIdx.x == 0) *n_items = carry;
 }
 
 // Reduce-scatter of 10 values across a warp in 12 shuffles.  Halving by lane
@@ -583,7 +563,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_composite_bwd(
         if (lane == 0) id = atomicAdd(queue, 1u);
         id = __shfl_sync(FULL, id, 0);
         if (id >= total) break;
-        const uint2 it = items[id];
+        const uint2 it = items[total - 1 - id];       // the forward appended the heaviest tiles' items last
         const int tile = static_cast<int>(it.x);
         const int q = static_cast<int>(it.y >> 24);
         const uint32_t seg = it.y & 0xFFFFFFu;
@@ -753,7 +733,7 @@ cudaError_t launch_fwd_setup(const CompositeBufs &cb, const uint2 *ranges, int T
         return 1;
     });
     const size_t smem = Tn <= kSetupSmemTiles ? static_cast<size_t>(Tn) * 8 : 0;
-    k_fwd_setup<<<1, 1024, smem, st>>>(ranges, Tn, cb.order, cb.seg_base, cb.qwork, cb.queue);
+    k_fwd_setup<<<1, 1024, smem, st>>>(ranges, Tn, cb.order, cb.seg_base, cb.qwork, cb.queue, cb.qdone);
     return cudaGetLastError();
 }
 
@@ -782,19 +762,15 @@ cudaError_t launch_composite_forward(const FwdJob *jobs, int n, cudaStream_t st,
 
 cudaError_t launch_bwd_setup(const CompositeBufs &cb, int Tx, int Ty, float4 *rec_grad, const uint32_t *vis_index,
                              const uint32_t *n_vis, int n, cudaStream_t st) {
-    const int tiles = Tx * Ty;
-    if (tiles == 0) return cudaSuccess;
-    static PerDevice attr;
-    attr.get([] {
-        cudaFuncSetAttribute(k_bwd_setup<kBwdPx>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSetupSmemTiles * 16);
-        return 1;
+    if (Tx * Ty == 0) return cudaSuccess;
+    static PerDevice cache;
+    const int sms = cache.get([] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return max(1, v);
     });
-    int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = tiles <= kSetupSmemTiles ? static_cast<size_t>(tiles) * 16 : 0;
-    k_bwd_setup<kBwdPx><<<1 + max(1, sms), 1024, smem, st>>>(cb.qwork, tiles, cb.order_bwd, cb.items, cb.n_items,
-                                                             cb.queue, vis_index, n_vis, n, rec_grad);
+    k_bwd_setup<<<sms, 1024, 0, st>>>(cb.queue, vis_index, n_vis, n, rec_grad);
     return cudaGetLastError();
 }
 

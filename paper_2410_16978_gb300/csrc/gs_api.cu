@@ -51,7 +51,7 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     o.partials = take(kMaxSortBlocks * 4);
     o.rec_grad = take(N * sizeof(Rec));
     o.tile_order = take(static_cast<size_t>(o.Tn) * 4);
-    o.tile_order_bwd = take(static_cast<size_t>(o.Tn) * 4);
+    o.qdone = take(static_cast<size_t>(o.Tn) * 4);
     o.seg_base = take(static_cast<size_t>(o.Tn) * 4);
     o.qwork = take(static_cast<size_t>(o.Tn) * 16);
     const size_t segs = D / kSeg + static_cast<size_t>(o.Tn) + 1;   // >= sum over tiles of ceil(len / kSeg)
@@ -204,7 +204,7 @@ CompositeBufs composite_bufs(void *ws, const Layout &L) {
     Ctl *ctl = at<Ctl>(ws, L.ctl);
     CompositeBufs cb;
     cb.order = at<uint32_t>(ws, L.tile_order);
-    cb.order_bwd = at<uint32_t>(ws, L.tile_order_bwd);
+    cb.qdone = at<uint32_t>(ws, L.qdone);
     cb.seg_base = at<uint32_t>(ws, L.seg_base);
     cb.qwork = at<uint32_t>(ws, L.qwork);
     cb.ckpt = at<float4>(ws, L.ckpt);
@@ -444,6 +444,9 @@ int front_bin(FrontCtx &f, const uint32_t *order, cudaStream_t st, FwdJob *job) 
     job->Tn = L.Tn;
     job->bg = make_float3(f.bg[0], f.bg[1], f.bg[2]);
     job->queue = cb.queue;
+    job->items = cb.items;
+    job->n_items = cb.n_items;
+    job->qdone = cb.qdone;
     return GS_OK;
 }
 

@@ -95,7 +95,7 @@ struct Layout {
     size_t ctl = 0, rec = 0, tiles = 0, depth = 0, sort_k[2] = {0, 0}, sort_v[2] = {0, 0}, order = 0, vis_index = 0,
            sort_hist = 0, sort_grp = 0, sort_cnt = 0, sort_status = 0, bin_m = 0,
            bin_rows = 0, bin_p = 0, rowlist = 0, list = 0, ranges = 0, t_final = 0, n_contrib = 0,
-           partials = 0, rec_grad = 0, tile_order = 0, tile_order_bwd = 0, seg_base = 0, qwork = 0,
+           partials = 0, rec_grad = 0, tile_order = 0, qdone = 0, seg_base = 0, qwork = 0,
            ckpt = 0, items = 0, total = 0;
 };
 
@@ -248,11 +248,11 @@ cudaError_t launch_prune(const float *contrib_max, int n, float thr, uint8_t *ke
 // Scratch of the compositor kernels (all in the render workspace).
 struct CompositeBufs {
     uint32_t *order;      // [Tn] forward tile order (heaviest first)
-    uint32_t *order_bwd;  // [Tn] backward tile order
+    uint32_t *qdone;      // [Tn] finished forward blocks per 8x8 block (FwdJob::qdone)
     uint32_t *seg_base;   // [Tn] first checkpoint segment of each tile
     uint32_t *qwork;      // [4 Tn] longest blended prefix of each 8x8 block
     float4 *ckpt;         // [segments][256] per-pixel (T, colour sum) every kSeg positions
-    uint2 *items;         // backward work items (tile, block << 24 | segment)
+    uint2 *items;         // backward work items (tile, block << 24 | segment), written by the forward
     uint32_t *n_items;
     uint32_t *queue;      // work-queue counter (forward and backward reuse it in turn)
 };
@@ -276,6 +276,9 @@ struct FwdJob {
     int W, H, Tx, Tn;
     float3 bg;
     uint32_t *queue;       // the view's work-queue counter (zeroed by its set-up)
+    uint2 *items;          // the view's backward work items, appended as the forward finishes 8x8 blocks
+    uint32_t *n_items;     // their count (zero at the start of the render)
+    uint32_t *qdone;       // [Tn] per tile, finished 8x4 forward blocks of each 8x8 block (a byte each; zeroed by the set-up)
 };
 // Per-view set-up before compositing: tile order, checkpoint bases, zeroed
 // block work and queue.  The backward's set-up also zeroes the record-gradient
