@@ -154,7 +154,7 @@ __device__ void order_tiles(int Tn, uint32_t *order, uint32_t *s_cnt, uint32_t *
 
 // Forward set-up (one CTA): heaviest-first tile order by list length, the
 // checkpoint base of every tile (exclusive prefix of its segment count), and
-// zeroed per-block work and queue.
+// zeroed meeting words of the 8x8 blocks and queue.
 // The set-up is a single CTA walking every tile several times; up to
 // kSetupSmemTiles tiles, the tile ranges are first staged in dynamic shared
 // memory so the later passes cost no memory round trips.
@@ -162,8 +162,7 @@ constexpr int kSetupSmemTiles = 8192;
 
 __global__ void __launch_bounds__(1024) k_fwd_setup(const uint2 *__restrict__ g_ranges, int Tn,
                                                     uint32_t *__restrict__ order, uint32_t *__restrict__ seg_base,
-                                                    uint32_t *__restrict__ qwork, uint32_t *__restrict__ queue,
-                                                    uint32_t *__restrict__ qdone) {
+                                                    uint32_t *__restrict__ queue, uint32_t *__restrict__ qdone) {
     __shared__ uint32_t s_cnt[kBuckets];
     __shared__ uint32_t s_w[32];
     extern __shared__ uint2 s_ranges[];
@@ -174,8 +173,7 @@ __global__ void __launch_bounds__(1024) k_fwd_setup(const uint2 *__restrict__ g_
         __syncthreads();
         ranges = s_ranges;
     }
-    for (int q = threadIdx.x; q < 4 * Tn; q += blockDim.x) qwork[q] = 0;
-    for (int t = threadIdx.x; t < Tn; t += blockDim.x) qdone[t] = 0;
+    for (int q = threadIdx.x; q < 8 * Tn; q += blockDim.x) qdone[q] = 0;   // 4 x 64-bit meeting words per tile
     order_tiles(Tn, order, s_cnt, s_w, ranges);
     uint32_t carry = 0;
     for (int t0 = 0; t0 < Tn; t0 += 1024) {
@@ -424,19 +422,28 @@ __global__ void __launch_bounds__(kFwdThreads) k_composite_fwd(const __grid_cons
         }
         const uint32_t wm = __reduce_max_sync(FULL, L.last);
         const int qd = (sub & 1) + 2 * (oy >> 3);      // the 8x8 block of the tile this 8x4 block is half of
-        if (lane == 0 && wm) atomicMax(&J.qwork[4 * tile + qd], wm);
         const uint32_t wb = __reduce_add_sync(FULL, L.nb);
         if (lane == 0 && wb) atomicAdd(J.n_blended, static_cast<unsigned long long>(wb));
-        // The second of the two 8x4 blocks of an 8x8 block to finish knows that block's longest blended prefix
-        // and appends its backward work items, one per kSeg positions of the prefix.  They come out in the
-        // order the forward finishes them, the heaviest tiles last; the backward takes them from the end.
+        // The two 8x4 blocks of an 8x8 block meet in one 64-bit word (finished blocks << 32 | longest blended
+        // prefix).  The second to finish knows the 8x8 block's longest blended prefix: it stores it for the
+        // backward and appends the block's backward work items, one per kSeg positions of the prefix.  They come
+        // out in the order the forward finishes them, the heaviest tiles last; the backward takes them from the end.
         uint32_t nsg = 0, ibase = 0;
         if (lane == 0) {
-            __threadfence();
-            const uint32_t prev = atomicAdd(&J.qdone[tile], 1u << (8 * qd));
-            if (((prev >> (8 * qd)) & 0xFFu) == 1u) {
-                __threadfence();
-                nsg = ceil_seg(atomicOr(&J.qwork[4 * tile + qd], 0u));
+            unsigned long long *meet = reinterpret_cast<unsigned long long *>(J.qdone) + 4 * tile + qd;
+            unsigned long long seen = 0ull, prev = ~0ull;
+            bool ok = false;
+            for (int round = 0; round < 3 && !ok; ++round) {   // two rounds at most: one other writer, once
+                const unsigned long long want =
+                    ((seen >> 32) + 1ull) << 32 | max(static_cast<uint32_t>(seen), wm);
+                prev = atomicCAS(meet, seen, want);
+                ok = prev == seen;
+                seen = prev;
+            }
+            if (ok && (prev >> 32) == 1ull) {
+                const uint32_t qm = max(static_cast<uint32_t>(prev), wm);
+                J.qwork[4 * tile + qd] = qm;
+                nsg = ceil_seg(qm);
                 if (nsg) ibase = atomicAdd(J.n_items, nsg);
             }
         }
@@ -733,7 +740,7 @@ cudaError_t launch_fwd_setup(const CompositeBufs &cb, const uint2 *ranges, int T
         return 1;
     });
     const size_t smem = Tn <= kSetupSmemTiles ? static_cast<size_t>(Tn) * 8 : 0;
-    k_fwd_setup<<<1, 1024, smem, st>>>(ranges, Tn, cb.order, cb.seg_base, cb.qwork, cb.queue, cb.qdone);
+    k_fwd_setup<<<1, 1024, smem, st>>>(ranges, Tn, cb.order, cb.seg_base, cb.queue, cb.qdone);
     return cudaGetLastError();
 }
 

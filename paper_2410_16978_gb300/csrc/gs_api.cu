@@ -51,7 +51,7 @@ bool make_layout(int64_t n, int W, int H, int64_t dup_cap, Layout *L) {
     o.partials = take(kMaxSortBlocks * 4);
     o.rec_grad = take(N * sizeof(Rec));
     o.tile_order = take(static_cast<size_t>(o.Tn) * 4);
-    o.qdone = take(static_cast<size_t>(o.Tn) * 4);
+    o.qdone = take(static_cast<size_t>(o.Tn) * 32);
     o.seg_base = take(static_cast<size_t>(o.Tn) * 4);
     o.qwork = take(static_cast<size_t>(o.Tn) * 16);
     const size_t segs = D / kSeg + static_cast<size_t>(o.Tn) + 1;   // >= sum over tiles of ceil(len / kSeg)

@@ -248,9 +248,9 @@ cudaError_t launch_prune(const float *contrib_max, int n, float thr, uint8_t *ke
 // Scratch of the compositor kernels (all in the render workspace).
 struct CompositeBufs {
     uint32_t *order;      // [Tn] forward tile order (heaviest first)
-    uint32_t *qdone;      // [Tn] finished forward blocks per 8x8 block (FwdJob::qdone)
+    uint32_t *qdone;      // [8 Tn] per 8x8 block, a 64-bit word where its two forward blocks meet (FwdJob::qdone)
     uint32_t *seg_base;   // [Tn] first checkpoint segment of each tile
-    uint32_t *qwork;      // [4 Tn] longest blended prefix of each 8x8 block
+    uint32_t *qwork;      // [4 Tn] longest blended prefix of each 8x8 block (stored by the forward)
     float4 *ckpt;         // [segments][256] per-pixel (T, colour sum) every kSeg positions
     uint2 *items;         // backward work items (tile, block << 24 | segment), written by the forward
     uint32_t *n_items;
@@ -278,7 +278,7 @@ struct FwdJob {
     uint32_t *queue;       // the view's work-queue counter (zeroed by its set-up)
     uint2 *items;          // the view's backward work items, appended as the forward finishes 8x8 blocks
     uint32_t *n_items;     // their count (zero at the start of the render)
-    uint32_t *qdone;       // [Tn] per tile, finished 8x4 forward blocks of each 8x8 block (a byte each; zeroed by the set-up)
+    uint32_t *qdone;       // [8 Tn] per 8x8 block, (finished 8x4 blocks << 32 | longest prefix) as 64 bits (zeroed by the set-up)
 };
 // Per-view set-up before compositing: tile order, checkpoint bases, zeroed
 // block work and queue.  The backward's set-up also zeroes the record-gradient
