@@ -66,26 +66,23 @@ def _env_int(k, d):
 # list summarised in profiles/c2_step_launch_list.md; ncu flushes the caches
 # before every kernel, so these are cold-cache bytes).  A figure is reported
 # only while the source file of the stage's kernels is byte-identical to the
-# one recorded here: the file as profiled, or a later one whose changes leave
-# the kernels and this workload's launches as they were (composite.cu: batched
-# serving launches no longer take a third CTA per SM; the step's launch is
-# a single view of 1 Mpixel, two CTAs per SM before and after).
+# one profiled.
 _CSRC = "paper_2410_16978_gb300/csrc/"
 _SHA = {"preprocess.cu": "eb1b766eb81eb63ee835a4bc6dbec6025330022db2616323c04256d968baad77",
         "sort.cu": "e150c0bf91f5999fb2aa087435f6814b59e87827a3e158c55ec96cf51630142d",
         "bin.cu": "eabdf26e203452d709036cf77aea72f5be28a70460e0e3189bbfab8690e19e2e",
-        "composite.cu": "27a5d6258709300c573a0b5afab8d159049b3fedf1728eb5790dae7df5fd410d",
+        "composite.cu": "e565523be6ac5bd421de1f94cfeeaf10e25dd7b0246be515cc9dc6f9d6651788",
         "preprocess_bwd.cu": "770f5bae4d75d26337f17e9c0c8194b9317d4b3449043b4bf36999300b41d3d1"}
 PROFILED_TRAFFIC = {   # stage: (bytes per step, source file, kernels)
-    "preprocess": (165778230, "preprocess.cu", "k_preprocess"),
-    "compact": (7835574, "sort.cu", "k_sort_hist"),
-    "depth_sort": (14910171, "sort.cu", "k_sort_pass x4"),
-    "bin_rows": (74242614, "bin.cu", "k_bin_rows x2, k_bin_rowscan"),
-    "bin_tiles": (27670070, "bin.cu", "k_bin_tiles x2, k_bin_tiles_scan"),
-    "composite": (35953408, "composite.cu", "k_composite_fwd"),
-    "composite_bwd": (72349243, "composite.cu", "k_composite_bwd"),
-    "preprocess_bwd": (448525095, "preprocess_bwd.cu", "k_preprocess_bwd"),
-    "prune": (9622705, "sort.cu", "k_scan_reduce, k_scan_down"),
+    "preprocess": (165798637, "preprocess.cu", "k_preprocess"),
+    "compact": (7833965, "sort.cu", "k_sort_hist"),
+    "depth_sort": (14909696, "sort.cu", "k_sort_pass x4"),
+    "bin_rows": (74287744, "bin.cu", "k_bin_rows x2, k_bin_rowscan"),
+    "bin_tiles": (27865837, "bin.cu", "k_bin_tiles x2, k_bin_tiles_scan"),
+    "composite": (36194176, "composite.cu", "k_composite_fwd"),
+    "composite_bwd": (72336974, "composite.cu", "k_composite_bwd"),
+    "preprocess_bwd": (448030148, "preprocess_bwd.cu", "k_preprocess_bwd"),
+    "prune": (9623217, "sort.cu", "k_scan_reduce, k_scan_down"),
 }
 
 

@@ -136,3 +136,44 @@ def test_backward_overwrites_every_element(glm):
     torch.cuda.synchronize()
     for f in FIELDS:
         assert bool(torch.isfinite(g[f]).all()), f
+
+
+def test_backward_repeats_and_follows_a_batched_render():
+    """The forward writes the backward's work items (one per 256 list positions
+    of every 8x8 block's longest blended prefix).  Two backward passes after
+    one render, and a backward after the same view rendered inside a
+    gs_render_batch launch, give the gradients of the first pass (up to the
+    rounding order of the gradient atomics)."""
+    from paper_2410_16978_gb300 import DeviceScene, Rasterizer, _lib
+    sc, cam, mask, planes, bg = WL["shells_ragged"]
+    ds = DeviceScene.from_host(sc)
+    dimg, dal = _upstream(cam.height, cam.width)
+    dI, dA = torch.from_numpy(dimg).cuda(), torch.from_numpy(dal).cuda()
+
+    def grads(rast):
+        cmax = torch.zeros(sc.n, device="cuda")
+        g = rast.backward(ds, cam, bg, dI, dA, 0xFFFFFFFF, None, cmax)
+        torch.cuda.synchronize()
+        return {k: v.cpu().numpy() for k, v in g.items()}, cmax.cpu().numpy()
+
+    r0 = Rasterizer(sc.n, cam.width, cam.height)
+    r0.render(ds, cam, mask, planes, bg)
+    first, cm_first = grads(r0)
+    again, cm_again = grads(r0)
+    r1 = Rasterizer(sc.n, cam.width, cam.height)
+    other = torch.zeros((3, cam.height, cam.width), device="cuda"), torch.zeros((cam.height, cam.width), device="cuda")
+    rb = Rasterizer(sc.n, cam.width, cam.height)
+    items = [dict(scene=ds.c_struct(), camera=_lib.make_camera(cam), layer_mask=mask, planes=list(planes), bg=bg,
+                  workspace=r1.workspace, ws_bytes=r1.ws_bytes, image=torch.empty_like(other[0]),
+                  alpha=torch.empty_like(other[1])),
+             dict(scene=ds.c_struct(), camera=_lib.make_camera(cam), layer_mask=0b1, planes=[], bg=bg,
+                  workspace=rb.workspace, ws_bytes=rb.ws_bytes, image=other[0], alpha=other[1])]
+    _lib.gs_render_batch(items, 0)
+    torch.cuda.synchronize()
+    assert r1.status().error == 0
+    batched, cm_batched = grads(r1)
+    for k in FIELDS:
+        scale = max(float(np.abs(first[k]).max()), 1e-30)
+        assert np.abs(again[k] - first[k]).max() <= 1e-6 * scale, k
+        assert np.abs(batched[k] - first[k]).max() <= 1e-6 * scale, k
+    assert np.array_equal(cm_again, cm_first) and np.array_equal(cm_batched, cm_first)
