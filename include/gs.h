@@ -352,8 +352,9 @@ enum {
     GS_STAGE_DEPTH_SORT,       /* S2: radix digit kernels on the depth bits (the first compacts) */
     GS_STAGE_BIN_ROWS,         /* S2: depth-ordered split of the pairs into tile rows */
     GS_STAGE_BIN_TILES,        /* S2: split of every row into its tiles, tile ranges */
-    GS_STAGE_COMPOSITE_SETUP,  /* S3/S4: compositor set-ups (tile orders, checkpoint bases, backward
-                                  items and the zeroed record gradients) */
+    GS_STAGE_COMPOSITE_SETUP,  /* S3/S4: compositor set-ups (forward tile order and checkpoint bases;
+                                  backward: zeroed record gradients; the forward writes the backward's
+                                  work items) */
     GS_STAGE_COMPOSITE,        /* S3 (one launch per gs_render or gs_render_batch call) */
     GS_STAGE_COMPOSITE_BWD,    /* S4a: the backward compositor */
     GS_STAGE_PREPROCESS_BWD,   /* S4b */
