@@ -134,14 +134,50 @@ __global__ void __launch_bounds__(kLW *kLH) k_loss_maps(const float *__restrict_
     }
 }
 
-// Pass 2: window sums of a, b, c and the gradient of the loss.
+// loss = (1 - lam) L1 + lam (1 - SSIM) + w_a LA from the block sums, by one CTA
+// of kLW * kLH threads in a fixed order (deterministic): each thread adds its
+// strided share of the block sums in single precision, then a tree in shared
+// memory (scratch: 3 * kLW * kLH floats).  The GB300's double-precision pipe is
+// narrow; converting and adding every block sum in double took 20 us.
+__device__ void loss_from_block_sums(const float *__restrict__ partials, int nb, size_t plane, float lam, float w_a,
+                                     float *__restrict__ loss, float *scratch) {
+    constexpr int NT = kLW * kLH;
+    const int tid = threadIdx.x;
+    float a[3] = {0.f, 0.f, 0.f};
+    for (int b = tid; b < nb; b += NT)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) a[q] += partials[3 * b + q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) scratch[q * NT + tid] = a[q];
+    __syncthreads();
+    for (int o = NT / 2; o > 0; o >>= 1) {
+        if (tid < o)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) scratch[q * NT + tid] += scratch[q * NT + tid + o];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const double n = 3.0 * static_cast<double>(plane);
+        *loss = static_cast<float>((1.0 - lam) * scratch[NT] / n + lam * (1.0 - scratch[0] / n) +
+                                   w_a * scratch[2 * NT] / static_cast<double>(plane));
+    }
+    __syncthreads();
+}
+
+// Pass 2: window sums of a, b, c and the gradient of the loss; the first CTA
+// also adds up pass 1's block sums into the loss.
 __global__ void __launch_bounds__(kLW *kLH) k_loss_grad(const float *__restrict__ X, const float *__restrict__ A,
                                                         const float *__restrict__ Ct, const float *__restrict__ At,
                                                         float3 bg, int W, int H, const Win win, float lam, float w_a,
                                                         const float *__restrict__ maps, float *__restrict__ dX,
-                                                        float *__restrict__ dA) {
+                                                        float *__restrict__ dA, const float *__restrict__ partials,
+                                                        float w_a_loss, float *__restrict__ loss) {
     __shared__ float s_m[3][kRH][kRW];
     __shared__ float s_h[3][kRH][kLW];
+    static_assert(3 * kRH * kRW >= 3 * kLW * kLH, "loss scratch in s_m");
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
+        loss_from_block_sums(partials, static_cast<int>(gridDim.x * gridDim.y * gridDim.z), static_cast<size_t>(W) * H,
+                             lam, w_a_loss, loss, &s_m[0][0][0]);
     const int ch = blockIdx.z;
     const float bgc = ch == 0 ? bg.x : (ch == 1 ? bg.y : bg.z);
     const size_t plane = static_cast<size_t>(W) * H;
@@ -183,43 +219,6 @@ __global__ void __launch_bounds__(kLW *kLH) k_loss_grad(const float *__restrict_
     const float dS = s[0] + 2.f * (x - kSsimShift) * s[1] + (y - kSsimShift) * s[2];
     dX[ch * plane + p] = ((1.f - lam) * sgn(x - y) - lam * dS) * inv_n;
     if (ch == 0 && dA) dA[p] = A ? w_a * sgn(A[p] - At[p]) / static_cast<float>(plane) : 0.f;
-}
-
-// loss = (1 - lam) L1 + lam (1 - SSIM) + w_a LA from the block sums (double,
-// one CTA, fixed order).  Eight block sums per thread are loaded before they
-// are added.
-constexpr int kRedThreads = 1024;
-__global__ void __launch_bounds__(kRedThreads) k_loss_reduce(const float *__restrict__ partials, int nb, size_t plane,
-                                                             float lam, float w_a, float *__restrict__ loss) {
-    __shared__ double s[3][kRedThreads];
-    double a[3] = {0.0, 0.0, 0.0};
-    for (int b0 = threadIdx.x; b0 < nb; b0 += 8 * kRedThreads) {
-        float v[8][3];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int b = b0 + u * kRedThreads;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) v[u][q] = b < nb ? partials[3 * b + q] : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-#pragma unroll
-            for (int q = 0; q < 3; ++q) a[q] += v[u][q];
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) s[q][threadIdx.x] = a[q];
-    __syncthreads();
-    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o)
-#pragma unroll
-            for (int q = 0; q < 3; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double n = 3.0 * static_cast<double>(plane);
-        *loss = static_cast<float>((1.0 - lam) * s[1][0] / n + lam * (1.0 - s[0][0] / n) +
-                                   w_a * s[2][0] / static_cast<double>(plane));
-    }
 }
 
 // Adam over the five parameter arrays seen as one index space; a Gaussian
@@ -384,9 +383,8 @@ cudaError_t launch_image_loss(const float *X, const float *A, const float *Ct, c
     float *partials = maps + 9 * plane;
     const dim3 grid((W + kLW - 1) / kLW, (H + kLH - 1) / kLH, 3);
     k_loss_maps<<<grid, kLW * kLH, 0, st>>>(X, A, Ct, At, bg, W, H, win, maps, partials);
-    k_loss_grad<<<grid, kLW * kLH, 0, st>>>(X, A, Ct, At, bg, W, H, win, lam, w_a, maps, dX, dA);
-    k_loss_reduce<<<1, kRedThreads, 0, st>>>(partials, static_cast<int>(grid.x * grid.y * grid.z), plane, lam,
-                                             A ? w_a : 0.f, loss);
+    k_loss_grad<<<grid, kLW * kLH, 0, st>>>(X, A, Ct, At, bg, W, H, win, lam, w_a, maps, dX, dA, partials,
+                                            A ? w_a : 0.f, loss);
     return cudaGetLastError();
 }
 
