@@ -146,7 +146,7 @@ __device__ __forceinline__ void warp_prefix_inplace(uint32_t *a, int n, int lane
 
 // The per-row scan of the row pass splits every row's kBinChunks chunk
 // counts into kRowParts parts, one CTA each.
-constexpr int kRowParts = 4;
+constexpr int kRowParts = 2;
 constexpr int kPartChunks = kBinChunks / kRowParts;
 static_assert(kPartChunks % 1024 == 0 && kPartChunks / 1024 <= kBinChunksPerThread, "row-scan part shape");
 
@@ -156,7 +156,8 @@ struct RowInfo {           // per tile row, in the workspace
     uint32_t pair_start;   // first pair (final list position) of the row
     uint32_t pairs;        // pairs of the row
     uint32_t piece_start;  // first piece of the row (pieces: kPiece-entry parts of row lists)
-    uint32_t part_base[kRowParts - 1];   // entries of the row in the chunk parts before parts 1, 2, 3
+    uint32_t part_base[kRowParts - 1];   // entries of the row in the chunk parts before parts 1 ..
+    uint32_t pad_[4 - kRowParts];        // (32 bytes in all)
 };
 
 // Pass 1 (SCATTER = false: count, true: write) over the chunks of the depth order.

@@ -27,7 +27,7 @@ constexpr float kEigenFloor = 0.1f;            // floor of (mid^2 - det) under t
 constexpr uint32_t kSeg = 256;                 // list positions per backward segment (checkpoint stride)
 constexpr int kCbMaxDim = 48;                  // SH codebook: coordinates per row, 3(K-1) <= 45 padded
 constexpr int kBinMaxDim = 256;                // tile rows and columns the binning handles (4096 px)
-constexpr int kBinBlocks = 1024;               // CTAs (of 8 chunk warps) of the row pass of the binning
+constexpr int kBinBlocks = 256;                // CTAs (of 8 chunk warps) of the row pass of the binning
 constexpr int kBinChunks = kBinBlocks * 8;     // chunks of the depth order in the row pass
 constexpr int kBinChunksPerThread = kBinChunks / 1024;
 
