@@ -70,15 +70,15 @@ def _env_int(k, d):
 _CSRC = "paper_2410_16978_gb300/csrc/"
 _SHA = {"preprocess.cu": "eb1b766eb81eb63ee835a4bc6dbec6025330022db2616323c04256d968baad77",
         "sort.cu": "e150c0bf91f5999fb2aa087435f6814b59e87827a3e158c55ec96cf51630142d",
-        "bin.cu": "eabdf26e203452d709036cf77aea72f5be28a70460e0e3189bbfab8690e19e2e",
+        "bin.cu": "7cedc04ab2c91de8c398824e382a72c0011f1e2d1510aba0fac2598cced73bcb",
         "composite.cu": "e565523be6ac5bd421de1f94cfeeaf10e25dd7b0246be515cc9dc6f9d6651788",
         "preprocess_bwd.cu": "770f5bae4d75d26337f17e9c0c8194b9317d4b3449043b4bf36999300b41d3d1"}
 PROFILED_TRAFFIC = {   # stage: (bytes per step, source file, kernels)
     "preprocess": (165798637, "preprocess.cu", "k_preprocess"),
     "compact": (7833965, "sort.cu", "k_sort_hist"),
     "depth_sort": (14909696, "sort.cu", "k_sort_pass x4"),
-    "bin_rows": (74287744, "bin.cu", "k_bin_rows x2, k_bin_rowscan"),
-    "bin_tiles": (27865837, "bin.cu", "k_bin_tiles x2, k_bin_tiles_scan"),
+    "bin_rows": (68223268, "bin.cu", "k_bin_rows x2, k_bin_rowscan"),
+    "bin_tiles": (25201133, "bin.cu", "k_bin_tiles x2, k_bin_tiles_scan"),
     "composite": (36194176, "composite.cu", "k_composite_fwd"),
     "composite_bwd": (72336974, "composite.cu", "k_composite_bwd"),
     "preprocess_bwd": (448030148, "preprocess_bwd.cu", "k_preprocess_bwd"),
